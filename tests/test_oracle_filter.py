@@ -1,0 +1,138 @@
+"""Filter-level pins for the oracle: recovery of a known transform, the
+exhaustive grid optimum on tiny masks, determinism and bit-exact resume."""
+import itertools
+
+import numpy as np
+import pytest
+
+import pfsynth
+
+
+def _dice_at(orc, pair, pose):
+    M, a = orc.pose_matrix(np.asarray(pose, np.float32), pair.src_dims, pair.src_origin,
+                           pair.tgt_origin)
+    n, A, B, C = (int(v) for v in orc.measure_mask(pair.src_mask, pair.tgt_mask, M, a)[0])
+    return orc.dice_from_counts(n, A, C, int((pair.tgt_mask != 0).sum()))
+
+
+@pytest.fixture(scope="module")
+def asym_pair():
+    return pfsynth.ellipsoid_pair(1, src_dims=(40, 40, 40), tgt_dims=(40, 40, 30),
+                                  tgt_origin=(0, 0, 10), semi_axes=(13, 9, 9), asymmetric=True,
+                                  max_rot_deg=10, max_trans=4)
+
+
+def test_recovers_generating_pose(orc, asym_pair):
+    p = asym_pair
+    r = orc.register("mask_dice", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, 256, 15,
+                     np.deg2rad(15), 6.0, seed=3, src_mask=p.src, tgt_mask=p.tgt)
+    est = r["est"]
+    err = est - p.true_pose.astype(np.float64)
+    assert np.all(np.abs(err[3:]) <= 1.0), err
+    assert np.all(np.abs(np.rad2deg(err[1:3])) <= 3.0), err
+    assert abs(np.rad2deg(err[0])) <= 6.0, err       # roll about the long axis is weakly seen
+    assert _dice_at(orc, p, est) >= 0.93
+    before = _dice_at(orc, p, np.zeros(6))
+    assert before < 0.85
+
+
+def test_reaches_exhaustive_grid_optimum(orc):
+    """The paper's exhaustive-search baseline idea on a tiny mask: the best
+    particle of the filter must score at least the best grid pose."""
+    p = pfsynth.ellipsoid_pair(5, src_dims=(12, 12, 12), tgt_dims=(12, 12, 12), tgt_origin=(0, 0, 0),
+                               semi_axes=(4.5, 3.0, 3.0), asymmetric=True, max_rot_deg=8,
+                               max_trans=1.5)
+    rot = np.deg2rad([-10, -5, 0, 5, 10])
+    tr = [-2, -1, 0, 1, 2]
+    grid = np.array(list(itertools.product(rot, rot, rot, tr, tr, tr)), np.float32)
+    mats, a = orc.pose_matrices(grid.T, p.src_dims, p.src_origin, p.tgt_origin)
+    counts = orc.measure_mask(p.src, p.tgt, mats, a).astype(np.int64)
+    bfull = int(p.tgt.sum())
+    grid_best = max(orc.dice_from_counts(c[0], c[1], c[3], bfull) for c in counts)
+    r = orc.register("mask_dice", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, 512, 15,
+                     np.deg2rad(12), 2.5, seed=1, src_mask=p.src, tgt_mask=p.tgt)
+    assert r["tr_score"].max() >= grid_best - 1e-12
+
+
+def test_deterministic_and_seed_sensitive(orc):
+    p = pfsynth.ellipsoid_pair(2, src_dims=(20, 20, 20), tgt_dims=(20, 20, 16), tgt_origin=(0, 0, 4),
+                               semi_axes=(7, 5, 5))
+    kw = dict(src_mask=p.src, tgt_mask=p.tgt)
+    args = ("mask_dice", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, 64, 5, 0.2, 3.0)
+    r1 = orc.register(*args, seed=7, **kw)
+    r2 = orc.register(*args, seed=7, **kw)
+    r3 = orc.register(*args, seed=8, **kw)
+    for k in ("tr_poses", "tr_mom", "tr_score", "tr_W", "tr_idx", "tr_est"):
+        assert np.array_equal(r1[k], r2[k])
+    assert not np.array_equal(r1["tr_poses"], r3["tr_poses"])
+
+
+def test_resume_is_bit_exact(orc):
+    """State = (particles, iteration index, seed): running 6 iterations equals
+    running 3, saving the cloud, and running 3 more from iteration 3."""
+    p = pfsynth.ellipsoid_pair(3, src_dims=(20, 20, 20), tgt_dims=(20, 20, 16), tgt_origin=(0, 0, 4),
+                               semi_axes=(7, 5, 5))
+    kw = dict(src_mask=p.src, tgt_mask=p.tgt, seed=11)
+    args = ("mask_ncc", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, 96)
+    full = orc.register(*args, 6, 0.25, 3.0, **kw)
+    a = orc.register(*args, 3, 0.25, 3.0, **kw)
+    b = orc.register(*args, 3, 0.25, 3.0, poses=a["poses"], k0=3, **kw)
+    assert np.array_equal(full["poses"], b["poses"])
+    assert np.array_equal(full["est"], b["est"])
+    assert np.array_equal(full["tr_idx"][3:], b["tr_idx"])
+
+
+def test_trace_is_consistent_with_the_steps(orc):
+    """Each iteration of the trace equals the single-step functions applied to
+    the previous iteration's output (prediction -> measurement -> update ->
+    estimation -> resampling)."""
+    p = pfsynth.ellipsoid_pair(4, src_dims=(18, 18, 18), tgt_dims=(18, 18, 14), tgt_origin=(0, 0, 4),
+                               semi_axes=(6, 4.5, 4.5))
+    lim = np.array([0.3, 0.3, 0.3, 3, 3, 3], np.float32)
+    N, K, seed = 48, 4, 5
+    r = orc.register("mask_dice", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, N, K,
+                     lim[:3], lim[3:], seed=seed, src_mask=p.src, tgt_mask=p.tgt)
+    x = orc.init_particles(N, seed, lim)
+    bfull = int(p.tgt.sum())
+    nmin = int(0.01 * p.tgt.size)
+    for k in range(K):
+        if k > 0:
+            x = orc.perturb(x, seed, k, orc.sigma(0.25, 0.8, k, lim), lim)
+        assert np.array_equal(x, r["tr_poses"][k])
+        mats, a = orc.pose_matrices(x, p.src_dims, p.src_origin, p.tgt_origin)
+        c = orc.measure_mask(p.src, p.tgt, mats, a)
+        assert np.array_equal(c, r["tr_mom"][k][:, 6:10])
+        s = np.array([orc.score("mask_dice", np.concatenate([np.zeros(6, np.uint64), ci]), bfull, nmin)
+                      for ci in c])
+        assert np.array_equal(s, r["tr_score"][k])
+        W = orc.weights(s, 5)
+        assert np.array_equal(W, r["tr_W"][k])
+        assert np.array_equal(orc.estimate(x, W), r["tr_est"][k])
+        idx = orc.resample(W, orc.resample_offset(seed, k))
+        assert np.array_equal(idx, r["tr_idx"][k])
+        x = np.ascontiguousarray(x[:, idx])
+
+
+def test_image_mode_improves_ncc(orc):
+    p = pfsynth.speckle_pair(4, src_dims=(40, 36, 32), overlap=(0.6, 0.7), max_rot_deg=8,
+                             max_trans=3, sigma=40.0)
+    r = orc.register("image_ncc", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, 128, 8,
+                     np.deg2rad(12), 5.0, seed=2, src=p.src, tgt=p.tgt)
+    s = r["tr_score"]
+    assert s.max(1)[-1] > s.max(1)[0]
+    M0, a = orc.pose_matrix(np.zeros(6, np.float32), p.src_dims, p.src_origin, p.tgt_origin)
+    Me, _ = orc.pose_matrix(r["est"].astype(np.float32), p.src_dims, p.src_origin, p.tgt_origin)
+    before = orc.ncc2_f64(p.src, p.tgt, M0, a)[0]
+    after = orc.ncc2_f64(p.src, p.tgt, Me, a)[0]
+    assert after > before
+
+
+def test_combined_mode_runs(orc):
+    p = pfsynth.speckle_pair(6, src_dims=(32, 30, 28), overlap=(0.6, 0.7), max_rot_deg=6,
+                             max_trans=2, with_masks=True)
+    r = orc.register("combined", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, 64, 4,
+                     np.deg2rad(10), 4.0, seed=3, src=p.src, tgt=p.tgt, src_mask=p.src_mask,
+                     tgt_mask=p.tgt_mask)
+    mom = r["tr_mom"][0]
+    assert np.all(mom[:, 0] > 0) and np.all(mom[:, 6] > 0)
+    assert np.all((r["tr_score"] >= 0) & (r["tr_score"] <= 1))
