@@ -86,7 +86,7 @@ def _declare(L):
     for name in ("orc_measure_mask", "orc_measure_image"):
         getattr(L, name).argtypes = [_u8p, _i32p, _u8p, _i32p, _f32p, _f32p, C.c_int32, _u64p]
     L.orc_ncc2_f64.argtypes = [_u8p, _i32p, _u8p, _i32p, _f32p, _f32p, C.c_int32, _f64p]
-    L.orc_ncc2_from_moments.argtypes = [C.c_uint64] * 7
+    L.orc_ncc2_from_moments.argtypes = [C.c_uint64] * 8
     L.orc_ncc2_from_moments.restype = C.c_double
     L.orc_dice_from_counts.argtypes = [C.c_uint64] * 5
     L.orc_dice_from_counts.restype = C.c_double
@@ -168,10 +168,11 @@ def measure_mask(src, tgt, mats, a):
 
 
 def measure_image(src, tgt, mats, a):
-    """moments [M,6] = (n, S1, S2, ST, T1, T2) for each 3x4 matrix."""
+    """moments [M,7] = (n, S1, S2 low, S2 high, ST, T1, T2) for each 3x4 matrix
+    (samples rounded to 15 fractional bits; S2 is a 128-bit sum)."""
     src, tgt = _c(src, np.uint8), _c(tgt, np.uint8)
     mats = _c(np.atleast_2d(mats), np.float32)
-    out = np.zeros((mats.shape[0], 6), np.uint64)
+    out = np.zeros((mats.shape[0], 7), np.uint64)
     lib().orc_measure_image(src, _dims(src), tgt, _dims(tgt), mats, _c(a, np.float32),
                             mats.shape[0], out)
     return out
@@ -187,6 +188,7 @@ def ncc2_f64(src, tgt, mats, a):
 
 
 def ncc2_from_moments(m, n_min=0):
+    """NCC^2 from the 7 image moments (n, S1, S2 lo, S2 hi, ST, T1, T2)."""
     m = [int(v) for v in m]
     return lib().orc_ncc2_from_moments(*m, int(n_min))
 
@@ -195,9 +197,12 @@ def dice_from_counts(n, A, C_, b_full, n_min=0):
     return lib().orc_dice_from_counts(int(n), int(A), int(C_), int(b_full), int(n_min))
 
 
-def score(mode, mom10, b_full=0, n_min=0):
+MOM_STRIDE = 12   # [n S1 S2lo S2hi ST T1 T2 0 | n_nn A B C]
+
+
+def score(mode, mom12, b_full=0, n_min=0):
     mode = MODES.get(mode, mode)
-    return lib().orc_score(int(mode), _c(mom10, np.uint64), int(b_full), int(n_min))
+    return lib().orc_score(int(mode), _c(mom12, np.uint64), int(b_full), int(n_min))
 
 
 def weights(scores, gamma_log2):
@@ -276,7 +281,7 @@ def register(mode, src_dims, src_origin, tgt_dims, tgt_origin, n_particles, n_it
 
     Returns a dict: est (fp64[6] of the last iteration), poses (the resampled
     cloud after the last iteration) and, with ``trace``, per-iteration arrays
-    poses [K,6,N], mom [K,N,10], score [K,N], W [K,N], idx [K,N], est [K,6].
+    poses [K,6,N], mom [K,N,12], score [K,N], W [K,N], idx [K,N], est [K,6].
     """
     mode = MODES.get(mode, mode)
     N, K = int(n_particles), int(n_iters)
@@ -293,7 +298,7 @@ def register(mode, src_dims, src_origin, tgt_dims, tgt_origin, n_particles, n_it
 
     vols = [None if v is None else _c(v, np.uint8) for v in (src, tgt, src_mask, tgt_mask)]
     if trace:
-        tr = dict(poses=np.zeros((K, 6, N), np.float32), mom=np.zeros((K, N, 10), np.uint64),
+        tr = dict(poses=np.zeros((K, 6, N), np.float32), mom=np.zeros((K, N, 12), np.uint64),
                   score=np.zeros((K, N), np.float64), W=np.zeros((K, N), np.uint64),
                   idx=np.zeros((K, N), np.int32), est=np.zeros((K, 6), np.float64))
         trp = [ptr(tr[k]) for k in ("poses", "mom", "score", "W", "idx", "est")]

@@ -260,35 +260,37 @@ void orc_measure_mask(const uint8_t *S, const int32_t sd[3], const uint8_t *T, c
 /* ------------------------------------------------------------------------ */
 /* Measurement, image mode: moments of the trilinear sample s and target t   */
 /* over the overlap set (voxels whose sample is inside the source grid).     */
-/* Reading: s is rounded to 10 fractional bits, s_q = rint(1024 s), so every */
-/* moment is an exact integer sum (order-free, identical on any hardware).   */
-/* s_q <= 255*1024 < 2^18, so S2 < 2^60 for up to 2^24 target voxels:       */
-/*   n, S1 = sum s_q, S2 = sum s_q^2, ST = sum s_q t, T1 = sum t, T2 = sum t^2 */
-/* mom: 6 per matrix.                                                        */
+/* Reading: s is rounded to 15 fractional bits, s_q = rint(32768 s), so     */
+/* every moment is an exact integer sum (order-free, identical on any        */
+/* hardware): n, S1 = sum s_q, S2 = sum s_q^2 (128-bit), ST = sum s_q t,      */
+/* T1 = sum t, T2 = sum t^2.  s_q < 2^23.                                    */
+/* mom: 7 per matrix = n, S1, S2 low word, S2 high word, ST, T1, T2.         */
 /* ------------------------------------------------------------------------ */
 void orc_measure_image(const uint8_t *S, const int32_t sd[3], const uint8_t *T, const int32_t td[3],
                        const float *mats, const float a[3], int32_t m, uint64_t *mom)
 {
     for (int32_t p = 0; p < m; ++p) {
         const float *M = mats + 12 * (int64_t)p;
-        uint64_t n = 0, S1 = 0, S2 = 0, ST = 0, T1 = 0, T2 = 0;
+        uint64_t n = 0, S1 = 0, ST = 0, T1 = 0, T2 = 0;
+        u128 S2 = 0;
         for (int z = 0; z < td[2]; ++z)
             for (int y = 0; y < td[1]; ++y)
                 for (int x = 0; x < td[0]; ++x) {
                     float q[3], s;
                     coord(M, a, x, y, z, q);
                     if (!tri_sample(S, sd, q, &s)) continue;
-                    uint64_t sq = (uint64_t)lrintf(s * 1024.0f);
+                    uint64_t sq = (uint64_t)lrintf(s * 32768.0f);
                     uint64_t t = T[x + (int64_t)td[0] * (y + (int64_t)td[1] * z)];
                     n += 1;
                     S1 += sq;
-                    S2 += sq * sq;
+                    S2 += (u128)(sq * sq);
                     ST += sq * t;
                     T1 += t;
                     T2 += t * t;
                 }
-        uint64_t *o = mom + 6 * (int64_t)p;
-        o[0] = n; o[1] = S1; o[2] = S2; o[3] = ST; o[4] = T1; o[5] = T2;
+        uint64_t *o = mom + 7 * (int64_t)p;
+        o[0] = n; o[1] = S1; o[2] = (uint64_t)S2; o[3] = (uint64_t)(S2 >> 64);
+        o[4] = ST; o[5] = T1; o[6] = T2;
     }
 }
 
@@ -366,10 +368,11 @@ static double u128_to_f64(u128 v)
     return (double)hi * 18446744073709551616.0 + (double)lo;
 }
 
-double orc_ncc2_from_moments(uint64_t n, uint64_t S1, uint64_t S2, uint64_t ST, uint64_t T1,
-                             uint64_t T2, uint64_t n_min)
+double orc_ncc2_from_moments(uint64_t n, uint64_t S1, uint64_t S2lo, uint64_t S2hi, uint64_t ST,
+                             uint64_t T1, uint64_t T2, uint64_t n_min)
 {
     if (n == 0 || n < n_min) return 0.0;
+    u128 S2 = ((u128)S2hi << 64) | S2lo;
     u128 nS2 = (u128)n * S2, S1S1 = (u128)S1 * S1;
     u128 nT2 = (u128)n * T2, T1T1 = (u128)T1 * T1;
     if (nS2 <= S1S1 || nT2 <= T1T1) return 0.0;
@@ -389,19 +392,19 @@ double orc_dice_from_counts(uint64_t n, uint64_t A, uint64_t C, uint64_t b_full,
 
 /* Score modes (reading): 0 mask Dice, 1 mask NCC^2 (binary moments), 2 image */
 /* NCC^2, 3 combined 0.5*(image NCC^2 + mask Dice).                          */
-/* mom10 = [n S1 S2 ST T1 T2 | n_nn A B C].                                  */
-double orc_score(int32_t mode, const uint64_t mom10[10], uint64_t b_full, uint64_t n_min)
+/* mom12 = [n S1 S2lo S2hi ST T1 T2 0 | n_nn A B C].                         */
+double orc_score(int32_t mode, const uint64_t mom12[12], uint64_t b_full, uint64_t n_min)
 {
-    const uint64_t *im = mom10, *mk = mom10 + 6;
+    const uint64_t *im = mom12, *mk = mom12 + 8;
     switch (mode) {
     case 0:
         return orc_dice_from_counts(mk[0], mk[1], mk[3], b_full, n_min);
     case 1:
-        return orc_ncc2_from_moments(mk[0], mk[1], mk[1], mk[3], mk[2], mk[2], n_min);
+        return orc_ncc2_from_moments(mk[0], mk[1], mk[1], 0, mk[3], mk[2], mk[2], n_min);
     case 2:
-        return orc_ncc2_from_moments(im[0], im[1], im[2], im[3], im[4], im[5], n_min);
+        return orc_ncc2_from_moments(im[0], im[1], im[2], im[3], im[4], im[5], im[6], n_min);
     case 3:
-        return 0.5 * (orc_ncc2_from_moments(im[0], im[1], im[2], im[3], im[4], im[5], n_min) +
+        return 0.5 * (orc_ncc2_from_moments(im[0], im[1], im[2], im[3], im[4], im[5], im[6], n_min) +
                       orc_dice_from_counts(mk[0], mk[1], mk[3], b_full, n_min));
     default:
         return 0.0;
@@ -524,7 +527,7 @@ uint32_t orc_resample_offset(uint64_t seed, int32_t k)
 /*   k > 0: prediction (perturb);  every k: pose -> matrix, measurement,     */
 /*   score, update (weights), estimation, resampling.                        */
 /* Output: the estimate of the last iteration.  Optional traces (NULL skips): */
-/*   tr_poses [K][6][N] (measured poses), tr_mom [K][N][10], tr_score [K][N], */
+/*   tr_poses [K][6][N] (measured poses), tr_mom [K][N][12], tr_score [K][N], */
 /*   tr_W [K][N], tr_idx [K][N], tr_est [K][6].                              */
 /* Volumes unused by the mode may be NULL.                                    */
 /* ------------------------------------------------------------------------ */
@@ -547,7 +550,7 @@ int32_t orc_register(int32_t mode, const uint8_t *src, const uint8_t *tgt, const
     float *x = poses_inout;
     float *xn = (float *)malloc(sizeof(float) * 6 * (size_t)N);
     float *mats = (float *)malloc(sizeof(float) * 12 * (size_t)N);
-    uint64_t *mom = (uint64_t *)calloc(10 * (size_t)N, sizeof(uint64_t));
+    uint64_t *mom = (uint64_t *)calloc(12 * (size_t)N, sizeof(uint64_t));
     double *s = (double *)malloc(sizeof(double) * (size_t)N);
     uint64_t *W = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
     int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
@@ -566,22 +569,22 @@ int32_t orc_register(int32_t mode, const uint8_t *src, const uint8_t *tgt, const
             for (int d = 0; d < 6; ++d) pose[d] = x[(int64_t)d * N + i];
             orc_pose_matrix(pose, sd, so, to, mats + 12 * (int64_t)i, a);
         }
-        memset(mom, 0, sizeof(uint64_t) * 10 * (size_t)N);
+        memset(mom, 0, sizeof(uint64_t) * 12 * (size_t)N);
         for (int32_t i = 0; i < N; ++i) {
             if (mode == 2 || mode == 3)
-                orc_measure_image(src, sd, tgt, td, mats + 12 * (int64_t)i, a, 1, mom + 10 * (int64_t)i);
+                orc_measure_image(src, sd, tgt, td, mats + 12 * (int64_t)i, a, 1, mom + 12 * (int64_t)i);
             if (mode == 0 || mode == 1 || mode == 3)
                 orc_measure_mask(src_mask, sd, tgt_mask, td, mats + 12 * (int64_t)i, a, 1,
-                                 mom + 10 * (int64_t)i + 6);
+                                 mom + 12 * (int64_t)i + 8);
         }
-        for (int32_t i = 0; i < N; ++i) s[i] = orc_score(mode, mom + 10 * (int64_t)i, b_full, n_min);
+        for (int32_t i = 0; i < N; ++i) s[i] = orc_score(mode, mom + 12 * (int64_t)i, b_full, n_min);
         orc_weights(s, N, gamma_log2, W);
         double est[6];
         orc_estimate(x, N, W, est);
         orc_resample(W, N, orc_resample_offset(seed, k), idx);
 
         if (tr_poses) memcpy(tr_poses + (int64_t)kk * 6 * N, x, sizeof(float) * 6 * (size_t)N);
-        if (tr_mom) memcpy(tr_mom + (int64_t)kk * 10 * N, mom, sizeof(uint64_t) * 10 * (size_t)N);
+        if (tr_mom) memcpy(tr_mom + (int64_t)kk * 12 * N, mom, sizeof(uint64_t) * 12 * (size_t)N);
         if (tr_score) memcpy(tr_score + (int64_t)kk * N, s, sizeof(double) * (size_t)N);
         if (tr_W) memcpy(tr_W + (int64_t)kk * N, W, sizeof(uint64_t) * (size_t)N);
         if (tr_idx) memcpy(tr_idx + (int64_t)kk * N, idx, sizeof(int32_t) * (size_t)N);

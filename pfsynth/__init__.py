@@ -379,7 +379,8 @@ def cached(fn, *args, cache_dir=None, **kwargs):
     """Memoise a generator call on disk (keyed by its arguments)."""
     import pickle
     cache_dir = cache_dir or os.environ.get("PFSYNTH_CACHE", "/tmp/pfsynth_cache")
-    key = hashlib.sha1(repr((fn.__name__, args, sorted(kwargs.items()))).encode()).hexdigest()[:16]
+    key = hashlib.sha1(pickle.dumps((fn.__name__, args, sorted(kwargs.items())),
+                                    protocol=4)).hexdigest()[:16]
     path = os.path.join(cache_dir, f"{fn.__name__}_{key}.pkl")
     if os.path.exists(path):
         try:

@@ -73,10 +73,13 @@ def integer_map_counts(src, tgt, P, b, image=False):
     if not image:
         sb, tb = (s != 0).astype(np.int64), (t != 0).astype(np.int64)
         return np.array([ok.sum(), sb.sum(), (tb * ok).sum(), (sb & tb).sum()], np.int64)
-    sq = 1024 * s
-    ok64 = ok.astype(np.int64)
-    return np.array([ok.sum(), sq.sum(), (sq * sq).sum(), (sq * t).sum(), (t * ok64).sum(),
-                     (t * t * ok64).sum()], np.int64)
+    sq = [32768 * int(v) for v in s]          # exact Python ints (S2 needs > 64 bits)
+    tt = [int(v) for v in t]
+    S2 = sum(v * v for v in sq)
+    okl = [int(v) for v in ok]
+    return np.array([sum(okl), sum(sq), S2 & (2**64 - 1), S2 >> 64, sum(a * b for a, b in zip(sq, tt)),
+                     sum(a * b for a, b in zip(tt, okl)), sum(a * a * b for a, b in zip(tt, okl))],
+                    dtype=np.uint64)
 
 
 def integer_map_warp(src, tgt_dims, P, b):

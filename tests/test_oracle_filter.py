@@ -101,8 +101,8 @@ def test_trace_is_consistent_with_the_steps(orc):
         assert np.array_equal(x, r["tr_poses"][k])
         mats, a = orc.pose_matrices(x, p.src_dims, p.src_origin, p.tgt_origin)
         c = orc.measure_mask(p.src, p.tgt, mats, a)
-        assert np.array_equal(c, r["tr_mom"][k][:, 6:10])
-        s = np.array([orc.score("mask_dice", np.concatenate([np.zeros(6, np.uint64), ci]), bfull, nmin)
+        assert np.array_equal(c, r["tr_mom"][k][:, 8:12])
+        s = np.array([orc.score("mask_dice", np.concatenate([np.zeros(8, np.uint64), ci]), bfull, nmin)
                       for ci in c])
         assert np.array_equal(s, r["tr_score"][k])
         W = orc.weights(s, 5)
@@ -134,5 +134,5 @@ def test_combined_mode_runs(orc):
                      np.deg2rad(10), 4.0, seed=3, src=p.src, tgt=p.tgt, src_mask=p.src_mask,
                      tgt_mask=p.tgt_mask)
     mom = r["tr_mom"][0]
-    assert np.all(mom[:, 0] > 0) and np.all(mom[:, 6] > 0)
+    assert np.all(mom[:, 0] > 0) and np.all(mom[:, 8] > 0)
     assert np.all((r["tr_score"] >= 0) & (r["tr_score"] <= 1))

@@ -140,7 +140,7 @@ def test_mask_identity_gives_dice_one(orc):
     n, A, B, C = (int(v) for v in orc.measure_mask(m, m, M, a)[0])
     assert n == m.size and A == B == C == int(m.sum())
     assert orc.dice_from_counts(n, A, C, int(m.sum())) == 1.0
-    assert orc.score("mask_ncc", np.array([0] * 6 + [n, A, B, C], np.uint64)) == 1.0
+    assert orc.score("mask_ncc", np.array([0] * 8 + [n, A, B, C], np.uint64)) == 1.0
 
 
 def test_mask_counts_general_pose_vs_bruteforce(orc):
@@ -245,9 +245,10 @@ def test_ncc_formula_against_exact_rationals(orc):
         s = rng.integers(0, 65281, 3)
         t = rng.integers(0, 256, 3)
         # consistent moments from a tiny synthetic sample scaled up
-        S1, S2, ST = int(s[0]) * n // 3, int(s[0]) ** 2 * n // 2, int(s[0]) * int(t[0]) * n // 4
+        sv = int(s[0]) * 128                      # samples up to 2^23 (15 fractional bits)
+        S1, S2, ST = sv * n // 3, sv ** 2 * n // 2, sv * int(t[0]) * n // 4
         T1, T2 = int(t[0]) * n // 3, int(t[0]) ** 2 * n // 2
-        m = [n, S1, S2, ST, T1, T2]
+        m = [n, S1, S2 & (2**64 - 1), S2 >> 64, ST, T1, T2]
         vs, vt = n * S2 - S1 * S1, n * T2 - T1 * T1
         if vs <= 0 or vt <= 0:
             assert orc.ncc2_from_moments(m) == 0.0
@@ -274,15 +275,15 @@ def test_image_identity_ncc_one(orc):
     M, a = orc.pose_matrix(np.zeros(6, np.float32), (15, 14, 13), np.zeros(3, np.float32),
                            np.zeros(3, np.float32))
     m = orc.measure_image(v, v, M, a)[0]
-    assert int(m[0]) == v.size and int(m[1]) == 1024 * int(v.astype(np.int64).sum())
+    assert int(m[0]) == v.size and int(m[1]) == 32768 * int(v.astype(np.int64).sum())
     assert abs(orc.ncc2_from_moments(m) - 1.0) < 1e-15
 
 
 def test_score_zero_cases(orc):
     # overlap below n_min, empty overlap, constant target
-    assert orc.ncc2_from_moments([5, 10, 30, 20, 2, 4], n_min=6) == 0.0
-    assert orc.ncc2_from_moments([0, 0, 0, 0, 0, 0]) == 0.0
-    assert orc.ncc2_from_moments([4, 1000, 400000, 4000, 16, 64]) == 0.0
+    assert orc.ncc2_from_moments([5, 10, 30, 0, 20, 2, 4], n_min=6) == 0.0
+    assert orc.ncc2_from_moments([0, 0, 0, 0, 0, 0, 0]) == 0.0
+    assert orc.ncc2_from_moments([4, 1000, 400000, 0, 4000, 16, 64]) == 0.0
     assert orc.dice_from_counts(10, 0, 0, 0) == 0.0
 
 
@@ -395,3 +396,20 @@ def test_warp_trilinear_vs_scipy(orc):
     want[ok] = np.rint(s).astype(np.int32)
     diff = np.abs(got - want)
     assert diff.max() <= 1 and np.mean(diff > 0) < 0.01
+
+
+def test_fixed_point_ncc_weak_correlation(orc):
+    """Near r = 0 the relative error of r^2 is largest (Eq. 2 is squared);
+    15 fractional bits keep even these scores within 1e-5 of the fp64 NCC."""
+    worst = 0.0
+    for seed in range(4):
+        src = pfsynth.random_image(100 + seed, (40, 37, 29))
+        tgt = pfsynth.random_image(200 + seed, (45, 33, 27))
+        so, to = np.array([0.0, 1.5, -2.0], np.float32), np.array([3.0, -1.0, 2.5], np.float32)
+        for pose in _rand_poses(10, rot=0.6, tr=8, seed=seed).astype(np.float32):
+            M, a = orc.pose_matrix(pose, src.shape[::-1], so, to)
+            fixed = orc.ncc2_from_moments(orc.measure_image(src, tgt, M, a)[0])
+            exact = orc.ncc2_f64(src, tgt, M, a)[0]
+            if exact > 0:
+                worst = max(worst, abs(fixed - exact) / exact)
+    assert worst <= 1e-5, worst
