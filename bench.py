@@ -1,0 +1,406 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 particle-filter registration path.
+
+One step = one whole registration of the image-based workload -- 224x208x176
+uint8 speckle volumes, N = 2048 particles, 50 iterations, +-30 deg / +-25
+voxel limits, trilinear NCC^2 -- followed by the warp of the 20-frame source
+sequence with the estimate (context creation, all iterations, estimate and
+warp inside the step).  Inputs are seeded synthetic stand-ins (pfsynth).
+
+Metric: particle-voxel evaluations per second, counted densely
+(N x iterations x target voxels per registration), and ms per registration.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank registers its own pair (independent
+problems, weak scaling); rank 0 prints one JSON line.  ``--impl reference``
+times the CPU oracle (the only reference this method has) on a bounded sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pfsynth  # noqa: E402
+
+WORKLOADS = {
+    "config1": dict(pfsynth.CONFIG1, kind="image_ncc", dims=(224, 208, 176)),
+    "config0": dict(pfsynth.CONFIG0, kind="mask_dice", dims=(64, 64, 64), n_frames=0),
+}
+METRIC = "particle-voxel evals/s (dense N*iters*target voxels per registration) and ms per registration"
+UNIT = "particle-voxel evals/s"
+
+# FP32 operations the arithmetic definition fixes per visited voxel of the
+# trilinear measurement: 3 mul + 3 add (coordinates), 3 floor, 3 subtract
+# (fractions), 7 lerps x 3 ops, 1 scale to 1/1024 fixed point.
+OPS_PER_EVAL = 34
+FP32_LANES_PER_SM = 128
+
+# DRAM traffic of one measurement launch from an ncu capture (profiles/), with
+# the hash of the kernel source it was taken on; reported as null once the
+# kernel changes.
+NCU_TRAFFIC = {"measure_cu_sha1": None, "bytes_per_launch": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config1")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-particles", type=int, default=32)
+    ap.add_argument("--cpu-sample-iters", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    def __init__(self, world):
+        self.world = world
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.dist = dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, v):
+        if self.world == 1:
+            return v
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v):
+        if self.world == 1:
+            return v
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.dist.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def load_workload(name, rank):
+    w = WORKLOADS[name]
+    if w["kind"] == "image_ncc":
+        pair = pfsynth.cached(pfsynth.speckle_pair, rank)
+        frames = pfsynth.cached(pfsynth.frame_sequence, pair, w["n_frames"]) if w["n_frames"] else None
+    else:
+        pair = pfsynth.ellipsoid_pair(rank)
+        frames = None
+    return w, pair, frames
+
+
+def dense_units(w, pair):
+    return w["n_particles"] * w["n_iters"] * int(np.prod(pair.tgt.shape))
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, pair, n_particles, n_iters):
+    """Time the oracle on a bounded sample of the workload: the same pair,
+    n_particles particles, n_iters iterations.  Returns (seconds, dense units)."""
+    import oracle
+    oracle.build()
+    kw = {}
+    if w["kind"] == "image_ncc":
+        kw = dict(src=pair.src, tgt=pair.tgt)
+    else:
+        kw = dict(src_mask=pair.src, tgt_mask=pair.tgt)
+    t0 = time.perf_counter()
+    oracle.register(w["kind"], pair.src_dims, pair.src_origin, pair.tgt_dims, pair.tgt_origin, n_particles,
+                    n_iters, np.deg2rad(w["rot_limit_deg"]), w["trans_limit"], seed=w["seed"], trace=False, **kw)
+    dt = time.perf_counter() - t0
+    return dt, n_particles * n_iters * int(np.prod(pair.tgt.shape))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w, pair, _ = load_workload(args.workload, 0)
+    n, k = args.cpu_sample_particles, 1
+    times, units = [], 0
+    for i in range(args.warmup + args.steps):
+        dt, u = oracle_sample(w, pair, n, k)
+        if i >= args.warmup:
+            times.append(dt)
+            units = u
+    tot = sum(times)
+    value = units * len(times) / tot
+    sample = (f"oracle (single-threaded C) on the same pair: {n} particles x {k} iteration "
+              f"({units:.3g} dense evals) per step; warp excluded")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": w["name"], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our path
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import paper_2504_19930_gb300 as pk
+
+    torch.cuda.set_device(local)
+    pk.build()
+    pk.load()
+    dist = Dist(world)
+    w, pair, frames = load_workload(args.workload, rank)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    src_d = torch.from_numpy(pair.src).to(dev)
+    tgt_d = torch.from_numpy(pair.tgt).to(dev)
+    fr_d = [torch.from_numpy(f).to(dev) for f in frames] if frames is not None else []
+    out_d = [torch.empty(pair.tgt.shape, dtype=torch.uint8, device=dev) for _ in fr_d]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    lr, lt = np.deg2rad(w["rot_limit_deg"]), w["trans_limit"]
+    kind = w["kind"]
+
+    def make_reg():
+        vols = dict(src=src_d, tgt=tgt_d) if kind != "mask_dice" else dict(src_mask=src_d, tgt_mask=tgt_d)
+        return pk.Registration(kind, src_origin=pair.src_origin, tgt_origin=pair.tgt_origin,
+                               n_particles=w["n_particles"], rot_limit=lr, trans_limit=lt, seed=w["seed"],
+                               **vols)
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps + args.warmup)]
+    rec = {"measure_ms": 0.0, "measure_launches": 0, "evals": 0, "warp_ms": 0.0}
+
+    def step(i, timed):
+        flush.fill_(i & 0xFF)                      # L2 flush (outside the timed events)
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        reg = make_reg()
+        if timed:
+            pk.pf_profile_begin(reg.ctx, w["n_iters"])
+        reg.step(w["n_iters"])
+        pose, _ = reg.estimate(with_score=False)
+        e1.record(stream)
+        if fr_d:
+            pk.warp_sequence(fr_d, pair.src_dims, pair.src_origin, out_d, pair.tgt_dims, pair.tgt_origin,
+                             pose, 1, stream=stream)
+        e2.record(stream)
+        if timed:
+            ms, n = pk.pf_profile_end(reg.ctx)
+            rec["measure_ms"] += ms
+            rec["measure_launches"] += n
+            _, _, _, evals = pk.pf_get_log(reg.ctx, capacity=w["n_iters"])
+            rec["evals"] += int(evals.sum())
+        reg.close()
+        return pose
+
+    for i in range(args.warmup):
+        step(i, False)
+    torch.cuda.synchronize()
+    gpu_id = local
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    launches0 = pk.pf_kernel_launches()
+    dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_id) as clocks:
+        t0 = time.perf_counter()
+        for i in range(args.warmup, args.warmup + args.steps):
+            pose = step(i, True)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    dist.barrier()
+    launches = pk.pf_kernel_launches() - launches0
+    step_ms = [ev[i][0].elapsed_time(ev[i][2]) for i in range(args.warmup, args.warmup + args.steps)]
+    warp_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.warmup, args.warmup + args.steps)]
+    local_s = sum(step_ms) / 1e3
+    t_max = dist.max(local_s)
+    units = dense_units(w, pair) * args.steps
+    total_units = dist.sum(units)
+    value = total_units / t_max
+    clk = clocks.summary()
+
+    # roofline of the dominant kernel (the measurement)
+    peaks = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz") or 2070.0
+    peak_ops = sm_count * FP32_LANES_PER_SM * mhz * 1e6
+    meas_s = rec["measure_ms"] / 1e3
+    achieved = rec["evals"] * OPS_PER_EVAL / meas_s if meas_s > 0 else 0.0
+    sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "measure.cu"), "rb")
+                       .read()).hexdigest()
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["measure_cu_sha1"] == sha else None
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TOP/s",
+                "frac": achieved / peak_ops if peak_ops else None, "traffic": traffic,
+                "kernel": "k_measure<image>", "ops_per_eval": OPS_PER_EVAL,
+                "evals_per_launch": rec["evals"] / max(rec["measure_launches"], 1),
+                "avg_launch_ms": rec["measure_ms"] / max(rec["measure_launches"], 1),
+                "share_of_step": rec["measure_ms"] / sum(step_ms),
+                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} fp32 lanes x {mhz:.0f} MHz (median SM clock sampled during the timed steps)"}
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        src_h = torch.from_numpy(pair.src).pin_memory()
+        tgt_h = torch.from_numpy(pair.tgt).pin_memory()
+        fr_h = [torch.from_numpy(f).pin_memory() for f in frames] if frames is not None else []
+        out_h = [torch.empty(pair.tgt.shape, dtype=torch.uint8).pin_memory() for _ in fr_h]
+        mode_kw = dict(src=src_h, tgt=tgt_h) if kind != "mask_dice" else dict(src_mask=src_h, tgt_mask=tgt_h)
+
+        def e2e_step():
+            return pk.register_sequence(kind, frames=fr_h, n_iters=w["n_iters"], src_origin=pair.src_origin,
+                                        tgt_origin=pair.tgt_origin, out=out_h, n_particles=w["n_particles"],
+                                        rot_limit=lr, trans_limit=lt, seed=w["seed"], **mode_kw)
+
+        e2e_step()                                 # warm-up of the host path
+        torch.cuda.synchronize()
+        dist.barrier()
+        times = []                                 # host wall time per call, L2 flush excluded
+        for _ in range(args.e2e_steps):
+            flush.fill_(2)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t1)
+        e2e_s = dist.max(sum(times))
+        h2d = pair.src.nbytes + pair.tgt.nbytes + sum(f.nbytes for f in (frames if frames is not None else []))
+        d2h = sum(o.numel() for o in out_h) + 6 * 4
+        e2e = {"value": dist.sum(units / args.steps * args.e2e_steps) / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": 1e3 * e2e_s / args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, k = args.cpu_sample_particles, args.cpu_sample_iters
+        dt, u = oracle_sample(w, pair, n, k)
+        cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} particles x {k} iterations of the same pair ({u:.3g} dense evals, "
+                         f"{dt:.1f} s single-threaded); warp excluded"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "volume": "x".join(map(str, pair.src_dims)),
+                       "n_particles": w["n_particles"], "n_iters": w["n_iters"],
+                       "frames_warped": len(fr_d), "mode": kind,
+                       "l2": "flushed before every step (256 MiB write, outside the timed events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "warp_ms_per_step": statistics.mean(warp_ms),
+                       "overlap_evals_per_step": rec["evals"] / args.steps},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "wall_s_timed": wall, "final_pose": [float(v) for v in pose],
+            "true_pose": [float(v) for v in pair.true_pose],
+        }
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * pfreg.h -- C ABI of the GB300 (sm_103a) particle-filter 3D-3D rigid
+ * registration library (libpfreg.so).
+ *
+ * The method: a sequential Monte Carlo (particle filter) search for the
+ * rigid transform that aligns a source volume or binary mask with a target
+ * (Eq. 1, Sec. 3.1), and the warp of every frame of the source sequence by
+ * the estimate (Abstract; Sec. 3.3).  Each particle is a 6-DOF pose
+ * [rx, ry, rz, tx, ty, tz] (radians, voxels; Eq. 3) drawn within the given
+ * rotation and translation limits; every iteration runs the cycle of the
+ * Fig. 1 caption: prediction (perturbation), measurement (each particle's
+ * transform warps the source into the target grid and a similarity is
+ * reduced over the voxels), update (weights), estimation and resampling.
+ *
+ * Conventions
+ *   Volumes: uint8, x fastest, index = x + X*(y + Y*z); dims = {X, Y, Z},
+ *   each >= 2 and <= 2048.  A grid's origin is the world position of voxel
+ *   (0,0,0) in voxel units (spacing 1).  A pose maps target voxel p to the
+ *   source continuous index q = R (p + o_T - c) + c + t - o_S with
+ *   R = Rz(rz) Rx(rx) Ry(ry) and c = o_S + (dims_S - 1)/2 the source centre.
+ *   Masks: nonzero voxels are 1.
+ *
+ * Errors: every call returns PF_OK (0) or a negative PF_E* code and never
+ * aborts; pf_last_error() gives the calling thread's last message.
+ * Threading: a context belongs to one CUDA stream; calls on one context are
+ * not thread-safe.  Different contexts are independent.
+ */
+#ifndef PFREG_H
+#define PFREG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PF_OK 0
+#define PF_EINVAL (-1)   /* bad argument: NULL, dims, limits, sizes, non-finite values */
+#define PF_ENOMEM (-2)   /* a device or pinned-host allocation failed */
+#define PF_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define PF_ESTATE (-5)   /* call not valid in the context's current state */
+
+typedef struct pf_ctx pf_ctx;
+
+/* A volume description.  data points to X*Y*Z bytes; is_device = 1 when it is
+ * a device pointer on the current device, 0 for host memory. */
+typedef struct {
+    const void *data;
+    int32_t dims[3];
+    float origin[3];
+    int32_t is_device;
+} pf_volume;
+
+/* Measurement modes (similarity of Sec. 3.3-3.4):
+ *   PF_MASK_DICE  nearest-neighbour mask sampling, Dice of Eq. 4 over the
+ *                 whole target grid (source taken as 0 outside its grid);
+ *   PF_MASK_NCC   nearest-neighbour mask sampling, squared NCC of Eq. 2 over
+ *                 the overlap;
+ *   PF_IMAGE_NCC  trilinear image sampling, squared NCC of Eq. 2 over the
+ *                 overlap;
+ *   PF_COMBINED   0.5 * (image NCC^2 + mask Dice), both from one sweep. */
+typedef enum { PF_MASK_DICE = 0, PF_MASK_NCC = 1, PF_IMAGE_NCC = 2, PF_COMBINED = 3 } pf_mode;
+
+/* Filter settings.  The paper states only that the method starts from
+ * rotation and translation limits (Abstract); the remaining settings are this
+ * library's readings of the Fig. 1 cycle:
+ *   sigma_k = sigma0_frac * limit * sigma_decay^k   (perturbation scale)
+ *   w_i     = (s_i / max s)^(2^gamma_log2)          (likelihood)
+ *   score 0 when the overlap has fewer than min_overlap_frac * |target| voxels. */
+typedef struct {
+    int32_t mode;             /* pf_mode */
+    int32_t n_particles;      /* 1 .. 65536 */
+    float rot_limit[3];       /* radians, each in (0, pi/2] */
+    float trans_limit[3];     /* voxels, each in (0, 2048] */
+    float sigma0_frac;        /* (0, 1] */
+    float sigma_decay;        /* (0, 1] */
+    int32_t gamma_log2;       /* 0 .. 10 */
+    uint64_t seed;            /* Philox4x32-10 key */
+    float min_overlap_frac;   /* [0, 1] */
+} pf_config;
+
+/* Fill cfg with the defaults: PF_MASK_DICE, N = 256, limits 15 deg / 8 voxels,
+ * sigma0_frac 0.25, sigma_decay 0.8, gamma_log2 5, seed 0,
+ * min_overlap_frac 0.01. */
+void pf_config_default(pf_config *cfg);
+
+/* Create a registration context (Sec. 3.1 problem statement: source and target
+ * volumes or masks, limits, N).  Copies (or bit-packs) the volumes into
+ * context-owned device memory on `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream), counts the target mask, and draws the initial
+ * particles uniformly within the limits (iteration index 0).
+ *   Image modes need src/tgt; mask modes need src_mask/tgt_mask; the combined
+ *   mode needs all four, with each mask on its image's grid.  Unused volumes
+ *   may be NULL.  The caller may free its buffers when the call returns.
+ * Errors: PF_EINVAL (missing volume, dims, limits, N), PF_ENOMEM, PF_ECUDA.
+ * On error *out is set to NULL. */
+int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt,
+                     const pf_volume *src_mask, const pf_volume *tgt_mask,
+                     const pf_config *cfg, void *cuda_stream);
+
+/* Run n_iters filter iterations k .. k+n_iters-1 (Fig. 1 cycle): for k > 0
+ * perturb every particle, then pose -> matrix, measure, score, weights,
+ * estimate, resample.  Asynchronous on the context's stream; each iteration
+ * is one CUDA-graph launch.  Errors: PF_EINVAL (n_iters < 0), PF_ECUDA. */
+int pf_step(pf_ctx *ctx, int32_t n_iters);
+
+/* Synchronise the stream and return the estimate of the last iteration
+ * (weighted mean pose) and, when score_out is not NULL, the score of that
+ * pose (one extra measurement).  PF_ESTATE before the first pf_step. */
+int pf_estimate(pf_ctx *ctx, float pose_out[6], double *score_out);
+
+/* Release the context and its device memory (NULL is accepted). */
+int pf_register_destroy(pf_ctx *ctx);
+
+/* Warp every frame of a sequence by one pose (Abstract; Sec. 3.3: the
+ * transform found on the end-diastolic frame is applied to all frames).
+ * frames_in / frames_out: host arrays of n_frames DEVICE pointers, each frame
+ * src_dims resp. tgt_dims bytes.  out(p) = round-half-even of the trilinear
+ * sample (interp = 1) or the nearest voxel (interp = 0) of the source at q(p),
+ * 0 where q(p) falls outside the source grid.  Allocates nothing; runs
+ * asynchronously on cuda_stream.  Errors: PF_EINVAL (NULL, dims, pose
+ * rotation outside [-pi/2, pi/2], non-finite pose), PF_ECUDA. */
+int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32_t src_dims[3],
+                  const float src_origin[3], uint8_t *const *frames_out,
+                  const int32_t tgt_dims[3], const float tgt_origin[3], const float pose[6],
+                  int32_t interp, void *cuda_stream);
+
+/* ---- inspection, checkpoint and test exports (host buffers, synchronous) ---- */
+
+/* Number of iterations run so far (the next iteration's index k). */
+int pf_get_iteration(pf_ctx *ctx, int32_t *k_out);
+
+/* Copy the state of the last iteration to host buffers (any may be NULL):
+ *   poses_measured [6][N]  the cloud that was measured (SoA, DOF-major)
+ *   moments        [N][12] n S1 S2lo S2hi ST T1 T2 0 | n_nn A B C: image
+ *                          moments of the trilinear samples rounded to
+ *                          s_q = rint(2^15 s) over the overlap (S2 = sum s_q^2
+ *                          as two 64-bit words), then the mask counts
+ *   scores [N], weights [N] (W = floor(w * 2^24)), resample_idx [N]
+ *   poses_next     [6][N]  the resampled cloud the next iteration starts from */
+int pf_get_state(pf_ctx *ctx, float *poses_measured, uint64_t *moments, double *scores,
+                 uint64_t *weights, int32_t *resample_idx, float *poses_next);
+
+/* Checkpoint resume: replace the cloud ([6][N] host, within the limits) and
+ * set the iteration index to k (the counter-based RNG makes the continuation
+ * bit-identical to an uninterrupted run). */
+int pf_set_state(pf_ctx *ctx, const float *poses6xN, int32_t k);
+
+/* Per-iteration log of the last min(k, capacity, 4096) iterations, oldest
+ * first (any array may be NULL): est [count][6] (fp64 estimate), best [count]
+ * (max score), ess [count] (effective sample size from the integer weights),
+ * evals [count] (particle-voxel evaluations measured: the summed overlap
+ * counts).  *count_inout: in = capacity of the caller's arrays, out = rows. */
+int pf_get_log(pf_ctx *ctx, double *est, double *best, double *ess, uint64_t *evals,
+               int32_t *count_inout);
+
+/* Measure M given 3x4 matrices (host, [M][12] = r00 r01 r02 b0 | r10 ... b2)
+ * with offset a (host float[3]): q = R (p - a) + b.  Writes moments [M][12]
+ * (host) in the layout of pf_get_state.  Used to inject exact matrices. */
+int pf_measure_matrices(pf_ctx *ctx, const float *mats, int32_t M, const float a[3],
+                        uint64_t *moments_out);
+
+/* Pose -> (matrix [12], offset a [3]) exactly as the filter computes it. */
+int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float src_origin[3],
+                   const float tgt_origin[3], float mat_out[12], float a_out[3]);
+
+/* Philox4x32-10 of (ctr, key) computed on the device (tests of the generator). */
+int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Timing of the measurement kernel (the hot loop) inside the iteration graph:
+ * pf_profile_begin arms CUDA events for the next `capacity` iterations run by
+ * pf_step (0 disarms); pf_profile_end synchronises and returns the summed
+ * device time of those measurement launches (ms) and how many were timed. */
+int pf_profile_begin(pf_ctx *ctx, int32_t capacity);
+int pf_profile_end(pf_ctx *ctx, double *total_ms, int32_t *n_timed);
+
+/* Number of this library's kernels launched in this process so far (each
+ * graph replay counts its kernels). */
+uint64_t pf_kernel_launches(void);
+
+/* The calling thread's last error message ("" if none). */
+const char *pf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFREG_H */

@@ -1,0 +1,405 @@
+"""GB300-native particle-filter 3D-3D rigid registration.
+
+Thin Python binding of ``libpfreg.so`` (C ABI in ``include/pfreg.h``).  It only
+marshals arguments: every step of the registration runs in the library's
+sm_103a kernels.  PyTorch provides device memory and streams.  There is no
+CPU fallback: when the library is missing or no GPU is present the calls
+raise.
+
+Functions carry the C names (``pf_register_init``, ``pf_step``,
+``pf_estimate``, ``warp_sequence``, ...).  :class:`Registration` wraps one
+context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+from ._build import build as _build_lib
+
+__all__ = [
+    "PF_MASK_DICE", "PF_MASK_NCC", "PF_IMAGE_NCC", "PF_COMBINED", "PfError", "load",
+    "pf_config_default", "pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy",
+    "warp_sequence", "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
+    "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_kernel_launches", "pf_last_error",
+    "pf_profile_begin", "pf_profile_end", "register_sequence",
+    "Registration", "MODES", "build", "library_path",
+]
+
+PF_MASK_DICE, PF_MASK_NCC, PF_IMAGE_NCC, PF_COMBINED = 0, 1, 2, 3
+MODES = {"mask_dice": 0, "mask_ncc": 1, "image_ncc": 2, "combined": 3}
+MOM_STRIDE = 12   # [n S1 S2lo S2hi ST T1 T2 0 | n_nn A B C]
+_ERRORS = {-1: "PF_EINVAL", -2: "PF_ENOMEM", -3: "PF_ECUDA", -5: "PF_ESTATE"}
+
+
+class PfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pf_volume(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("dims", C.c_int32 * 3), ("origin", C.c_float * 3),
+                ("is_device", C.c_int32)]
+
+
+class pf_config(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("n_particles", C.c_int32), ("rot_limit", C.c_float * 3),
+                ("trans_limit", C.c_float * 3), ("sigma0_frac", C.c_float),
+                ("sigma_decay", C.c_float), ("gamma_log2", C.c_int32), ("seed", C.c_uint64),
+                ("min_overlap_frac", C.c_float)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def build(force: bool = False) -> str:
+    return _build_lib(force=force)
+
+
+def load():
+    """Load libpfreg.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    f"libpfreg.so not found at {_LIB_PATH}; build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(_LIB_PATH)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i32, u64 = C.c_void_p, C.c_int32, C.c_uint64
+    L.pf_config_default.argtypes = [C.POINTER(pf_config)]
+    L.pf_config_default.restype = None
+    L.pf_register_init.argtypes = [C.POINTER(vp), C.POINTER(pf_volume), C.POINTER(pf_volume),
+                                   C.POINTER(pf_volume), C.POINTER(pf_volume), C.POINTER(pf_config), vp]
+    L.pf_step.argtypes = [vp, i32]
+    L.pf_estimate.argtypes = [vp, vp, vp]
+    L.pf_register_destroy.argtypes = [vp]
+    L.warp_sequence.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32, vp]
+    L.pf_get_iteration.argtypes = [vp, vp]
+    L.pf_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.pf_set_state.argtypes = [vp, vp, i32]
+    L.pf_get_log.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pf_measure_matrices.argtypes = [vp, vp, i32, vp, vp]
+    L.pf_pose_matrix.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pf_philox.argtypes = [vp, vp, vp]
+    L.pf_profile_begin.argtypes = [vp, i32]
+    L.pf_profile_end.argtypes = [vp, vp, vp]
+    L.pf_kernel_launches.argtypes = []
+    L.pf_kernel_launches.restype = u64
+    L.pf_last_error.argtypes = []
+    L.pf_last_error.restype = C.c_char_p
+    for name in ("pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy", "warp_sequence",
+                 "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
+                 "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_profile_begin",
+                 "pf_profile_end"):
+        getattr(L, name).restype = C.c_int
+
+
+def pf_last_error() -> str:
+    return load().pf_last_error().decode()
+
+
+def _check(rc):
+    if rc != 0:
+        raise PfError(rc, pf_last_error())
+    return rc
+
+
+def _ptr(a):
+    """ctypes pointer of a numpy array (host) or torch tensor (host or device).
+    The caller keeps ``a`` alive for the duration of the C call."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(a.data_ptr())
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_volume(vol, origin=(0.0, 0.0, 0.0), dims=None):
+    """pf_volume from a (Z,Y,X) uint8 numpy array or torch tensor (CPU or CUDA)."""
+    if vol is None:
+        return None
+    is_dev = 0
+    if isinstance(vol, np.ndarray):
+        if vol.dtype != np.uint8 or vol.ndim != 3 or not vol.flags.c_contiguous:
+            raise ValueError("volume must be a C-contiguous (Z,Y,X) uint8 array")
+        shape = vol.shape
+    else:
+        import torch
+        if vol.dtype != torch.uint8 or vol.dim() != 3 or not vol.is_contiguous():
+            raise ValueError("volume must be a contiguous (Z,Y,X) uint8 tensor")
+        shape = tuple(vol.shape)
+        is_dev = 1 if vol.is_cuda else 0
+    v = pf_volume()
+    v.data = _ptr(vol).value
+    d = dims if dims is not None else (shape[2], shape[1], shape[0])
+    v.dims[:] = [int(x) for x in d]
+    v.origin[:] = [float(x) for x in origin]
+    v.is_device = is_dev
+    return v
+
+
+def pf_config_default() -> pf_config:
+    cfg = pf_config()
+    load().pf_config_default(C.byref(cfg))
+    return cfg
+
+
+def make_config(mode="mask_dice", n_particles=256, rot_limit=0.2617994, trans_limit=8.0,
+                sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, seed=0, min_overlap_frac=0.01):
+    cfg = pf_config_default()
+    cfg.mode = MODES.get(mode, mode)
+    cfg.n_particles = int(n_particles)
+    cfg.rot_limit[:] = [float(v) for v in np.broadcast_to(np.asarray(rot_limit, np.float32), (3,))]
+    cfg.trans_limit[:] = [float(v) for v in np.broadcast_to(np.asarray(trans_limit, np.float32), (3,))]
+    cfg.sigma0_frac = float(sigma0_frac)
+    cfg.sigma_decay = float(sigma_decay)
+    cfg.gamma_log2 = int(gamma_log2)
+    cfg.seed = int(seed)
+    cfg.min_overlap_frac = float(min_overlap_frac)
+    return cfg
+
+
+def pf_register_init(src, tgt, src_mask, tgt_mask, cfg, stream=None):
+    """Create a context; volumes are pf_volume structures (or None)."""
+    ctx = C.c_void_p()
+    ref = lambda v: C.byref(v) if v is not None else None  # noqa: E731
+    _check(load().pf_register_init(C.byref(ctx), ref(src), ref(tgt), ref(src_mask), ref(tgt_mask),
+                                   C.byref(cfg), _stream_handle(stream)))
+    return ctx
+
+
+def pf_step(ctx, n_iters):
+    _check(load().pf_step(ctx, int(n_iters)))
+
+
+def pf_estimate(ctx, with_score=True):
+    pose = np.zeros(6, np.float32)
+    score = C.c_double()
+    _check(load().pf_estimate(ctx, _ptr(pose), C.byref(score) if with_score else None))
+    return pose, (score.value if with_score else None)
+
+
+def pf_register_destroy(ctx):
+    _check(load().pf_register_destroy(ctx))
+
+
+def warp_sequence(frames_in, src_dims, src_origin, frames_out, tgt_dims, tgt_origin, pose,
+                  interp=1, stream=None):
+    """frames_in / frames_out: sequences of CUDA uint8 tensors (one per frame)."""
+    n = len(frames_in)
+    if len(frames_out) != n:
+        raise ValueError("frames_in and frames_out differ in length")
+    fin = (C.c_void_p * max(n, 1))(*[f.data_ptr() for f in frames_in])
+    fout = (C.c_void_p * max(n, 1))(*[f.data_ptr() for f in frames_out])
+    sd, so = _np(src_dims, np.int32), _np(src_origin, np.float32)
+    td, to, ps = _np(tgt_dims, np.int32), _np(tgt_origin, np.float32), _np(pose, np.float32)
+    _check(load().warp_sequence(fin, n, _ptr(sd), _ptr(so), fout, _ptr(td), _ptr(to), _ptr(ps), int(interp),
+                                _stream_handle(stream)))
+
+
+def pf_get_iteration(ctx) -> int:
+    k = C.c_int32()
+    _check(load().pf_get_iteration(ctx, C.byref(k)))
+    return k.value
+
+
+def pf_get_state(ctx, n_particles):
+    N = int(n_particles)
+    out = dict(poses_measured=np.zeros((6, N), np.float32),
+               moments=np.zeros((N, MOM_STRIDE), np.uint64), scores=np.zeros(N, np.float64),
+               weights=np.zeros(N, np.uint64), resample_idx=np.zeros(N, np.int32),
+               poses_next=np.zeros((6, N), np.float32))
+    _check(load().pf_get_state(ctx, *[_ptr(out[k]) for k in ("poses_measured", "moments", "scores",
+                                                              "weights", "resample_idx", "poses_next")]))
+    return out
+
+
+def pf_set_state(ctx, poses6xN, k):
+    p = _np(poses6xN, np.float32)
+    _check(load().pf_set_state(ctx, _ptr(p), int(k)))
+
+
+def pf_get_log(ctx, capacity=4096):
+    """(est [n,6], best [n], ess [n], evals [n]) for the last n iterations."""
+    est = np.zeros((capacity, 6), np.float64)
+    best = np.zeros(capacity, np.float64)
+    ess = np.zeros(capacity, np.float64)
+    evals = np.zeros(capacity, np.uint64)
+    n = C.c_int32(capacity)
+    _check(load().pf_get_log(ctx, _ptr(est), _ptr(best), _ptr(ess), _ptr(evals), C.byref(n)))
+    k = n.value
+    return est[:k], best[:k], ess[:k], evals[:k]
+
+
+def pf_measure_matrices(ctx, mats, a):
+    m = _np(np.atleast_2d(mats), np.float32)
+    out = np.zeros((m.shape[0], MOM_STRIDE), np.uint64)
+    av = _np(a, np.float32)
+    _check(load().pf_measure_matrices(ctx, _ptr(m), m.shape[0], _ptr(av), _ptr(out)))
+    return out
+
+
+def pf_pose_matrix(pose, src_dims, src_origin, tgt_origin):
+    M = np.zeros(12, np.float32)
+    a = np.zeros(3, np.float32)
+    ps, sd = _np(pose, np.float32), _np(src_dims, np.int32)
+    so, to = _np(src_origin, np.float32), _np(tgt_origin, np.float32)
+    _check(load().pf_pose_matrix(_ptr(ps), _ptr(sd), _ptr(so), _ptr(to),
+                                 _ptr(M), _ptr(a)))
+    return M, a
+
+
+def pf_philox(ctr, key):
+    out = np.zeros(4, np.uint32)
+    c, k = _np(ctr, np.uint32), _np(key, np.uint32)
+    _check(load().pf_philox(_ptr(c), _ptr(k), _ptr(out)))
+    return out
+
+
+def pf_profile_begin(ctx, capacity):
+    _check(load().pf_profile_begin(ctx, int(capacity)))
+
+
+def pf_profile_end(ctx):
+    """(summed measurement-kernel ms, number of timed iterations)."""
+    tot = C.c_double()
+    n = C.c_int32()
+    _check(load().pf_profile_end(ctx, C.byref(tot), C.byref(n)))
+    return tot.value, n.value
+
+
+def pf_kernel_launches() -> int:
+    return int(load().pf_kernel_launches())
+
+
+class Registration:
+    """One registration context.
+
+    Volumes are (Z,Y,X) uint8 numpy arrays (host) or torch tensors (host or
+    CUDA); the library copies them into its own device memory.
+    """
+
+    def __init__(self, mode, src=None, tgt=None, src_mask=None, tgt_mask=None,
+                 src_origin=(0, 0, 0), tgt_origin=(0, 0, 0), stream=None, **cfg):
+        self.cfg = make_config(mode, **cfg)
+        self.N = self.cfg.n_particles
+        self.stream = stream
+        vols = [make_volume(src, src_origin), make_volume(tgt, tgt_origin),
+                make_volume(src_mask, src_origin), make_volume(tgt_mask, tgt_origin)]
+        self.ctx = pf_register_init(*vols, self.cfg, stream)
+
+    def step(self, n_iters=1):
+        pf_step(self.ctx, n_iters)
+        return self
+
+    def estimate(self, with_score=True):
+        return pf_estimate(self.ctx, with_score)
+
+    @property
+    def iteration(self):
+        return pf_get_iteration(self.ctx)
+
+    def state(self):
+        return pf_get_state(self.ctx, self.N)
+
+    def set_state(self, poses6xN, k):
+        pf_set_state(self.ctx, poses6xN, k)
+
+    def log(self):
+        return pf_get_log(self.ctx)
+
+    def measure(self, mats, a):
+        return pf_measure_matrices(self.ctx, mats, a)
+
+    def close(self):
+        if self.ctx is not None:
+            pf_register_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _to_cuda(a, stream=None):
+    import torch
+    if isinstance(a, np.ndarray):
+        a = torch.from_numpy(np.ascontiguousarray(a))
+    if a.is_cuda:
+        return a
+    return a.cuda(non_blocking=True)
+
+
+def register_sequence(mode, src, tgt, frames, n_iters, src_origin=(0, 0, 0), tgt_origin=(0, 0, 0),
+                      src_mask=None, tgt_mask=None, interp=1, out=None, with_score=False, **cfg):
+    """Register source to target, then warp every source frame by the estimate.
+
+    The whole user-facing path: volumes (host numpy / host or pinned torch /
+    CUDA tensors) go to the device, ``n_iters`` filter iterations run, the
+    estimate comes back, and all frames are warped into the target grid.
+    ``frames`` is a sequence (or (F,Z,Y,X) array) of source-grid frames.
+    ``out``: optional list of host (pinned) uint8 tensors for the warped frames;
+    when given they are filled and returned, else CUDA tensors are returned.
+
+    Returns (pose float32[6], score or None, warped frames).
+    """
+    import torch
+    reg = Registration(mode, src=src, tgt=tgt, src_mask=src_mask, tgt_mask=tgt_mask,
+                       src_origin=src_origin, tgt_origin=tgt_origin, **cfg)
+    try:
+        reg.step(n_iters)
+        pose, score = reg.estimate(with_score)
+    finally:
+        reg.close()
+    ref = src if src is not None else src_mask
+    tgt_ref = tgt if tgt is not None else tgt_mask
+    sdims = (ref.shape[2], ref.shape[1], ref.shape[0])
+    tshape = tuple(tgt_ref.shape)
+    fin = [_to_cuda(f) for f in frames]
+    fout = [torch.empty(tshape, dtype=torch.uint8, device="cuda") for _ in fin]
+    warp_sequence(fin, sdims, src_origin, fout, (tshape[2], tshape[1], tshape[0]), tgt_origin, pose,
+                  interp)
+    if out is not None:
+        for o, f in zip(out, fout):
+            o.copy_(f, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return pose, score, out
+    return pose, score, fout

@@ -1,0 +1,620 @@
+// api.cu -- the C ABI declared in include/pfreg.h.
+//
+// Host code here only validates arguments, owns device memory, moves bytes
+// and launches kernels; every arithmetic step of the registration runs in the
+// kernels of measure.cu, filter.cu and warp.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pfreg.h"
+#include "kernels.h"
+
+using namespace pfreg;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local bool g_capturing = false;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+    } while (0)
+
+constexpr float kHalfPi = 1.57079637f;   // fp32 rounding of pi/2 (>= pi/2)
+constexpr int kMaxDim = 2048;
+constexpr size_t kMaxSourceVoxels = (size_t)1 << 28;   // 32-bit gather indices into the packed copy
+constexpr size_t kMaxTargetVoxels = (size_t)1 << 26;   // keeps n * S2 within 128 bits
+constexpr int kLogCapacity = 4096;
+
+bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+int check_volume(const pf_volume *v, const char *name) {
+    if (!v) return fail(PF_EINVAL, "%s is NULL", name);
+    if (!v->data) return fail(PF_EINVAL, "%s->data is NULL", name);
+    for (int d = 0; d < 3; ++d)
+        if (v->dims[d] < 2 || v->dims[d] > kMaxDim)
+            return fail(PF_EINVAL, "%s dims[%d] = %d outside [2, %d]", name, d, v->dims[d], kMaxDim);
+    if (!finite3(v->origin)) return fail(PF_EINVAL, "%s origin is not finite", name);
+    return PF_OK;
+}
+
+size_t nvox(const int32_t d[3]) { return (size_t)d[0] * d[1] * d[2]; }
+
+bool same_grid(const pf_volume *a, const pf_volume *b) {
+    for (int d = 0; d < 3; ++d)
+        if (a->dims[d] != b->dims[d] || a->origin[d] != b->origin[d]) return false;
+    return true;
+}
+
+int check_config(const pf_config *c) {
+    if (!c) return fail(PF_EINVAL, "cfg is NULL");
+    if (c->mode < PF_MASK_DICE || c->mode > PF_COMBINED) return fail(PF_EINVAL, "mode %d unknown", c->mode);
+    if (c->n_particles < 1 || c->n_particles > kMaxParticles)
+        return fail(PF_EINVAL, "n_particles %d outside [1, %d]", c->n_particles, kMaxParticles);
+    for (int d = 0; d < 3; ++d) {
+        if (!(c->rot_limit[d] > 0.0f && c->rot_limit[d] <= kHalfPi))
+            return fail(PF_EINVAL, "rot_limit[%d] = %g outside (0, pi/2]", d, (double)c->rot_limit[d]);
+        if (!(c->trans_limit[d] > 0.0f && c->trans_limit[d] <= 2048.0f))
+            return fail(PF_EINVAL, "trans_limit[%d] = %g outside (0, 2048]", d, (double)c->trans_limit[d]);
+    }
+    if (!(c->sigma0_frac > 0.0f && c->sigma0_frac <= 1.0f)) return fail(PF_EINVAL, "sigma0_frac outside (0, 1]");
+    if (!(c->sigma_decay > 0.0f && c->sigma_decay <= 1.0f)) return fail(PF_EINVAL, "sigma_decay outside (0, 1]");
+    if (c->gamma_log2 < 0 || c->gamma_log2 > 10) return fail(PF_EINVAL, "gamma_log2 outside [0, 10]");
+    if (!(c->min_overlap_frac >= 0.0f && c->min_overlap_frac <= 1.0f))
+        return fail(PF_EINVAL, "min_overlap_frac outside [0, 1]");
+    return PF_OK;
+}
+
+// Device copy of a volume description's bytes (into dst, n bytes).
+cudaError_t copy_in(void *dst, const pf_volume *v, size_t n, cudaStream_t s) {
+    return cudaMemcpyAsync(dst, v->data, n, v->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+}
+
+Geometry make_geometry(const int32_t sd[3], const float so[3], const int32_t td[3], const float to[3]) {
+    Geometry g;
+    for (int d = 0; d < 3; ++d) {
+        g.sd[d] = sd[d];
+        g.td[d] = td[d];
+        g.so[d] = so[d];
+        g.to[d] = to[d];
+        // a = c - o_T with c = o_S + (dims_S - 1)/2: fp64 then one rounding
+        const double c = (double)so[d] + (double)(sd[d] - 1) / 2.0;
+        g.a[d] = (float)(c - (double)to[d]);
+    }
+    return g;
+}
+
+}  // namespace
+
+namespace pfreg {
+bool capturing() { return g_capturing; }
+}  // namespace pfreg
+
+struct pf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    pf_config cfg{};
+    FilterParams P{};
+    FilterBuffers B{};
+    MeasureArgs MA{};
+    bool img = false, mask = false;
+    uint8_t *tgt_img = nullptr, *tgt_mask = nullptr;
+    uint32_t *src_quad = nullptr;
+    uint32_t *src_bits = nullptr;
+    unsigned long long *d_u64 = nullptr;   // small scratch: counts
+    double *d_score = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // timing of the measurement kernel inside the iteration graph: two event
+    // record nodes around it whose events are swapped per launch
+    cudaEvent_t ev_before = nullptr, ev_after = nullptr;
+    cudaGraphNode_t node_before = nullptr, node_after = nullptr;
+    std::vector<cudaEvent_t> prof_events;   // 2 per timed iteration
+    int prof_next = 0;
+    bool prof_default = true;               // the record nodes hold ev_before/ev_after
+    // scratch for pf_measure_matrices / the estimate's score
+    float *x_mats = nullptr;
+    unsigned long long *x_mom = nullptr;
+    int x_cap = 0;
+    std::vector<void *> allocs;
+
+    template <class T>
+    cudaError_t alloc(T **p, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+        if (e == cudaSuccess) {
+            allocs.push_back(q);
+            *p = static_cast<T *>(q);
+        }
+        return e;
+    }
+    ~pf_ctx() {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaEvent_t e : prof_events) cudaEventDestroy(e);
+        if (ev_before) cudaEventDestroy(ev_before);
+        if (ev_after) cudaEventDestroy(ev_after);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (void *p : allocs) cudaFree(p);
+        if (x_mats) cudaFree(x_mats);
+        if (x_mom) cudaFree(x_mom);
+    }
+};
+
+namespace {
+
+int ensure_scratch(pf_ctx *c, int M) {
+    if (M <= c->x_cap) return PF_OK;
+    if (c->x_mats) cudaFree(c->x_mats);
+    if (c->x_mom) cudaFree(c->x_mom);
+    c->x_mats = nullptr;
+    c->x_mom = nullptr;
+    c->x_cap = 0;
+    CU(cudaMalloc(&c->x_mats, sizeof(float) * 12 * (size_t)M));
+    CU(cudaMalloc(&c->x_mom, sizeof(unsigned long long) * kMomStride * (size_t)M));
+    c->x_cap = M;
+    return PF_OK;
+}
+
+// Measurement of M matrices already in c->x_mats into c->x_mom (zeroed here).
+int measure_scratch(pf_ctx *c, int M, const float a[3]) {
+    CU(cudaMemsetAsync(c->x_mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)M, c->stream));
+    MeasureArgs ma = c->MA;
+    ma.mats = c->x_mats;
+    ma.mom = c->x_mom;
+    ma.P = M;
+    for (int d = 0; d < 3; ++d) ma.g.a[d] = a[d];
+    CU(launch_measure(ma, c->img, c->mask, c->stream));
+    return PF_OK;
+}
+
+// One filter iteration as a CUDA graph: predict -> measure -> finalise, with
+// event-record nodes around the measurement kernel (for pf_profile_*).
+int build_graph(pf_ctx *c) {
+    CU(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    CU(cudaEventCreate(&c->ev_before));
+    CU(cudaEventCreate(&c->ev_after));
+    g_capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t es[6];
+        es[0] = launch_predict(c->P, c->B, c->cap_stream);
+        es[1] = cudaEventRecordWithFlags(c->ev_before, c->cap_stream, cudaEventRecordExternal);
+        es[2] = launch_measure(c->MA, c->img, c->mask, c->cap_stream);
+        es[3] = cudaEventRecordWithFlags(c->ev_after, c->cap_stream, cudaEventRecordExternal);
+        es[4] = launch_finalise(c->P, c->B, c->cap_stream);
+        es[5] = cudaStreamEndCapture(c->cap_stream, &c->graph);
+        for (cudaError_t x : es)
+            if (x != cudaSuccess && e == cudaSuccess) e = x;
+    }
+    g_capturing = false;
+    if (e != cudaSuccess) return fail(PF_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    size_t n = 0;
+    CU(cudaGraphGetNodes(c->graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CU(cudaGraphGetNodes(c->graph, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        CU(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        CU(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        if (ev == c->ev_before) c->node_before = nd;
+        if (ev == c->ev_after) c->node_after = nd;
+    }
+    if (!c->node_before || !c->node_after) return fail(PF_ECUDA, "timing nodes not found in the graph");
+    CU(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    return PF_OK;
+}
+
+int set_record_events(pf_ctx *c, cudaEvent_t before, cudaEvent_t after) {
+    CU(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_before, before));
+    CU(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_after, after));
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pf_config_default(pf_config *cfg) {
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->mode = PF_MASK_DICE;
+    cfg->n_particles = 256;
+    for (int d = 0; d < 3; ++d) {
+        cfg->rot_limit[d] = 0.2617994f;   // 15 degrees
+        cfg->trans_limit[d] = 8.0f;
+    }
+    cfg->sigma0_frac = 0.25f;
+    cfg->sigma_decay = 0.8f;
+    cfg->gamma_log2 = 5;
+    cfg->seed = 0;
+    cfg->min_overlap_frac = 0.01f;
+}
+
+const char *pf_last_error(void) { return g_err.c_str(); }
+
+uint64_t pf_kernel_launches(void) { return launches(); }
+
+int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, const pf_volume *src_mask,
+                     const pf_volume *tgt_mask, const pf_config *cfg, void *cuda_stream) {
+    if (!out) return fail(PF_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    const bool img = cfg->mode == PF_IMAGE_NCC || cfg->mode == PF_COMBINED;
+    const bool mask = cfg->mode != PF_IMAGE_NCC;
+    if (img) {
+        if ((rc = check_volume(src, "src")) || (rc = check_volume(tgt, "tgt"))) return rc;
+    }
+    if (mask) {
+        if ((rc = check_volume(src_mask, "src_mask")) || (rc = check_volume(tgt_mask, "tgt_mask"))) return rc;
+    }
+    if (img && mask && (!same_grid(src, src_mask) || !same_grid(tgt, tgt_mask)))
+        return fail(PF_EINVAL, "combined mode: each mask must share its image's dims and origin");
+    const pf_volume *S = img ? src : src_mask;
+    const pf_volume *T = img ? tgt : tgt_mask;
+    if (nvox(S->dims) > kMaxSourceVoxels) return fail(PF_EINVAL, "source has more than 2^28 voxels");
+    if (nvox(T->dims) > kMaxTargetVoxels) return fail(PF_EINVAL, "target has more than 2^26 voxels");
+
+    pf_ctx *c = new (std::nothrow) pf_ctx();
+    if (!c) return fail(PF_ENOMEM, "host allocation failed");
+    auto bail = [&](int code) {
+        delete c;
+        return code;
+    };
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA, "%s: %s", #call, \
+                             cudaGetErrorString(e_)));                                        \
+    } while (0)
+
+    CK(cudaGetDevice(&c->device));
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->cfg = *cfg;
+    c->img = img;
+    c->mask = mask;
+    const int N = cfg->n_particles;
+    const Geometry g = make_geometry(S->dims, S->origin, T->dims, T->origin);
+    const size_t ns = nvox(S->dims), nt = nvox(T->dims);
+
+    FilterParams &P = c->P;
+    P.g = g;
+    P.mode = cfg->mode;
+    P.N = N;
+    for (int d = 0; d < 3; ++d) {
+        P.lim[d] = cfg->rot_limit[d];
+        P.lim[3 + d] = cfg->trans_limit[d];
+    }
+    P.sigma0_frac = cfg->sigma0_frac;
+    P.sigma_decay = cfg->sigma_decay;
+    P.gamma_log2 = cfg->gamma_log2;
+    P.seed = cfg->seed;
+    P.n_min = (uint64_t)((double)cfg->min_overlap_frac * (double)nt);
+    P.b_full = 0;
+    P.log_capacity = kLogCapacity;
+
+    FilterBuffers &B = c->B;
+    CK(c->alloc(&B.poses, 6 * (size_t)N));
+    CK(c->alloc(&B.poses_meas, 6 * (size_t)N));
+    CK(c->alloc(&B.mats, 12 * (size_t)N));
+    CK(c->alloc(&B.mom, (size_t)kMomStride * N));
+    CK(c->alloc(&B.scores, (size_t)N));
+    CK(c->alloc(&B.W, (size_t)N));
+    CK(c->alloc(&B.C, (size_t)N));
+    CK(c->alloc(&B.idx, (size_t)N));
+    CK(c->alloc(&B.k, 1));
+    CK(c->alloc(&B.log, (size_t)kLogCapacity));
+    CK(c->alloc(&c->d_u64, 4));
+    CK(c->alloc(&c->d_score, 1));
+
+    if (img) {
+        uint8_t *raw = nullptr;
+        CK(c->alloc(&c->src_quad, ns));
+        CK(c->alloc(&c->tgt_img, nt));
+        const uint8_t *sp = static_cast<const uint8_t *>(src->data);
+        if (!src->is_device) {
+            CK(cudaMallocAsync(&raw, ns, c->stream));
+            CK(copy_in(raw, src, ns, c->stream));
+            sp = raw;
+        }
+        CK(launch_pack_quads(sp, S->dims, c->src_quad, c->stream));
+        if (raw) CK(cudaFreeAsync(raw, c->stream));
+        CK(copy_in(c->tgt_img, tgt, nt, c->stream));
+    }
+    if (mask) {
+        uint8_t *tmp = nullptr;
+        CK(c->alloc(&c->src_bits, (ns + 31) / 32));
+        CK(c->alloc(&c->tgt_mask, nt));
+        const uint8_t *sm = static_cast<const uint8_t *>(src_mask->data);
+        const uint8_t *tm = static_cast<const uint8_t *>(tgt_mask->data);
+        if (!src_mask->is_device || !tgt_mask->is_device) CK(c->alloc(&tmp, ns > nt ? ns : nt));
+        if (!src_mask->is_device) {
+            CK(copy_in(tmp, src_mask, ns, c->stream));
+            sm = tmp;
+        }
+        CK(launch_pack_bits(sm, (int64_t)ns, c->src_bits, c->stream));
+        if (!tgt_mask->is_device) {
+            CK(cudaStreamSynchronize(c->stream));   // tmp is reused for the target
+            CK(copy_in(tmp, tgt_mask, nt, c->stream));
+            tm = tmp;
+        }
+        CK(launch_binarise(tm, c->tgt_mask, (int64_t)nt, c->stream));
+        CK(cudaMemsetAsync(c->d_u64, 0, sizeof(unsigned long long), c->stream));
+        CK(launch_count_nonzero(c->tgt_mask, (int64_t)nt, c->d_u64, c->stream));
+        unsigned long long bfull = 0;
+        CK(cudaMemcpyAsync(&bfull, c->d_u64, sizeof bfull, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        P.b_full = bfull;
+    }
+
+    MeasureArgs &MA = c->MA;
+    MA.src_quad = c->src_quad;
+    MA.tgt_img = c->tgt_img;
+    MA.src_bits = c->src_bits;
+    MA.tgt_mask = c->tgt_mask;
+    MA.mats = B.mats;
+    MA.mom = B.mom;
+    MA.g = g;
+    MA.P = N;
+    MA.rows_per_item = rows_per_item_for(g.td[0]);
+    MA.n_rowblocks = (g.td[1] * g.td[2] + MA.rows_per_item - 1) / MA.rows_per_item;
+
+    CK(cudaMemsetAsync(B.k, 0, sizeof(int32_t), c->stream));
+    CK(cudaMemsetAsync(B.mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)N, c->stream));
+    CK(launch_init_particles(P, B, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    rc = build_graph(c);
+    if (rc) return bail(rc);
+#undef CK
+    *out = c;
+    return PF_OK;
+}
+
+int pf_step(pf_ctx *c, int32_t n_iters) {
+    if (!c) return fail(PF_EINVAL, "ctx is NULL");
+    if (n_iters < 0) return fail(PF_EINVAL, "n_iters < 0");
+    for (int32_t i = 0; i < n_iters; ++i) {
+        const int slot = c->prof_next;
+        if (2 * slot + 1 < (int)c->prof_events.size()) {
+            int rc = set_record_events(c, c->prof_events[2 * slot], c->prof_events[2 * slot + 1]);
+            if (rc) return rc;
+            c->prof_default = false;
+            ++c->prof_next;
+        } else if (!c->prof_default) {
+            int rc = set_record_events(c, c->ev_before, c->ev_after);
+            if (rc) return rc;
+            c->prof_default = true;
+        }
+        CU(cudaGraphLaunch(c->exec, c->stream));
+        count_launches(3);
+    }
+    return PF_OK;
+}
+
+int pf_profile_begin(pf_ctx *c, int32_t capacity) {
+    if (!c) return fail(PF_EINVAL, "ctx is NULL");
+    if (capacity < 0 || capacity > (1 << 16)) return fail(PF_EINVAL, "capacity outside [0, 65536]");
+    CU(cudaStreamSynchronize(c->stream));
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    c->prof_events.clear();
+    c->prof_next = 0;
+    for (int32_t i = 0; i < 2 * capacity; ++i) {
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        c->prof_events.push_back(e);
+    }
+    return PF_OK;
+}
+
+int pf_profile_end(pf_ctx *c, double *total_ms, int32_t *n_timed) {
+    if (!c || !total_ms || !n_timed) return fail(PF_EINVAL, "NULL argument");
+    CU(cudaStreamSynchronize(c->stream));
+    double tot = 0.0;
+    for (int i = 0; i < c->prof_next; ++i) {
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, c->prof_events[2 * i], c->prof_events[2 * i + 1]));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *n_timed = c->prof_next;
+    for (cudaEvent_t e : c->prof_events) cudaEventDestroy(e);
+    c->prof_events.clear();
+    c->prof_next = 0;
+    return PF_OK;
+}
+
+int pf_get_iteration(pf_ctx *c, int32_t *k_out) {
+    if (!c || !k_out) return fail(PF_EINVAL, "NULL argument");
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaMemcpy(k_out, c->B.k, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return PF_OK;
+}
+
+int pf_estimate(pf_ctx *c, float pose_out[6], double *score_out) {
+    if (!c || !pose_out) return fail(PF_EINVAL, "NULL argument");
+    int32_t k = 0;
+    int rc = pf_get_iteration(c, &k);
+    if (rc) return rc;
+    if (k <= 0) return fail(PF_ESTATE, "no iteration has run yet");
+    IterLog L;
+    CU(cudaMemcpy(&L, c->B.log + ((k - 1) % kLogCapacity), sizeof L, cudaMemcpyDeviceToHost));
+    for (int d = 0; d < 6; ++d) pose_out[d] = (float)L.est[d];
+    if (score_out) {
+        if ((rc = ensure_scratch(c, 1))) return rc;
+        float *d_pose = reinterpret_cast<float *>(c->x_mom);   // 6 floats of staging
+        CU(cudaMemcpyAsync(d_pose, pose_out, sizeof(float) * 6, cudaMemcpyHostToDevice, c->stream));
+        CU(launch_pose_matrix(d_pose, c->P.g, c->x_mats, c->stream));
+        if ((rc = measure_scratch(c, 1, c->P.g.a))) return rc;
+        CU(launch_score_one(c->P.mode, c->x_mom, c->P.b_full, c->P.n_min, c->d_score, c->stream));
+        CU(cudaMemcpyAsync(score_out, c->d_score, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return PF_OK;
+}
+
+int pf_get_state(pf_ctx *c, float *poses_measured, uint64_t *moments, double *scores, uint64_t *weights,
+                 int32_t *resample_idx, float *poses_next) {
+    if (!c) return fail(PF_EINVAL, "ctx is NULL");
+    const size_t N = (size_t)c->P.N;
+    CU(cudaStreamSynchronize(c->stream));
+    if (poses_measured) CU(cudaMemcpy(poses_measured, c->B.poses_meas, 6 * N * sizeof(float), cudaMemcpyDeviceToHost));
+    if (moments) CU(cudaMemcpy(moments, c->B.mom, kMomStride * N * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (scores) CU(cudaMemcpy(scores, c->B.scores, N * sizeof(double), cudaMemcpyDeviceToHost));
+    if (weights) CU(cudaMemcpy(weights, c->B.W, N * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    if (resample_idx) CU(cudaMemcpy(resample_idx, c->B.idx, N * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (poses_next) CU(cudaMemcpy(poses_next, c->B.poses, 6 * N * sizeof(float), cudaMemcpyDeviceToHost));
+    return PF_OK;
+}
+
+int pf_set_state(pf_ctx *c, const float *poses6xN, int32_t k) {
+    if (!c || !poses6xN) return fail(PF_EINVAL, "NULL argument");
+    if (k < 0) return fail(PF_EINVAL, "k < 0");
+    const int N = c->P.N;
+    for (int d = 0; d < 6; ++d)
+        for (int i = 0; i < N; ++i) {
+            const float v = poses6xN[(size_t)d * N + i];
+            if (!std::isfinite(v) || v > c->P.lim[d] || v < -c->P.lim[d])
+                return fail(PF_EINVAL, "pose[%d][%d] = %g outside the limits", d, i, (double)v);
+        }
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaMemcpy(c->B.poses, poses6xN, 6 * (size_t)N * sizeof(float), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(c->B.k, &k, sizeof k, cudaMemcpyHostToDevice));
+    return PF_OK;
+}
+
+int pf_get_log(pf_ctx *c, double *est, double *best, double *ess, uint64_t *evals, int32_t *count_inout) {
+    if (!c || !count_inout) return fail(PF_EINVAL, "NULL argument");
+    int32_t k = 0;
+    int rc = pf_get_iteration(c, &k);
+    if (rc) return rc;
+    int32_t n = *count_inout;
+    if (n < 0) n = 0;
+    if (n > k) n = k;
+    if (n > kLogCapacity) n = kLogCapacity;
+    std::vector<IterLog> L(kLogCapacity);
+    CU(cudaMemcpy(L.data(), c->B.log, sizeof(IterLog) * kLogCapacity, cudaMemcpyDeviceToHost));
+    for (int32_t r = 0; r < n; ++r) {
+        const IterLog &e = L[(k - n + r) % kLogCapacity];
+        if (est)
+            for (int d = 0; d < 6; ++d) est[6 * r + d] = e.est[d];
+        if (best) best[r] = e.best;
+        if (ess) ess[r] = e.ess;
+        if (evals) evals[r] = e.evals;
+    }
+    *count_inout = n;
+    return PF_OK;
+}
+
+int pf_measure_matrices(pf_ctx *c, const float *mats, int32_t M, const float a[3], uint64_t *moments_out) {
+    if (!c || !mats || !a || !moments_out) return fail(PF_EINVAL, "NULL argument");
+    if (M < 1 || M > (1 << 20)) return fail(PF_EINVAL, "M = %d outside [1, 2^20]", M);
+    for (size_t i = 0; i < 12 * (size_t)M; ++i)
+        if (!std::isfinite(mats[i])) return fail(PF_EINVAL, "matrix entry %zu is not finite", i);
+    if (!finite3(a)) return fail(PF_EINVAL, "a is not finite");
+    int rc = ensure_scratch(c, M);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(c->x_mats, mats, sizeof(float) * 12 * (size_t)M, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = measure_scratch(c, M, a))) return rc;
+    CU(cudaMemcpyAsync(moments_out, c->x_mom, sizeof(uint64_t) * kMomStride * (size_t)M,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return PF_OK;
+}
+
+int pf_register_destroy(pf_ctx *c) {
+    if (!c) return PF_OK;
+    cudaStreamSynchronize(c->stream);
+    delete c;
+    return PF_OK;
+}
+
+int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float src_origin[3],
+                   const float tgt_origin[3], float mat_out[12], float a_out[3]) {
+    if (!pose || !src_dims || !src_origin || !tgt_origin || !mat_out || !a_out)
+        return fail(PF_EINVAL, "NULL argument");
+    for (int d = 0; d < 6; ++d)
+        if (!std::isfinite(pose[d])) return fail(PF_EINVAL, "pose is not finite");
+    for (int d = 0; d < 3; ++d)
+        if (!(std::fabs(pose[d]) <= kHalfPi)) return fail(PF_EINVAL, "rotation outside [-pi/2, pi/2]");
+    const int32_t td[3] = {2, 2, 2};
+    const Geometry g = make_geometry(src_dims, src_origin, td, tgt_origin);
+    float *d = nullptr;
+    CU(cudaMalloc(&d, sizeof(float) * 18));
+    cudaError_t e = cudaMemcpy(d, pose, sizeof(float) * 6, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_pose_matrix(d, g, d + 6, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(mat_out, d + 6, sizeof(float) * 12, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(PF_ECUDA, "pf_pose_matrix: %s", cudaGetErrorString(e));
+    for (int i = 0; i < 3; ++i) a_out[i] = g.a[i];
+    return PF_OK;
+}
+
+int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    if (!ctr || !key || !out) return fail(PF_EINVAL, "NULL argument");
+    uint32_t h[6] = {ctr[0], ctr[1], ctr[2], ctr[3], key[0], key[1]};
+    uint32_t *d = nullptr;
+    CU(cudaMalloc(&d, sizeof(uint32_t) * 10));
+    cudaError_t e = cudaMemcpy(d, h, sizeof h, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox(d, d + 6, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d + 6, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(PF_ECUDA, "pf_philox: %s", cudaGetErrorString(e));
+    return PF_OK;
+}
+
+int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32_t src_dims[3],
+                  const float src_origin[3], uint8_t *const *frames_out, const int32_t tgt_dims[3],
+                  const float tgt_origin[3], const float pose[6], int32_t interp, void *cuda_stream) {
+    if (!frames_in || !frames_out || !src_dims || !src_origin || !tgt_dims || !tgt_origin || !pose)
+        return fail(PF_EINVAL, "NULL argument");
+    if (n_frames < 0) return fail(PF_EINVAL, "n_frames < 0");
+    if (interp != 0 && interp != 1) return fail(PF_EINVAL, "interp must be 0 or 1");
+    for (int d = 0; d < 3; ++d) {
+        if (src_dims[d] < 2 || src_dims[d] > kMaxDim || tgt_dims[d] < 1 || tgt_dims[d] > kMaxDim)
+            return fail(PF_EINVAL, "dims out of range");
+    }
+    if (!finite3(src_origin) || !finite3(tgt_origin)) return fail(PF_EINVAL, "origin is not finite");
+    for (int d = 0; d < 6; ++d)
+        if (!std::isfinite(pose[d])) return fail(PF_EINVAL, "pose is not finite");
+    for (int d = 0; d < 3; ++d)
+        if (!(std::fabs(pose[d]) <= kHalfPi)) return fail(PF_EINVAL, "rotation outside [-pi/2, pi/2]");
+    for (int32_t f = 0; f < n_frames; ++f)
+        if (!frames_in[f] || !frames_out[f]) return fail(PF_EINVAL, "frame %d pointer is NULL", f);
+    const Geometry g = make_geometry(src_dims, src_origin, tgt_dims, tgt_origin);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    for (int32_t f0 = 0; f0 < n_frames; f0 += WarpFrames::kMax) {
+        WarpFrames wf;
+        const int n = (n_frames - f0) < WarpFrames::kMax ? (n_frames - f0) : WarpFrames::kMax;
+        for (int j = 0; j < WarpFrames::kMax; ++j) {
+            wf.in[j] = j < n ? frames_in[f0 + j] : nullptr;
+            wf.out[j] = j < n ? frames_out[f0 + j] : nullptr;
+        }
+        CU(launch_warp(wf, n, pose, g, interp, s));
+    }
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// device.cuh -- device building blocks of the registration path (sm_103a).
+//
+// Every float operation on the parity path is an explicit round-to-nearest
+// intrinsic (__fadd_rn, __fmul_rn, __dadd_rn, ...), which nvcc never fuses
+// into an FMA, so the bits are fixed by the order written here.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pfreg {
+
+// fp64 / fp32 round-to-nearest operations (never contracted into an FMA).
+#define PF_HD __device__ __forceinline__
+PF_HD double d_mul(double a, double b) { return __dmul_rn(a, b); }
+PF_HD double d_add(double a, double b) { return __dadd_rn(a, b); }
+PF_HD double d_sub(double a, double b) { return __dsub_rn(a, b); }
+PF_HD double d_div(double a, double b) { return __ddiv_rn(a, b); }
+PF_HD float d2f(double a) { return __double2float_rn(a); }
+PF_HD double u64_to_f64(unsigned long long v) { return __ull2double_rn(v); }
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplications by the Philox constants, XOR of the high halves with the
+// other words and the round key, word permutation; the key advances by the
+// two Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct u32x4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) { return __umulhi(a, b); }
+
+__device__ __forceinline__ u32x4 philox10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = mulhi32(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = mulhi32(0xCD9E8D57u, c.z);
+        c = u32x4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Philox stream ids (counter word 2): one per use of randomness.
+enum : uint32_t { kStreamInit = 0, kStreamPerturb = 1, kStreamResample = 2 };
+
+__device__ __forceinline__ u32x4 philox_seeded(uint64_t seed, uint32_t w0, uint32_t w1,
+                                               uint32_t w2, uint32_t w3) {
+    return philox10(u32x4{w0, w1, w2, w3}, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+// Uniform in [0,1) from the top 24 bits of a draw (exact in fp32).
+__device__ __forceinline__ float unit24(uint32_t u) {
+    return __fmul_rn((float)(u >> 8), 5.9604644775390625e-08f);  // 2^-24
+}
+
+// ---------------------------------------------------------------------------
+// fp64 sin / cos, |x| <= pi/2: Taylor series, term k = term k-1 * (-x^2) /
+// ((2k)(2k+1)) (sin) or / ((2k-1)(2k)) (cos), 14 terms, summed smallest first.
+// Written out so host and device agree bit for bit without either libm.
+// ---------------------------------------------------------------------------
+PF_HD double taylor_sin(double x) {
+    const double mx2 = -d_mul(x, x);
+    double t[14];
+    t[0] = x;
+    for (int k = 1; k < 14; ++k) t[k] = d_div(d_mul(t[k - 1], mx2), (double)((2 * k) * (2 * k + 1)));
+    double s = 0.0;
+    for (int k = 13; k >= 0; --k) s = d_add(s, t[k]);
+    return s;
+}
+
+PF_HD double taylor_cos(double x) {
+    const double mx2 = -d_mul(x, x);
+    double t[14];
+    t[0] = 1.0;
+    for (int k = 1; k < 14; ++k) t[k] = d_div(d_mul(t[k - 1], mx2), (double)((2 * k - 1) * (2 * k)));
+    double s = 0.0;
+    for (int k = 13; k >= 0; --k) s = d_add(s, t[k]);
+    return s;
+}
+
+// 3x3 product C = A B, each entry accumulated from 0 in k order (fp64).
+PF_HD void mat3_mul(const double A[9], const double B[9], double C[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc = d_add(acc, d_mul(A[3 * i + k], B[3 * k + j]));
+            C[3 * i + j] = acc;
+        }
+}
+
+// Eq. 3: pose -> 3x4 matrix [r00 r01 r02 b0 | r10 r11 r12 b1 | r20 r21 r22 b2]
+// with R = Rz(rz) Rx(rx) Ry(ry) (fp64, rounded once to fp32) and
+// b = (c + t) - o_S, c = o_S + (dims_S - 1)/2.  (a = c - o_T is per geometry.)
+struct Geometry {
+    int32_t sd[3];      // source dims
+    int32_t td[3];      // target dims
+    float so[3];        // source origin
+    float to[3];        // target origin
+    float a[3];         // c - o_T (fp32)
+};
+
+// Source-grid centre c_d and a_d = c_d - o_T,d.
+PF_HD double grid_centre(const Geometry &g, int d) {
+    return d_add((double)g.so[d], d_div((double)(g.sd[d] - 1), 2.0));
+}
+
+// Per-particle pose -> matrix on the device: sin/cos of the three angles
+// (taylor_sin / taylor_cos), R = Rz Rx Ry, b = (c + t) - o_S.
+
+PF_HD void matrix_from_sincos(const float pose[6], double sa, double ca, double sb, double cb,
+                               double sg, double cg, const Geometry &g, float M[12]) {
+    const double Rx[9] = {1.0, 0.0, 0.0, 0.0, ca, -sa, 0.0, sa, ca};
+    const double Ry[9] = {cb, 0.0, sb, 0.0, 1.0, 0.0, -sb, 0.0, cb};
+    const double Rz[9] = {cg, -sg, 0.0, sg, cg, 0.0, 0.0, 0.0, 1.0};
+    double XY[9], R[9];
+    mat3_mul(Rx, Ry, XY);
+    mat3_mul(Rz, XY, R);
+    for (int i = 0; i < 3; ++i) {
+        const double b = d_sub(d_add(grid_centre(g, i), (double)pose[3 + i]), (double)g.so[i]);
+        M[4 * i + 0] = d2f(R[3 * i + 0]);
+        M[4 * i + 1] = d2f(R[3 * i + 1]);
+        M[4 * i + 2] = d2f(R[3 * i + 2]);
+        M[4 * i + 3] = d2f(b);
+    }
+}
+
+PF_HD void pose_to_matrix(const float pose[6], const Geometry &g, float M[12]) {
+    matrix_from_sincos(pose, taylor_sin((double)pose[0]), taylor_cos((double)pose[0]),
+                       taylor_sin((double)pose[1]), taylor_cos((double)pose[1]),
+                       taylor_sin((double)pose[2]), taylor_cos((double)pose[2]), g, M);
+}
+
+// Per-row hoisted part of the coordinate: K_i = (r_i1*dy + r_i2*dz) + b_i.
+// Then q_i = r_i0*dx + K_i with dx = x - a0 (fixed fp32 order, no FMA).
+__device__ __forceinline__ float row_K(float r1, float r2, float b, float dy, float dz) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(r1, dy), __fmul_rn(r2, dz)), b);
+}
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float f) {
+    return __fadd_rn(a, __fmul_rn(f, __fsub_rn(b, a)));
+}
+
+// Conservative x-range of one target row whose samples can fall inside
+// [lo_d, hi_d] on every axis d: q_d(x) = r_d0 (x - a0) + K_d.  q_d is monotone
+// in x (rounding is monotone), so the exact inside set of a row is an
+// interval; this range contains it with a margin (delta in q, 1 voxel in x),
+// and every voxel in it is still tested with the exact predicate.
+__device__ __forceinline__ void row_interval(const float r0[3], const float K[3], float a0,
+                                             const float lo[3], const float hi[3], int X,
+                                             int &x_begin, int &x_end) {
+    const float delta = 0.0625f;
+    float xmin = -1.0f, xmax = (float)X;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float L = lo[d] - delta - K[d], H = hi[d] + delta - K[d];
+        if (fabsf(r0[d]) < 1e-20f) {
+            if (L > 0.0f || H < 0.0f) { xmin = 1.0f; xmax = 0.0f; }
+        } else {
+            float u = L / r0[d] + a0, v = H / r0[d] + a0;
+            if (u > v) { const float t = u; u = v; v = t; }
+            xmin = fmaxf(xmin, u);
+            xmax = fminf(xmax, v);
+        }
+    }
+    if (!(xmin <= xmax)) { x_begin = 0; x_end = 0; return; }
+    xmin = fmaxf(xmin, -1.0f);
+    xmax = fminf(xmax, (float)X);
+    x_begin = max(0, (int)floorf(xmin) - 1);
+    x_end = min(X, (int)ceilf(xmax) + 2);
+    if (x_end < x_begin) x_end = x_begin;
+}
+
+}  // namespace pfreg

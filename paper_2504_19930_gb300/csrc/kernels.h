@@ -1,0 +1,93 @@
+// kernels.h -- launch interfaces between the C-ABI host code and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace pfreg {
+
+constexpr int kMomStride = 12;   // n S1 S2lo S2hi ST T1 T2 0 | n_nn A B C
+constexpr int kMaxParticles = 65536;
+
+// Measurement of P matrices (Fig. 1 "measurement"): moments accumulated
+// (atomically, integer) into mom[P][12], which the caller zeroes first.
+struct MeasureArgs {
+    const uint32_t *src_quad;   // image modes: quad-packed source (launch_pack_quads)
+    const uint8_t *tgt_img;
+    const uint32_t *src_bits;   // mask modes: source mask, 1 bit per voxel
+    const uint8_t *tgt_mask;    // mask modes: target mask bytes (0/1)
+    const float *mats;          // [P][12]
+    unsigned long long *mom;    // [P][12]
+    Geometry g;
+    int P;
+    int rows_per_item;          // target rows per work item
+    int n_rowblocks;            // ceil(rows / rows_per_item)
+};
+
+// Filter parameters shared by the per-iteration kernels.
+struct FilterParams {
+    Geometry g;
+    int mode;
+    int N;
+    float lim[6];
+    float sigma0_frac, sigma_decay;
+    int gamma_log2;
+    uint64_t seed;
+    uint64_t n_min;             // overlap threshold (voxels)
+    uint64_t b_full;            // |T| of the target mask (Dice denominator)
+    int log_capacity;
+};
+
+struct IterLog {
+    double est[6];
+    double best;
+    double ess;
+    unsigned long long evals;   // particle-voxel evaluations visited (sum of overlap counts)
+    int32_t best_idx;
+    int32_t k;
+};
+
+struct FilterBuffers {
+    float *poses;               // [6][N] current cloud (resampled)
+    float *poses_meas;          // [6][N] cloud measured in the last iteration
+    float *mats;                // [N][12]
+    unsigned long long *mom;    // [N][12]
+    double *scores;             // [N]
+    unsigned long long *W;      // [N]
+    unsigned long long *C;      // [N] inclusive scan of W
+    int32_t *idx;               // [N]
+    int32_t *k;                 // iteration counter (device)
+    IterLog *log;               // [log_capacity]
+};
+
+cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream_t s);
+cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_t *quad, cudaStream_t s);
+int rows_per_item_for(int target_x);
+cudaError_t launch_init_particles(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
+cudaError_t launch_predict(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
+cudaError_t launch_finalise(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
+cudaError_t launch_pack_bits(const uint8_t *mask, int64_t nvox, uint32_t *bits, cudaStream_t s);
+cudaError_t launch_count_nonzero(const uint8_t *v, int64_t n, unsigned long long *out, cudaStream_t s);
+cudaError_t launch_binarise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t s);
+cudaError_t launch_pose_matrix(const float *pose, Geometry g, float *mat_out, cudaStream_t s);
+cudaError_t launch_score_one(int mode, const unsigned long long *mom, unsigned long long b_full,
+                             unsigned long long n_min, double *out, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *ctr_key, uint32_t *out, cudaStream_t s);
+
+struct WarpFrames {
+    static constexpr int kMax = 64;
+    const uint8_t *in[kMax];
+    uint8_t *out[kMax];
+};
+cudaError_t launch_warp(const WarpFrames &f, int n, const float pose[6], Geometry g, int interp,
+                        cudaStream_t s);
+
+// Process-wide count of kernel launches issued by this library (launches
+// recorded while a CUDA graph is being captured are not counted; each graph
+// replay counts its kernels instead).
+bool capturing();
+void count_launches(uint64_t n);
+uint64_t launches();
+
+}  // namespace pfreg

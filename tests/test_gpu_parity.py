@@ -128,7 +128,7 @@ def test_integer_maps_exact(pk, mode):
         got = reg.measure(mats, np.zeros(3, np.float32))
     for i, (P, b) in enumerate(cases):
         want = bf.integer_map_counts(src, tgt, P, b, image=(mode == "image_ncc"))
-        g = got[i, 6:10] if mode == "mask_dice" else got[i, 0:6]
+        g = got[i, 8:12] if mode == "mask_dice" else got[i, 0:7]
         assert g.tolist() == want.tolist(), (i, P, b)
 
 
@@ -155,13 +155,13 @@ def test_measure_random_poses_bit_exact(pk, orc, mode, sdims, tdims):
     tgtm = (tgt != 0).astype(np.uint8) if mode == "combined" else tgt
     if mode in ("mask_dice", "combined"):
         want = orc.measure_mask(srcm, tgtm, mats, a)
-        assert np.array_equal(got[:, 6:10], want)
+        assert np.array_equal(got[:, 8:12], want)
     if mode in ("image_ncc", "combined"):
         want = orc.measure_image(src, tgt, mats, a)
-        assert np.array_equal(got[:, 0:6], want)
+        assert np.array_equal(got[:, 0:7], want)
         f64 = orc.ncc2_f64(src, tgt, mats, a)
         for i in range(len(mats)):
-            s = orc.ncc2_from_moments(got[i, 0:6])
+            s = orc.ncc2_from_moments(got[i, 0:7])
             assert abs(s - f64[i]) <= NCC_RTOL * f64[i], (i, s, f64[i])
 
 
@@ -176,7 +176,7 @@ def test_measure_degenerate_cases(pk, orc):
     with _measure_ctx(pk, "image_ncc", src, src) as reg:
         got = reg.measure(np.stack([far[0], ident]), a)
     assert np.all(got[0] == 0)
-    assert got[1, 0] == src.size and got[1, 1] == 1024 * int(src.astype(np.int64).sum())
+    assert got[1, 0] == src.size and got[1, 1] == 32768 * int(src.astype(np.int64).sum())
     tiny = pfsynth.random_image(6, (2, 2, 2))
     tgt = pfsynth.random_image(7, (5, 4, 3))
     rng = np.random.default_rng(9)
@@ -184,7 +184,7 @@ def test_measure_degenerate_cases(pk, orc):
     mats, a = orc.pose_matrices(poses.T, (2, 2, 2), np.zeros(3, np.float32), np.array([-1.5, -1, -0.5], np.float32))
     with _measure_ctx(pk, "image_ncc", tiny, tgt) as reg:
         got = reg.measure(mats, a)
-    assert np.array_equal(got[:, 0:6], orc.measure_image(tiny, tgt, mats, a))
+    assert np.array_equal(got[:, 0:7], orc.measure_image(tiny, tgt, mats, a))
 
 
 # ---------------------------------------------------------- whole filter
@@ -250,7 +250,7 @@ def test_config0_full_registration_bit_exact(pk, orc):
         assert score == want
         _, best, ess, evals = reg.log()
         assert len(best) == c["n_iters"] and best[-1] > 0.9 and np.all(ess > 0)
-        assert evals[-1] == int(ref["tr_mom"][-1][:, 6].sum())
+        assert evals[-1] == int(ref["tr_mom"][-1][:, 8].sum())
 
 
 def test_config1_full_size_sampled(pk, orc):
@@ -275,7 +275,7 @@ def test_config1_full_size_sampled(pk, orc):
                 assert np.array_equal(x, orc.perturb(prev_next, seed, k, orc.sigma(0.25, 0.8, k, lim), lim))
             sample = np.random.default_rng(k).choice(N, 3, replace=False)
             mats, a = orc.pose_matrices(x[:, sample], pair.src_dims, pair.src_origin, pair.tgt_origin)
-            assert np.array_equal(st["moments"][sample, 0:6], orc.measure_image(pair.src, pair.tgt, mats, a))
+            assert np.array_equal(st["moments"][sample, 0:7], orc.measure_image(pair.src, pair.tgt, mats, a))
             f64 = orc.ncc2_f64(pair.src, pair.tgt, mats, a)
             for j, i in enumerate(sample):
                 assert abs(st["scores"][i] - f64[j]) <= NCC_RTOL * f64[j]
