@@ -536,7 +536,13 @@ int pf_measure_matrices(pf_ctx *c, const float *mats, int32_t M, const float a[3
     if (!finite3(a)) return fail(PF_EINVAL, "a is not finite");
     int rc = ensure_scratch(c, M);
     if (rc) return rc;
-    CU(cudaMemcpyAsync(c->x_mats, mats, sizeof(float) * 12 * (size_t)M, cudaMemcpyHostToDevice, c->stream));
+    // The measurement kernel relies on no offset b being -0 (then no sample
+    // coordinate is -0); b + 0 turns -0 into +0 and leaves every other value.
+    std::vector<float> m(mats, mats + 12 * (size_t)M);
+    for (size_t i = 0; i < (size_t)M; ++i)
+        for (int r = 0; r < 3; ++r) m[12 * i + 4 * r + 3] += 0.0f;
+    CU(cudaMemcpyAsync(c->x_mats, m.data(), sizeof(float) * 12 * (size_t)M, cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));   // m is released on return
     if ((rc = measure_scratch(c, M, a))) return rc;
     CU(cudaMemcpyAsync(moments_out, c->x_mom, sizeof(uint64_t) * kMomStride * (size_t)M,
                        cudaMemcpyDeviceToHost, c->stream));

@@ -51,9 +51,48 @@ __device__ __forceinline__ uint32_t int_of(float v) {
     return __float_as_uint(__fadd_rn(v, kTwo23)) - kTwo23Bits;
 }
 
+// Packed fp32 pairs (Blackwell f32x2): two independent IEEE round-to-nearest
+// adds or subtracts per instruction, lane-wise identical to __fadd_rn /
+// __fsub_rn.  They are used only where no product feeds them: ptxas fuses a
+// single-use packed multiply into a following packed add (an FMA, one rounding
+// instead of two) even under .rn, so every product and every add that consumes
+// a product stays a scalar __fmul_rn / __fadd_rn, which are never contracted.
+struct f2 {
+    float x, y;
+};
+__device__ __forceinline__ f2 pair(float a, float b) { return f2{a, b}; }
+__device__ __forceinline__ f2 splat(float a) { return f2{a, a}; }
+#define PF_F32X2(NAME, OP)                                                                         \
+    __device__ __forceinline__ f2 NAME(f2 a, f2 b) {                                               \
+        f2 d;                                                                                      \
+        asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t" OP        \
+            ".rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0,%1}, rd;}"                                       \
+            : "=f"(d.x), "=f"(d.y)                                                                 \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                             \
+        return d;                                                                                  \
+    }
+PF_F32X2(add2, "add")
+PF_F32X2(sub2, "sub")
+#undef PF_F32X2
+
+// a + f*(b - a) for two voxels: packed difference, scalar product and sum.
+__device__ __forceinline__ f2 lerp2(f2 a, f2 b, f2 f) {
+    const f2 d = sub2(b, a);
+    return f2{__fadd_rn(a.x, __fmul_rn(f.x, d.x)), __fadd_rn(a.y, __fmul_rn(f.y, d.y))};
+}
+// the same with biased end points A = 2^23 + a, B = 2^23 + b.
+__device__ __forceinline__ f2 lerp2_biased(f2 A, f2 B, f2 f) {
+    const f2 base = sub2(A, splat(kTwo23)), d = sub2(B, A);
+    return f2{__fadd_rn(base.x, __fmul_rn(f.x, d.x)), __fadd_rn(base.y, __fmul_rn(f.y, d.y))};
+}
+// q = r*dx + K for two voxels (scalar: a product feeds the add).
+__device__ __forceinline__ f2 coord2(float r, f2 dx, float K) {
+    return f2{__fadd_rn(__fmul_rn(r, dx.x), K), __fadd_rn(__fmul_rn(r, dx.y), K)};
+}
+
 struct ImgAcc {
-    uint32_t n = 0, S1 = 0, T1 = 0, T2 = 0;
-    unsigned long long S2 = 0, ST = 0;
+    uint32_t n = 0, T1 = 0, T2 = 0, S1row = 0;
+    unsigned long long S1 = 0, S2 = 0, ST = 0;
 };
 struct MaskAcc {
     uint32_t n = 0, A = 0, B = 0, C = 0;
@@ -61,63 +100,107 @@ struct MaskAcc {
 
 struct Row {
     float K0, K1, K2;
-    size_t trow;
+    uint32_t trow;      // r * TX (< 2^26)
 };
 
-template <bool IMG, bool MASK>
-__device__ __forceinline__ void eval_voxel(const MeasureArgs &a, const uint32_t *__restrict__ bits,
-                                           const float r0x, const float r0y, const float r0z,
-                                           const Row &row, int x, float xf, ImgAcc &ia, MaskAcc &ma) {
+// Inside test of the trilinear sample, 0 <= q <= D-1 in fp32, as an unsigned
+// compare of the bit patterns: q is never -0 (its offset b is never -0, so a
+// sum r*dx + K cannot round to -0), non-negative floats order like their bits,
+// and negative values and NaNs have bit patterns above any bound.
+__device__ __forceinline__ bool inside_tri(float qx, float qy, float qz, uint32_t bx, uint32_t by, uint32_t bz) {
+    return (__float_as_uint(qx) <= bx) & (__float_as_uint(qy) <= by) & (__float_as_uint(qz) <= bz);
+}
+
+template <bool MASK>
+__device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t *__restrict__ bits, float qx,
+                                           float qy, float qz, uint32_t tidx, bool valid, MaskAcc &ma) {
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
     const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
-    const float dx = __fsub_rn(xf, a.g.a[0]);
-    const float qx = __fadd_rn(__fmul_rn(r0x, dx), row.K0);
-    const float qy = __fadd_rn(__fmul_rn(r0y, dx), row.K1);
-    const float qz = __fadd_rn(__fmul_rn(r0z, dx), row.K2);
+    const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
+    const bool in = valid & (hx >= 0.0f) & (hx < (float)SX) & (hy >= 0.0f) & (hy < (float)SY) & (hz >= 0.0f) &
+                    (hz < (float)SZ);
+    if (in) {
+        const uint32_t si = int_of(floorf(hx)) + (uint32_t)SX * int_of(floorf(hy)) + SXY * int_of(floorf(hz));
+        const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
+        const uint32_t tb = __ldg(a.tgt_mask + tidx);
+        ma.n += 1;
+        ma.A += sb;
+        ma.B += tb;
+        ma.C += sb & tb;
+    }
+}
+
+// Voxels x and x + 32 of one row (the second only when valid1).
+template <bool IMG, bool MASK>
+__device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *__restrict__ bits, const float r0x,
+                                          const float r0y, const float r0z, const Row &row, int x, float xf,
+                                          bool valid1, ImgAcc &ia, MaskAcc &ma) {
+    const f2 dx = sub2(pair(xf, __fadd_rn(xf, 32.0f)), splat(a.g.a[0]));
+    const f2 qx = coord2(r0x, dx, row.K0);
+    const f2 qy = coord2(r0y, dx, row.K1);
+    const f2 qz = coord2(r0z, dx, row.K2);
+    const uint32_t t0i = row.trow + (uint32_t)x;
+    const uint32_t t1i = valid1 ? t0i + 32u : t0i;
     if (IMG) {
-        const float Dm1x = (float)(SX - 1), Dm1y = (float)(SY - 1), Dm1z = (float)(SZ - 1);
-        const bool in = (qx >= 0.0f) & (qx <= Dm1x) & (qy >= 0.0f) & (qy <= Dm1y) & (qz >= 0.0f) &
-                        (qz <= Dm1z);
-        // base corner min(floor q, D-2); clamped into the grid for voxels outside
-        const float fx0 = fminf(fmaxf(floorf(qx), 0.0f), (float)(SX - 2));
-        const float fy0 = fminf(fmaxf(floorf(qy), 0.0f), (float)(SY - 2));
-        const float fz0 = fminf(fmaxf(floorf(qz), 0.0f), (float)(SZ - 2));
-        const float fx = __fsub_rn(qx, fx0), fy = __fsub_rn(qy, fy0), fz = __fsub_rn(qz, fz0);
-        const uint32_t idx = int_of(fx0) + (uint32_t)SX * int_of(fy0) + SXY * int_of(fz0);
-        const uint32_t w0 = __ldg(a.src_quad + idx);
-        const uint32_t w1 = __ldg(a.src_quad + idx + SXY);
-        const float c00 = lerp_biased(byte_biased(w0, 0), byte_biased(w0, 1), fx);
-        const float c10 = lerp_biased(byte_biased(w0, 2), byte_biased(w0, 3), fx);
-        const float c01 = lerp_biased(byte_biased(w1, 0), byte_biased(w1, 1), fx);
-        const float c11 = lerp_biased(byte_biased(w1, 2), byte_biased(w1, 3), fx);
-        const float c0 = lerp_rn(c00, c10, fy), c1 = lerp_rn(c01, c11, fy);
-        const float s = lerp_rn(c0, c1, fz);
-        const uint32_t sq = __float_as_uint(__fadd_rn(s, 256.0f)) - k256Bits;   // rint(2^15 s)
-        const uint32_t t = __ldg(a.tgt_img + row.trow + x);
-        if (in) {
+        const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
+        const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
+        const uint32_t bx = __float_as_uint((float)(SX - 1)), by = __float_as_uint((float)(SY - 1)),
+                       bz = __float_as_uint((float)(SZ - 1));
+        const bool in0 = inside_tri(qx.x, qy.x, qz.x, bx, by, bz);
+        const bool in1 = valid1 & inside_tri(qx.y, qy.y, qz.y, bx, by, bz);
+        // base corner min(floor q, D-2) and fraction q - base
+        const float Dm2x = (float)(SX - 2), Dm2y = (float)(SY - 2), Dm2z = (float)(SZ - 2);
+        const f2 flx = pair(fminf(floorf(qx.x), Dm2x), fminf(floorf(qx.y), Dm2x));
+        const f2 fly = pair(fminf(floorf(qy.x), Dm2y), fminf(floorf(qy.y), Dm2y));
+        const f2 flz = pair(fminf(floorf(qz.x), Dm2z), fminf(floorf(qz.y), Dm2z));
+        const f2 fx = sub2(qx, flx), fy = sub2(qy, fly), fz = sub2(qz, flz);
+        const f2 bxv = add2(flx, splat(kTwo23)), byv = add2(fly, splat(kTwo23)), bzv = add2(flz, splat(kTwo23));
+        uint32_t i0 = (__float_as_uint(bxv.x) - kTwo23Bits) + (uint32_t)SX * (__float_as_uint(byv.x) - kTwo23Bits) +
+                      SXY * (__float_as_uint(bzv.x) - kTwo23Bits);
+        uint32_t i1 = (__float_as_uint(bxv.y) - kTwo23Bits) + (uint32_t)SX * (__float_as_uint(byv.y) - kTwo23Bits) +
+                      SXY * (__float_as_uint(bzv.y) - kTwo23Bits);
+        i0 = in0 ? i0 : 0u;   // outside voxels read a valid word and are not accumulated
+        i1 = in1 ? i1 : 0u;
+        const uint32_t w00 = __ldg(a.src_quad + i0), w01 = __ldg(a.src_quad + i0 + SXY);
+        const uint32_t w10 = __ldg(a.src_quad + i1), w11 = __ldg(a.src_quad + i1 + SXY);
+        const uint32_t t0 = __ldg(a.tgt_img + t0i), t1 = __ldg(a.tgt_img + t1i);
+        const f2 c00 = lerp2_biased(pair(byte_biased(w00, 0), byte_biased(w10, 0)),
+                                    pair(byte_biased(w00, 1), byte_biased(w10, 1)), fx);
+        const f2 c10 = lerp2_biased(pair(byte_biased(w00, 2), byte_biased(w10, 2)),
+                                    pair(byte_biased(w00, 3), byte_biased(w10, 3)), fx);
+        const f2 c01 = lerp2_biased(pair(byte_biased(w01, 0), byte_biased(w11, 0)),
+                                    pair(byte_biased(w01, 1), byte_biased(w11, 1)), fx);
+        const f2 c11 = lerp2_biased(pair(byte_biased(w01, 2), byte_biased(w11, 2)),
+                                    pair(byte_biased(w01, 3), byte_biased(w11, 3)), fx);
+        const f2 c0 = lerp2(c00, c10, fy), c1 = lerp2(c01, c11, fy);
+        const f2 s = add2(lerp2(c0, c1, fz), splat(256.0f));
+        const uint32_t sq0 = __float_as_uint(s.x) - k256Bits;   // rint(2^15 s)
+        const uint32_t sq1 = __float_as_uint(s.y) - k256Bits;
+        if (in0) {
             ia.n += 1;
-            ia.S1 += sq;
-            ia.S2 += (unsigned long long)sq * sq;
-            ia.ST += (unsigned long long)sq * t;
-            ia.T1 += t;
-            ia.T2 += t * t;
+            ia.S1row += sq0;
+            ia.S2 += (unsigned long long)sq0 * sq0;
+            ia.ST += (unsigned long long)sq0 * t0;
+            ia.T1 += t0;
+            ia.T2 += t0 * t0;
+        }
+        if (in1) {
+            ia.n += 1;
+            ia.S1row += sq1;
+            ia.S2 += (unsigned long long)sq1 * sq1;
+            ia.ST += (unsigned long long)sq1 * t1;
+            ia.T1 += t1;
+            ia.T2 += t1 * t1;
         }
     }
     if (MASK) {
-        const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
-        const bool in = (hx >= 0.0f) & (hx < (float)SX) & (hy >= 0.0f) & (hy < (float)SY) & (hz >= 0.0f) &
-                        (hz < (float)SZ);
-        if (in) {
-            const uint32_t si = int_of(floorf(hx)) + (uint32_t)SX * int_of(floorf(hy)) + SXY * int_of(floorf(hz));
-            const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
-            const uint32_t tb = __ldg(a.tgt_mask + row.trow + x);
-            ma.n += 1;
-            ma.A += sb;
-            ma.B += tb;
-            ma.C += sb & tb;
-        }
+        mask_voxel<MASK>(a, bits, qx.x, qy.x, qz.x, t0i, true, ma);
+        mask_voxel<MASK>(a, bits, qx.y, qy.y, qz.y, t1i, valid1, ma);
     }
 }
+
+constexpr int kRowsPerWarp = 32;
+constexpr int kRowsPerItem = kRowsPerWarp * kWarps;
 
 template <bool IMG, bool MASK, bool MASK_SMEM>
 __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
@@ -142,10 +225,11 @@ __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
     hi[1] = MASK ? (float)SY - 0.5f : (float)(SY - 1);
     hi[2] = MASK ? (float)SZ - 0.5f : (float)(SZ - 1);
 
-    const long long items = (long long)a.P * a.n_rowblocks;
+    const int n_rowblocks = (rows + kRowsPerItem - 1) / kRowsPerItem;
+    const long long items = (long long)a.P * n_rowblocks;
     for (long long item = blockIdx.x; item < items; item += gridDim.x) {
-        const int p = (int)(item / a.n_rowblocks);
-        const int rb = (int)(item - (long long)p * a.n_rowblocks);
+        const int p = (int)(item / n_rowblocks);
+        const int rb = (int)(item - (long long)p * n_rowblocks);
         const float *Mp = a.mats + 12 * (size_t)p;
         float M[12];
 #pragma unroll
@@ -154,26 +238,39 @@ __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
         ImgAcc ia;
         MaskAcc ma;
 
-        const int row_end = min(rows, (rb + 1) * a.rows_per_item);
-        for (int r = rb * a.rows_per_item + warp; r < row_end; r += kWarps) {
-            const int y = r % TY, z = r / TY;
+        // lane l prepares row (first + l): hoisted K and its clipped x-range
+        const int first = rb * kRowsPerItem + warp * kRowsPerWarp;
+        const int my_row = first + lane;
+        float myK0 = 0.0f, myK1 = 0.0f, myK2 = 0.0f;
+        int my_xb = 0, my_xe = 0;
+        if (my_row < rows) {
+            const int y = my_row % TY, z = my_row / TY;
             const float dy = __fsub_rn((float)y, a.g.a[1]);
             const float dz = __fsub_rn((float)z, a.g.a[2]);
+            myK0 = row_K(M[1], M[2], M[3], dy, dz);
+            myK1 = row_K(M[5], M[6], M[7], dy, dz);
+            myK2 = row_K(M[9], M[10], M[11], dy, dz);
+            const float K[3] = {myK0, myK1, myK2};
+            row_interval(r0, K, a.g.a[0], lo, hi, TX, my_xb, my_xe);
+        }
+        const int nrows = min(kRowsPerWarp, rows - first);
+        for (int j = 0; j < nrows; ++j) {
+            const int xb = __shfl_sync(0xffffffffu, my_xb, j);
+            const int xe = __shfl_sync(0xffffffffu, my_xe, j);
+            if (xb >= xe) continue;                       // warp-uniform
             Row row;
-            row.K0 = row_K(M[1], M[2], M[3], dy, dz);
-            row.K1 = row_K(M[5], M[6], M[7], dy, dz);
-            row.K2 = row_K(M[9], M[10], M[11], dy, dz);
-            row.trow = (size_t)r * TX;
-            const float K[3] = {row.K0, row.K1, row.K2};
-            int xb, xe;
-            row_interval(r0, K, a.g.a[0], lo, hi, TX, xb, xe);
+            row.K0 = __shfl_sync(0xffffffffu, myK0, j);
+            row.K1 = __shfl_sync(0xffffffffu, myK1, j);
+            row.K2 = __shfl_sync(0xffffffffu, myK2, j);
+            row.trow = (uint32_t)(first + j) * (uint32_t)TX;
             int x = xb + lane;
             float xf = (float)x;
-            for (; x + 32 < xe; x += 64, xf += 64.0f) {
-                eval_voxel<IMG, MASK>(a, bits, r0[0], r0[1], r0[2], row, x, xf, ia, ma);
-                eval_voxel<IMG, MASK>(a, bits, r0[0], r0[1], r0[2], row, x + 32, xf + 32.0f, ia, ma);
+            for (; x < xe; x += 64, xf = __fadd_rn(xf, 64.0f))
+                eval_pair<IMG, MASK>(a, bits, r0[0], r0[1], r0[2], row, x, xf, x + 32 < xe, ia, ma);
+            if (IMG) {
+                ia.S1 += ia.S1row;
+                ia.S1row = 0;
             }
-            if (x < xe) eval_voxel<IMG, MASK>(a, bits, r0[0], r0[1], r0[2], row, x, xf, ia, ma);
         }
 
         // block reduction and one integer atomic per moment (S2: 128-bit)
@@ -183,7 +280,7 @@ __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
             v[1] = warp_sum64(ia.S1);
             v[2] = warp_sum64(ia.S2);
             v[4] = warp_sum64(ia.ST);
-            v[5] = __reduce_add_sync(0xffffffffu, ia.T1);
+            v[5] = warp_sum64(ia.T1);
             v[6] = warp_sum64(ia.T2);
         }
         if (MASK) {
@@ -228,7 +325,8 @@ cudaError_t launch_variant(const MeasureArgs &a, size_t smem, cudaStream_t s) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const long long items = (long long)a.P * a.n_rowblocks;
+    const int rows = a.g.td[1] * a.g.td[2];
+    const long long items = (long long)a.P * ((rows + kRowsPerItem - 1) / kRowsPerItem);
     // persistent grid: every SM full, a few items per CTA
     long long grid = (long long)sms * per_sm * (SMEM ? 1 : 4);
     if (grid > items) grid = items;
@@ -254,14 +352,11 @@ __global__ void k_pack_quads(const uint8_t *__restrict__ S, int SX, int SY, int 
 
 }  // namespace
 
-// Rows per work item: each thread then visits at most 255 voxels of one
-// particle per item, which keeps its 32-bit partial sums exact.
-int rows_per_item_for(int X) {
-    const int segs = (X + 31) / 32;
-    int per_warp = 255 / segs;
-    if (per_warp < 1) per_warp = 1;
-    return per_warp * kWarps;
-}
+// Rows per work item (32 per warp).  A thread then visits at most
+// 32 * ceil(X/32) <= 2048 voxels of one particle per item (X <= 2048), so its
+// 32-bit partial sums n, T1 < 2^20 and T2 < 2^27 stay exact; S1 is moved to
+// 64 bits after every row (a row adds < 64 * 2^23).
+int rows_per_item_for(int) { return kRowsPerItem; }
 
 cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_t *quad, cudaStream_t s) {
     const size_t n = (size_t)dims[0] * dims[1] * dims[2];
