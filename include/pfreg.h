@@ -161,6 +161,25 @@ int pf_get_log(pf_ctx *ctx, double *est, double *best, double *ess, uint64_t *ev
 int pf_measure_matrices(pf_ctx *ctx, const float *mats, int32_t M, const float a[3],
                         uint64_t *moments_out);
 
+/* Allocation-free variant of pf_measure_matrices (no counterpart in the
+ * paper: it is a service for callers that cannot allocate device memory once
+ * they are running -- an acquisition or control loop that must not stall on
+ * the allocator or fail midway, a process held to a fixed device-memory
+ * budget after start-up, or code where allocation calls are not permitted).
+ * Same inputs and output as pf_measure_matrices (host matrices, host
+ * moments [M][12]) with M <= PF_NOALLOC_MAX_MATRICES; larger M returns
+ * PF_EINVAL.  It calls no cudaMalloc or cudaFree: the uploaded matrices and
+ * the moment accumulators live in one fixed library-wide device array
+ * (PF_NOALLOC_MAX_MATRICES x 144 bytes, 576 KiB) that every GPU loading the
+ * library holds until the process exits.  The first call on a device looks up
+ * that array's device address (once per device); make that first call before
+ * any CUDA stream capture.  All calls share the one array: calls that overlap
+ * on the GPU (different streams or contexts at the same time) race; the
+ * accumulators are cleared at the start of every call.  Synchronous. */
+#define PF_NOALLOC_MAX_MATRICES 4096
+int pf_measure_matrices_noalloc(pf_ctx *ctx, const float *mats, int32_t M, const float a[3],
+                                uint64_t *moments_out);
+
 /* Pose -> (matrix [12], offset a [3]) exactly as the filter computes it. */
 int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float src_origin[3],
                    const float tgt_origin[3], float mat_out[12], float a_out[3]);

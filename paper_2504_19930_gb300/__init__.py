@@ -26,7 +26,7 @@ __all__ = [
     "pf_config_default", "pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy",
     "warp_sequence", "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
     "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_kernel_launches", "pf_last_error",
-    "pf_profile_begin", "pf_profile_end", "register_sequence",
+    "pf_profile_begin", "pf_profile_end", "register_sequence", "pf_measure_matrices_noalloc",
     "Registration", "MODES", "build", "library_path",
 ]
 
@@ -98,6 +98,7 @@ def _declare(L):
     L.pf_measure_matrices.argtypes = [vp, vp, i32, vp, vp]
     L.pf_pose_matrix.argtypes = [vp, vp, vp, vp, vp, vp]
     L.pf_philox.argtypes = [vp, vp, vp]
+    L.pf_measure_matrices_noalloc.argtypes = [vp, vp, i32, vp, vp]
     L.pf_profile_begin.argtypes = [vp, i32]
     L.pf_profile_end.argtypes = [vp, vp, vp]
     L.pf_kernel_launches.argtypes = []
@@ -107,7 +108,7 @@ def _declare(L):
     for name in ("pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy", "warp_sequence",
                  "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
                  "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_profile_begin",
-                 "pf_profile_end"):
+                 "pf_profile_end", "pf_measure_matrices_noalloc"):
         getattr(L, name).restype = C.c_int
 
 
@@ -266,6 +267,20 @@ def pf_measure_matrices(ctx, mats, a):
     out = np.zeros((m.shape[0], MOM_STRIDE), np.uint64)
     av = _np(a, np.float32)
     _check(load().pf_measure_matrices(ctx, _ptr(m), m.shape[0], _ptr(av), _ptr(out)))
+    return out
+
+
+NOALLOC_MAX_MATRICES = 4096
+
+
+def pf_measure_matrices_noalloc(ctx, mats, a):
+    """pf_measure_matrices without device allocation (fixed shared scratch of
+    NOALLOC_MAX_MATRICES matrices; for callers that cannot allocate while
+    running).  Calls that overlap on the GPU race on that scratch."""
+    m = _np(np.atleast_2d(mats), np.float32)
+    out = np.zeros((m.shape[0], MOM_STRIDE), np.uint64)
+    av = _np(a, np.float32)
+    _check(load().pf_measure_matrices_noalloc(ctx, _ptr(m), m.shape[0], _ptr(av), _ptr(out)))
     return out
 
 

@@ -624,3 +624,19 @@ int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32
 }
 
 }  // extern "C"
+
+namespace pfreg {
+
+// Measurement set-up of a context, for entry points defined in other files.
+int ctx_measure_setup(pf_ctx *c, MeasureArgs *ma, bool *img, bool *mask, cudaStream_t *stream) {
+    if (!c) return fail(PF_EINVAL, "ctx is NULL");
+    *ma = c->MA;
+    *img = c->img;
+    *mask = c->mask;
+    *stream = c->stream;
+    return PF_OK;
+}
+
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+}  // namespace pfreg
