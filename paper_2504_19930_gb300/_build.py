@@ -42,7 +42,13 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link; returns the library path.  Skips work when fresh."""
+    """Compile and link; returns the library path.  Skips work when fresh.
+    Extra nvcc flags may also come from the PFREG_NVCC_FLAGS environment
+    variable (kernel variants for A/B timing); they force a rebuild."""
+    env_flags = os.environ.get("PFREG_NVCC_FLAGS", "").split()
+    extra_flags = list(extra_flags) + env_flags
+    if extra_flags:
+        force = True
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)

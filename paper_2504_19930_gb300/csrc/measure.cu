@@ -62,6 +62,10 @@ struct f2 {
 };
 __device__ __forceinline__ f2 pair(float a, float b) { return f2{a, b}; }
 __device__ __forceinline__ f2 splat(float a) { return f2{a, a}; }
+#ifndef PF_USE_F32X2
+#define PF_USE_F32X2 1
+#endif
+#if PF_USE_F32X2
 #define PF_F32X2(NAME, OP)                                                                         \
     __device__ __forceinline__ f2 NAME(f2 a, f2 b) {                                               \
         f2 d;                                                                                      \
@@ -74,6 +78,10 @@ __device__ __forceinline__ f2 splat(float a) { return f2{a, a}; }
 PF_F32X2(add2, "add")
 PF_F32X2(sub2, "sub")
 #undef PF_F32X2
+#else
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return f2{__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)}; }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return f2{__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)}; }
+#endif
 
 // a + f*(b - a) for two voxels: packed difference, scalar product and sum.
 __device__ __forceinline__ f2 lerp2(f2 a, f2 b, f2 f) {
@@ -111,14 +119,15 @@ __device__ __forceinline__ bool inside_tri(float qx, float qy, float qz, uint32_
     return (__float_as_uint(qx) <= bx) & (__float_as_uint(qy) <= by) & (__float_as_uint(qz) <= bz);
 }
 
-template <bool MASK>
+template <bool EXACT>
 __device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t *__restrict__ bits, float qx,
                                            float qy, float qz, uint32_t tidx, bool valid, MaskAcc &ma) {
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
     const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
     const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
-    const bool in = valid & (hx >= 0.0f) & (hx < (float)SX) & (hy >= 0.0f) & (hy < (float)SY) & (hz >= 0.0f) &
-                    (hz < (float)SZ);
+    const bool in = EXACT ? valid
+                          : (valid & (hx >= 0.0f) & (hx < (float)SX) & (hy >= 0.0f) & (hy < (float)SY) &
+                             (hz >= 0.0f) & (hz < (float)SZ));
     if (in) {
         const uint32_t si = int_of(floorf(hx)) + (uint32_t)SX * int_of(floorf(hy)) + SXY * int_of(floorf(hz));
         const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
@@ -130,8 +139,9 @@ __device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t 
     }
 }
 
-// Voxels x and x + 32 of one row (the second only when valid1).
-template <bool IMG, bool MASK>
+// Voxels x and x + 32 of one row (the second only when valid1).  EXACT: the
+// caller visits only the row's exact inside interval, so no voxel is tested.
+template <bool IMG, bool MASK, bool EXACT>
 __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *__restrict__ bits, const float r0x,
                                           const float r0y, const float r0z, const Row &row, int x, float xf,
                                           bool valid1, ImgAcc &ia, MaskAcc &ma) {
@@ -146,8 +156,8 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
         const uint32_t bx = __float_as_uint((float)(SX - 1)), by = __float_as_uint((float)(SY - 1)),
                        bz = __float_as_uint((float)(SZ - 1));
-        const bool in0 = inside_tri(qx.x, qy.x, qz.x, bx, by, bz);
-        const bool in1 = valid1 & inside_tri(qx.y, qy.y, qz.y, bx, by, bz);
+        const bool in0 = EXACT ? true : inside_tri(qx.x, qy.x, qz.x, bx, by, bz);
+        const bool in1 = EXACT ? valid1 : (valid1 & inside_tri(qx.y, qy.y, qz.y, bx, by, bz));
         // base corner min(floor q, D-2) and fraction q - base
         const float Dm2x = (float)(SX - 2), Dm2y = (float)(SY - 2), Dm2z = (float)(SZ - 2);
         const f2 flx = pair(fminf(floorf(qx.x), Dm2x), fminf(floorf(qx.y), Dm2x));
@@ -159,8 +169,12 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
                       SXY * (__float_as_uint(bzv.x) - kTwo23Bits);
         uint32_t i1 = (__float_as_uint(bxv.y) - kTwo23Bits) + (uint32_t)SX * (__float_as_uint(byv.y) - kTwo23Bits) +
                       SXY * (__float_as_uint(bzv.y) - kTwo23Bits);
-        i0 = in0 ? i0 : 0u;   // outside voxels read a valid word and are not accumulated
-        i1 = in1 ? i1 : 0u;
+        if (!EXACT) {
+            i0 = in0 ? i0 : 0u;   // outside voxels read a valid word and are not accumulated
+            i1 = in1 ? i1 : 0u;
+        } else {
+            i1 = valid1 ? i1 : i0;
+        }
         const uint32_t w00 = __ldg(a.src_quad + i0), w01 = __ldg(a.src_quad + i0 + SXY);
         const uint32_t w10 = __ldg(a.src_quad + i1), w11 = __ldg(a.src_quad + i1 + SXY);
         const uint32_t t0 = __ldg(a.tgt_img + t0i), t1 = __ldg(a.tgt_img + t1i);
@@ -194,18 +208,95 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         }
     }
     if (MASK) {
-        mask_voxel<MASK>(a, bits, qx.x, qy.x, qz.x, t0i, true, ma);
-        mask_voxel<MASK>(a, bits, qx.y, qy.y, qz.y, t1i, valid1, ma);
+        mask_voxel<EXACT>(a, bits, qx.x, qy.x, qz.x, t0i, true, ma);
+        mask_voxel<EXACT>(a, bits, qx.y, qy.y, qz.y, t1i, valid1, ma);
     }
 }
 
 constexpr int kRowsPerWarp = 32;
-constexpr int kRowsPerItem = kRowsPerWarp * kWarps;
+constexpr int kItemsPerWarp = 8;   // consecutive items: one particle, adjacent row blocks
 
+// Coordinate q_d(x) of target voxel x of a row (fixed order, no FMA).
+__device__ __forceinline__ float coord1(float r, float K, float a0, int x) {
+    return __fadd_rn(__fmul_rn(r, __fsub_rn(__int2float_rn(x), a0)), K);
+}
+
+// Exact inside interval [xl, xr] of one row, searched within the conservative
+// range [xb, xe) that contains it.  Each q_d(x) is monotone in x (rounding is
+// monotone), so of the two conditions per axis (lower bound, upper bound) one
+// can only turn true as x grows and the other only turn false.  "inc" is the
+// conjunction of the first kind, "dec" of the second; the inside set is
+// [first x with inc, last x with dec], found by two fixed-length binary
+// searches (no divergence across lanes).  TRI: 0 <= q <= D-1 (trilinear);
+// otherwise 0 <= q + 0.5 < D (nearest neighbour).
+template <bool TRI>
+__device__ __forceinline__ void axis_conds(float q, float D, bool &lower, bool &upper) {
+    if (TRI) {
+        lower = q >= 0.0f;
+        upper = q <= D - 1.0f;
+    } else {
+        const float h = __fadd_rn(q, 0.5f);
+        lower = h >= 0.0f;
+        upper = h < D;
+    }
+}
+
+template <bool TRI>
+__device__ __forceinline__ void exact_interval(const float r0[3], const float K[3], float a0, const float D[3],
+                                               int xb, int xe, int &xl, int &xr) {
+    bool constant_ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (r0[d] == 0.0f) {   // q_d does not depend on x
+            bool lo, up;
+            axis_conds<TRI>(coord1(r0[d], K[d], a0, xb), D[d], lo, up);
+            constant_ok &= lo & up;
+        }
+    }
+    auto inc = [&](int x) {
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            bool lo, up;
+            axis_conds<TRI>(coord1(r0[d], K[d], a0, x), D[d], lo, up);
+            ok &= r0[d] > 0.0f ? lo : (r0[d] < 0.0f ? up : true);
+        }
+        return ok;
+    };
+    auto dec = [&](int x) {
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            bool lo, up;
+            axis_conds<TRI>(coord1(r0[d], K[d], a0, x), D[d], lo, up);
+            ok &= r0[d] > 0.0f ? up : (r0[d] < 0.0f ? lo : true);
+        }
+        return ok;
+    };
+    int pl = xb - 1, pr = xb - 1;
+#pragma unroll 1
+    for (int step = 2048; step > 0; step >>= 1) {
+        if (pl + step < xe && !inc(pl + step)) pl += step;
+        if (pr + step < xe && dec(pr + step)) pr += step;
+    }
+    xl = pl + 1;
+    xr = constant_ok ? pr : xl - 1;
+}
+
+// Measurement kernel.  Work item = (particle, 32 target rows), taken by one
+// warp; each warp takes kItemsPerWarp consecutive items (spatially adjacent
+// rows of one particle) and the grid covers all items in several waves, so
+// no block barrier is needed after the optional shared-memory load of the
+// mask and finished CTAs are replaced by fresh ones.
+// EXACT (single-mode kernels): lanes first find their row's exact inside
+// interval, and the sweep evaluates only inside voxels.
+#ifndef PF_MEASURE_MIN_BLOCKS
+#define PF_MEASURE_MIN_BLOCKS 1
+#endif
 template <bool IMG, bool MASK, bool MASK_SMEM>
-__global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
+__global__ void __launch_bounds__(kThreads, PF_MEASURE_MIN_BLOCKS) k_measure(const MeasureArgs a) {
     extern __shared__ uint32_t smem_bits[];
-    __shared__ unsigned long long red[kWarps][kMomStride];
+    constexpr bool EXACT = IMG != MASK;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
@@ -224,12 +315,15 @@ __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
     hi[0] = MASK ? (float)SX - 0.5f : (float)(SX - 1);
     hi[1] = MASK ? (float)SY - 0.5f : (float)(SY - 1);
     hi[2] = MASK ? (float)SZ - 0.5f : (float)(SZ - 1);
+    const float D[3] = {(float)SX, (float)SY, (float)SZ};
 
-    const int n_rowblocks = (rows + kRowsPerItem - 1) / kRowsPerItem;
-    const long long items = (long long)a.P * n_rowblocks;
-    for (long long item = blockIdx.x; item < items; item += gridDim.x) {
-        const int p = (int)(item / n_rowblocks);
-        const int rb = (int)(item - (long long)p * n_rowblocks);
+    const int nblocks = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
+    const long long items = (long long)a.P * nblocks;
+    const long long item0 = ((long long)blockIdx.x * kWarps + warp) * kItemsPerWarp;
+    const long long item1 = min(items, item0 + kItemsPerWarp);
+    for (long long item = item0; item < item1; ++item) {
+        const int p = (int)(item / nblocks);
+        const int rb = (int)(item - (long long)p * nblocks);
         const float *Mp = a.mats + 12 * (size_t)p;
         float M[12];
 #pragma unroll
@@ -238,8 +332,8 @@ __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
         ImgAcc ia;
         MaskAcc ma;
 
-        // lane l prepares row (first + l): hoisted K and its clipped x-range
-        const int first = rb * kRowsPerItem + warp * kRowsPerWarp;
+        // lane l prepares row (first + l): hoisted K and its x-range
+        const int first = rb * kRowsPerWarp;
         const int my_row = first + lane;
         float myK0 = 0.0f, myK1 = 0.0f, myK2 = 0.0f;
         int my_xb = 0, my_xe = 0;
@@ -252,6 +346,12 @@ __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
             myK2 = row_K(M[9], M[10], M[11], dy, dz);
             const float K[3] = {myK0, myK1, myK2};
             row_interval(r0, K, a.g.a[0], lo, hi, TX, my_xb, my_xe);
+            if (EXACT && my_xb < my_xe) {
+                int xl, xr;
+                exact_interval<IMG>(r0, K, a.g.a[0], D, my_xb, my_xe, xl, xr);
+                my_xb = xl;
+                my_xe = xr + 1;
+            }
         }
         const int nrows = min(kRowsPerWarp, rows - first);
         for (int j = 0; j < nrows; ++j) {
@@ -266,49 +366,41 @@ __global__ void __launch_bounds__(kThreads) k_measure(const MeasureArgs a) {
             int x = xb + lane;
             float xf = (float)x;
             for (; x < xe; x += 64, xf = __fadd_rn(xf, 64.0f))
-                eval_pair<IMG, MASK>(a, bits, r0[0], r0[1], r0[2], row, x, xf, x + 32 < xe, ia, ma);
+                eval_pair<IMG, MASK, EXACT>(a, bits, r0[0], r0[1], r0[2], row, x, xf, x + 32 < xe, ia, ma);
             if (IMG) {
                 ia.S1 += ia.S1row;
                 ia.S1row = 0;
             }
         }
 
-        // block reduction and one integer atomic per moment (S2: 128-bit)
-        unsigned long long v[kMomStride] = {0};
+        // warp reduction and one integer atomic per moment (S2: 128-bit)
+        unsigned long long *dst = a.mom + (size_t)p * kMomStride;
         if (IMG) {
-            v[0] = __reduce_add_sync(0xffffffffu, ia.n);
-            v[1] = warp_sum64(ia.S1);
-            v[2] = warp_sum64(ia.S2);
-            v[4] = warp_sum64(ia.ST);
-            v[5] = warp_sum64(ia.T1);
-            v[6] = warp_sum64(ia.T2);
-        }
-        if (MASK) {
-            v[8] = __reduce_add_sync(0xffffffffu, ma.n);
-            v[9] = __reduce_add_sync(0xffffffffu, ma.A);
-            v[10] = __reduce_add_sync(0xffffffffu, ma.B);
-            v[11] = __reduce_add_sync(0xffffffffu, ma.C);
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < kMomStride; ++j) red[warp][j] = v[j];
-        }
-        __syncthreads();
-        if (threadIdx.x < kMomStride) {
-            const int j = threadIdx.x;
-            const bool used = (j < 8) ? (IMG && j != 3 && j != 7) : MASK;
-            if (used) {
-                unsigned long long s = 0;
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w) s += red[w][j];
-                unsigned long long *dst = a.mom + (size_t)p * kMomStride;
-                if (s) {
-                    const unsigned long long old = atomicAdd(dst + j, s);
-                    if (j == 2 && old + s < old) atomicAdd(dst + 3, 1ull);   // carry into S2's high word
-                }
+            const unsigned long long n = __reduce_add_sync(0xffffffffu, ia.n);
+            const unsigned long long S1 = warp_sum64(ia.S1), S2 = warp_sum64(ia.S2), ST = warp_sum64(ia.ST);
+            const unsigned long long T1 = warp_sum64(ia.T1), T2 = warp_sum64(ia.T2);
+            if (lane == 0 && n) {
+                atomicAdd(dst + 0, n);
+                atomicAdd(dst + 1, S1);
+                const unsigned long long old = atomicAdd(dst + 2, S2);
+                if (old + S2 < old) atomicAdd(dst + 3, 1ull);   // carry into S2's high word
+                atomicAdd(dst + 4, ST);
+                atomicAdd(dst + 5, T1);
+                atomicAdd(dst + 6, T2);
             }
         }
-        __syncthreads();
+        if (MASK) {
+            const unsigned long long n = __reduce_add_sync(0xffffffffu, ma.n);
+            const unsigned long long A = __reduce_add_sync(0xffffffffu, ma.A);
+            const unsigned long long B = __reduce_add_sync(0xffffffffu, ma.B);
+            const unsigned long long C = __reduce_add_sync(0xffffffffu, ma.C);
+            if (lane == 0 && n) {
+                atomicAdd(dst + 8, n);
+                if (A) atomicAdd(dst + 9, A);
+                if (B) atomicAdd(dst + 10, B);
+                if (C) atomicAdd(dst + 11, C);
+            }
+        }
     }
 }
 
@@ -319,17 +411,10 @@ cudaError_t launch_variant(const MeasureArgs &a, size_t smem, cudaStream_t s) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
     const int rows = a.g.td[1] * a.g.td[2];
-    const long long items = (long long)a.P * ((rows + kRowsPerItem - 1) / kRowsPerItem);
-    // persistent grid: every SM full, a few items per CTA
-    long long grid = (long long)sms * per_sm * (SMEM ? 1 : 4);
-    if (grid > items) grid = items;
+    const long long items = (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
+    const long long per_cta = (long long)kWarps * kItemsPerWarp;
+    long long grid = (items + per_cta - 1) / per_cta;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, kThreads, smem, s>>>(a);
     count_launches(1);
@@ -352,11 +437,11 @@ __global__ void k_pack_quads(const uint8_t *__restrict__ S, int SX, int SY, int 
 
 }  // namespace
 
-// Rows per work item (32 per warp).  A thread then visits at most
+// Rows per work item (one warp, 32 rows).  A thread then visits at most
 // 32 * ceil(X/32) <= 2048 voxels of one particle per item (X <= 2048), so its
 // 32-bit partial sums n, T1 < 2^20 and T2 < 2^27 stay exact; S1 is moved to
 // 64 bits after every row (a row adds < 64 * 2^23).
-int rows_per_item_for(int) { return kRowsPerItem; }
+int rows_per_item_for(int) { return kRowsPerWarp; }
 
 cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_t *quad, cudaStream_t s) {
     const size_t n = (size_t)dims[0] * dims[1] * dims[2];
