@@ -78,11 +78,15 @@ typedef struct {
     int32_t gamma_log2;       /* 0 .. 10 */
     uint64_t seed;            /* Philox4x32-10 key */
     float min_overlap_frac;   /* [0, 1] */
+    int32_t trace_estimate;   /* 1: after every iteration warp the source mask with the
+                                 estimate and log its Dice against the target mask (Sec. 3.2:
+                                 the masks validate image-based registration after each
+                                 iteration); needs both masks, also in image mode */
 } pf_config;
 
 /* Fill cfg with the defaults: PF_MASK_DICE, N = 256, limits 15 deg / 8 voxels,
  * sigma0_frac 0.25, sigma_decay 0.8, gamma_log2 5, seed 0,
- * min_overlap_frac 0.01. */
+ * min_overlap_frac 0.01, trace_estimate 0. */
 void pf_config_default(pf_config *cfg);
 
 /* Create a registration context (Sec. 3.1 problem statement: source and target
@@ -91,8 +95,10 @@ void pf_config_default(pf_config *cfg);
  * legacy default stream), counts the target mask, and draws the initial
  * particles uniformly within the limits (iteration index 0).
  *   Image modes need src/tgt; mask modes need src_mask/tgt_mask; the combined
- *   mode needs all four, with each mask on its image's grid.  Unused volumes
- *   may be NULL.  The caller may free its buffers when the call returns.
+ *   mode needs all four, with each mask on its image's grid.  Image mode may
+ *   also take both masks (on the image grids) to trace the estimate's Dice.
+ *   Unused volumes may be NULL.  The caller may free its buffers when the
+ *   call returns.
  * Errors: PF_EINVAL (missing volume, dims, limits, N), PF_ENOMEM, PF_ECUDA.
  * On error *out is set to NULL. */
 int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt,
@@ -151,8 +157,10 @@ int pf_set_state(pf_ctx *ctx, const float *poses6xN, int32_t k);
  * first (any array may be NULL): est [count][6] (fp64 estimate), best [count]
  * (max score), ess [count] (effective sample size from the integer weights),
  * evals [count] (particle-voxel evaluations measured: the summed overlap
- * counts).  *count_inout: in = capacity of the caller's arrays, out = rows. */
-int pf_get_log(pf_ctx *ctx, double *est, double *best, double *ess, uint64_t *evals,
+ * counts), est_dice [count] (Dice of the masks at the estimate rounded to
+ * fp32, -1 unless trace_estimate).  *count_inout: in = capacity of the
+ * caller's arrays, out = rows written. */
+int pf_get_log(pf_ctx *ctx, double *est, double *best, double *ess, uint64_t *evals, double *est_dice,
                int32_t *count_inout);
 
 /* Measure M given 3x4 matrices (host, [M][12] = r00 r01 r02 b0 | r10 ... b2)

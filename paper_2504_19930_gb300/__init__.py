@@ -51,7 +51,7 @@ class pf_config(C.Structure):
     _fields_ = [("mode", C.c_int32), ("n_particles", C.c_int32), ("rot_limit", C.c_float * 3),
                 ("trans_limit", C.c_float * 3), ("sigma0_frac", C.c_float),
                 ("sigma_decay", C.c_float), ("gamma_log2", C.c_int32), ("seed", C.c_uint64),
-                ("min_overlap_frac", C.c_float)]
+                ("min_overlap_frac", C.c_float), ("trace_estimate", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -94,7 +94,7 @@ def _declare(L):
     L.pf_get_iteration.argtypes = [vp, vp]
     L.pf_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.pf_set_state.argtypes = [vp, vp, i32]
-    L.pf_get_log.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pf_get_log.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.pf_measure_matrices.argtypes = [vp, vp, i32, vp, vp]
     L.pf_pose_matrix.argtypes = [vp, vp, vp, vp, vp, vp]
     L.pf_philox.argtypes = [vp, vp, vp]
@@ -176,7 +176,8 @@ def pf_config_default() -> pf_config:
 
 
 def make_config(mode="mask_dice", n_particles=256, rot_limit=0.2617994, trans_limit=8.0,
-                sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, seed=0, min_overlap_frac=0.01):
+                sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, seed=0, min_overlap_frac=0.01,
+                trace_estimate=False):
     cfg = pf_config_default()
     cfg.mode = MODES.get(mode, mode)
     cfg.n_particles = int(n_particles)
@@ -187,6 +188,7 @@ def make_config(mode="mask_dice", n_particles=256, rot_limit=0.2617994, trans_li
     cfg.gamma_log2 = int(gamma_log2)
     cfg.seed = int(seed)
     cfg.min_overlap_frac = float(min_overlap_frac)
+    cfg.trace_estimate = int(bool(trace_estimate))
     return cfg
 
 
@@ -251,15 +253,17 @@ def pf_set_state(ctx, poses6xN, k):
 
 
 def pf_get_log(ctx, capacity=4096):
-    """(est [n,6], best [n], ess [n], evals [n]) for the last n iterations."""
+    """(est [n,6], best [n], ess [n], evals [n], est_dice [n]) for the last n
+    iterations (est_dice is -1 unless the context traces the estimate)."""
     est = np.zeros((capacity, 6), np.float64)
     best = np.zeros(capacity, np.float64)
     ess = np.zeros(capacity, np.float64)
     evals = np.zeros(capacity, np.uint64)
+    dice = np.zeros(capacity, np.float64)
     n = C.c_int32(capacity)
-    _check(load().pf_get_log(ctx, _ptr(est), _ptr(best), _ptr(ess), _ptr(evals), C.byref(n)))
+    _check(load().pf_get_log(ctx, _ptr(est), _ptr(best), _ptr(ess), _ptr(evals), _ptr(dice), C.byref(n)))
     k = n.value
-    return est[:k], best[:k], ess[:k], evals[:k]
+    return est[:k], best[:k], ess[:k], evals[:k], dice[:k]
 
 
 def pf_measure_matrices(ctx, mats, a):
@@ -383,8 +387,9 @@ def _to_cuda(a, stream=None):
     return a.cuda(non_blocking=True)
 
 
-def register_sequence(mode, src, tgt, frames, n_iters, src_origin=(0, 0, 0), tgt_origin=(0, 0, 0),
-                      src_mask=None, tgt_mask=None, interp=1, out=None, with_score=False, **cfg):
+def register_sequence(mode, src=None, tgt=None, frames=(), n_iters=1, src_origin=(0, 0, 0),
+                      tgt_origin=(0, 0, 0), src_mask=None, tgt_mask=None, interp=1, out=None,
+                      with_score=False, **cfg):
     """Register source to target, then warp every source frame by the estimate.
 
     The whole user-facing path: volumes (host numpy / host or pinned torch /

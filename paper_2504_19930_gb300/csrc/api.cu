@@ -116,7 +116,7 @@ struct pf_ctx {
     FilterParams P{};
     FilterBuffers B{};
     MeasureArgs MA{};
-    bool img = false, mask = false;
+    bool img = false, mask = false, trace = false;
     uint8_t *tgt_img = nullptr, *tgt_mask = nullptr;
     uint32_t *src_quad = nullptr;
     uint32_t *src_bits = nullptr;
@@ -202,6 +202,16 @@ int build_graph(pf_ctx *c) {
         es[2] = launch_measure(c->MA, c->img, c->mask, c->cap_stream);
         es[3] = cudaEventRecordWithFlags(c->ev_after, c->cap_stream, cudaEventRecordExternal);
         es[4] = launch_finalise(c->P, c->B, c->cap_stream);
+        if (c->trace) {   // the estimate's mask Dice, logged every iteration
+            MeasureArgs tm = c->MA;
+            tm.mats = c->B.trace_mat;
+            tm.mom = c->B.trace_mom;
+            tm.P = 1;
+            cudaError_t t1 = launch_trace_prepare(c->P, c->B, c->cap_stream);
+            cudaError_t t2 = launch_measure(tm, false, true, c->cap_stream);
+            cudaError_t t3 = launch_trace_finish(c->P, c->B, c->cap_stream);
+            es[4] = es[4] != cudaSuccess ? es[4] : t1 != cudaSuccess ? t1 : t2 != cudaSuccess ? t2 : t3;
+        }
         es[5] = cudaStreamEndCapture(c->cap_stream, &c->graph);
         for (cudaError_t x : es)
             if (x != cudaSuccess && e == cudaSuccess) e = x;
@@ -250,6 +260,7 @@ void pf_config_default(pf_config *cfg) {
     cfg->gamma_log2 = 5;
     cfg->seed = 0;
     cfg->min_overlap_frac = 0.01f;
+    cfg->trace_estimate = 0;
 }
 
 const char *pf_last_error(void) { return g_err.c_str(); }
@@ -272,6 +283,15 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     }
     if (img && mask && (!same_grid(src, src_mask) || !same_grid(tgt, tgt_mask)))
         return fail(PF_EINVAL, "combined mode: each mask must share its image's dims and origin");
+    // Image mode may carry the masks too, for tracing the estimate's Dice.
+    const bool have_masks = mask || (src_mask != nullptr && tgt_mask != nullptr);
+    if (img && !mask && have_masks) {
+        if ((rc = check_volume(src_mask, "src_mask")) || (rc = check_volume(tgt_mask, "tgt_mask"))) return rc;
+        if (!same_grid(src, src_mask) || !same_grid(tgt, tgt_mask))
+            return fail(PF_EINVAL, "tracing masks must share their image's dims and origin");
+    }
+    if (cfg->trace_estimate && !have_masks)
+        return fail(PF_EINVAL, "trace_estimate needs src_mask and tgt_mask");
     const pf_volume *S = img ? src : src_mask;
     const pf_volume *T = img ? tgt : tgt_mask;
     if (nvox(S->dims) > kMaxSourceVoxels) return fail(PF_EINVAL, "source has more than 2^28 voxels");
@@ -296,6 +316,7 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     c->cfg = *cfg;
     c->img = img;
     c->mask = mask;
+    c->trace = cfg->trace_estimate != 0;
     const int N = cfg->n_particles;
     const Geometry g = make_geometry(S->dims, S->origin, T->dims, T->origin);
     const size_t ns = nvox(S->dims), nt = nvox(T->dims);
@@ -344,7 +365,9 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
         if (raw) CK(cudaFreeAsync(raw, c->stream));
         CK(copy_in(c->tgt_img, tgt, nt, c->stream));
     }
-    if (mask) {
+    CK(c->alloc(&B.trace_mat, 12));
+    CK(c->alloc(&B.trace_mom, (size_t)kMomStride));
+    if (have_masks) {
         uint8_t *tmp = nullptr;
         CK(c->alloc(&c->src_bits, (ns + 31) / 32));
         CK(c->alloc(&c->tgt_mask, nt));
@@ -409,7 +432,7 @@ int pf_step(pf_ctx *c, int32_t n_iters) {
             c->prof_default = true;
         }
         CU(cudaGraphLaunch(c->exec, c->stream));
-        count_launches(3);
+        count_launches(c->trace ? 6 : 3);
     }
     return PF_OK;
 }
@@ -505,7 +528,8 @@ int pf_set_state(pf_ctx *c, const float *poses6xN, int32_t k) {
     return PF_OK;
 }
 
-int pf_get_log(pf_ctx *c, double *est, double *best, double *ess, uint64_t *evals, int32_t *count_inout) {
+int pf_get_log(pf_ctx *c, double *est, double *best, double *ess, uint64_t *evals, double *est_dice,
+               int32_t *count_inout) {
     if (!c || !count_inout) return fail(PF_EINVAL, "NULL argument");
     int32_t k = 0;
     int rc = pf_get_iteration(c, &k);
@@ -523,6 +547,7 @@ int pf_get_log(pf_ctx *c, double *est, double *best, double *ess, uint64_t *eval
         if (best) best[r] = e.best;
         if (ess) ess[r] = e.ess;
         if (evals) evals[r] = e.evals;
+        if (est_dice) est_dice[r] = e.est_dice;
     }
     *count_inout = n;
     return PF_OK;

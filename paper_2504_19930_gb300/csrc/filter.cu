@@ -219,11 +219,34 @@ __global__ void __launch_bounds__(kFinThreads) k_finalise(const FilterParams P, 
         L.best = sh_best;
         L.best_idx = sh_best_idx;
         L.evals = sh_evals;
+        L.est_dice = -1.0;
         const double Sd = (double)S;
         L.ess = w2 > 0.0 ? Sd * Sd / w2 : 0.0;
         L.k = k;
         *B.k = k + 1;
     }
+}
+
+// Estimate of iteration k-1 (the counter has advanced) rounded to fp32, as
+// the pose whose matrix the masks are warped with; zeroes the counts.
+__global__ void k_trace_prepare(const FilterParams P, const FilterBuffers B) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k = *B.k - 1;
+    const IterLog &L = B.log[k % P.log_capacity];
+    float pose[6];
+    for (int d = 0; d < 6; ++d) pose[d] = __double2float_rn(L.est[d]);
+    float M[12];
+    pose_to_matrix(pose, P.g, M);
+    for (int j = 0; j < 12; ++j) B.trace_mat[j] = M[j];
+    for (int j = 0; j < kMomStride; ++j) B.trace_mom[j] = 0ull;
+}
+
+// Dice (Eq. 4, whole target grid, no overlap threshold) of the estimate.
+__global__ void k_trace_finish(const FilterParams P, const FilterBuffers B) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int k = *B.k - 1;
+    const unsigned long long *m = B.trace_mom + 8;
+    B.log[k % P.log_capacity].est_dice = dice_from_counts(m[0], m[1], m[3], P.b_full, 0ull);
 }
 
 __global__ void k_pack_bits(const uint8_t *mask, int64_t nvox, uint32_t *bits) {
@@ -295,6 +318,18 @@ cudaError_t launch_predict(const FilterParams &p, const FilterBuffers &b, cudaSt
 
 cudaError_t launch_finalise(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
     k_finalise<<<1, kFinThreads, 0, s>>>(p, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_prepare(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
+    k_trace_prepare<<<1, 32, 0, s>>>(p, b);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_finish(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
+    k_trace_finish<<<1, 32, 0, s>>>(p, b);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ struct IterLog {
     double best;
     double ess;
     unsigned long long evals;   // particle-voxel evaluations visited (sum of overlap counts)
+    double est_dice;            // Dice of the masks at the estimate (-1 when not traced)
     int32_t best_idx;
     int32_t k;
 };
@@ -59,6 +60,8 @@ struct FilterBuffers {
     int32_t *idx;               // [N]
     int32_t *k;                 // iteration counter (device)
     IterLog *log;               // [log_capacity]
+    float *trace_mat;           // [12] matrix of the estimate (tracing)
+    unsigned long long *trace_mom;   // [12] its mask counts (tracing)
 };
 
 cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream_t s);
@@ -67,6 +70,11 @@ int rows_per_item_for(int target_x);
 cudaError_t launch_init_particles(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
 cudaError_t launch_predict(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
 cudaError_t launch_finalise(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
+// Tracing of the estimate (Sec. 3.2: the masks are warped with the estimate
+// and their overlap score is taken after every iteration): matrix of the
+// last iteration's estimate, then (after a mask measurement) its Dice.
+cudaError_t launch_trace_prepare(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
+cudaError_t launch_trace_finish(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
 cudaError_t launch_pack_bits(const uint8_t *mask, int64_t nvox, uint32_t *bits, cudaStream_t s);
 cudaError_t launch_count_nonzero(const uint8_t *v, int64_t n, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_binarise(const uint8_t *in, uint8_t *out, int64_t n, cudaStream_t s);

@@ -110,3 +110,10 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(pk, "_lib", None)
     with pytest.raises(RuntimeError, match="libpfreg.so not found"):
         pk.load()
+
+
+def test_trace_without_masks_is_rejected(pk):
+    v = pk.make_volume(np.zeros((4, 4, 4), np.uint8))
+    cfg = pk.make_config("image_ncc", trace_estimate=True)
+    rc, ctx = _init_rc(pk, cfg, [v, v, None, None])
+    assert rc == -1 and ctx is None and "trace_estimate" in pk.pf_last_error()

@@ -42,6 +42,7 @@ def _reg(pk, mode, pair, N, lim_r, lim_t, seed, device=True, **kw):
         args.update(src=d(pair.src), tgt=d(pair.tgt))
     if mode != "image_ncc":
         args.update(src_mask=d(pair.src_mask), tgt_mask=d(pair.tgt_mask))
+    args.update({k: kw.pop(k) for k in ("src_mask", "tgt_mask") if k in kw})
     return pk.Registration(mode, src_origin=pair.src_origin, tgt_origin=pair.tgt_origin, n_particles=N,
                            rot_limit=lim_r, trans_limit=lim_t, seed=seed, **args, **kw)
 
@@ -248,7 +249,7 @@ def test_config0_full_registration_bit_exact(pk, orc):
         nmin = int(float(np.float32(0.01)) * pair.tgt.size)
         want = orc.dice_from_counts(cnt[0], cnt[1], cnt[3], int(pair.tgt.sum()), nmin)
         assert score == want
-        _, best, ess, evals = reg.log()
+        _, best, ess, evals, _ = reg.log()
         assert len(best) == c["n_iters"] and best[-1] > 0.9 and np.all(ess > 0)
         assert evals[-1] == int(ref["tr_mom"][-1][:, 8].sum())
 
@@ -287,7 +288,7 @@ def test_config1_full_size_sampled(pk, orc):
             assert np.array_equal(st["resample_idx"], idx)
             assert np.array_equal(st["poses_next"], x[:, idx])
             est = orc.estimate(x, W)
-            log_est, _, _, log_evals = reg.log()
+            log_est, _, _, log_evals, _ = reg.log()
             assert log_evals[-1] == int(st["moments"][:, 0].sum())
             assert np.all(np.abs(log_est[-1] - est) <= np.array([ROT_TOL] * 3 + [TRANS_TOL] * 3))
             prev_next = st["poses_next"]
@@ -341,3 +342,25 @@ def test_kernel_launches_are_counted(pk):
         reg.step(4)
         reg.estimate(False)
     assert pk.pf_kernel_launches() - before >= 12
+
+
+@pytest.mark.parametrize("mode", ["image_ncc", "mask_dice"])
+def test_estimate_dice_trace(pk, orc, mode):
+    """Sec. 3.2: the masks are warped with the estimate after every iteration
+    and their Dice is logged.  The traced Dice equals the oracle's Dice at the
+    same fp32 estimate, and tracing leaves the filter's trajectory unchanged."""
+    pair = pfsynth.speckle_pair(11, src_dims=(40, 36, 32), tgt_dims=(39, 35, 30), overlap=(0.6, 0.7),
+                                max_rot_deg=8, max_trans=3, with_masks=True)
+    N, K, lr, lt = 128, 6, 0.2, 4.0
+    ref = _oracle_run(orc, mode, pair, N, K, lr, lt, seed=5)
+    with _reg(pk, mode, pair, N, lr, lt, 5, trace_estimate=True,
+              **({"src_mask": _cuda(pair.src_mask), "tgt_mask": _cuda(pair.tgt_mask)}
+                 if mode == "image_ncc" else {})) as reg:
+        _assert_trajectory(reg, ref, K)
+        est, _, _, _, dice = reg.log()
+    assert len(dice) == K and np.all(dice >= 0)
+    bfull = int((pair.tgt_mask != 0).sum())
+    for k in range(K):
+        M, a = orc.pose_matrix(est[k].astype(np.float32), pair.src_dims, pair.src_origin, pair.tgt_origin)
+        c = orc.measure_mask(pair.src_mask, pair.tgt_mask, M, a)[0]
+        assert dice[k] == orc.dice_from_counts(c[0], c[1], c[3], bfull, 0), k
