@@ -38,6 +38,7 @@ import pfsynth  # noqa: E402
 WORKLOADS = {
     "config1": dict(pfsynth.CONFIG1, kind="image_ncc", dims=(224, 208, 176)),
     "config0": dict(pfsynth.CONFIG0, kind="mask_dice", dims=(64, 64, 64), n_frames=0),
+    "config2": dict(name="batch64_mixed_96to256_n512to8192_k20to60", kind="batch", n_regs=64),
 }
 METRIC = "particle-voxel evals/s (dense N*iters*target voxels per registration) and ms per registration"
 UNIT = "particle-voxel evals/s"
@@ -62,6 +63,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config1")
+    ap.add_argument("--batch-regs", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-particles", type=int, default=32)
@@ -209,7 +211,12 @@ def oracle_sample(w, pair, n_particles, n_iters):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w, pair, _ = load_workload(args.workload, 0)
+    if args.workload == "config2":      # a bounded sample of one image-based member
+        m = batch_members(2, 7)[1]
+        w = dict(name=WORKLOADS["config2"]["name"], kind=m["mode"], rot_limit_deg=30.0, trans_limit=25.0, seed=1)
+        pair = m["pair"]
+    else:
+        w, pair, _ = load_workload(args.workload, 0)
     n, k = args.cpu_sample_particles, 1
     times, units = [], 0
     for i in range(args.warmup + args.steps):
@@ -425,11 +432,111 @@ def run_ours(args, rank, world, local):
     dist.close()
 
 
+def batch_members(n_regs, seed):
+    """The batched workload: registration r draws its grid (each axis 96..256),
+    particle count {512, 1024, 4096, 8192}, iteration count 20..60 and mode
+    (even r: mask Dice on an ellipsoid mask pair, odd r: image NCC on a speckle
+    pair), all from one seeded generator."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_regs):
+        dims = tuple(int(v) for v in rng.integers(96, 257, 3))
+        N = int(rng.choice([512, 1024, 4096, 8192]))
+        K = int(rng.integers(20, 61))
+        if r % 2 == 0:
+            pair = pfsynth.cached(pfsynth.ellipsoid_pair, seed * 1000 + r, src_dims=dims, tgt_dims=dims,
+                                  tgt_origin=(0.0, 0.0, float(int(0.2 * dims[2]))),
+                                  semi_axes=(0.31 * dims[0], 0.22 * dims[1], 0.22 * dims[2]),
+                                  max_trans=0.06 * min(dims))
+            out.append(dict(mode="mask_dice", pair=pair, N=N, K=K, rot=np.deg2rad(15.0),
+                            trans=float(0.12 * min(dims))))
+        else:
+            pair = pfsynth.cached(pfsynth.speckle_pair, seed * 1000 + r, src_dims=dims)
+            out.append(dict(mode="image_ncc", pair=pair, N=N, K=K, rot=np.deg2rad(30.0), trans=25.0))
+    return out
+
+
+def run_batch(args, rank, world, local):
+    """Batched registrations: all members stepped together (pf_batch) against
+    the same members stepped one after another, both timed with CUDA events
+    around the iterations only (context creation excluded from both)."""
+    import torch
+
+    import paper_2504_19930_gb300 as pk
+
+    torch.cuda.set_device(local)
+    pk.build()
+    pk.load()
+    dist = Dist(world)
+    members = batch_members(args.batch_regs, 7 + rank)
+    dev = torch.device("cuda", local)
+    dev_vols = []
+    for m in members:
+        p = m["pair"]
+        if m["mode"] == "mask_dice":
+            dev_vols.append(dict(src_mask=torch.from_numpy(p.src_mask).to(dev),
+                                 tgt_mask=torch.from_numpy(p.tgt_mask).to(dev)))
+        else:
+            dev_vols.append(dict(src=torch.from_numpy(p.src).to(dev), tgt=torch.from_numpy(p.tgt).to(dev)))
+
+    def make_all():
+        return [pk.Registration(m["mode"], src_origin=m["pair"].src_origin, tgt_origin=m["pair"].tgt_origin,
+                                n_particles=m["N"], rot_limit=m["rot"], trans_limit=m["trans"], seed=r,
+                                **dev_vols[r]) for r, m in enumerate(members)]
+
+    stream = torch.cuda.current_stream()
+    units = sum(m["N"] * m["K"] * int(np.prod(m["pair"].tgt.shape)) for m in members)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res = {"batched": [], "sequential": []}
+    for i in range(args.warmup + args.steps):
+        for how in ("batched", "sequential"):
+            regs = make_all()
+            batch = pk.Batch(regs, [m["K"] for m in members]) if how == "batched" else None
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if batch is not None:
+                batch.run()
+            else:
+                for r, m in zip(regs, members):
+                    r.step(m["K"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                res[how].append(e0.elapsed_time(e1) / 1e3)
+            if batch is not None:
+                batch.close()
+            for r in regs:
+                r.close()
+    tb = dist.max(sum(res["batched"]))
+    ts = dist.max(sum(res["sequential"]))
+    total = dist.sum(units * args.steps)
+    if rank == 0:
+        line = {"metric": METRIC, "value": total / tb, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * tb / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["config2"]["name"], "registrations": len(members),
+                           "mask_based": sum(m["mode"] == "mask_dice" for m in members),
+                           "particles": [m["N"] for m in members], "iterations": [m["K"] for m in members],
+                           "dense_evals_per_step": units,
+                           "sequential_ms_per_step": 1e3 * ts / args.steps,
+                           "batched_speedup_vs_sequential": ts / tb,
+                           "l2": "flushed before every step (256 MiB write, outside the timed events)"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "config2":
+        run_batch(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

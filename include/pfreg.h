@@ -132,6 +132,33 @@ int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32
                   const int32_t tgt_dims[3], const float tgt_origin[3], const float pose[6],
                   int32_t interp, void *cuda_stream);
 
+/* ---- batches: many registrations stepped together ---- */
+
+/* A batch steps several registrations (each created by pf_register_init, all
+ * on one device and one stream, any mix of modes, volume sizes and particle
+ * counts) together.  One batch iteration is one CUDA-graph launch: prediction
+ * of every particle of every running registration, their measurements (image,
+ * mask and combined registrations as three concurrent launches over their
+ * concatenated work items) and one update/resampling block per registration.
+ * n_iters[r] is registration r's total iteration count.  Members are ordered
+ * by remaining iterations, so the running ones are a prefix; one graph is
+ * captured per such prefix (on first use) and its grids cover only the
+ * running members' work.  Every registration
+ * follows exactly the arithmetic of pf_step (same results bit for bit).
+ * While in a batch, a context must not be stepped on its own (the batch
+ * counts the remaining iterations on the host); its state,
+ * estimate and log are read with the usual calls.  Tracing is not applied in
+ * batches.  The batch borrows the contexts: destroy it before them.
+ * Errors: PF_EINVAL (NULL, n outside 1..65536, repeated context, different
+ * devices or streams, negative count), PF_ENOMEM, PF_ECUDA. */
+typedef struct pf_batch pf_batch;
+int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_t *n_iters);
+/* Launch n_iters batch iterations (asynchronous on the contexts' stream). */
+int pf_batch_step(pf_batch *b, int32_t n_iters);
+/* Launch as many batch iterations as the longest remaining registration needs. */
+int pf_batch_run(pf_batch *b);
+int pf_batch_destroy(pf_batch *b);
+
 /* ---- inspection, checkpoint and test exports (host buffers, synchronous) ---- */
 
 /* Number of iterations run so far (the next iteration's index k). */

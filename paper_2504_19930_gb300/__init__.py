@@ -27,6 +27,7 @@ __all__ = [
     "warp_sequence", "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
     "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_kernel_launches", "pf_last_error",
     "pf_profile_begin", "pf_profile_end", "register_sequence", "pf_measure_matrices_noalloc",
+    "Batch", "pf_batch_create", "pf_batch_step", "pf_batch_run", "pf_batch_destroy",
     "Registration", "MODES", "build", "library_path",
 ]
 
@@ -99,6 +100,10 @@ def _declare(L):
     L.pf_pose_matrix.argtypes = [vp, vp, vp, vp, vp, vp]
     L.pf_philox.argtypes = [vp, vp, vp]
     L.pf_measure_matrices_noalloc.argtypes = [vp, vp, i32, vp, vp]
+    L.pf_batch_create.argtypes = [C.POINTER(vp), vp, i32, vp]
+    L.pf_batch_step.argtypes = [vp, i32]
+    L.pf_batch_run.argtypes = [vp]
+    L.pf_batch_destroy.argtypes = [vp]
     L.pf_profile_begin.argtypes = [vp, i32]
     L.pf_profile_end.argtypes = [vp, vp, vp]
     L.pf_kernel_launches.argtypes = []
@@ -108,7 +113,8 @@ def _declare(L):
     for name in ("pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy", "warp_sequence",
                  "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
                  "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_profile_begin",
-                 "pf_profile_end", "pf_measure_matrices_noalloc"):
+                 "pf_profile_end", "pf_measure_matrices_noalloc", "pf_batch_create", "pf_batch_step",
+                 "pf_batch_run", "pf_batch_destroy"):
         getattr(L, name).restype = C.c_int
 
 
@@ -423,3 +429,57 @@ def register_sequence(mode, src=None, tgt=None, frames=(), n_iters=1, src_origin
         torch.cuda.current_stream().synchronize()
         return pose, score, out
     return pose, score, fout
+
+
+def pf_batch_create(ctxs, n_iters):
+    """Batch of contexts (c_void_p handles) with per-registration counts."""
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    its = _np(n_iters, np.int32)
+    b = C.c_void_p()
+    _check(load().pf_batch_create(C.byref(b), arr, len(ctxs), _ptr(its)))
+    return b
+
+
+def pf_batch_step(b, n_iters):
+    _check(load().pf_batch_step(b, int(n_iters)))
+
+
+def pf_batch_run(b):
+    _check(load().pf_batch_run(b))
+
+
+def pf_batch_destroy(b):
+    _check(load().pf_batch_destroy(b))
+
+
+class Batch:
+    """Several Registration objects (same stream) stepped together."""
+
+    def __init__(self, registrations, n_iters):
+        self.regs = list(registrations)
+        self.handle = pf_batch_create([r.ctx for r in self.regs], n_iters)
+
+    def run(self):
+        pf_batch_run(self.handle)
+        return self
+
+    def step(self, n_iters=1):
+        pf_batch_step(self.handle, n_iters)
+        return self
+
+    def close(self):
+        if self.handle is not None:
+            pf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

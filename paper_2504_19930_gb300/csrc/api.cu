@@ -9,6 +9,8 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <algorithm>
+#include <map>
 
 #include "../../include/pfreg.h"
 #include "kernels.h"
@@ -365,6 +367,7 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
         if (raw) CK(cudaFreeAsync(raw, c->stream));
         CK(copy_in(c->tgt_img, tgt, nt, c->stream));
     }
+    CK(c->alloc(&B.stats, 2));
     CK(c->alloc(&B.trace_mat, 12));
     CK(c->alloc(&B.trace_mom, (size_t)kMomStride));
     if (have_masks) {
@@ -432,7 +435,7 @@ int pf_step(pf_ctx *c, int32_t n_iters) {
             c->prof_default = true;
         }
         CU(cudaGraphLaunch(c->exec, c->stream));
-        count_launches(c->trace ? 6 : 3);
+        count_launches(c->trace ? 8 : 5);
     }
     return PF_OK;
 }
@@ -665,3 +668,218 @@ int ctx_measure_setup(pf_ctx *c, MeasureArgs *ma, bool *img, bool *mask, cudaStr
 int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 }  // namespace pfreg
+
+// ---------------------------------------------------------------------------
+// Batches of registrations stepped together.
+// ---------------------------------------------------------------------------
+struct pf_batch {
+    std::vector<pf_ctx *> ctxs;        // in batch order: remaining iterations, descending
+    std::vector<int32_t> remaining;    // iterations each member still has to run
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr, side[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
+    BatchReg *regs = nullptr;          // device table, batch order
+    int32_t *lists = nullptr;          // three lists back to back: image, mask, combined
+    long long *offs = nullptr;         // three item prefixes back to back (len + 1 each)
+    long long *poffs = nullptr;        // particle prefix (n + 1)
+    long long *poffs32 = nullptr;      // particle prefix, each member padded to whole warps
+    int32_t *lptr[3] = {nullptr, nullptr, nullptr};
+    long long *optr[3] = {nullptr, nullptr, nullptr};
+    std::vector<int32_t> list_h[3];            // members of each list (batch positions)
+    std::vector<long long> offs_h[3], poffs_h, poffs32_h;
+    std::map<int, cudaGraphExec_t> phase;      // graph per number of active members
+    ~pf_batch() {
+        for (auto &kv : phase) cudaGraphExecDestroy(kv.second);
+        for (cudaStream_t s : {cap, side[0], side[1]})
+            if (s) cudaStreamDestroy(s);
+        for (cudaEvent_t e : {fork, join[0], join[1]})
+            if (e) cudaEventDestroy(e);
+        for (void *p : {(void *)regs, (void *)lists, (void *)offs, (void *)poffs, (void *)poffs32})
+            if (p) cudaFree(p);
+    }
+};
+
+namespace {
+
+// Members of list k among the first `active` batch positions.
+int list_prefix(const pf_batch *b, int k, int active) {
+    const auto &L = b->list_h[k];
+    return (int)(std::lower_bound(L.begin(), L.end(), active) - L.begin());
+}
+
+// The graph of one batch iteration with the first `active` members running:
+// prediction of their particles, their measurements (three concurrent
+// launches: image, mask and combined members), one update block each.  The
+// grids cover exactly the active members' work.
+int batch_phase_graph(pf_batch *b, int active, cudaGraphExec_t *out) {
+    auto it = b->phase.find(active);
+    if (it != b->phase.end()) {
+        *out = it->second;
+        return PF_OK;
+    }
+    int nl[3];
+    for (int k = 0; k < 3; ++k) nl[k] = list_prefix(b, k, active);
+    cudaGraph_t g = nullptr;
+    g_capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t es[12] = {cudaSuccess};
+        es[0] = launch_predict_batch(b->regs, b->poffs, active, b->poffs_h[active], b->cap);
+        es[1] = cudaEventRecord(b->fork, b->cap);
+        es[2] = cudaStreamWaitEvent(b->side[0], b->fork, 0);
+        es[3] = cudaStreamWaitEvent(b->side[1], b->fork, 0);
+        es[4] = launch_measure_batch(b->regs, b->lptr[0], b->optr[0], nl[0], b->offs_h[0][nl[0]], true, false, b->cap);
+        es[5] = launch_measure_batch(b->regs, b->lptr[1], b->optr[1], nl[1], b->offs_h[1][nl[1]], false, true,
+                                     b->side[0]);
+        es[6] = launch_measure_batch(b->regs, b->lptr[2], b->optr[2], nl[2], b->offs_h[2][nl[2]], true, true,
+                                     b->side[1]);
+        es[7] = cudaEventRecord(b->join[0], b->side[0]);
+        es[8] = cudaEventRecord(b->join[1], b->side[1]);
+        es[9] = cudaStreamWaitEvent(b->cap, b->join[0], 0);
+        es[10] = cudaStreamWaitEvent(b->cap, b->join[1], 0);
+        es[11] = launch_finalise_batch(b->regs, b->poffs32, active, b->poffs32_h[active], b->cap);
+        cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+        for (cudaError_t x : es)
+            if (x != cudaSuccess && e == cudaSuccess) e = x;
+        if (e == cudaSuccess) e = ee;
+    }
+    g_capturing = false;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(PF_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(PF_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+    b->phase[active] = x;
+    *out = x;
+    return PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_t *n_iters) {
+    if (!out) return fail(PF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || !n_iters || n < 1 || n > 65536) return fail(PF_EINVAL, "need 1..65536 contexts and counts");
+    for (int32_t r = 0; r < n; ++r) {
+        if (!ctxs[r]) return fail(PF_EINVAL, "context %d is NULL", r);
+        if (n_iters[r] < 0) return fail(PF_EINVAL, "n_iters[%d] < 0", r);
+        if (ctxs[r]->device != ctxs[0]->device) return fail(PF_EINVAL, "contexts are on different devices");
+        if (ctxs[r]->stream != ctxs[0]->stream) return fail(PF_EINVAL, "contexts use different streams");
+        for (int32_t q = 0; q < r; ++q)
+            if (ctxs[q] == ctxs[r]) return fail(PF_EINVAL, "context %d appears twice", r);
+    }
+    // Batch order: remaining iterations descending, so the members still
+    // running always form a prefix.
+    std::vector<int32_t> rem(n);
+    for (int32_t r = 0; r < n; ++r) {
+        int32_t k = 0;
+        int rc = pf_get_iteration(ctxs[r], &k);
+        if (rc) return rc;
+        rem[r] = n_iters[r] > k ? n_iters[r] - k : 0;
+    }
+    std::vector<int32_t> order(n);
+    for (int32_t r = 0; r < n; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return rem[x] > rem[y]; });
+
+    pf_batch *b = new (std::nothrow) pf_batch();
+    if (!b) return fail(PF_ENOMEM, "host allocation failed");
+    auto bail = [&](int code) {
+        delete b;
+        return code;
+    };
+#define BK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? PF_ENOMEM : PF_ECUDA, "%s: %s", #call, \
+                             cudaGetErrorString(e_)));                                        \
+    } while (0)
+    b->stream = ctxs[0]->stream;
+    std::vector<BatchReg> regs(n);
+    b->poffs_h.assign(1, 0);
+    b->poffs32_h.assign(1, 0);
+    for (int k = 0; k < 3; ++k) b->offs_h[k].assign(1, 0);
+    for (int32_t pos = 0; pos < n; ++pos) {
+        pf_ctx *c = ctxs[order[pos]];
+        b->ctxs.push_back(c);
+        b->remaining.push_back(rem[order[pos]]);
+        regs[pos].ma = c->MA;
+        regs[pos].P = c->P;
+        regs[pos].B = c->B;
+        regs[pos].n_iters = n_iters[order[pos]];
+        regs[pos].img = c->img;
+        regs[pos].mask = c->mask;
+        const int kind = (c->img && c->mask) ? 2 : (c->img ? 0 : 1);
+        b->list_h[kind].push_back(pos);
+        b->offs_h[kind].push_back(b->offs_h[kind].back() + measure_items(c->MA));
+        b->poffs_h.push_back(b->poffs_h.back() + c->P.N);
+        b->poffs32_h.push_back(b->poffs32_h.back() + (c->P.N + 31) / 32 * 32);
+    }
+    BK(cudaMalloc(&b->regs, sizeof(BatchReg) * n));
+    BK(cudaMalloc(&b->lists, sizeof(int32_t) * (size_t)n + 4));
+    BK(cudaMalloc(&b->offs, sizeof(long long) * (size_t)(n + 3)));
+    BK(cudaMalloc(&b->poffs, sizeof(long long) * (size_t)(n + 1)));
+    BK(cudaMalloc(&b->poffs32, sizeof(long long) * (size_t)(n + 1)));
+    BK(cudaMemcpy(b->regs, regs.data(), sizeof(BatchReg) * n, cudaMemcpyHostToDevice));
+    BK(cudaMemcpy(b->poffs, b->poffs_h.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    BK(cudaMemcpy(b->poffs32, b->poffs32_h.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
+    size_t lpos = 0, opos = 0;
+    for (int k = 0; k < 3; ++k) {
+        b->lptr[k] = b->lists + lpos;
+        b->optr[k] = b->offs + opos;
+        if (!b->list_h[k].empty())
+            BK(cudaMemcpy(b->lptr[k], b->list_h[k].data(), sizeof(int32_t) * b->list_h[k].size(),
+                          cudaMemcpyHostToDevice));
+        BK(cudaMemcpy(b->optr[k], b->offs_h[k].data(), sizeof(long long) * b->offs_h[k].size(),
+                      cudaMemcpyHostToDevice));
+        lpos += b->list_h[k].size();
+        opos += b->offs_h[k].size();
+    }
+    BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    BK(cudaStreamCreateWithFlags(&b->side[0], cudaStreamNonBlocking));
+    BK(cudaStreamCreateWithFlags(&b->side[1], cudaStreamNonBlocking));
+    BK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    BK(cudaEventCreateWithFlags(&b->join[0], cudaEventDisableTiming));
+    BK(cudaEventCreateWithFlags(&b->join[1], cudaEventDisableTiming));
+#undef BK
+    *out = b;
+    return PF_OK;
+}
+
+int pf_batch_step(pf_batch *b, int32_t n_iters) {
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    if (n_iters < 0) return fail(PF_EINVAL, "n_iters < 0");
+    for (int32_t i = 0; i < n_iters; ++i) {
+        int active = 0;
+        while (active < (int)b->remaining.size() && b->remaining[active] > 0) ++active;
+        if (active == 0) break;
+        cudaGraphExec_t x = nullptr;
+        int rc = batch_phase_graph(b, active, &x);
+        if (rc) return rc;
+        CU(cudaGraphLaunch(x, b->stream));
+        int kernels = 4;   // prediction, scores, weights, update
+        for (int k = 0; k < 3; ++k) kernels += list_prefix(b, k, active) > 0;
+        count_launches(kernels);
+        for (int r = 0; r < active; ++r) --b->remaining[r];
+    }
+    return PF_OK;
+}
+
+int pf_batch_run(pf_batch *b) {
+    if (!b) return fail(PF_EINVAL, "batch is NULL");
+    return pf_batch_step(b, b->remaining.empty() ? 0 : b->remaining[0]);
+}
+
+int pf_batch_destroy(pf_batch *b) {
+    if (!b) return PF_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    delete b;
+    return PF_OK;
+}
+
+}  // extern "C"

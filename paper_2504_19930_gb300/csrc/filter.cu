@@ -30,120 +30,146 @@ __global__ void k_init(const FilterParams P, float *poses) {
 // eps = (u1+u2+u3+u4 - 2) sqrt(3) from Philox counter (i, k, PERTURB, d),
 // scale sigma_kd = sigma0_frac * L_d * decay^k, clamped to the limits), then
 // the pose -> matrix map of Eq. 3 and zeroed moment accumulators.
-__global__ void k_predict(const FilterParams P, const FilterBuffers B) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
+//
+// One particle per group of 8 lanes: lane d < 6 perturbs DOF d; lanes 0-2
+// take sin of the three angles and lanes 3-5 their cos (fp64 runs at 2
+// operations per clock per SM on this part, so spreading the six series over
+// lanes and over many small blocks is what bounds this kernel's latency);
+// lane 0 assembles the matrix.  Every lane of the group must call this.
+constexpr int kGroup = 8;
+
+__device__ __forceinline__ void predict_particle(const FilterParams &P, const FilterBuffers &B, int i, int j,
+                                                 unsigned gmask, int gbase) {
     const int k = *B.k;
-    float x[6];
-#pragma unroll
-    for (int d = 0; d < 6; ++d) x[d] = B.poses[(size_t)d * P.N + i];
-    if (k > 0) {
+    float x = j < 6 ? B.poses[(size_t)j * P.N + i] : 0.0f;
+    if (k > 0 && j < 6) {
         double pk = 1.0;
-        for (int j = 0; j < k; ++j) pk = __dmul_rn(pk, (double)P.sigma_decay);
+        for (int q = 0; q < k; ++q) pk = __dmul_rn(pk, (double)P.sigma_decay);
         const float sqrt3 = 1.7320508075688772f;
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            const float sig = __double2float_rn(__dmul_rn(__dmul_rn((double)P.sigma0_frac, (double)P.lim[d]), pk));
-            const u32x4 r = philox_seeded(P.seed, (uint32_t)i, (uint32_t)k, kStreamPerturb, (uint32_t)d);
-            const float e = __fmul_rn(
-                __fsub_rn(__fadd_rn(__fadd_rn(__fadd_rn(unit24(r.x), unit24(r.y)), unit24(r.z)), unit24(r.w)), 2.0f),
-                sqrt3);
-            float v = __fadd_rn(x[d], __fmul_rn(sig, e));
-            if (v > P.lim[d]) v = P.lim[d];
-            if (v < -P.lim[d]) v = -P.lim[d];
-            x[d] = v;
-            B.poses[(size_t)d * P.N + i] = v;
-        }
+        const float sig = __double2float_rn(__dmul_rn(__dmul_rn((double)P.sigma0_frac, (double)P.lim[j]), pk));
+        const u32x4 r = philox_seeded(P.seed, (uint32_t)i, (uint32_t)k, kStreamPerturb, (uint32_t)j);
+        const float e = __fmul_rn(
+            __fsub_rn(__fadd_rn(__fadd_rn(__fadd_rn(unit24(r.x), unit24(r.y)), unit24(r.z)), unit24(r.w)), 2.0f),
+            sqrt3);
+        float v = __fadd_rn(x, __fmul_rn(sig, e));
+        if (v > P.lim[j]) v = P.lim[j];
+        if (v < -P.lim[j]) v = -P.lim[j];
+        x = v;
+        B.poses[(size_t)j * P.N + i] = v;
     }
-    float M[12];
-    pose_to_matrix(x, P.g, M);
+    // lanes 0-2: sin(angle j); lanes 3-5: cos(angle j-3)
+    const float ang = __shfl_sync(gmask, x, gbase + (j < 3 ? j : (j < 6 ? j - 3 : 0)));
+    double tv = 0.0;
+    if (j < 3) tv = taylor_sin((double)ang);
+    else if (j < 6) tv = taylor_cos((double)ang);
+    double sc[6];
+    float pose[6];
 #pragma unroll
-    for (int j = 0; j < 12; ++j) B.mats[(size_t)i * 12 + j] = M[j];
+    for (int q = 0; q < 6; ++q) {
+        sc[q] = __shfl_sync(gmask, tv, gbase + q);
+        pose[q] = __shfl_sync(gmask, x, gbase + q);
+    }
+    if (j == 0) {
+        float M[12];
+        matrix_from_sincos(pose, sc[0], sc[3], sc[1], sc[4], sc[2], sc[5], P.g, M);
 #pragma unroll
-    for (int j = 0; j < kMomStride; ++j) B.mom[(size_t)i * kMomStride + j] = 0ull;
+        for (int q = 0; q < 12; ++q) B.mats[(size_t)i * 12 + q] = M[q];
+    }
+    for (int q = j; q < kMomStride; q += kGroup) B.mom[(size_t)i * kMomStride + q] = 0ull;
+    if (i == 0 && j == kGroup - 1) {   // accumulators of the score kernel
+        B.stats[0] = 0ull;
+        B.stats[1] = 0ull;
+    }
+}
+
+__global__ void __launch_bounds__(32) k_predict(const FilterParams P, const FilterBuffers B) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) / kGroup;   // whole groups exit together
+    if (g >= P.N) return;
+    const int lane = threadIdx.x & 31, gbase = lane & ~(kGroup - 1);
+    predict_particle(P, B, g, lane - gbase, 0xFFu << gbase, gbase);
 }
 
 constexpr int kFinThreads = 1024;
 constexpr int kFinWarps = kFinThreads / 32;
 
-__device__ __forceinline__ double block_sum_f64(double v, double *sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < 32) {
-        t = sh[threadIdx.x];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t = __dadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
-        if (threadIdx.x == 0) sh[0] = t;
-    }
-    __syncthreads();
-    return sh[0];
-}
+constexpr int kCdfSmem = 12288;            // CDF entries staged in shared memory (96 KiB)
 
-// Update, estimation and resampling of one iteration, in one CTA:
-//   1. score s_i from the integer moments (Eq. 2 / Eq. 4), max s (first index);
-//   2. W_i = floor((s_i / max s)^(2^g) * 2^24);
-//   3. inclusive integer scan C of W (warp shuffles + warp totals);
-//   4. estimate = sum W_i x_i / sum W_i per DOF (fp64), effective sample size;
-//   5. systematic resampling: T_j = floor((j 2^32 + u) S / (N 2^32)),
-//      a_j = min{i : C_i > T_j} (binary search), gather the poses;
-//   6. log the iteration and advance k.
-__global__ void __launch_bounds__(kFinThreads) k_finalise(const FilterParams P, const FilterBuffers B) {
-    __shared__ double sh_d[kFinWarps];
-    __shared__ unsigned long long sh_u[kFinWarps];
-    __shared__ int sh_i[kFinWarps];
-    __shared__ double sh_best;
-    __shared__ int sh_best_idx;
-    __shared__ unsigned long long sh_evals;
-    const int N = P.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int k = *B.k;
-
-    // 1. scores and the arg-max (smallest index among equal maxima)
-    double bmax = -1.0;
-    int bidx = INT_MAX;
-    unsigned long long evals = 0;
-    const int n_col = (P.mode == 2 || P.mode == 3) ? 0 : 8;
-    for (int i = tid; i < N; i += kFinThreads) {
+// Update, part 1 (one thread per particle, many CTAs): score s_i from the
+// integer moments (Eq. 2 / Eq. 4); the maximum score, kept as the bits of a
+// non-negative double (which order like the values) by a 64-bit atomic max,
+// and the number of evaluations (sum of the overlap counts).  stats[0..1] are
+// zeroed by the prediction kernel.
+__device__ __forceinline__ void score_particle(const FilterParams &P, const FilterBuffers &B, int i, bool valid) {
+    double s = 0.0;
+    unsigned long long ev = 0;
+    if (valid) {
         const unsigned long long *m = B.mom + (size_t)i * kMomStride;
-        const double s = score_from_moments(P.mode, m, P.b_full, P.n_min);
+        s = score_from_moments(P.mode, m, P.b_full, P.n_min);
         B.scores[i] = s;
-        evals += m[n_col];
-        if (s > bmax) { bmax = s; bidx = i; }
+        ev = m[(P.mode == 2 || P.mode == 3) ? 0 : 8];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) evals += __shfl_xor_sync(0xffffffffu, evals, o);
-    if (lane == 0) sh_u[warp] = evals;
+    unsigned long long bits = (unsigned long long)__double_as_longlong(s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bmax, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-        if (ov > bmax || (ov == bmax && oi < bidx)) { bmax = ov; bidx = oi; }
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+        bits = ob > bits ? ob : bits;
+        ev += __shfl_xor_sync(0xffffffffu, ev, o);
     }
-    if (lane == 0) { sh_d[warp] = bmax; sh_i[warp] = bidx; }
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long ev = 0;
-        for (int w = 0; w < kFinWarps; ++w) ev += sh_u[w];
-        sh_evals = ev;
-        double m = sh_d[0];
-        int mi = sh_i[0];
-        for (int w = 1; w < kFinWarps; ++w)
-            if (sh_d[w] > m || (sh_d[w] == m && sh_i[w] < mi)) { m = sh_d[w]; mi = sh_i[w]; }
-        sh_best = m;
-        sh_best_idx = mi;
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(B.stats + 0, bits);
+        if (ev) atomicAdd(B.stats + 1, ev);
     }
-    __syncthreads();
-    const double smax = sh_best > 0.0 ? sh_best : 0.0;
+}
 
-    // 2. quantised likelihood weights
-    for (int i = tid; i < N; i += kFinThreads) B.W[i] = quantised_weight(B.scores[i], smax, P.gamma_log2);
-    __syncthreads();
+// Update, part 2: W_i = floor((s_i / max s)^(2^g) * 2^24).
+__device__ __forceinline__ void weight_particle(const FilterParams &P, const FilterBuffers &B, int i) {
+    const double smax = __longlong_as_double((long long)B.stats[0]);
+    B.W[i] = quantised_weight(B.scores[i], smax > 0.0 ? smax : 0.0, P.gamma_log2);
+}
 
-    // 3. inclusive scan C of W, 1024 at a time with a running carry
+__global__ void __launch_bounds__(128) k_score(const FilterParams P, const FilterBuffers B) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    score_particle(P, B, i, i < P.N);
+}
+
+__global__ void __launch_bounds__(128) k_weights(const FilterParams P, const FilterBuffers B) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < P.N) weight_particle(P, B, i);
+}
+
+// Update, part 3, estimation and resampling of one iteration, in one CTA:
+//   1. arg-max: the first particle whose score equals the maximum;
+//   2. inclusive integer scan C of W (warp shuffles + warp totals), staged
+//      in shared memory when it fits;
+//   3. estimate = sum W_i x_i / sum W_i per DOF (fp64, before resampling)
+//      and sum W_i^2 (effective sample size), one 7-value block reduction;
+//   4. systematic resampling: T_j = floor((j 2^32 + u) S / (N 2^32)),
+//      a_j = min{i : C_i > T_j} (binary search), gather the poses;
+//   5. log the iteration and advance k.
+__device__ __forceinline__ void finalise_block(const FilterParams &P, const FilterBuffers &B) {
+    extern __shared__ unsigned long long sh_cdf[];
+    __shared__ double sh_d[kFinWarps][7];
+    __shared__ unsigned long long sh_u[kFinWarps];
+    __shared__ int sh_i[kFinWarps];
+    __shared__ double sh_est[7];
+    __shared__ int sh_best_idx;
+    const int N = P.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int k = *B.k;
+    const bool cdf_in_smem = N <= kCdfSmem;
+    const unsigned long long smax_bits = B.stats[0];
+
+    // 1. first index attaining the maximum
+    int bidx = INT_MAX;
+    for (int i = tid; i < N; i += kFinThreads)
+        if ((unsigned long long)__double_as_longlong(B.scores[i]) == smax_bits) {
+            bidx = i;
+            break;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bidx = min(bidx, __shfl_xor_sync(0xffffffffu, bidx, o));
+    if (lane == 0) sh_i[warp] = bidx;
+
+    // 2. inclusive scan C of W, 1024 at a time with a running carry
     unsigned long long carry = 0;
     for (int base = 0; base < N; base += kFinThreads) {
         const int i = base + tid;
@@ -166,33 +192,48 @@ __global__ void __launch_bounds__(kFinThreads) k_finalise(const FilterParams P, 
         }
         __syncthreads();
         const unsigned long long off = (warp > 0 ? sh_u[warp - 1] : 0ull) + carry;
-        if (i < N) B.C[i] = v + off;
+        if (i < N) {
+            B.C[i] = v + off;
+            if (cdf_in_smem) sh_cdf[i] = v + off;
+        }
         carry += sh_u[kFinWarps - 1];
         __syncthreads();
     }
     const unsigned long long S = carry;
 
-    // 4. estimate (before resampling) and effective sample size
-    double est[6];
-    for (int d = 0; d < 6; ++d) {
-        double acc = 0.0;
-        for (int i = tid; i < N; i += kFinThreads) {
-            const double x = (double)B.poses[(size_t)d * N + i];
-            acc = __dadd_rn(acc, S > 0 ? __dmul_rn((double)B.W[i], x) : x);
-        }
-        const double tot = block_sum_f64(acc, sh_d);
-        est[d] = S > 0 ? __ddiv_rn(tot, (double)S) : __ddiv_rn(tot, (double)N);
-    }
-    double w2 = 0.0;
+    // 3. estimate and sum of squared weights, one block reduction of 7 values
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = tid; i < N; i += kFinThreads) {
         const double w = (double)B.W[i];
-        w2 = __dadd_rn(w2, __dmul_rn(w, w));
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const double x = (double)B.poses[(size_t)d * N + i];
+            acc[d] = __dadd_rn(acc[d], S > 0 ? __dmul_rn(w, x) : x);
+        }
+        acc[6] = __dadd_rn(acc[6], __dmul_rn(w, w));
     }
-    w2 = block_sum_f64(w2, sh_d);
-
-    // 5. resampling: keep the measured cloud, gather the copies
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[d] = __dadd_rn(acc[d], __shfl_xor_sync(0xffffffffu, acc[d], o));
+        if (lane == 0) sh_d[warp][d] = acc[d];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int bi = sh_i[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bi = min(bi, __shfl_xor_sync(0xffffffffu, bi, o));
+        if (lane == 0) sh_best_idx = bi;
+        if (lane < 7) {
+            double t = 0.0;
+            for (int w = 0; w < kFinWarps; ++w) t = __dadd_rn(t, sh_d[w][lane]);
+            sh_est[lane] = t;
+        }
+    }
+    // 4. resampling: keep the measured cloud, gather the copies
     for (size_t e = tid; e < (size_t)6 * N; e += kFinThreads) B.poses_meas[e] = B.poses[e];
     __syncthreads();
+    const unsigned long long *cdf = cdf_in_smem ? sh_cdf : B.C;
     const uint32_t u = philox_seeded(P.seed, 0u, (uint32_t)k, kStreamResample, 0u).x;
     for (int j = tid; j < N; j += kFinThreads) {
         int a = j;
@@ -203,7 +244,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalise(const FilterParams P, 
             int lo = 0, hi = N - 1;          // first i with C_i > T (exists: C_{N-1} = S > T)
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (B.C[mid] > T) hi = mid; else lo = mid + 1;
+                if (cdf[mid] > T) hi = mid; else lo = mid + 1;
             }
             a = lo;
         }
@@ -212,33 +253,113 @@ __global__ void __launch_bounds__(kFinThreads) k_finalise(const FilterParams P, 
         for (int d = 0; d < 6; ++d) B.poses[(size_t)d * N + j] = B.poses_meas[(size_t)d * N + a];
     }
 
-    // 6. log and advance the iteration counter
+    // 5. log and advance the iteration counter
     if (tid == 0) {
         IterLog &L = B.log[k % P.log_capacity];
-        for (int d = 0; d < 6; ++d) L.est[d] = est[d];
-        L.best = sh_best;
+        for (int d = 0; d < 6; ++d)
+            L.est[d] = S > 0 ? __ddiv_rn(sh_est[d], (double)S) : __ddiv_rn(sh_est[d], (double)N);
+        L.best = __longlong_as_double((long long)smax_bits);
         L.best_idx = sh_best_idx;
-        L.evals = sh_evals;
+        L.evals = B.stats[1];
         L.est_dice = -1.0;
-        const double Sd = (double)S;
+        const double Sd = (double)S, w2 = sh_est[6];
         L.ess = w2 > 0.0 ? Sd * Sd / w2 : 0.0;
         L.k = k;
         *B.k = k + 1;
     }
 }
 
+__global__ void __launch_bounds__(kFinThreads) k_finalise(const FilterParams P, const FilterBuffers B) {
+    finalise_block(P, B);
+}
+
+// Batched prediction: group of 8 lanes -> (registration, particle) by binary
+// search on the particle prefix; registrations that have finished are skipped
+// (every lane of a group takes the same branch).
+__global__ void __launch_bounds__(32) k_predict_batch(const BatchReg *__restrict__ regs,
+                                                      const long long *__restrict__ poffs, int nregs) {
+    const long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGroup;
+    if (g >= poffs[nregs]) return;
+    int lo = 0, hi = nregs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (poffs[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const BatchReg &R = regs[lo];
+    if (*R.B.k >= R.n_iters) return;
+    const int lane = threadIdx.x & 31, gbase = lane & ~(kGroup - 1);
+    predict_particle(R.P, R.B, (int)(g - poffs[lo]), lane - gbase, 0xFFu << gbase, gbase);
+}
+
+// Batched update: scores and weights over all particles, each registration's
+// particles padded to whole warps (poffs32) so that every warp belongs to one
+// registration; then one CTA per registration.
+__device__ __forceinline__ int find_reg(const long long *offs, int n, long long g) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128) k_score_batch(const BatchReg *__restrict__ regs,
+                                                     const long long *__restrict__ poffs32, int nregs) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gw = g & ~31ll;                   // warp-uniform
+    if (gw >= poffs32[nregs]) return;
+    const int r = find_reg(poffs32, nregs, gw);
+    const BatchReg &R = regs[r];
+    if (*R.B.k >= R.n_iters) return;
+    const int i = (int)(g - poffs32[r]);
+    score_particle(R.P, R.B, i, i < R.P.N);
+}
+
+__global__ void __launch_bounds__(128) k_weights_batch(const BatchReg *__restrict__ regs,
+                                                       const long long *__restrict__ poffs32, int nregs) {
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= poffs32[nregs]) return;
+    const int r = find_reg(poffs32, nregs, g);
+    const BatchReg &R = regs[r];
+    if (*R.B.k >= R.n_iters) return;
+    const int i = (int)(g - poffs32[r]);
+    if (i < R.P.N) weight_particle(R.P, R.B, i);
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_finalise_batch(const BatchReg *__restrict__ regs) {
+    const BatchReg &R = regs[blockIdx.x];
+    if (*R.B.k >= R.n_iters) return;   // block-uniform: before any barrier
+    finalise_block(R.P, R.B);
+}
+
+// Matrix of one pose by a group of 8 lanes (lanes 0-2: sin of the angles,
+// 3-5: their cos; lane 0 assembles); every lane of the group calls this and
+// lane 0 holds M on return.
+__device__ __forceinline__ void group_pose_matrix(const float pose[6], int j, unsigned gmask, int gbase,
+                                                  const Geometry &g, float M[12]) {
+    double tv = 0.0;
+    if (j < 3) tv = taylor_sin((double)pose[j]);
+    else if (j < 6) tv = taylor_cos((double)pose[j - 3]);
+    double sc[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sc[q] = __shfl_sync(gmask, tv, gbase + q);
+    if (j == 0) matrix_from_sincos(pose, sc[0], sc[3], sc[1], sc[4], sc[2], sc[5], g, M);
+}
+
 // Estimate of iteration k-1 (the counter has advanced) rounded to fp32, as
 // the pose whose matrix the masks are warped with; zeroes the counts.
 __global__ void k_trace_prepare(const FilterParams P, const FilterBuffers B) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= kGroup) return;
+    const int j = threadIdx.x;
     const int k = *B.k - 1;
     const IterLog &L = B.log[k % P.log_capacity];
     float pose[6];
     for (int d = 0; d < 6; ++d) pose[d] = __double2float_rn(L.est[d]);
     float M[12];
-    pose_to_matrix(pose, P.g, M);
-    for (int j = 0; j < 12; ++j) B.trace_mat[j] = M[j];
-    for (int j = 0; j < kMomStride; ++j) B.trace_mom[j] = 0ull;
+    group_pose_matrix(pose, j, 0xFFu, 0, P.g, M);
+    if (j == 0)
+        for (int q = 0; q < 12; ++q) B.trace_mat[q] = M[q];
+    for (int q = j; q < kMomStride; q += kGroup) B.trace_mom[q] = 0ull;
 }
 
 // Dice (Eq. 4, whole target grid, no overlap threshold) of the estimate.
@@ -275,12 +396,13 @@ __global__ void k_binarise(const uint8_t *in, uint8_t *out, int64_t n) {
 }
 
 __global__ void k_pose_matrix(const float *pose, Geometry g, float *out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        float x[6], M[12];
-        for (int d = 0; d < 6; ++d) x[d] = pose[d];
-        pose_to_matrix(x, g, M);
-        for (int j = 0; j < 12; ++j) out[j] = M[j];
-    }
+    if (blockIdx.x != 0 || threadIdx.x >= kGroup) return;
+    const int j = threadIdx.x;
+    float x[6], M[12];
+    for (int d = 0; d < 6; ++d) x[d] = pose[d];
+    group_pose_matrix(x, j, 0xFFu, 0, g, M);
+    if (j == 0)
+        for (int q = 0; q < 12; ++q) out[q] = M[q];
 }
 
 __global__ void k_score_one(int mode, const unsigned long long *mom, unsigned long long b_full,
@@ -311,14 +433,40 @@ cudaError_t launch_init_particles(const FilterParams &p, const FilterBuffers &b,
 }
 
 cudaError_t launch_predict(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
-    k_predict<<<blocks_for(p.N, 128), 128, 0, s>>>(p, b);
+    k_predict<<<blocks_for((int64_t)p.N * kGroup, 32), 32, 0, s>>>(p, b);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalise(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
-    k_finalise<<<1, kFinThreads, 0, s>>>(p, b);
+cudaError_t launch_predict_batch(const BatchReg *regs, const long long *poffs, int nregs, long long total,
+                                 cudaStream_t s) {
+    if (nregs <= 0 || total <= 0) return cudaSuccess;
+    k_predict_batch<<<blocks_for(total * kGroup, 32), 32, 0, s>>>(regs, poffs, nregs);
     count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalise_batch(const BatchReg *regs, const long long *poffs32, int nregs, long long total32,
+                                  cudaStream_t s) {
+    if (nregs <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_finalise_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kCdfSmem * sizeof(unsigned long long)));
+    if (e != cudaSuccess) return e;
+    k_score_batch<<<blocks_for(total32, 128), 128, 0, s>>>(regs, poffs32, nregs);
+    k_weights_batch<<<blocks_for(total32, 128), 128, 0, s>>>(regs, poffs32, nregs);
+    k_finalise_batch<<<nregs, kFinThreads, kCdfSmem * sizeof(unsigned long long), s>>>(regs);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalise(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_finalise, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(kCdfSmem * sizeof(unsigned long long)));
+    if (e != cudaSuccess) return e;
+    k_score<<<blocks_for(p.N, 128), 128, 0, s>>>(p, b);
+    k_weights<<<blocks_for(p.N, 128), 128, 0, s>>>(p, b);
+    k_finalise<<<1, kFinThreads, kCdfSmem * sizeof(unsigned long long), s>>>(p, b);
+    count_launches(3);
     return cudaGetLastError();
 }
 

@@ -60,11 +60,13 @@ struct FilterBuffers {
     int32_t *idx;               // [N]
     int32_t *k;                 // iteration counter (device)
     IterLog *log;               // [log_capacity]
+    unsigned long long *stats;  // [2] max score (fp64 bits) and evaluation count of the iteration
     float *trace_mat;           // [12] matrix of the estimate (tracing)
     unsigned long long *trace_mom;   // [12] its mask counts (tracing)
 };
 
 cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream_t s);
+long long measure_items(const MeasureArgs &a);   // work items of one measurement launch
 cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_t *quad, cudaStream_t s);
 int rows_per_item_for(int target_x);
 cudaError_t launch_init_particles(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
@@ -90,6 +92,29 @@ struct WarpFrames {
 };
 cudaError_t launch_warp(const WarpFrames &f, int n, const float pose[6], Geometry g, int interp,
                         cudaStream_t s);
+
+// One registration of a batch (device table entry): its measurement
+// arguments, filter parameters and buffers, and its iteration count.
+struct BatchReg {
+    MeasureArgs ma;
+    FilterParams P;
+    FilterBuffers B;
+    int32_t n_iters;
+    int32_t img, mask;
+};
+
+// Batched kernels over many registrations: measurement over the listed
+// registrations' concatenated items (offs = item prefix), prediction over all
+// particles (poffs = particle prefix), and the update: scores and weights over
+// all particles with each registration padded to whole warps (poffs32), then
+// one CTA per registration.
+// Registrations whose iteration counter has reached n_iters are skipped.
+cudaError_t launch_measure_batch(const BatchReg *regs, const int32_t *list, const long long *offs, int nlist,
+                                 long long total_items, bool img, bool mask, cudaStream_t s);
+cudaError_t launch_predict_batch(const BatchReg *regs, const long long *poffs, int nregs, long long total,
+                                 cudaStream_t s);
+cudaError_t launch_finalise_batch(const BatchReg *regs, const long long *poffs32, int nregs, long long total32,
+                                  cudaStream_t s);
 
 // Process-wide count of kernel launches issued by this library (launches
 // recorded while a CUDA graph is being captured are not counted; each graph

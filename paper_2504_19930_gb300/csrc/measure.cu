@@ -41,10 +41,6 @@ __device__ __forceinline__ float byte_biased(uint32_t w, uint32_t k) {
     return __uint_as_float(__byte_perm(w, kTwo23Bits, 0x7540u | k));
 }
 
-// lerp with biased end points A = 2^23 + a, B = 2^23 + b: a + f*(b - a).
-__device__ __forceinline__ float lerp_biased(float A, float B, float f) {
-    return __fadd_rn(__fsub_rn(A, kTwo23), __fmul_rn(f, __fsub_rn(B, A)));
-}
 
 // Integer value of an integral float v in [0, 2^22).
 __device__ __forceinline__ uint32_t int_of(float v) {
@@ -283,124 +279,153 @@ __device__ __forceinline__ void exact_interval(const float r0[3], const float K[
     xr = constant_ok ? pr : xl - 1;
 }
 
-// Measurement kernel.  Work item = (particle, 32 target rows), taken by one
-// warp; each warp takes kItemsPerWarp consecutive items (spatially adjacent
-// rows of one particle) and the grid covers all items in several waves, so
-// no block barrier is needed after the optional shared-memory load of the
-// mask and finished CTAs are replaced by fresh ones.
-// EXACT (single-mode kernels): lanes first find their row's exact inside
-// interval, and the sweep evaluates only inside voxels.
-#ifndef PF_MEASURE_MIN_BLOCKS
-#define PF_MEASURE_MIN_BLOCKS 1
-#endif
-template <bool IMG, bool MASK, bool MASK_SMEM>
-__global__ void __launch_bounds__(kThreads, PF_MEASURE_MIN_BLOCKS) k_measure(const MeasureArgs a) {
-    extern __shared__ uint32_t smem_bits[];
+// One work item = (particle p, 32 target rows), processed by one warp: lane l
+// prepares row (first + l) -- hoisted K and its x-range (exact when EXACT) --
+// then the warp sweeps the rows, reduces the moments and adds them to
+// mom[p] with one integer atomic each (S2 is 128-bit).
+template <bool IMG, bool MASK>
+__device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_t *__restrict__ bits,
+                                             long long item, int lane) {
     constexpr bool EXACT = IMG != MASK;
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
     const int TX = a.g.td[0], TY = a.g.td[1];
     const int rows = a.g.td[1] * a.g.td[2];
-
-    const uint32_t *bits = a.src_bits;
-    if (MASK && MASK_SMEM) {
-        const int nwords = (int)(((size_t)SX * SY * SZ + 31) / 32);
-        for (int i = threadIdx.x; i < nwords; i += kThreads) smem_bits[i] = a.src_bits[i];
-        __syncthreads();
-        bits = smem_bits;
-    }
     float lo[3], hi[3];
     lo[0] = lo[1] = lo[2] = MASK ? -0.5f : 0.0f;
     hi[0] = MASK ? (float)SX - 0.5f : (float)(SX - 1);
     hi[1] = MASK ? (float)SY - 0.5f : (float)(SY - 1);
     hi[2] = MASK ? (float)SZ - 0.5f : (float)(SZ - 1);
     const float D[3] = {(float)SX, (float)SY, (float)SZ};
-
     const int nblocks = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
-    const long long items = (long long)a.P * nblocks;
+
+    const int p = (int)(item / nblocks);
+    const int rb = (int)(item - (long long)p * nblocks);
+    const float *Mp = a.mats + 12 * (size_t)p;
+    float M[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) M[i] = __ldg(Mp + i);
+    const float r0[3] = {M[0], M[4], M[8]};
+    ImgAcc ia;
+    MaskAcc ma;
+
+    const int first = rb * kRowsPerWarp;
+    const int my_row = first + lane;
+    float myK0 = 0.0f, myK1 = 0.0f, myK2 = 0.0f;
+    int my_xb = 0, my_xe = 0;
+    if (my_row < rows) {
+        const int y = my_row % TY, z = my_row / TY;
+        const float dy = __fsub_rn((float)y, a.g.a[1]);
+        const float dz = __fsub_rn((float)z, a.g.a[2]);
+        myK0 = row_K(M[1], M[2], M[3], dy, dz);
+        myK1 = row_K(M[5], M[6], M[7], dy, dz);
+        myK2 = row_K(M[9], M[10], M[11], dy, dz);
+        const float K[3] = {myK0, myK1, myK2};
+        row_interval(r0, K, a.g.a[0], lo, hi, TX, my_xb, my_xe);
+        if (EXACT && my_xb < my_xe) {
+            int xl, xr;
+            exact_interval<IMG>(r0, K, a.g.a[0], D, my_xb, my_xe, xl, xr);
+            my_xb = xl;
+            my_xe = xr + 1;
+        }
+    }
+    const int nrows = min(kRowsPerWarp, rows - first);
+    for (int j = 0; j < nrows; ++j) {
+        const int xb = __shfl_sync(0xffffffffu, my_xb, j);
+        const int xe = __shfl_sync(0xffffffffu, my_xe, j);
+        if (xb >= xe) continue;                       // warp-uniform
+        Row row;
+        row.K0 = __shfl_sync(0xffffffffu, myK0, j);
+        row.K1 = __shfl_sync(0xffffffffu, myK1, j);
+        row.K2 = __shfl_sync(0xffffffffu, myK2, j);
+        row.trow = (uint32_t)(first + j) * (uint32_t)TX;
+        int x = xb + lane;
+        float xf = (float)x;
+        for (; x < xe; x += 64, xf = __fadd_rn(xf, 64.0f))
+            eval_pair<IMG, MASK, EXACT>(a, bits, r0[0], r0[1], r0[2], row, x, xf, x + 32 < xe, ia, ma);
+        if (IMG) {
+            ia.S1 += ia.S1row;
+            ia.S1row = 0;
+        }
+    }
+
+    // warp reduction and one integer atomic per moment (S2: 128-bit)
+    unsigned long long *dst = a.mom + (size_t)p * kMomStride;
+    if (IMG) {
+        const unsigned long long n = __reduce_add_sync(0xffffffffu, ia.n);
+        const unsigned long long S1 = warp_sum64(ia.S1), S2 = warp_sum64(ia.S2), ST = warp_sum64(ia.ST);
+        const unsigned long long T1 = warp_sum64(ia.T1), T2 = warp_sum64(ia.T2);
+        if (lane == 0 && n) {
+            atomicAdd(dst + 0, n);
+            atomicAdd(dst + 1, S1);
+            const unsigned long long old = atomicAdd(dst + 2, S2);
+            if (old + S2 < old) atomicAdd(dst + 3, 1ull);   // carry into S2's high word
+            atomicAdd(dst + 4, ST);
+            atomicAdd(dst + 5, T1);
+            atomicAdd(dst + 6, T2);
+        }
+    }
+    if (MASK) {
+        const unsigned long long n = __reduce_add_sync(0xffffffffu, ma.n);
+        const unsigned long long A = __reduce_add_sync(0xffffffffu, ma.A);
+        const unsigned long long B = __reduce_add_sync(0xffffffffu, ma.B);
+        const unsigned long long C = __reduce_add_sync(0xffffffffu, ma.C);
+        if (lane == 0 && n) {
+            atomicAdd(dst + 8, n);
+            if (A) atomicAdd(dst + 9, A);
+            if (B) atomicAdd(dst + 10, B);
+            if (C) atomicAdd(dst + 11, C);
+        }
+    }
+}
+
+// Measurement kernel of one registration.  Each warp takes kItemsPerWarp
+// consecutive items (spatially adjacent rows of one particle) and the grid
+// covers all items in several waves, so no block barrier is needed after the
+// optional shared-memory load of the mask and finished CTAs are replaced by
+// fresh ones.  Single-mode kernels visit only each row's exact inside
+// interval (EXACT).
+#ifndef PF_MEASURE_MIN_BLOCKS
+#define PF_MEASURE_MIN_BLOCKS 1
+#endif
+template <bool IMG, bool MASK, bool MASK_SMEM>
+__global__ void __launch_bounds__(kThreads, PF_MEASURE_MIN_BLOCKS) k_measure(const MeasureArgs a) {
+    extern __shared__ uint32_t smem_bits[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t *bits = a.src_bits;
+    if (MASK && MASK_SMEM) {
+        const int nwords = (int)(((size_t)a.g.sd[0] * a.g.sd[1] * a.g.sd[2] + 31) / 32);
+        for (int i = threadIdx.x; i < nwords; i += kThreads) smem_bits[i] = a.src_bits[i];
+        __syncthreads();
+        bits = smem_bits;
+    }
+    const int rows = a.g.td[1] * a.g.td[2];
+    const long long items = (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
     const long long item0 = ((long long)blockIdx.x * kWarps + warp) * kItemsPerWarp;
     const long long item1 = min(items, item0 + kItemsPerWarp);
+    for (long long item = item0; item < item1; ++item) measure_item<IMG, MASK>(a, bits, item, lane);
+}
+
+// Measurement of many registrations in one launch: the items of the listed
+// registrations are concatenated (offs = prefix of their item counts); each
+// item finds its registration by binary search, and registrations that have
+// run all their iterations are skipped.
+template <bool IMG, bool MASK>
+__global__ void __launch_bounds__(kThreads) k_measure_batch(const BatchReg *__restrict__ regs,
+                                                            const int32_t *__restrict__ list,
+                                                            const long long *__restrict__ offs, int nlist) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long total = offs[nlist];
+    const long long item0 = ((long long)blockIdx.x * kWarps + warp) * kItemsPerWarp;
+    const long long item1 = min(total, item0 + kItemsPerWarp);
     for (long long item = item0; item < item1; ++item) {
-        const int p = (int)(item / nblocks);
-        const int rb = (int)(item - (long long)p * nblocks);
-        const float *Mp = a.mats + 12 * (size_t)p;
-        float M[12];
-#pragma unroll
-        for (int i = 0; i < 12; ++i) M[i] = __ldg(Mp + i);
-        const float r0[3] = {M[0], M[4], M[8]};
-        ImgAcc ia;
-        MaskAcc ma;
-
-        // lane l prepares row (first + l): hoisted K and its x-range
-        const int first = rb * kRowsPerWarp;
-        const int my_row = first + lane;
-        float myK0 = 0.0f, myK1 = 0.0f, myK2 = 0.0f;
-        int my_xb = 0, my_xe = 0;
-        if (my_row < rows) {
-            const int y = my_row % TY, z = my_row / TY;
-            const float dy = __fsub_rn((float)y, a.g.a[1]);
-            const float dz = __fsub_rn((float)z, a.g.a[2]);
-            myK0 = row_K(M[1], M[2], M[3], dy, dz);
-            myK1 = row_K(M[5], M[6], M[7], dy, dz);
-            myK2 = row_K(M[9], M[10], M[11], dy, dz);
-            const float K[3] = {myK0, myK1, myK2};
-            row_interval(r0, K, a.g.a[0], lo, hi, TX, my_xb, my_xe);
-            if (EXACT && my_xb < my_xe) {
-                int xl, xr;
-                exact_interval<IMG>(r0, K, a.g.a[0], D, my_xb, my_xe, xl, xr);
-                my_xb = xl;
-                my_xe = xr + 1;
-            }
+        int lo = 0, hi = nlist - 1;                  // last r with offs[r] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= item) lo = mid; else hi = mid - 1;
         }
-        const int nrows = min(kRowsPerWarp, rows - first);
-        for (int j = 0; j < nrows; ++j) {
-            const int xb = __shfl_sync(0xffffffffu, my_xb, j);
-            const int xe = __shfl_sync(0xffffffffu, my_xe, j);
-            if (xb >= xe) continue;                       // warp-uniform
-            Row row;
-            row.K0 = __shfl_sync(0xffffffffu, myK0, j);
-            row.K1 = __shfl_sync(0xffffffffu, myK1, j);
-            row.K2 = __shfl_sync(0xffffffffu, myK2, j);
-            row.trow = (uint32_t)(first + j) * (uint32_t)TX;
-            int x = xb + lane;
-            float xf = (float)x;
-            for (; x < xe; x += 64, xf = __fadd_rn(xf, 64.0f))
-                eval_pair<IMG, MASK, EXACT>(a, bits, r0[0], r0[1], r0[2], row, x, xf, x + 32 < xe, ia, ma);
-            if (IMG) {
-                ia.S1 += ia.S1row;
-                ia.S1row = 0;
-            }
-        }
-
-        // warp reduction and one integer atomic per moment (S2: 128-bit)
-        unsigned long long *dst = a.mom + (size_t)p * kMomStride;
-        if (IMG) {
-            const unsigned long long n = __reduce_add_sync(0xffffffffu, ia.n);
-            const unsigned long long S1 = warp_sum64(ia.S1), S2 = warp_sum64(ia.S2), ST = warp_sum64(ia.ST);
-            const unsigned long long T1 = warp_sum64(ia.T1), T2 = warp_sum64(ia.T2);
-            if (lane == 0 && n) {
-                atomicAdd(dst + 0, n);
-                atomicAdd(dst + 1, S1);
-                const unsigned long long old = atomicAdd(dst + 2, S2);
-                if (old + S2 < old) atomicAdd(dst + 3, 1ull);   // carry into S2's high word
-                atomicAdd(dst + 4, ST);
-                atomicAdd(dst + 5, T1);
-                atomicAdd(dst + 6, T2);
-            }
-        }
-        if (MASK) {
-            const unsigned long long n = __reduce_add_sync(0xffffffffu, ma.n);
-            const unsigned long long A = __reduce_add_sync(0xffffffffu, ma.A);
-            const unsigned long long B = __reduce_add_sync(0xffffffffu, ma.B);
-            const unsigned long long C = __reduce_add_sync(0xffffffffu, ma.C);
-            if (lane == 0 && n) {
-                atomicAdd(dst + 8, n);
-                if (A) atomicAdd(dst + 9, A);
-                if (B) atomicAdd(dst + 10, B);
-                if (C) atomicAdd(dst + 11, C);
-            }
-        }
+        const BatchReg &R = regs[list[lo]];
+        if (*R.B.k >= R.n_iters) continue;          // warp-uniform
+        measure_item<IMG, MASK>(R.ma, R.ma.src_bits, item - offs[lo], lane);
     }
 }
 
@@ -450,6 +475,23 @@ cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_
     k_pack_quads<<<g, 256, 0, s>>>(src, dims[0], dims[1], dims[2], quad);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_measure_batch(const BatchReg *regs, const int32_t *list, const long long *offs, int nlist,
+                                 long long total_items, bool img, bool mask, cudaStream_t s) {
+    if (nlist <= 0 || total_items <= 0) return cudaSuccess;
+    const long long per_cta = (long long)kWarps * kItemsPerWarp;
+    const unsigned grid = (unsigned)((total_items + per_cta - 1) / per_cta);
+    if (img && mask) k_measure_batch<true, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist);
+    else if (img) k_measure_batch<true, false><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist);
+    else k_measure_batch<false, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+long long measure_items(const MeasureArgs &a) {
+    const int rows = a.g.td[1] * a.g.td[2];
+    return (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
 }
 
 cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream_t s) {

@@ -117,3 +117,11 @@ def test_trace_without_masks_is_rejected(pk):
     cfg = pk.make_config("image_ncc", trace_estimate=True)
     rc, ctx = _init_rc(pk, cfg, [v, v, None, None])
     assert rc == -1 and ctx is None and "trace_estimate" in pk.pf_last_error()
+
+
+def test_batch_arguments_are_validated(pk):
+    lib = pk.load()
+    out = C.c_void_p(7)
+    assert lib.pf_batch_create(C.byref(out), None, 0, None) == -1 and out.value is None
+    assert lib.pf_batch_step(None, 1) == -1 and lib.pf_batch_run(None) == -1
+    assert lib.pf_batch_destroy(None) == 0
