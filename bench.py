@@ -39,6 +39,7 @@ WORKLOADS = {
     "config1": dict(pfsynth.CONFIG1, kind="image_ncc", dims=(224, 208, 176)),
     "config0": dict(pfsynth.CONFIG0, kind="mask_dice", dims=(64, 64, 64), n_frames=0),
     "config2": dict(name="batch64_mixed_96to256_n512to8192_k20to60", kind="batch", n_regs=64),
+    "config4": dict(pfsynth.CONFIG4, kind="combined", dims=(256, 256, 256)),
 }
 METRIC = "particle-voxel evals/s (dense N*iters*target voxels per registration) and ms per registration"
 UNIT = "particle-voxel evals/s"
@@ -47,6 +48,9 @@ UNIT = "particle-voxel evals/s"
 # trilinear measurement: 3 mul + 3 add (coordinates), 3 floor, 3 subtract
 # (fractions), 7 lerps x 3 ops, 1 scale to 1/1024 fixed point.
 OPS_PER_EVAL = 34
+# nearest-neighbour mask sample: 3 mul + 3 add (coordinates), 3 add (+0.5),
+# 3 floor; the combined score does both on one coordinate.
+OPS_PER_EVAL_MODE = {"image_ncc": OPS_PER_EVAL, "mask_dice": 12, "combined": OPS_PER_EVAL + 6}
 FP32_LANES_PER_SM = 128
 
 # DRAM traffic of one measurement launch from an ncu capture (profiles/), with
@@ -176,7 +180,11 @@ def measured_peaks():
 
 def load_workload(name, rank):
     w = WORKLOADS[name]
-    if w["kind"] == "image_ncc":
+    if w["kind"] == "combined":
+        pair = pfsynth.cached(pfsynth.speckle_pair, rank, src_dims=w["dims"], with_masks=True,
+                              max_rot_deg=20.0, max_trans=15.0)
+        frames = pfsynth.cached(pfsynth.frame_sequence, pair, w["n_frames"])
+    elif w["kind"] == "image_ncc":
         pair = pfsynth.cached(pfsynth.speckle_pair, rank, with_masks=True)
         frames = pfsynth.cached(pfsynth.frame_sequence, pair, w["n_frames"]) if w["n_frames"] else None
     else:
@@ -196,9 +204,10 @@ def oracle_sample(w, pair, n_particles, n_iters):
     n_particles particles, n_iters iterations.  Returns (seconds, dense units)."""
     import oracle
     oracle.build()
-    kw = {}
     if w["kind"] == "image_ncc":
         kw = dict(src=pair.src, tgt=pair.tgt)
+    elif w["kind"] == "combined":
+        kw = dict(src=pair.src, tgt=pair.tgt, src_mask=pair.src_mask, tgt_mask=pair.tgt_mask)
     else:
         kw = dict(src_mask=pair.src, tgt_mask=pair.tgt)
     t0 = time.perf_counter()
@@ -261,8 +270,14 @@ def run_ours(args, rank, world, local):
     lr, lt = np.deg2rad(w["rot_limit_deg"]), w["trans_limit"]
     kind = w["kind"]
 
+    if kind == "combined":
+        smask_d = torch.from_numpy(pair.src_mask).to(dev)
+        tmask_d = torch.from_numpy(pair.tgt_mask).to(dev)
+
     def make_reg():
         vols = dict(src=src_d, tgt=tgt_d) if kind != "mask_dice" else dict(src_mask=src_d, tgt_mask=tgt_d)
+        if kind == "combined":
+            vols.update(src_mask=smask_d, tgt_mask=tmask_d)
         return pk.Registration(kind, src_origin=pair.src_origin, tgt_origin=pair.tgt_origin,
                                n_particles=w["n_particles"], rot_limit=lr, trans_limit=lt, seed=w["seed"],
                                **vols)
@@ -328,13 +343,15 @@ def run_ours(args, rank, world, local):
     mhz = clk["sm_mhz"] or peaks.get("sm_max_mhz") or 2070.0
     peak_ops = sm_count * FP32_LANES_PER_SM * mhz * 1e6
     meas_s = rec["measure_ms"] / 1e3
-    achieved = rec["evals"] * OPS_PER_EVAL / meas_s if meas_s > 0 else 0.0
+    ops = OPS_PER_EVAL_MODE[kind]
+    achieved = rec["evals"] * ops / meas_s if meas_s > 0 else 0.0
     sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "measure.cu"), "rb")
                        .read()).hexdigest()
     traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["measure_cu_sha1"] == sha else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TOP/s",
                 "frac": achieved / peak_ops if peak_ops else None, "traffic": traffic,
-                "kernel": "k_measure<image>", "ops_per_eval": OPS_PER_EVAL,
+                "kernel": {"image_ncc": "k_measure<image>", "mask_dice": "k_measure<mask>",
+                           "combined": "k_measure<image+mask>"}[kind], "ops_per_eval": ops,
                 "evals_per_launch": rec["evals"] / max(rec["measure_launches"], 1),
                 "avg_launch_ms": rec["measure_ms"] / max(rec["measure_launches"], 1),
                 "share_of_step": rec["measure_ms"] / sum(step_ms),
@@ -378,6 +395,9 @@ def run_ours(args, rank, world, local):
         fr_h = [torch.from_numpy(f).pin_memory() for f in frames] if frames is not None else []
         out_h = [torch.empty(pair.tgt.shape, dtype=torch.uint8).pin_memory() for _ in fr_h]
         mode_kw = dict(src=src_h, tgt=tgt_h) if kind != "mask_dice" else dict(src_mask=src_h, tgt_mask=tgt_h)
+        if kind == "combined":
+            mode_kw.update(src_mask=torch.from_numpy(pair.src_mask).pin_memory(),
+                           tgt_mask=torch.from_numpy(pair.tgt_mask).pin_memory())
 
         def e2e_step():
             return pk.register_sequence(kind, frames=fr_h, n_iters=w["n_iters"], src_origin=pair.src_origin,

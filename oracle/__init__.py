@@ -296,6 +296,14 @@ def register(mode, src_dims, src_origin, tgt_dims, tgt_origin, n_particles, n_it
         keep.append(a)
         return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
+    need = {MODES["image_ncc"]: (1, 1, 0, 0), MODES["mask_dice"]: (0, 0, 1, 1),
+            MODES["mask_ncc"]: (0, 0, 1, 1), MODES["combined"]: (1, 1, 1, 1)}[mode]
+    for v, n, name, dims in zip((src, tgt, src_mask, tgt_mask), need, ("src", "tgt", "src_mask", "tgt_mask"),
+                                (src_dims, tgt_dims, src_dims, tgt_dims)):
+        if n and v is None:
+            raise ValueError(f"register: mode needs {name}")
+        if v is not None and np.size(v) != int(np.prod(np.asarray(dims, np.int64))):
+            raise ValueError(f"register: {name} has {np.size(v)} voxels, dims are {tuple(dims)}")
     vols = [None if v is None else _c(v, np.uint8) for v in (src, tgt, src_mask, tgt_mask)]
     if trace:
         tr = dict(poses=np.zeros((K, 6, N), np.float32), mom=np.zeros((K, N, 12), np.uint64),

@@ -364,3 +364,33 @@ def test_estimate_dice_trace(pk, orc, mode):
         M, a = orc.pose_matrix(est[k].astype(np.float32), pair.src_dims, pair.src_origin, pair.tgt_origin)
         c = orc.measure_mask(pair.src_mask, pair.tgt_mask, M, a)[0]
         assert dice[k] == orc.dice_from_counts(c[0], c[1], c[3], bfull, 0), k
+
+
+def test_config4_full_size_sampled(pk, orc):
+    """The combined stress workload at full size (256^3 image + LV mask,
+    N=16384, +-45 deg / +-32 voxels, score 0.5 (NCC^2 + Dice)): one iteration
+    on the GPU; the oracle re-measures sampled particles (image moments and
+    mask counts) and recomputes every cheap step on the GPU's state."""
+    c = pfsynth.CONFIG4
+    pair = pfsynth.cached(pfsynth.speckle_pair, 0, src_dims=(256, 256, 256), with_masks=True,
+                          max_rot_deg=20.0, max_trans=15.0)
+    N, lr, lt, seed = c["n_particles"], np.deg2rad(c["rot_limit_deg"]), c["trans_limit"], c["seed"]
+    lim = np.array([lr] * 3 + [lt] * 3, np.float32)
+    nmin = int(float(np.float32(0.01)) * pair.tgt.size)
+    bfull = int((pair.tgt_mask != 0).sum())
+    with _reg(pk, "combined", pair, N, lr, lt, seed) as reg:
+        reg.step(1)
+        st = reg.state()
+        x = st["poses_measured"]
+        assert np.array_equal(x, orc.init_particles(N, seed, lim))
+        sample = np.random.default_rng(4).choice(N, 3, replace=False)
+        mats, a = orc.pose_matrices(x[:, sample], pair.src_dims, pair.src_origin, pair.tgt_origin)
+        assert np.array_equal(st["moments"][sample, 0:7], orc.measure_image(pair.src, pair.tgt, mats, a))
+        assert np.array_equal(st["moments"][sample, 8:12], orc.measure_mask(pair.src_mask, pair.tgt_mask, mats, a))
+        s = np.array([orc.score("combined", m, bfull, nmin) for m in st["moments"]])
+        assert np.array_equal(st["scores"], s)
+        W = orc.weights(s, 5)
+        assert np.array_equal(st["weights"], W)
+        idx = orc.resample(W, orc.resample_offset(seed, 0))
+        assert np.array_equal(st["resample_idx"], idx)
+        assert np.array_equal(st["poses_next"], x[:, idx])

@@ -136,3 +136,12 @@ def test_combined_mode_runs(orc):
     mom = r["tr_mom"][0]
     assert np.all(mom[:, 0] > 0) and np.all(mom[:, 8] > 0)
     assert np.all((r["tr_score"] >= 0) & (r["tr_score"] <= 1))
+
+
+def test_missing_or_misshapen_volumes_are_rejected(orc):
+    p = pfsynth.ellipsoid_pair(3, src_dims=(12, 11, 10), tgt_dims=(12, 11, 10), semi_axes=(4, 3, 3))
+    args = (p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, 8, 1, 0.1, 1.0)
+    with pytest.raises(ValueError, match="needs src"):
+        orc.register("combined", *args, src_mask=p.src, tgt_mask=p.tgt)
+    with pytest.raises(ValueError, match="voxels"):
+        orc.register("mask_dice", *args, src_mask=p.src[:-1], tgt_mask=p.tgt)
