@@ -159,6 +159,35 @@ int pf_batch_step(pf_batch *b, int32_t n_iters);
 int pf_batch_run(pf_batch *b);
 int pf_batch_destroy(pf_batch *b);
 
+/* ---- one iteration in two halves: the measurement sharded over processes ---- */
+
+/* The measurement is > 99 % of an iteration and each particle's moments are
+ * independent (Fig. 1 "measurement"), so several processes (one per GPU) can
+ * share one registration: each creates the same context (same volumes,
+ * config and seed), and per iteration
+ *   pf_step_measure(ctx, lo_r, hi_r)      on rank r, disjoint slices covering 0..N
+ *   element-wise integer SUM of the moment buffers over the ranks
+ *   pf_step_update(ctx)                   on every rank
+ * The prediction and the update are repeated on every rank (cheap and
+ * deterministic), so every rank holds the same cloud, bit for bit equal to
+ * pf_step on one GPU: outside its slice a rank's moments stay 0 and exactly
+ * one rank contributes each word, so the sum (in uint64 or int64) is exact.
+ *
+ * pf_step_measure: predict (k > 0: perturb) all N particles, zero all
+ * moments, measure particles p_begin .. p_end-1 (0 <= p_begin <= p_end <= N).
+ * pf_step_update: scores, weights, estimate, resampling, log (and the traced
+ * estimate Dice), k += 1.  Both are asynchronous on the context's stream;
+ * they are plain launches, not the iteration graph, and are not timed by
+ * pf_profile_*.  Errors: PF_EINVAL (NULL, slice out of range), PF_ECUDA. */
+int pf_step_measure(pf_ctx *ctx, int32_t p_begin, int32_t p_end);
+int pf_step_update(pf_ctx *ctx);
+
+/* The device address of the context's moment buffer, uint64 [N][12] (layout
+ * of pf_get_state), for a collective that sums it in place between the two
+ * halves.  Owned by the context; valid until pf_register_destroy.  *n_words =
+ * 12 N.  Errors: PF_EINVAL (NULL). */
+int pf_moments_device(pf_ctx *ctx, uint64_t **moments, int64_t *n_words);
+
 /* ---- inspection, checkpoint and test exports (host buffers, synchronous) ---- */
 
 /* Number of iterations run so far (the next iteration's index k). */

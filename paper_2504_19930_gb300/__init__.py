@@ -27,6 +27,7 @@ __all__ = [
     "warp_sequence", "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
     "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_kernel_launches", "pf_last_error",
     "pf_profile_begin", "pf_profile_end", "register_sequence", "pf_measure_matrices_noalloc",
+    "pf_step_measure", "pf_step_update", "pf_moments_device",
     "Batch", "pf_batch_create", "pf_batch_step", "pf_batch_run", "pf_batch_destroy",
     "Registration", "MODES", "build", "library_path",
 ]
@@ -106,6 +107,9 @@ def _declare(L):
     L.pf_batch_destroy.argtypes = [vp]
     L.pf_profile_begin.argtypes = [vp, i32]
     L.pf_profile_end.argtypes = [vp, vp, vp]
+    L.pf_step_measure.argtypes = [vp, i32, i32]
+    L.pf_step_update.argtypes = [vp]
+    L.pf_moments_device.argtypes = [vp, vp, vp]
     L.pf_kernel_launches.argtypes = []
     L.pf_kernel_launches.restype = u64
     L.pf_last_error.argtypes = []
@@ -209,6 +213,30 @@ def pf_register_init(src, tgt, src_mask, tgt_mask, cfg, stream=None):
 
 def pf_step(ctx, n_iters):
     _check(load().pf_step(ctx, int(n_iters)))
+
+
+def pf_step_measure(ctx, p_begin, p_end):
+    _check(load().pf_step_measure(ctx, int(p_begin), int(p_end)))
+
+
+def pf_step_update(ctx):
+    _check(load().pf_step_update(ctx))
+
+
+def pf_moments_device(ctx):
+    """(device address, number of uint64 words) of the context's moment buffer."""
+    ptr = C.c_void_p()
+    n = C.c_int64()
+    _check(load().pf_moments_device(ctx, C.byref(ptr), C.byref(n)))
+    return ptr.value, n.value
+
+
+class _DeviceWords:
+    """A device buffer of int64 words seen through ``__cuda_array_interface__``."""
+
+    def __init__(self, ptr, n):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<i8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None, "stream": None}
 
 
 def pf_estimate(ctx, with_score=True):
@@ -365,6 +393,19 @@ class Registration:
 
     def measure(self, mats, a):
         return pf_measure_matrices(self.ctx, mats, a)
+
+    # one iteration in two halves (the measurement sharded over processes)
+    def step_measure(self, p_begin, p_end):
+        pf_step_measure(self.ctx, p_begin, p_end)
+
+    def step_update(self):
+        pf_step_update(self.ctx)
+
+    def moments(self):
+        """The moment buffer as a CUDA int64 tensor [12 N] (a view, not a copy)."""
+        import torch
+        ptr, n = pf_moments_device(self.ctx)
+        return torch.as_tensor(_DeviceWords(ptr, n), device="cuda")
 
     def close(self):
         if self.ctx is not None:

@@ -440,6 +440,43 @@ int pf_step(pf_ctx *c, int32_t n_iters) {
     return PF_OK;
 }
 
+int pf_step_measure(pf_ctx *c, int32_t p_begin, int32_t p_end) {
+    if (!c) return fail(PF_EINVAL, "ctx is NULL");
+    if (p_begin < 0 || p_end < p_begin || p_end > c->P.N)
+        return fail(PF_EINVAL, "slice [%d, %d) outside [0, %d]", p_begin, p_end, c->P.N);
+    CU(launch_predict(c->P, c->B, c->stream));
+    if (p_end > p_begin) {
+        MeasureArgs ma = c->MA;
+        ma.mats = c->B.mats + 12 * (size_t)p_begin;
+        ma.mom = c->B.mom + kMomStride * (size_t)p_begin;
+        ma.P = p_end - p_begin;
+        CU(launch_measure(ma, c->img, c->mask, c->stream));
+    }
+    return PF_OK;
+}
+
+int pf_step_update(pf_ctx *c) {
+    if (!c) return fail(PF_EINVAL, "ctx is NULL");
+    CU(launch_finalise(c->P, c->B, c->stream));
+    if (c->trace) {
+        MeasureArgs tm = c->MA;
+        tm.mats = c->B.trace_mat;
+        tm.mom = c->B.trace_mom;
+        tm.P = 1;
+        CU(launch_trace_prepare(c->P, c->B, c->stream));
+        CU(launch_measure(tm, false, true, c->stream));
+        CU(launch_trace_finish(c->P, c->B, c->stream));
+    }
+    return PF_OK;
+}
+
+int pf_moments_device(pf_ctx *c, uint64_t **moments, int64_t *n_words) {
+    if (!c || !moments || !n_words) return fail(PF_EINVAL, "NULL argument");
+    *moments = reinterpret_cast<uint64_t *>(c->B.mom);
+    *n_words = (int64_t)kMomStride * c->P.N;
+    return PF_OK;
+}
+
 int pf_profile_begin(pf_ctx *c, int32_t capacity) {
     if (!c) return fail(PF_EINVAL, "ctx is NULL");
     if (capacity < 0 || capacity > (1 << 16)) return fail(PF_EINVAL, "capacity outside [0, 65536]");
