@@ -90,8 +90,8 @@ __device__ __forceinline__ f2 lerp2_biased(f2 A, f2 B, f2 f) {
     return f2{__fadd_rn(base.x, __fmul_rn(f.x, d.x)), __fadd_rn(base.y, __fmul_rn(f.y, d.y))};
 }
 // q = r*dx + K for two voxels (scalar: a product feeds the add).
-__device__ __forceinline__ f2 coord2(float r, f2 dx, float K) {
-    return f2{__fadd_rn(__fmul_rn(r, dx.x), K), __fadd_rn(__fmul_rn(r, dx.y), K)};
+__device__ __forceinline__ f2 coord2(float r, f2 dx, f2 K) {
+    return f2{__fadd_rn(__fmul_rn(r, dx.x), K.x), __fadd_rn(__fmul_rn(r, dx.y), K.y)};
 }
 
 struct ImgAcc {
@@ -102,9 +102,13 @@ struct MaskAcc {
     uint32_t n = 0, A = 0, B = 0, C = 0;
 };
 
-struct Row {
-    float K0, K1, K2;
-    uint32_t trow;      // r * TX (< 2^26)
+// Two voxels handed to eval_pair: their x as floats, the row offsets K of
+// each voxel's row and their target indices (in bounds even for a voxel
+// that is not taken).
+struct PairIn {
+    f2 xf;
+    f2 K0, K1, K2;
+    uint32_t t0, t1;
 };
 
 // Inside test of the trilinear sample, 0 <= q <= D-1 in fp32, as an unsigned
@@ -128,48 +132,52 @@ __device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t 
         const uint32_t si = int_of(floorf(hx)) + (uint32_t)SX * int_of(floorf(hy)) + SXY * int_of(floorf(hz));
         const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
         const uint32_t tb = __ldg(a.tgt_mask + tidx);
-        ma.n += 1;
+        if (!EXACT) ma.n += 1;
         ma.A += sb;
         ma.B += tb;
         ma.C += sb & tb;
     }
 }
 
-// Voxels x and x + 32 of one row (the second only when valid1).  EXACT: the
-// caller visits only the row's exact inside interval, so no voxel is tested.
-template <bool IMG, bool MASK, bool EXACT>
+// Two voxels.  EXACT: the caller visits only exact inside intervals, so no
+// voxel is tested and the overlap count n is added per row by the caller;
+// FULL: both voxels are taken (no validity predicates); otherwise valid0 /
+// valid1 mark the voxels to take.
+// For EXACT the x base corner is floor(q) unclamped: at q = D-1 it reads the
+// packed neighbour byte 0 with fraction 0, a + 0*(0 - a) = a, which equals
+// the clamped a' + 1*(b' - a') = b' exactly since the end points are integers
+// (y and z keep the clamp: their end points are interpolated values).
+template <bool IMG, bool MASK, bool EXACT, bool FULL>
 __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *__restrict__ bits, const float r0x,
-                                          const float r0y, const float r0z, const Row &row, int x, float xf,
+                                          const float r0y, const float r0z, const PairIn &v, bool valid0,
                                           bool valid1, ImgAcc &ia, MaskAcc &ma) {
-    const f2 dx = sub2(pair(xf, __fadd_rn(xf, 32.0f)), splat(a.g.a[0]));
-    const f2 qx = coord2(r0x, dx, row.K0);
-    const f2 qy = coord2(r0y, dx, row.K1);
-    const f2 qz = coord2(r0z, dx, row.K2);
-    const uint32_t t0i = row.trow + (uint32_t)x;
-    const uint32_t t1i = valid1 ? t0i + 32u : t0i;
+    if (FULL) valid0 = valid1 = true;
+    const f2 dx = sub2(v.xf, splat(a.g.a[0]));
+    const f2 qx = coord2(r0x, dx, v.K0);
+    const f2 qy = coord2(r0y, dx, v.K1);
+    const f2 qz = coord2(r0z, dx, v.K2);
+    const uint32_t t0i = v.t0, t1i = v.t1;
     if (IMG) {
         const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
         const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
+        const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY);   // folds the three int_of
         const uint32_t bx = __float_as_uint((float)(SX - 1)), by = __float_as_uint((float)(SY - 1)),
                        bz = __float_as_uint((float)(SZ - 1));
-        const bool in0 = EXACT ? true : inside_tri(qx.x, qy.x, qz.x, bx, by, bz);
+        const bool in0 = EXACT ? valid0 : (valid0 & inside_tri(qx.x, qy.x, qz.x, bx, by, bz));
         const bool in1 = EXACT ? valid1 : (valid1 & inside_tri(qx.y, qy.y, qz.y, bx, by, bz));
         // base corner min(floor q, D-2) and fraction q - base
         const float Dm2x = (float)(SX - 2), Dm2y = (float)(SY - 2), Dm2z = (float)(SZ - 2);
-        const f2 flx = pair(fminf(floorf(qx.x), Dm2x), fminf(floorf(qx.y), Dm2x));
+        const f2 flx = EXACT ? pair(floorf(qx.x), floorf(qx.y))
+                             : pair(fminf(floorf(qx.x), Dm2x), fminf(floorf(qx.y), Dm2x));
         const f2 fly = pair(fminf(floorf(qy.x), Dm2y), fminf(floorf(qy.y), Dm2y));
         const f2 flz = pair(fminf(floorf(qz.x), Dm2z), fminf(floorf(qz.y), Dm2z));
         const f2 fx = sub2(qx, flx), fy = sub2(qy, fly), fz = sub2(qz, flz);
         const f2 bxv = add2(flx, splat(kTwo23)), byv = add2(fly, splat(kTwo23)), bzv = add2(flz, splat(kTwo23));
-        uint32_t i0 = (__float_as_uint(bxv.x) - kTwo23Bits) + (uint32_t)SX * (__float_as_uint(byv.x) - kTwo23Bits) +
-                      SXY * (__float_as_uint(bzv.x) - kTwo23Bits);
-        uint32_t i1 = (__float_as_uint(bxv.y) - kTwo23Bits) + (uint32_t)SX * (__float_as_uint(byv.y) - kTwo23Bits) +
-                      SXY * (__float_as_uint(bzv.y) - kTwo23Bits);
-        if (!EXACT) {
-            i0 = in0 ? i0 : 0u;   // outside voxels read a valid word and are not accumulated
+        uint32_t i0 = __float_as_uint(bxv.x) + (uint32_t)SX * __float_as_uint(byv.x) + SXY * __float_as_uint(bzv.x) + bias;
+        uint32_t i1 = __float_as_uint(bxv.y) + (uint32_t)SX * __float_as_uint(byv.y) + SXY * __float_as_uint(bzv.y) + bias;
+        if (!FULL) {
+            i0 = in0 ? i0 : 0u;   // voxels not taken read a valid word and are not accumulated
             i1 = in1 ? i1 : 0u;
-        } else {
-            i1 = valid1 ? i1 : i0;
         }
         const uint32_t w00 = __ldg(a.src_quad + i0), w01 = __ldg(a.src_quad + i0 + SXY);
         const uint32_t w10 = __ldg(a.src_quad + i1), w11 = __ldg(a.src_quad + i1 + SXY);
@@ -187,7 +195,7 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const uint32_t sq0 = __float_as_uint(s.x) - k256Bits;   // rint(2^15 s)
         const uint32_t sq1 = __float_as_uint(s.y) - k256Bits;
         if (in0) {
-            ia.n += 1;
+            if (!EXACT) ia.n += 1;
             ia.S1row += sq0;
             ia.S2 += (unsigned long long)sq0 * sq0;
             ia.ST += (unsigned long long)sq0 * t0;
@@ -195,7 +203,7 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
             ia.T2 += t0 * t0;
         }
         if (in1) {
-            ia.n += 1;
+            if (!EXACT) ia.n += 1;
             ia.S1row += sq1;
             ia.S2 += (unsigned long long)sq1 * sq1;
             ia.ST += (unsigned long long)sq1 * t1;
@@ -204,7 +212,7 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         }
     }
     if (MASK) {
-        mask_voxel<EXACT>(a, bits, qx.x, qy.x, qz.x, t0i, true, ma);
+        mask_voxel<EXACT>(a, bits, qx.x, qy.x, qz.x, t0i, valid0, ma);
         mask_voxel<EXACT>(a, bits, qx.y, qy.y, qz.y, t1i, valid1, ma);
     }
 }
@@ -222,8 +230,8 @@ __device__ __forceinline__ float coord1(float r, float K, float a0, int x) {
 // monotone), so of the two conditions per axis (lower bound, upper bound) one
 // can only turn true as x grows and the other only turn false.  "inc" is the
 // conjunction of the first kind, "dec" of the second; the inside set is
-// [first x with inc, last x with dec], found by two fixed-length binary
-// searches (no divergence across lanes).  TRI: 0 <= q <= D-1 (trilinear);
+// [first x with inc, last x with dec], found by a few linear probes from
+// each end and, when those do not reach it, a binary search.  TRI: 0 <= q <= D-1 (trilinear);
 // otherwise 0 <= q + 0.5 < D (nearest neighbour).
 template <bool TRI>
 __device__ __forceinline__ void axis_conds(float q, float D, bool &lower, bool &upper) {
@@ -269,14 +277,35 @@ __device__ __forceinline__ void exact_interval(const float r0[3], const float K[
         }
         return ok;
     };
-    int pl = xb - 1, pr = xb - 1;
-#pragma unroll 1
-    for (int step = 2048; step > 0; step >>= 1) {
-        if (pl + step < xe && !inc(pl + step)) pl += step;
-        if (pr + step < xe && dec(pr + step)) pr += step;
+    // the conservative ends are usually within a few voxels of the exact
+    // ones: probe up to four voxels inward, then fall back to binary search
+    int l = xb, cnt = 0;
+    while (l < xe && !inc(l)) {
+        ++l;
+        if (++cnt == 4) break;
     }
-    xl = pl + 1;
-    xr = constant_ok ? pr : xl - 1;
+    if (cnt == 4 && l < xe) {   // inc(l - 1) is false
+        int pl = l - 1;
+#pragma unroll 1
+        for (int step = 2048; step > 0; step >>= 1)
+            if (pl + step < xe && !inc(pl + step)) pl += step;
+        l = pl + 1;
+    }
+    int r = xe - 1;
+    cnt = 0;
+    while (r >= xb && !dec(r)) {
+        --r;
+        if (++cnt == 4) break;
+    }
+    if (cnt == 4 && r >= xb) {  // dec(r + 1) is false
+        int pr = xb - 1;
+#pragma unroll 1
+        for (int step = 2048; step > 0; step >>= 1)
+            if (pr + step <= r && dec(pr + step)) pr += step;
+        r = pr;
+    }
+    xl = l;
+    xr = constant_ok ? r : xl - 1;
 }
 
 // One work item = (particle p, 32 target rows), processed by one warp: lane l
@@ -329,22 +358,106 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
         }
     }
     const int nrows = min(kRowsPerWarp, rows - first);
-    for (int j = 0; j < nrows; ++j) {
-        const int xb = __shfl_sync(0xffffffffu, my_xb, j);
-        const int xe = __shfl_sync(0xffffffffu, my_xe, j);
-        if (xb >= xe) continue;                       // warp-uniform
-        Row row;
-        row.K0 = __shfl_sync(0xffffffffu, myK0, j);
-        row.K1 = __shfl_sync(0xffffffffu, myK1, j);
-        row.K2 = __shfl_sync(0xffffffffu, myK2, j);
-        row.trow = (uint32_t)(first + j) * (uint32_t)TX;
-        int x = xb + lane;
-        float xf = (float)x;
-        for (; x < xe; x += 64, xf = __fadd_rn(xf, 64.0f))
-            eval_pair<IMG, MASK, EXACT>(a, bits, r0[0], r0[1], r0[2], row, x, xf, x + 32 < xe, ia, ma);
-        if (IMG) {
-            ia.S1 += ia.S1row;
-            ia.S1row = 0;
+    if (EXACT) {
+        // The rows' exact intervals are visited as one sequence in passes of
+        // 64 voxels (lane l takes entries l and l + 32): a pass inside one
+        // row has no predicates; a pass across a row end takes the rest of
+        // that row and the start of the next non-empty row.
+        const uint32_t my_len = (lane < nrows && my_xb < my_xe) ? (uint32_t)(my_xe - my_xb) : 0u;
+        if (IMG) ia.n = my_len;     // the warp sum is the item's overlap count
+        else ma.n = my_len;
+        uint32_t live = __ballot_sync(0xffffffffu, my_len != 0u);
+        if (live) {
+            int j0 = __ffs(live) - 1;
+            live &= live - 1;
+            int pos = __shfl_sync(0xffffffffu, my_xb, j0), end0 = __shfl_sync(0xffffffffu, my_xe, j0);
+            float K0 = __shfl_sync(0xffffffffu, myK0, j0), K1 = __shfl_sync(0xffffffffu, myK1, j0),
+                  K2 = __shfl_sync(0xffffffffu, myK2, j0);
+            uint32_t trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
+            float xf = (float)(pos + lane);
+            for (;;) {
+                const int len0 = end0 - pos;
+                if (len0 >= 64) {
+                    const uint32_t t = trow0 + (uint32_t)(pos + lane);
+                    const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), splat(K0), splat(K1), splat(K2), t, t + 32u};
+                    eval_pair<IMG, MASK, true, true>(a, bits, r0[0], r0[1], r0[2], v, true, true, ia, ma);
+                    pos += 64;
+                    xf = __fadd_rn(xf, 64.0f);
+                    continue;
+                }
+                const bool has1 = live != 0u;
+                if (len0 == 0 && !has1) break;
+                const int j1 = has1 ? __ffs(live) - 1 : j0;
+                const int xb1 = __shfl_sync(0xffffffffu, my_xb, j1), xe1 = __shfl_sync(0xffffffffu, my_xe, j1);
+                const float L0 = __shfl_sync(0xffffffffu, myK0, j1), L1 = __shfl_sync(0xffffffffu, myK1, j1),
+                            L2 = __shfl_sync(0xffffffffu, myK2, j1);
+                const int len1 = has1 ? xe1 - xb1 : 0;
+                const uint32_t trow1 = (uint32_t)(first + j1) * (uint32_t)TX;
+                const int e0 = lane, e1 = lane + 32;          // entries of this pass
+                const bool in0a = e0 < len0, in1a = e1 < len0;
+                const bool ok0 = in0a || e0 - len0 < len1, ok1 = in1a || e1 - len0 < len1;
+                // entries past both rows read voxel 0 of row j0 and are not taken
+                const int x0 = in0a ? pos + e0 : (ok0 ? xb1 + e0 - len0 : 0);
+                const int x1 = in1a ? pos + e1 : (ok1 ? xb1 + e1 - len0 : 0);
+                const PairIn v{pair((float)x0, (float)x1), pair(in0a ? K0 : L0, in1a ? K0 : L0),
+                               pair(in0a ? K1 : L1, in1a ? K1 : L1), pair(in0a ? K2 : L2, in1a ? K2 : L2),
+                               (in0a || !ok0 ? trow0 : trow1) + (uint32_t)x0,
+                               (in1a || !ok1 ? trow0 : trow1) + (uint32_t)x1};
+                eval_pair<IMG, MASK, true, false>(a, bits, r0[0], r0[1], r0[2], v, ok0, ok1, ia, ma);
+                if (IMG) {
+                    ia.S1 += ia.S1row;
+                    ia.S1row = 0;
+                }
+                if (!has1) break;
+                live &= live - 1;
+                const int used1 = 64 - len0;                  // entries taken from row j1
+                if (len1 > used1) {
+                    j0 = j1;
+                    pos = xb1 + used1;
+                    end0 = xe1;
+                    K0 = L0;
+                    K1 = L1;
+                    K2 = L2;
+                    trow0 = trow1;
+                } else {
+                    if (!live) break;
+                    j0 = __ffs(live) - 1;
+                    live &= live - 1;
+                    pos = __shfl_sync(0xffffffffu, my_xb, j0);
+                    end0 = __shfl_sync(0xffffffffu, my_xe, j0);
+                    K0 = __shfl_sync(0xffffffffu, myK0, j0);
+                    K1 = __shfl_sync(0xffffffffu, myK1, j0);
+                    K2 = __shfl_sync(0xffffffffu, myK2, j0);
+                    trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
+                }
+                xf = (float)(pos + lane);
+            }
+            if (IMG) {
+                ia.S1 += ia.S1row;
+                ia.S1row = 0;
+            }
+        }
+    } else {
+        for (int j = 0; j < nrows; ++j) {
+            const int xb = __shfl_sync(0xffffffffu, my_xb, j);
+            const int xe = __shfl_sync(0xffffffffu, my_xe, j);
+            if (xb >= xe) continue;                       // warp-uniform
+            const f2 K0 = splat(__shfl_sync(0xffffffffu, myK0, j));
+            const f2 K1 = splat(__shfl_sync(0xffffffffu, myK1, j));
+            const f2 K2 = splat(__shfl_sync(0xffffffffu, myK2, j));
+            const uint32_t trow = (uint32_t)(first + j) * (uint32_t)TX;
+            int x = xb + lane;
+            float xf = (float)x;
+            for (; x < xe; x += 64, xf = __fadd_rn(xf, 64.0f)) {
+                const bool valid1 = x + 32 < xe;
+                const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), K0, K1, K2, trow + (uint32_t)x,
+                               valid1 ? trow + (uint32_t)x + 32u : trow};
+                eval_pair<IMG, MASK, false, false>(a, bits, r0[0], r0[1], r0[2], v, true, valid1, ia, ma);
+            }
+            if (IMG) {
+                ia.S1 += ia.S1row;
+                ia.S1row = 0;
+            }
         }
     }
 
@@ -384,11 +497,18 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
 // optional shared-memory load of the mask and finished CTAs are replaced by
 // fresh ones.  Single-mode kernels visit only each row's exact inside
 // interval (EXACT).
-#ifndef PF_MEASURE_MIN_BLOCKS
-#define PF_MEASURE_MIN_BLOCKS 1
+// Resident CTAs per SM the register allocation must allow: image-only 4
+// (64 registers), combined 3 (80; at 4 it spills), mask 4 (56 needed).
+#ifndef PF_MEASURE_MIN_BLOCKS_IMG
+#define PF_MEASURE_MIN_BLOCKS_IMG 4
+#endif
+#ifndef PF_MEASURE_MIN_BLOCKS_COMBINED
+#define PF_MEASURE_MIN_BLOCKS_COMBINED 3
 #endif
 template <bool IMG, bool MASK, bool MASK_SMEM>
-__global__ void __launch_bounds__(kThreads, PF_MEASURE_MIN_BLOCKS) k_measure(const MeasureArgs a) {
+__global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_COMBINED
+                                                        : (IMG ? PF_MEASURE_MIN_BLOCKS_IMG : 4))
+    k_measure(const MeasureArgs a) {
     extern __shared__ uint32_t smem_bits[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t *bits = a.src_bits;
@@ -409,8 +529,9 @@ __global__ void __launch_bounds__(kThreads, PF_MEASURE_MIN_BLOCKS) k_measure(con
 // registrations are concatenated (offs = prefix of their item counts); each
 // item finds its registration by binary search, and registrations that have
 // run all their iterations are skipped.
+// (The registration lookup costs registers: tighter bounds than these spill.)
 template <bool IMG, bool MASK>
-__global__ void __launch_bounds__(kThreads) k_measure_batch(const BatchReg *__restrict__ regs,
+__global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batch(const BatchReg *__restrict__ regs,
                                                             const int32_t *__restrict__ list,
                                                             const long long *__restrict__ offs, int nlist) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
