@@ -3,10 +3,14 @@
 //
 // out(p) = rint(trilinear(frame, q(p))) (round half to even, 0..255) or the
 // nearest voxel, 0 where q(p) is outside the source grid.  A persistent grid
-// (a few CTAs per SM) walks frame-major over groups of 4 consecutive target
-// voxels of a row; each CTA first builds the pose's matrix in shared memory
-// (six lanes take the fp64 sin/cos in parallel), so a launch covers up to 64
-// frames with one pose passed by value.
+// (a few CTAs per SM) walks frame-major over target rows, one row per warp
+// at a time: lanes take x = lane + 32 j, voxels outside the row's
+// conservative inside range are written 0 without sampling.  Each CTA
+// first builds the pose's matrix in shared memory (six lanes take the fp64
+// sin/cos in parallel), so a launch covers up to 64 frames with one pose
+// passed by value.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace pfreg {
@@ -14,7 +18,6 @@ namespace pfreg {
 namespace {
 
 constexpr int kWarpThreads = 256;
-constexpr int kVox = 4;   // target voxels per thread
 
 struct WarpArgs {
     WarpFrames f;
@@ -22,13 +25,20 @@ struct WarpArgs {
     Geometry g;
     int interp;
     int n_frames;
-    int row_groups;   // ceil(X / kVox)
 };
 
+// integer value of a float holding a non-negative integer below 2^23
+__device__ __forceinline__ uint32_t uint_of(float v) {
+    return __float_as_uint(__fadd_rn(v, 8388608.0f)) - 0x4B000000u;
+}
+
+// One output voxel; WIDE: the frame has 2^31 voxels or more (64-bit offsets).
+template <bool WIDE>
 __device__ __forceinline__ uint8_t warp_voxel(const uint8_t *__restrict__ S, const WarpArgs &a,
                                               const float *M, int x, float K0, float K1, float K2) {
+    using idx_t = typename std::conditional<WIDE, size_t, uint32_t>::type;
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
-    const size_t SXY = (size_t)SX * SY;
+    const idx_t sx = (idx_t)SX, sxy = (idx_t)SX * (idx_t)SY;
     const float dx = __fsub_rn((float)x, a.g.a[0]);
     const float qx = __fadd_rn(__fmul_rn(M[0], dx), K0);
     const float qy = __fadd_rn(__fmul_rn(M[4], dx), K1);
@@ -37,8 +47,8 @@ __device__ __forceinline__ uint8_t warp_voxel(const uint8_t *__restrict__ S, con
         const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
         if (!(hx >= 0.0f && hx < (float)SX && hy >= 0.0f && hy < (float)SY && hz >= 0.0f && hz < (float)SZ))
             return 0;
-        return __ldg(S + (size_t)(int)floorf(hx) + (size_t)SX * (size_t)(int)floorf(hy) +
-                     SXY * (size_t)(int)floorf(hz));
+        return __ldg(S + (idx_t)uint_of(floorf(hx)) + sx * (idx_t)uint_of(floorf(hy)) +
+                     sxy * (idx_t)uint_of(floorf(hz)));
     }
     if (!(qx >= 0.0f && qx <= (float)(SX - 1) && qy >= 0.0f && qy <= (float)(SY - 1) && qz >= 0.0f &&
           qz <= (float)(SZ - 1)))
@@ -47,11 +57,11 @@ __device__ __forceinline__ uint8_t warp_voxel(const uint8_t *__restrict__ S, con
     const float fy0 = fminf(floorf(qy), (float)(SY - 2));
     const float fz0 = fminf(floorf(qz), (float)(SZ - 2));
     const float fx = __fsub_rn(qx, fx0), fy = __fsub_rn(qy, fy0), fz = __fsub_rn(qz, fz0);
-    const uint8_t *p = S + (size_t)(int)fx0 + (size_t)SX * (size_t)(int)fy0 + SXY * (size_t)(int)fz0;
+    const uint8_t *p = S + (idx_t)uint_of(fx0) + sx * (idx_t)uint_of(fy0) + sxy * (idx_t)uint_of(fz0);
     const float v000 = __ldg(p), v100 = __ldg(p + 1);
-    const float v010 = __ldg(p + SX), v110 = __ldg(p + SX + 1);
-    const float v001 = __ldg(p + SXY), v101 = __ldg(p + SXY + 1);
-    const float v011 = __ldg(p + SXY + SX), v111 = __ldg(p + SXY + SX + 1);
+    const float v010 = __ldg(p + sx), v110 = __ldg(p + sx + 1);
+    const float v001 = __ldg(p + sxy), v101 = __ldg(p + sxy + 1);
+    const float v011 = __ldg(p + sxy + sx), v111 = __ldg(p + sxy + sx + 1);
     const float c00 = lerp_rn(v000, v100, fx), c10 = lerp_rn(v010, v110, fx);
     const float c01 = lerp_rn(v001, v101, fx), c11 = lerp_rn(v011, v111, fx);
     const float c0 = lerp_rn(c00, c10, fy), c1 = lerp_rn(c01, c11, fy);
@@ -59,6 +69,7 @@ __device__ __forceinline__ uint8_t warp_voxel(const uint8_t *__restrict__ S, con
     return (uint8_t)(v < 0 ? 0 : (v > 255 ? 255 : v));
 }
 
+template <bool WIDE>
 __global__ void __launch_bounds__(kWarpThreads) k_warp(const WarpArgs a) {
     __shared__ double sc[6];
     __shared__ float Ms[12];
@@ -72,34 +83,33 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const WarpArgs a) {
     float M[12];
 #pragma unroll
     for (int j = 0; j < 12; ++j) M[j] = Ms[j];
+    const float r0[3] = {M[0], M[4], M[8]};
+    const float SXf = (float)a.g.sd[0], SYf = (float)a.g.sd[1], SZf = (float)a.g.sd[2];
+    float lo[3], hi[3];
+    lo[0] = lo[1] = lo[2] = a.interp ? 0.0f : -0.5f;
+    hi[0] = a.interp ? SXf - 1.0f : SXf - 0.5f;
+    hi[1] = a.interp ? SYf - 1.0f : SYf - 0.5f;
+    hi[2] = a.interp ? SZf - 1.0f : SZf - 0.5f;
 
-    const int TX = a.g.td[0], TY = a.g.td[1], TZ = a.g.td[2];
-    const long long per_frame = (long long)a.row_groups * TY * TZ;
-    const long long total = per_frame * a.n_frames;
-    for (long long gi = (long long)blockIdx.x * kWarpThreads + threadIdx.x; gi < total;
-         gi += (long long)gridDim.x * kWarpThreads) {
-        const int f = (int)(gi / per_frame);
-        const long long li = gi - (long long)f * per_frame;
-        const int r = (int)(li / a.row_groups);
-        const int x0 = (int)(li - (long long)r * a.row_groups) * kVox;
+    const int TX = a.g.td[0], TY = a.g.td[1];
+    const int lane = threadIdx.x & 31;
+    const long long rows = (long long)TY * a.g.td[2];
+    const long long total = rows * a.n_frames;
+    const long long nwarps = (long long)gridDim.x * (kWarpThreads / 32);
+    for (long long gr = (long long)blockIdx.x * (kWarpThreads / 32) + (threadIdx.x >> 5); gr < total;
+         gr += nwarps) {
+        const int f = (int)(gr / rows);
+        const int r = (int)(gr - (long long)f * rows);
         const int y = r % TY, z = r / TY;
         const float dy = __fsub_rn((float)y, a.g.a[1]), dz = __fsub_rn((float)z, a.g.a[2]);
-        const float K0 = row_K(M[1], M[2], M[3], dy, dz);
-        const float K1 = row_K(M[5], M[6], M[7], dy, dz);
-        const float K2 = row_K(M[9], M[10], M[11], dy, dz);
+        const float K[3] = {row_K(M[1], M[2], M[3], dy, dz), row_K(M[5], M[6], M[7], dy, dz),
+                            row_K(M[9], M[10], M[11], dy, dz)};
+        int xb, xe;
+        row_interval(r0, K, a.g.a[0], lo, hi, TX, xb, xe);
         const uint8_t *S = a.f.in[f];
         uint8_t *O = a.f.out[f] + (size_t)r * TX;
-        uint8_t v[kVox];
-#pragma unroll
-        for (int j = 0; j < kVox; ++j) v[j] = (x0 + j < TX) ? warp_voxel(S, a, M, x0 + j, K0, K1, K2) : 0;
-        if (x0 + kVox <= TX && ((reinterpret_cast<uintptr_t>(O + x0) & 3) == 0)) {
-            *reinterpret_cast<uint32_t *>(O + x0) =
-                (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) | ((uint32_t)v[3] << 24);
-        } else {
-#pragma unroll
-            for (int j = 0; j < kVox; ++j)
-                if (x0 + j < TX) O[x0 + j] = v[j];
-        }
+        for (int x = lane; x < TX; x += 32)
+            O[x] = (x >= xb && x < xe) ? warp_voxel<WIDE>(S, a, M, x, K[0], K[1], K[2]) : (uint8_t)0;
     }
 }
 
@@ -114,17 +124,21 @@ cudaError_t launch_warp(const WarpFrames &f, int n, const float pose[6], Geometr
     a.g = g;
     a.interp = interp;
     a.n_frames = n;
-    a.row_groups = (g.td[0] + kVox - 1) / kVox;
-    const long long total = (long long)a.row_groups * g.td[1] * g.td[2] * n;
+    const bool wide = (long long)g.sd[0] * g.sd[1] * g.sd[2] >= (1ll << 31);
+    const long long rows = (long long)g.td[1] * g.td[2] * n;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp, kWarpThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wide ? k_warp<true> : k_warp<false>,
+                                                                  kWarpThreads, 0);
     if (e != cudaSuccess) return e;
     long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    const long long need = (total + kWarpThreads - 1) / kWarpThreads;
+    const long long need = (rows + kWarpThreads / 32 - 1) / (kWarpThreads / 32);
     if (grid > need) grid = need;
-    k_warp<<<(unsigned)grid, kWarpThreads, 0, s>>>(a);
+    if (wide)
+        k_warp<true><<<(unsigned)grid, kWarpThreads, 0, s>>>(a);
+    else
+        k_warp<false><<<(unsigned)grid, kWarpThreads, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
