@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -46,7 +47,7 @@ UNIT = "particle-voxel evals/s"
 
 # FP32 operations the arithmetic definition fixes per visited voxel of the
 # trilinear measurement: 3 mul + 3 add (coordinates), 3 floor, 3 subtract
-# (fractions), 7 lerps x 3 ops, 1 scale to 1/1024 fixed point.
+# (fractions), 7 lerps x 3 ops, 1 rounding to 15 fractional bits.
 OPS_PER_EVAL = 34
 # nearest-neighbour mask sample: 3 mul + 3 add (coordinates), 3 add (+0.5),
 # 3 floor; the combined score does both on one coordinate.
@@ -72,6 +73,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-particles", type=int, default=32)
     ap.add_argument("--cpu-sample-iters", type=int, default=2)
+    ap.add_argument("--cpu-all-cores-particles", type=int, default=512)
     return ap.parse_args()
 
 
@@ -217,6 +219,41 @@ def oracle_sample(w, pair, n_particles, n_iters):
     return dt, n_particles * n_iters * int(np.prod(pair.tgt.shape))
 
 
+def _measure_chunk(task):
+    """Pool worker: the oracle's measurement of a chunk of matrices."""
+    kind, src, tgt, smask, tmask, mats, a = task
+    import oracle
+    if kind in ("image_ncc", "combined"):
+        oracle.measure_image(src, tgt, mats, a)
+    if kind != "image_ncc":
+        oracle.measure_mask(smask, tmask, mats, a)
+    return len(mats)
+
+
+def oracle_measure_all_cores(w, pair, n_particles, cores):
+    """The oracle's measurement (the > 99 % part of an iteration) of
+    n_particles initial-cloud matrices, split over ``cores`` spawned
+    processes.  Returns (seconds, dense units, cores)."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    lim = np.array([np.deg2rad(w["rot_limit_deg"])] * 3 + [w["trans_limit"]] * 3, np.float32)
+    x = oracle.init_particles(n_particles, w["seed"], lim)
+    mats, a = oracle.pose_matrices(x, pair.src_dims, pair.src_origin, pair.tgt_origin)
+    if w["kind"] == "mask_dice":
+        vols = (None, None, pair.src, pair.tgt)
+    else:
+        vols = (pair.src, pair.tgt, pair.src_mask, pair.tgt_mask)
+    chunks = [c for c in np.array_split(mats, cores) if len(c)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_measure_chunk, [(w["kind"], *vols, mats[:1], a)] * cores)   # start-up, untimed
+        t0 = time.perf_counter()
+        pool.map(_measure_chunk, [(w["kind"], *vols, c, a) for c in chunks])
+        dt = time.perf_counter() - t0
+    return dt, n_particles * int(np.prod(pair.tgt.shape)), cores
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -357,6 +394,19 @@ def run_ours(args, rank, world, local):
                 "share_of_step": rec["measure_ms"] / sum(step_ms),
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} fp32 lanes x {mhz:.0f} MHz (median SM clock sampled during the timed steps)"}
 
+    # the sequence warp: algorithmic bytes (each frame read once, each output
+    # written once) against the measured HBM copy rate
+    roofline_warp = None
+    if fr_d:
+        wbytes = sum(f.nbytes for f in frames) + sum(o.numel() for o in out_d)
+        wsec = statistics.mean(warp_ms) / 1e3
+        hbm = peaks.get("hbm_gbs")
+        roofline_warp = {"bound": "hbm", "kernel": "k_warp", "achieved": wbytes / wsec / 1e9 if wsec > 0 else None,
+                         "peak": hbm, "unit": "GB/s",
+                         "frac": (wbytes / wsec / 1e9 / hbm) if (hbm and wsec > 0) else None,
+                         "bytes_per_launch": int(wbytes), "ms": 1e3 * wsec,
+                         "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy)"}
+
     # end to end through the public API from pinned host buffers
     # Time-to-Dice: one traced registration (untimed) warps the LV-cavity
     # masks with the estimate after every iteration (Sec. 3.2 validation);
@@ -426,9 +476,17 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, k = args.cpu_sample_particles, args.cpu_sample_iters
         dt, u = oracle_sample(w, pair, n, k)
+        ncpu = os.cpu_count() or 1
         cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} particles x {k} iterations of the same pair ({u:.3g} dense evals, "
-                         f"{dt:.1f} s single-threaded); warp excluded"}
+                         f"{dt:.1f} s single-threaded); warp excluded",
+               "host": f"{ncpu} cores, {platform.machine()}"}
+        if args.cpu_all_cores_particles > 0 and ncpu > 1:
+            dt2, u2, c2 = oracle_measure_all_cores(w, pair, args.cpu_all_cores_particles, ncpu)
+            cpu["all_cores"] = {
+                "value": u2 / dt2, "unit": UNIT, "cores": c2,
+                "sample": f"measurement only: {args.cpu_all_cores_particles} particles of the initial cloud "
+                          f"split over {c2} spawned processes ({dt2:.1f} s)"}
 
     if rank == 0:
         line = {
@@ -442,8 +500,10 @@ def run_ours(args, rank, world, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "warp_ms_per_step": statistics.mean(warp_ms),
                        "overlap_evals_per_step": rec["evals"] / args.steps,
+                       "overlap_evals_per_s": rec["evals"] / local_s,
                        "time_to_dice": trace},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roofline, "roofline_warp": roofline_warp, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
             "wall_s_timed": wall, "final_pose": [float(v) for v in pose],
             "true_pose": [float(v) for v in pair.true_pose],

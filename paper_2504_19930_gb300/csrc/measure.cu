@@ -74,9 +74,22 @@ __device__ __forceinline__ f2 splat(float a) { return f2{a, a}; }
 PF_F32X2(add2, "add")
 PF_F32X2(sub2, "sub")
 #undef PF_F32X2
+// a*b + c, used only on integer-valued operands whose products and sums stay
+// below 2^24, where every rounding is exact (index arithmetic).
+__device__ __forceinline__ f2 fma2_exact(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\tmov.b64 rc, {%6,%7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0,%1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
 #else
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return f2{__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)}; }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return f2{__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)}; }
+__device__ __forceinline__ f2 fma2_exact(f2 a, f2 b, f2 c) {
+    return f2{__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)};
+}
 #endif
 
 // a + f*(b - a) for two voxels: packed difference, scalar product and sum.
@@ -109,79 +122,94 @@ struct PairIn {
     f2 xf;
     f2 K0, K1, K2;
     uint32_t t0, t1;
+    // FULL: address of the first voxel's target byte (the second is 32
+    // further): image target, or mask target in the mask modes; tpm: the
+    // mask target in the combined mode
+    const uint8_t *tp, *tpm;
 };
 
-// Inside test of the trilinear sample, 0 <= q <= D-1 in fp32, as an unsigned
-// compare of the bit patterns: q is never -0 (its offset b is never -0, so a
-// sum r*dx + K cannot round to -0), non-negative floats order like their bits,
-// and negative values and NaNs have bit patterns above any bound.
-__device__ __forceinline__ bool inside_tri(float qx, float qy, float qz, uint32_t bx, uint32_t by, uint32_t bz) {
-    return (__float_as_uint(qx) <= bx) & (__float_as_uint(qy) <= by) & (__float_as_uint(qz) <= bz);
-}
-
-template <bool EXACT>
+// Nearest-neighbour mask sample of one voxel the caller has placed inside
+// the source grid (valid: the voxel is taken).
 __device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t *__restrict__ bits, float qx,
-                                           float qy, float qz, uint32_t tidx, bool valid, MaskAcc &ma) {
-    const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
+                                           float qy, float qz, const uint8_t *tptr, bool valid, MaskAcc &ma) {
+    const int SX = a.g.sd[0], SY = a.g.sd[1];
     const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
-    const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
-    const bool in = EXACT ? valid
-                          : (valid & (hx >= 0.0f) & (hx < (float)SX) & (hy >= 0.0f) & (hy < (float)SY) &
-                             (hz >= 0.0f) & (hz < (float)SZ));
-    if (in) {
+    if (valid) {
+        const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
         const uint32_t si = int_of(floorf(hx)) + (uint32_t)SX * int_of(floorf(hy)) + SXY * int_of(floorf(hz));
         const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
-        const uint32_t tb = __ldg(a.tgt_mask + tidx);
-        if (!EXACT) ma.n += 1;
+        const uint32_t tb = __ldg(tptr);
         ma.A += sb;
         ma.B += tb;
         ma.C += sb & tb;
     }
 }
 
-// Two voxels.  EXACT: the caller visits only exact inside intervals, so no
-// voxel is tested and the overlap count n is added per row by the caller;
-// FULL: both voxels are taken (no validity predicates); otherwise valid0 /
-// valid1 mark the voxels to take.
-// For EXACT the x base corner is floor(q) unclamped: at q = D-1 it reads the
-// packed neighbour byte 0 with fraction 0, a + 0*(0 - a) = a, which equals
-// the clamped a' + 1*(b' - a') = b' exactly since the end points are integers
+// Two voxels of the exact inside intervals the caller visits (no voxel is
+// tested here; the overlap counts are added per row by the caller).  valid0 /
+// valid1: the voxel is taken (for the mask, and for the image unless
+// ivalid0 / ivalid1 say otherwise in the combined mode, whose image interval
+// lies inside the mask's).  FULL: both voxels taken for every score, no
+// predicates; IFULL: both taken for the image.
+// The x base corner is floor(q) unclamped: at q = D-1 it reads the packed
+// neighbour byte 0 with fraction 0, a + 0*(0 - a) = a, which equals the
+// clamped a' + 1*(b' - a') = b' exactly since the end points are integers
 // (y and z keep the clamp: their end points are interpolated values).
-template <bool IMG, bool MASK, bool EXACT, bool FULL>
+// NOCLAMP: the caller knows q_y < D_y - 1 and q_z < D_z - 1 for both voxels,
+// where min(floor q, D - 2) = floor q.  FIDX: the source has at most 2^23
+// voxels and the quad index is formed in fp32 (exact integers below 2^24)
+// as 2^23 + index, read through a base address lowered by 2^23 words.
+template <bool IMG, bool MASK, bool FULL, bool IFULL, bool NOCLAMP, bool FIDX>
 __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *__restrict__ bits, const float r0x,
                                           const float r0y, const float r0z, const PairIn &v, bool valid0,
-                                          bool valid1, ImgAcc &ia, MaskAcc &ma) {
+                                          bool valid1, bool ivalid0, bool ivalid1, ImgAcc &ia, MaskAcc &ma) {
     if (FULL) valid0 = valid1 = true;
     const f2 dx = sub2(v.xf, splat(a.g.a[0]));
     const f2 qx = coord2(r0x, dx, v.K0);
     const f2 qy = coord2(r0y, dx, v.K1);
     const f2 qz = coord2(r0z, dx, v.K2);
-    const uint32_t t0i = v.t0, t1i = v.t1;
     if (IMG) {
         const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
         const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
-        const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY);   // folds the three int_of
-        const uint32_t bx = __float_as_uint((float)(SX - 1)), by = __float_as_uint((float)(SY - 1)),
-                       bz = __float_as_uint((float)(SZ - 1));
-        const bool in0 = EXACT ? valid0 : (valid0 & inside_tri(qx.x, qy.x, qz.x, bx, by, bz));
-        const bool in1 = EXACT ? valid1 : (valid1 & inside_tri(qx.y, qy.y, qz.y, bx, by, bz));
+        const bool in0 = IFULL || (MASK ? ivalid0 : valid0);
+        const bool in1 = IFULL || (MASK ? ivalid1 : valid1);
         // base corner min(floor q, D-2) and fraction q - base
-        const float Dm2x = (float)(SX - 2), Dm2y = (float)(SY - 2), Dm2z = (float)(SZ - 2);
-        const f2 flx = EXACT ? pair(floorf(qx.x), floorf(qx.y))
-                             : pair(fminf(floorf(qx.x), Dm2x), fminf(floorf(qx.y), Dm2x));
-        const f2 fly = pair(fminf(floorf(qy.x), Dm2y), fminf(floorf(qy.y), Dm2y));
-        const f2 flz = pair(fminf(floorf(qz.x), Dm2z), fminf(floorf(qz.y), Dm2z));
+        const float Dm2y = (float)(SY - 2), Dm2z = (float)(SZ - 2);
+        const f2 flx = pair(floorf(qx.x), floorf(qx.y));
+        const f2 fly = NOCLAMP ? pair(floorf(qy.x), floorf(qy.y))
+                               : pair(fminf(floorf(qy.x), Dm2y), fminf(floorf(qy.y), Dm2y));
+        const f2 flz = NOCLAMP ? pair(floorf(qz.x), floorf(qz.y))
+                               : pair(fminf(floorf(qz.x), Dm2z), fminf(floorf(qz.y), Dm2z));
         const f2 fx = sub2(qx, flx), fy = sub2(qy, fly), fz = sub2(qz, flz);
-        const f2 bxv = add2(flx, splat(kTwo23)), byv = add2(fly, splat(kTwo23)), bzv = add2(flz, splat(kTwo23));
-        uint32_t i0 = __float_as_uint(bxv.x) + (uint32_t)SX * __float_as_uint(byv.x) + SXY * __float_as_uint(bzv.x) + bias;
-        uint32_t i1 = __float_as_uint(bxv.y) + (uint32_t)SX * __float_as_uint(byv.y) + SXY * __float_as_uint(bzv.y) + bias;
-        if (!FULL) {
-            i0 = in0 ? i0 : 0u;   // voxels not taken read a valid word and are not accumulated
-            i1 = in1 ? i1 : 0u;
+        const uint32_t *qbase;
+        uint32_t i0, i1;
+        if (FIDX) {
+            const f2 w = fma2_exact(splat((float)SXY), flz,
+                                    fma2_exact(splat((float)SX), fly, add2(flx, splat(kTwo23))));
+            i0 = __float_as_uint(w.x);
+            i1 = __float_as_uint(w.y);
+            qbase = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(a.src_quad) -
+                                                       (uintptr_t)kTwo23Bits * 4u);
+            if (!IFULL) {
+                i0 = in0 ? i0 : kTwo23Bits;   // voxels not taken read word 0 and are not accumulated
+                i1 = in1 ? i1 : kTwo23Bits;
+            }
+        } else {
+            const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY);   // folds the three int_of
+            const f2 bxv = add2(flx, splat(kTwo23)), byv = add2(fly, splat(kTwo23)),
+                     bzv = add2(flz, splat(kTwo23));
+            i0 = __float_as_uint(bxv.x) + (uint32_t)SX * __float_as_uint(byv.x) + SXY * __float_as_uint(bzv.x) + bias;
+            i1 = __float_as_uint(bxv.y) + (uint32_t)SX * __float_as_uint(byv.y) + SXY * __float_as_uint(bzv.y) + bias;
+            qbase = a.src_quad;
+            if (!IFULL) {
+                i0 = in0 ? i0 : 0u;   // voxels not taken read word 0 and are not accumulated
+                i1 = in1 ? i1 : 0u;
+            }
         }
-        const uint32_t w00 = __ldg(a.src_quad + i0), w01 = __ldg(a.src_quad + i0 + SXY);
-        const uint32_t w10 = __ldg(a.src_quad + i1), w11 = __ldg(a.src_quad + i1 + SXY);
-        const uint32_t t0 = __ldg(a.tgt_img + t0i), t1 = __ldg(a.tgt_img + t1i);
+        const uint32_t w00 = __ldg(qbase + i0), w01 = __ldg(qbase + i0 + SXY);
+        const uint32_t w10 = __ldg(qbase + i1), w11 = __ldg(qbase + i1 + SXY);
+        const uint32_t t0 = FULL ? __ldg(v.tp) : __ldg(a.tgt_img + v.t0);
+        const uint32_t t1 = FULL ? __ldg(v.tp + 32) : __ldg(a.tgt_img + v.t1);
         const f2 c00 = lerp2_biased(pair(byte_biased(w00, 0), byte_biased(w10, 0)),
                                     pair(byte_biased(w00, 1), byte_biased(w10, 1)), fx);
         const f2 c10 = lerp2_biased(pair(byte_biased(w00, 2), byte_biased(w10, 2)),
@@ -195,7 +223,6 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const uint32_t sq0 = __float_as_uint(s.x) - k256Bits;   // rint(2^15 s)
         const uint32_t sq1 = __float_as_uint(s.y) - k256Bits;
         if (in0) {
-            if (!EXACT) ia.n += 1;
             ia.S1row += sq0;
             ia.S2 += (unsigned long long)sq0 * sq0;
             ia.ST += (unsigned long long)sq0 * t0;
@@ -203,7 +230,6 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
             ia.T2 += t0 * t0;
         }
         if (in1) {
-            if (!EXACT) ia.n += 1;
             ia.S1row += sq1;
             ia.S2 += (unsigned long long)sq1 * sq1;
             ia.ST += (unsigned long long)sq1 * t1;
@@ -212,8 +238,9 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         }
     }
     if (MASK) {
-        mask_voxel<EXACT>(a, bits, qx.x, qy.x, qz.x, t0i, valid0, ma);
-        mask_voxel<EXACT>(a, bits, qx.y, qy.y, qz.y, t1i, valid1, ma);
+        const uint8_t *tm = IMG ? v.tpm : v.tp;   // FULL: the mask target's address
+        mask_voxel(a, bits, qx.x, qy.x, qz.x, FULL ? tm : a.tgt_mask + v.t0, valid0, ma);
+        mask_voxel(a, bits, qx.y, qy.y, qz.y, FULL ? tm + 32 : a.tgt_mask + v.t1, valid1, ma);
     }
 }
 
@@ -309,13 +336,15 @@ __device__ __forceinline__ void exact_interval(const float r0[3], const float K[
 }
 
 // One work item = (particle p, 32 target rows), processed by one warp: lane l
-// prepares row (first + l) -- hoisted K and its x-range (exact when EXACT) --
-// then the warp sweeps the rows, reduces the moments and adds them to
-// mom[p] with one integer atomic each (S2 is 128-bit).
-template <bool IMG, bool MASK>
+// prepares row (first + l) -- hoisted K, the exact inside interval [vb, ve)
+// the row is visited over (nearest-neighbour for the mask modes, trilinear
+// for the image mode) and, combined, the trilinear interval [ib, ie) inside
+// it -- then the warp sweeps the intervals, reduces the moments and adds
+// them to mom[p] with one integer atomic each (S2 is 128-bit).
+template <bool IMG, bool MASK, bool FIDX>
 __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_t *__restrict__ bits,
                                              long long item, int lane) {
-    constexpr bool EXACT = IMG != MASK;
+    constexpr bool BOTH = IMG && MASK;
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
     const int TX = a.g.td[0], TY = a.g.td[1];
     const int rows = a.g.td[1] * a.g.td[2];
@@ -340,7 +369,8 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
     const int first = rb * kRowsPerWarp;
     const int my_row = first + lane;
     float myK0 = 0.0f, myK1 = 0.0f, myK2 = 0.0f;
-    int my_xb = 0, my_xe = 0;
+    int my_vb = 0, my_ve = 0, my_ib = 0, my_ie = 0;
+    bool my_noclamp = false;
     if (my_row < rows) {
         const int y = my_row % TY, z = my_row / TY;
         const float dy = __fsub_rn((float)y, a.g.a[1]);
@@ -349,115 +379,140 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
         myK1 = row_K(M[5], M[6], M[7], dy, dz);
         myK2 = row_K(M[9], M[10], M[11], dy, dz);
         const float K[3] = {myK0, myK1, myK2};
-        row_interval(r0, K, a.g.a[0], lo, hi, TX, my_xb, my_xe);
-        if (EXACT && my_xb < my_xe) {
+        int xb, xe;
+        row_interval(r0, K, a.g.a[0], lo, hi, TX, xb, xe);
+        if (xb < xe) {
             int xl, xr;
-            exact_interval<IMG>(r0, K, a.g.a[0], D, my_xb, my_xe, xl, xr);
-            my_xb = xl;
-            my_xe = xr + 1;
+            exact_interval<!MASK>(r0, K, a.g.a[0], D, xb, xe, xl, xr);
+            my_vb = xl;
+            my_ve = xr + 1 > xl ? xr + 1 : xl;
+            if (BOTH && my_vb < my_ve) {
+                // the trilinear inside set lies within the nearest-neighbour one
+                exact_interval<true>(r0, K, a.g.a[0], D, my_vb, my_ve, xl, xr);
+                my_ib = xl;
+                my_ie = xr + 1 > xl ? xr + 1 : xl;
+            } else {
+                my_ib = my_vb;
+                my_ie = my_ve;
+            }
+            if (IMG && my_ib < my_ie) {
+                // q_y, q_z are monotone along the row: below D - 1 at both
+                // image interval ends means below it on the whole row
+                const int l = my_ib, r = my_ie - 1;
+                const float yl = coord1(r0[1], K[1], a.g.a[0], l), yr = coord1(r0[1], K[1], a.g.a[0], r);
+                const float zl = coord1(r0[2], K[2], a.g.a[0], l), zr = coord1(r0[2], K[2], a.g.a[0], r);
+                my_noclamp = fmaxf(yl, yr) < (float)(SY - 1) && fmaxf(zl, zr) < (float)(SZ - 1);
+            }
         }
     }
-    const int nrows = min(kRowsPerWarp, rows - first);
-    if (EXACT) {
-        // The rows' exact intervals are visited as one sequence in passes of
-        // 64 voxels (lane l takes entries l and l + 32): a pass inside one
-        // row has no predicates; a pass across a row end takes the rest of
-        // that row and the start of the next non-empty row.
-        const uint32_t my_len = (lane < nrows && my_xb < my_xe) ? (uint32_t)(my_xe - my_xb) : 0u;
-        if (IMG) ia.n = my_len;     // the warp sum is the item's overlap count
-        else ma.n = my_len;
-        uint32_t live = __ballot_sync(0xffffffffu, my_len != 0u);
-        if (live) {
-            int j0 = __ffs(live) - 1;
-            live &= live - 1;
-            int pos = __shfl_sync(0xffffffffu, my_xb, j0), end0 = __shfl_sync(0xffffffffu, my_xe, j0);
-            float K0 = __shfl_sync(0xffffffffu, myK0, j0), K1 = __shfl_sync(0xffffffffu, myK1, j0),
-                  K2 = __shfl_sync(0xffffffffu, myK2, j0);
-            uint32_t trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
-            float xf = (float)(pos + lane);
-            for (;;) {
-                const int len0 = end0 - pos;
-                if (len0 >= 64) {
-                    const uint32_t t = trow0 + (uint32_t)(pos + lane);
-                    const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), splat(K0), splat(K1), splat(K2), t, t + 32u};
-                    eval_pair<IMG, MASK, true, true>(a, bits, r0[0], r0[1], r0[2], v, true, true, ia, ma);
-                    pos += 64;
-                    xf = __fadd_rn(xf, 64.0f);
-                    continue;
-                }
-                const bool has1 = live != 0u;
-                if (len0 == 0 && !has1) break;
-                const int j1 = has1 ? __ffs(live) - 1 : j0;
-                const int xb1 = __shfl_sync(0xffffffffu, my_xb, j1), xe1 = __shfl_sync(0xffffffffu, my_xe, j1);
-                const float L0 = __shfl_sync(0xffffffffu, myK0, j1), L1 = __shfl_sync(0xffffffffu, myK1, j1),
-                            L2 = __shfl_sync(0xffffffffu, myK2, j1);
-                const int len1 = has1 ? xe1 - xb1 : 0;
-                const uint32_t trow1 = (uint32_t)(first + j1) * (uint32_t)TX;
-                const int e0 = lane, e1 = lane + 32;          // entries of this pass
-                const bool in0a = e0 < len0, in1a = e1 < len0;
-                const bool ok0 = in0a || e0 - len0 < len1, ok1 = in1a || e1 - len0 < len1;
-                // entries past both rows read voxel 0 of row j0 and are not taken
-                const int x0 = in0a ? pos + e0 : (ok0 ? xb1 + e0 - len0 : 0);
-                const int x1 = in1a ? pos + e1 : (ok1 ? xb1 + e1 - len0 : 0);
-                const PairIn v{pair((float)x0, (float)x1), pair(in0a ? K0 : L0, in1a ? K0 : L0),
-                               pair(in0a ? K1 : L1, in1a ? K1 : L1), pair(in0a ? K2 : L2, in1a ? K2 : L2),
-                               (in0a || !ok0 ? trow0 : trow1) + (uint32_t)x0,
-                               (in1a || !ok1 ? trow0 : trow1) + (uint32_t)x1};
-                eval_pair<IMG, MASK, true, false>(a, bits, r0[0], r0[1], r0[2], v, ok0, ok1, ia, ma);
-                if (IMG) {
-                    ia.S1 += ia.S1row;
-                    ia.S1row = 0;
-                }
-                if (!has1) break;
-                live &= live - 1;
-                const int used1 = 64 - len0;                  // entries taken from row j1
-                if (len1 > used1) {
-                    j0 = j1;
-                    pos = xb1 + used1;
-                    end0 = xe1;
-                    K0 = L0;
-                    K1 = L1;
-                    K2 = L2;
-                    trow0 = trow1;
+    // Overlap counts: each lane holds its own row's interval lengths; the warp
+    // sums below give the item's counts.
+    if (IMG) ia.n = (uint32_t)(my_ie - my_ib);
+    if (MASK) ma.n = (uint32_t)(my_ve - my_vb);
+
+    // The rows' visit intervals are swept as one sequence in passes of 64
+    // voxels (lane l takes entries l and l + 32): a pass inside one row has
+    // no validity predicates; a pass across a row end takes the rest of that
+    // row and the start of the next non-empty row.
+    uint32_t live = __ballot_sync(0xffffffffu, my_ve > my_vb);
+    const uint32_t noclamp = __ballot_sync(0xffffffffu, my_noclamp);
+    const uint8_t *tgt = IMG ? a.tgt_img : a.tgt_mask;
+    if (live) {
+        int j0 = __ffs(live) - 1;
+        live &= live - 1;
+        int pos = __shfl_sync(0xffffffffu, my_vb, j0), end0 = __shfl_sync(0xffffffffu, my_ve, j0);
+        int ib0 = __shfl_sync(0xffffffffu, my_ib, j0), ie0 = __shfl_sync(0xffffffffu, my_ie, j0);
+        float K0 = __shfl_sync(0xffffffffu, myK0, j0), K1 = __shfl_sync(0xffffffffu, myK1, j0),
+              K2 = __shfl_sync(0xffffffffu, myK2, j0);
+        uint32_t trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
+        float xf = (float)(pos + lane);
+        uint32_t toff = trow0 + (uint32_t)(pos + lane);
+        for (;;) {
+            const int len0 = end0 - pos;
+            if (len0 >= 64) {
+                const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), splat(K0), splat(K1), splat(K2), 0u, 0u,
+                               tgt + toff, a.tgt_mask + toff};
+                const bool nc = IMG && ((noclamp >> j0) & 1u);
+                if (BOTH && !(pos >= ib0 && pos + 64 <= ie0)) {   // the image interval ends in this pass
+                    const int x = pos + lane;
+                    const bool iv0 = x >= ib0 && x < ie0, iv1 = x + 32 >= ib0 && x + 32 < ie0;
+                    if (nc)
+                        eval_pair<IMG, MASK, true, false, true, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true, true,
+                                                                      iv0, iv1, ia, ma);
+                    else
+                        eval_pair<IMG, MASK, true, false, false, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true,
+                                                                       true, iv0, iv1, ia, ma);
+                } else if (nc) {
+                    eval_pair<IMG, MASK, true, true, true, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true, true, true,
+                                                                 true, ia, ma);
                 } else {
-                    if (!live) break;
-                    j0 = __ffs(live) - 1;
-                    live &= live - 1;
-                    pos = __shfl_sync(0xffffffffu, my_xb, j0);
-                    end0 = __shfl_sync(0xffffffffu, my_xe, j0);
-                    K0 = __shfl_sync(0xffffffffu, myK0, j0);
-                    K1 = __shfl_sync(0xffffffffu, myK1, j0);
-                    K2 = __shfl_sync(0xffffffffu, myK2, j0);
-                    trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
+                    eval_pair<IMG, MASK, true, true, false, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true, true,
+                                                                  true, true, ia, ma);
                 }
-                xf = (float)(pos + lane);
+                pos += 64;
+                xf = __fadd_rn(xf, 64.0f);
+                toff += 64u;
+                continue;
             }
+            const bool has1 = live != 0u;
+            if (len0 == 0 && !has1) break;
+            const int j1 = has1 ? __ffs(live) - 1 : j0;
+            const int xb1 = __shfl_sync(0xffffffffu, my_vb, j1), xe1 = __shfl_sync(0xffffffffu, my_ve, j1);
+            const int ib1 = __shfl_sync(0xffffffffu, my_ib, j1), ie1 = __shfl_sync(0xffffffffu, my_ie, j1);
+            const float L0 = __shfl_sync(0xffffffffu, myK0, j1), L1 = __shfl_sync(0xffffffffu, myK1, j1),
+                        L2 = __shfl_sync(0xffffffffu, myK2, j1);
+            const int len1 = has1 ? xe1 - xb1 : 0;
+            const uint32_t trow1 = (uint32_t)(first + j1) * (uint32_t)TX;
+            const int e0 = lane, e1 = lane + 32;          // entries of this pass
+            const bool in0a = e0 < len0, in1a = e1 < len0;
+            const bool ok0 = in0a || e0 - len0 < len1, ok1 = in1a || e1 - len0 < len1;
+            // entries past both rows read voxel 0 of row j0 and are not taken
+            const int x0 = in0a ? pos + e0 : (ok0 ? xb1 + e0 - len0 : 0);
+            const int x1 = in1a ? pos + e1 : (ok1 ? xb1 + e1 - len0 : 0);
+            const bool iv0 = ok0 && (in0a ? x0 >= ib0 && x0 < ie0 : x0 >= ib1 && x0 < ie1);
+            const bool iv1 = ok1 && (in1a ? x1 >= ib0 && x1 < ie0 : x1 >= ib1 && x1 < ie1);
+            const PairIn v{pair((float)x0, (float)x1), pair(in0a ? K0 : L0, in1a ? K0 : L0),
+                           pair(in0a ? K1 : L1, in1a ? K1 : L1), pair(in0a ? K2 : L2, in1a ? K2 : L2),
+                           (in0a || !ok0 ? trow0 : trow1) + (uint32_t)x0,
+                           (in1a || !ok1 ? trow0 : trow1) + (uint32_t)x1, nullptr, nullptr};
+            eval_pair<IMG, MASK, false, false, false, FIDX>(a, bits, r0[0], r0[1], r0[2], v, ok0, ok1, iv0, iv1,
+                                                            ia, ma);
             if (IMG) {
                 ia.S1 += ia.S1row;
                 ia.S1row = 0;
             }
+            if (!has1) break;
+            live &= live - 1;
+            const int used1 = 64 - len0;                  // entries taken from row j1
+            if (len1 > used1) {
+                j0 = j1;
+                pos = xb1 + used1;
+                end0 = xe1;
+                ib0 = ib1;
+                ie0 = ie1;
+                K0 = L0;
+                K1 = L1;
+                K2 = L2;
+                trow0 = trow1;
+            } else {
+                if (!live) break;
+                j0 = __ffs(live) - 1;
+                live &= live - 1;
+                pos = __shfl_sync(0xffffffffu, my_vb, j0);
+                end0 = __shfl_sync(0xffffffffu, my_ve, j0);
+                ib0 = __shfl_sync(0xffffffffu, my_ib, j0);
+                ie0 = __shfl_sync(0xffffffffu, my_ie, j0);
+                K0 = __shfl_sync(0xffffffffu, myK0, j0);
+                K1 = __shfl_sync(0xffffffffu, myK1, j0);
+                K2 = __shfl_sync(0xffffffffu, myK2, j0);
+                trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
+            }
+            xf = (float)(pos + lane);
+            toff = trow0 + (uint32_t)(pos + lane);
         }
-    } else {
-        for (int j = 0; j < nrows; ++j) {
-            const int xb = __shfl_sync(0xffffffffu, my_xb, j);
-            const int xe = __shfl_sync(0xffffffffu, my_xe, j);
-            if (xb >= xe) continue;                       // warp-uniform
-            const f2 K0 = splat(__shfl_sync(0xffffffffu, myK0, j));
-            const f2 K1 = splat(__shfl_sync(0xffffffffu, myK1, j));
-            const f2 K2 = splat(__shfl_sync(0xffffffffu, myK2, j));
-            const uint32_t trow = (uint32_t)(first + j) * (uint32_t)TX;
-            int x = xb + lane;
-            float xf = (float)x;
-            for (; x < xe; x += 64, xf = __fadd_rn(xf, 64.0f)) {
-                const bool valid1 = x + 32 < xe;
-                const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), K0, K1, K2, trow + (uint32_t)x,
-                               valid1 ? trow + (uint32_t)x + 32u : trow};
-                eval_pair<IMG, MASK, false, false>(a, bits, r0[0], r0[1], r0[2], v, true, valid1, ia, ma);
-            }
-            if (IMG) {
-                ia.S1 += ia.S1row;
-                ia.S1row = 0;
-            }
+        if (IMG) {
+            ia.S1 += ia.S1row;
+            ia.S1row = 0;
         }
     }
 
@@ -495,17 +550,16 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
 // consecutive items (spatially adjacent rows of one particle) and the grid
 // covers all items in several waves, so no block barrier is needed after the
 // optional shared-memory load of the mask and finished CTAs are replaced by
-// fresh ones.  Single-mode kernels visit only each row's exact inside
-// interval (EXACT).
-// Resident CTAs per SM the register allocation must allow: image-only 4
-// (64 registers), combined 3 (80; at 4 it spills), mask 4 (56 needed).
+// fresh ones.
+// Resident CTAs per SM the register allocation must allow: image-only and
+// combined 3 (80 registers; 4 CTAs, 64 registers, measured no faster), mask 4.
 #ifndef PF_MEASURE_MIN_BLOCKS_IMG
-#define PF_MEASURE_MIN_BLOCKS_IMG 4
+#define PF_MEASURE_MIN_BLOCKS_IMG 3
 #endif
 #ifndef PF_MEASURE_MIN_BLOCKS_COMBINED
 #define PF_MEASURE_MIN_BLOCKS_COMBINED 3
 #endif
-template <bool IMG, bool MASK, bool MASK_SMEM>
+template <bool IMG, bool MASK, bool MASK_SMEM, bool FIDX>
 __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_COMBINED
                                                         : (IMG ? PF_MEASURE_MIN_BLOCKS_IMG : 4))
     k_measure(const MeasureArgs a) {
@@ -522,7 +576,7 @@ __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_
     const long long items = (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
     const long long item0 = ((long long)blockIdx.x * kWarps + warp) * kItemsPerWarp;
     const long long item1 = min(items, item0 + kItemsPerWarp);
-    for (long long item = item0; item < item1; ++item) measure_item<IMG, MASK>(a, bits, item, lane);
+    for (long long item = item0; item < item1; ++item) measure_item<IMG, MASK, FIDX>(a, bits, item, lane);
 }
 
 // Measurement of many registrations in one launch: the items of the listed
@@ -546,13 +600,13 @@ __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batc
         }
         const BatchReg &R = regs[list[lo]];
         if (*R.B.k >= R.n_iters) continue;          // warp-uniform
-        measure_item<IMG, MASK>(R.ma, R.ma.src_bits, item - offs[lo], lane);
+        measure_item<IMG, MASK, false>(R.ma, R.ma.src_bits, item - offs[lo], lane);
     }
 }
 
-template <bool IMG, bool MASK, bool SMEM>
+template <bool IMG, bool MASK, bool SMEM, bool FIDX = false>
 cudaError_t launch_variant(const MeasureArgs &a, size_t smem, cudaStream_t s) {
-    auto kern = k_measure<IMG, MASK, SMEM>;
+    auto kern = k_measure<IMG, MASK, SMEM, FIDX>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -584,9 +638,10 @@ __global__ void k_pack_quads(const uint8_t *__restrict__ S, int SX, int SY, int 
 }  // namespace
 
 // Rows per work item (one warp, 32 rows).  A thread then visits at most
-// 32 * ceil(X/32) <= 2048 voxels of one particle per item (X <= 2048), so its
-// 32-bit partial sums n, T1 < 2^20 and T2 < 2^27 stay exact; S1 is moved to
-// 64 bits after every row (a row adds < 64 * 2^23).
+// 2 * ceil(32 X / 64) <= 2048 voxels of one particle per item (X <= 2048), so
+// its 32-bit partial sums n, T1 < 2^20 and T2 < 2^27 stay exact; S1 is moved
+// to 64 bits after every pass across a row end (in between, the passes of one
+// row add < 32 * 2 * 2^23).
 int rows_per_item_for(int) { return kRowsPerWarp; }
 
 cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_t *quad, cudaStream_t s) {
@@ -620,9 +675,15 @@ cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream
     const size_t nvox = (size_t)a.g.sd[0] * a.g.sd[1] * a.g.sd[2];
     const size_t smem_bits = ((nvox + 31) / 32) * 4;
     const bool smem = mask && smem_bits <= 160 * 1024;
-    if (img && mask) return smem ? launch_variant<true, true, true>(a, smem_bits, s)
-                                 : launch_variant<true, true, false>(a, 0, s);
-    if (img) return launch_variant<true, false, false>(a, 0, s);
+    const bool fidx = nvox <= ((size_t)1 << 23);   // quad indices formed in fp32
+    if (img && mask) {
+        if (smem) return fidx ? launch_variant<true, true, true, true>(a, smem_bits, s)
+                              : launch_variant<true, true, true, false>(a, smem_bits, s);
+        return fidx ? launch_variant<true, true, false, true>(a, 0, s)
+                    : launch_variant<true, true, false, false>(a, 0, s);
+    }
+    if (img) return fidx ? launch_variant<true, false, false, true>(a, 0, s)
+                         : launch_variant<true, false, false, false>(a, 0, s);
     return smem ? launch_variant<false, true, true>(a, smem_bits, s)
                 : launch_variant<false, true, false>(a, 0, s);
 }
