@@ -57,8 +57,8 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of one measurement launch from an ncu capture (profiles/), with
 # the hash of the kernel source it was taken on; reported as null once the
 # kernel changes.
-NCU_TRAFFIC = {"measure_cu_sha1": "b8bbc4c498d029315999f65dbd2d9d25a2361c25",
-               "bytes_per_launch": 34672896 + 3840}   # profiles/measure_image224x208x176_n2048.md
+NCU_TRAFFIC = {"measure_cu_sha1": "0f955ba575eedb960c4103da547d882557290c93",
+               "bytes_per_launch": 34772224}   # the ncu capture summarised under profiles/
 
 
 def parse():
