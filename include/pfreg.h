@@ -43,13 +43,18 @@ extern "C" {
 
 typedef struct pf_ctx pf_ctx;
 
-/* A volume description.  data points to X*Y*Z bytes; is_device = 1 when it is
- * a device pointer on the current device, 0 for host memory. */
+/* A volume description.  data points to X*Y*Z bytes, x fastest; is_device =
+ * 1 when it is a device pointer on the current device, 0 for host memory.
+ * origin is the world position of voxel (0,0,0) and spacing the voxel size
+ * per axis (Table 1 lists anisotropic ones), both in world units (mm);
+ * voxel p sits at origin + spacing * p.  Translations and their limits are
+ * in the same world units.  Spacing must be finite and > 0 (1 = voxel units). */
 typedef struct {
     const void *data;
     int32_t dims[3];
     float origin[3];
     int32_t is_device;
+    float spacing[3];
 } pf_volume;
 
 /* Measurement modes (similarity of Sec. 3.3-3.4):
@@ -72,7 +77,7 @@ typedef struct {
     int32_t mode;             /* pf_mode */
     int32_t n_particles;      /* 1 .. 65536 */
     float rot_limit[3];       /* radians, each in (0, pi/2] */
-    float trans_limit[3];     /* voxels, each in (0, 2048] */
+    float trans_limit[3];     /* world units (voxels at unit spacing), each in (0, 2048] */
     float sigma0_frac;        /* (0, 1] */
     float sigma_decay;        /* (0, 1] */
     int32_t gamma_log2;       /* 0 .. 10 */
@@ -82,11 +87,23 @@ typedef struct {
                                  estimate and log its Dice against the target mask (Sec. 3.2:
                                  the masks validate image-based registration after each
                                  iteration); needs both masks, also in image mode */
+    int32_t estimator;        /* pf_estimator: how the estimate's rotation is averaged */
 } pf_config;
+
+/* Estimate of an iteration (Fig. 1 "estimation"), from the measured cloud
+ * and its integer weights W (uniform when all W are 0):
+ *   PF_EST_MEAN        weighted mean of the six pose parameters;
+ *   PF_EST_QUATERNION  translations as above; the rotation is the weighted
+ *                      quaternion average, the eigenvector of the largest
+ *                      eigenvalue of sum_i W_i q_i q_i^T (sign-free), turned
+ *                      back into the R = Rz Rx Ry angles.  Unlike the angle
+ *                      mean it is not biased by the curvature of the angle
+ *                      parametrisation when the cloud is wide. */
+typedef enum { PF_EST_MEAN = 0, PF_EST_QUATERNION = 1 } pf_estimator;
 
 /* Fill cfg with the defaults: PF_MASK_DICE, N = 256, limits 15 deg / 8 voxels,
  * sigma0_frac 0.25, sigma_decay 0.8, gamma_log2 5, seed 0,
- * min_overlap_frac 0.01, trace_estimate 0. */
+ * min_overlap_frac 0.01, trace_estimate 0, estimator PF_EST_MEAN. */
 void pf_config_default(pf_config *cfg);
 
 /* Create a registration context (Sec. 3.1 problem statement: source and target
@@ -124,13 +141,14 @@ int pf_register_destroy(pf_ctx *ctx);
  * frames_in / frames_out: host arrays of n_frames DEVICE pointers, each frame
  * src_dims resp. tgt_dims bytes.  out(p) = round-half-even of the trilinear
  * sample (interp = 1) or the nearest voxel (interp = 0) of the source at q(p),
- * 0 where q(p) falls outside the source grid.  Allocates nothing; runs
- * asynchronously on cuda_stream.  Errors: PF_EINVAL (NULL, dims, pose
- * rotation outside [-pi/2, pi/2], non-finite pose), PF_ECUDA. */
+ * 0 where q(p) falls outside the source grid.  Spacings may be NULL (1).
+ * Allocates nothing; runs asynchronously on cuda_stream.  Errors: PF_EINVAL
+ * (NULL, dims, spacing, pose rotation outside [-pi/2, pi/2], non-finite
+ * pose), PF_ECUDA. */
 int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32_t src_dims[3],
-                  const float src_origin[3], uint8_t *const *frames_out,
-                  const int32_t tgt_dims[3], const float tgt_origin[3], const float pose[6],
-                  int32_t interp, void *cuda_stream);
+                  const float src_origin[3], const float src_spacing[3], uint8_t *const *frames_out,
+                  const int32_t tgt_dims[3], const float tgt_origin[3], const float tgt_spacing[3],
+                  const float pose[6], int32_t interp, void *cuda_stream);
 
 /* ---- batches: many registrations stepped together ---- */
 
@@ -244,9 +262,12 @@ int pf_measure_matrices(pf_ctx *ctx, const float *mats, int32_t M, const float a
 int pf_measure_matrices_noalloc(pf_ctx *ctx, const float *mats, int32_t M, const float a[3],
                                 uint64_t *moments_out);
 
-/* Pose -> (matrix [12], offset a [3]) exactly as the filter computes it. */
+/* Pose -> (matrix [12], offset a [3]) exactly as the filter computes it
+ * (Eq. 3 with the spacings: M = diag(1/s_S) R diag(s_T), b and a in source
+ * resp. target voxel units).  src_spacing / tgt_spacing may be NULL (1). */
 int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float src_origin[3],
-                   const float tgt_origin[3], float mat_out[12], float a_out[3]);
+                   const float src_spacing[3], const float tgt_origin[3], const float tgt_spacing[3],
+                   float mat_out[12], float a_out[3]);
 
 /* Philox4x32-10 of (ctr, key) computed on the device (tests of the generator). */
 int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -83,6 +83,7 @@ def _declare(L):
     L.orc_cos.restype = C.c_double
     L.orc_rotation.argtypes = [_f32p, _f64p]
     L.orc_pose_matrix.argtypes = [_f32p, _i32p, _f32p, _f32p, _f32p, _f32p]
+    L.orc_pose_matrix_sp.argtypes = [_f32p, _i32p, _f32p, _vp, _f32p, _vp, _f32p, _f32p]
     for name in ("orc_measure_mask", "orc_measure_image"):
         getattr(L, name).argtypes = [_u8p, _i32p, _u8p, _i32p, _f32p, _f32p, C.c_int32, _u64p]
     L.orc_ncc2_f64.argtypes = [_u8p, _i32p, _u8p, _i32p, _f32p, _f32p, C.c_int32, _f64p]
@@ -101,7 +102,7 @@ def _declare(L):
     L.orc_resample_offset.argtypes = [C.c_uint64, C.c_int32]
     L.orc_resample_offset.restype = C.c_uint32
     L.orc_register.argtypes = [
-        C.c_int32, _vp, _vp, _vp, _vp, _i32p, _f32p, _i32p, _f32p, C.c_int32, C.c_int32,
+        C.c_int32, _vp, _vp, _vp, _vp, _i32p, _f32p, _vp, _i32p, _f32p, _vp, C.c_int32, C.c_int32,
         _f32p, _f32p, C.c_float, C.c_float, C.c_int32, C.c_uint64, C.c_float,
         _f32p, C.c_int32, C.c_int32, _f64p, _vp, _vp, _vp, _vp, _vp, _vp]
     L.orc_register.restype = C.c_int32
@@ -138,22 +139,33 @@ def rotation(pose):
     return R.reshape(3, 3)
 
 
-def pose_matrix(pose, src_dims, src_origin, tgt_origin):
-    """(M float32[12], a float32[3]) with q = R (p - a) + b."""
+def _sp(spacing):
+    """Spacing argument: None (unit) or float32[3]."""
+    return None if spacing is None else _c(np.broadcast_to(np.asarray(spacing, np.float32), (3,)), np.float32)
+
+
+def pose_matrix(pose, src_dims, src_origin, tgt_origin, src_spacing=None, tgt_spacing=None):
+    """(M float32[12], a float32[3]) with q = M3 (p - a) + b (voxel units)."""
     M = np.zeros(12, np.float32)
     a = np.zeros(3, np.float32)
-    lib().orc_pose_matrix(_c(pose, np.float32), _c(src_dims, np.int32), _c(src_origin, np.float32),
-                          _c(tgt_origin, np.float32), M, a)
+    ss, ts = _sp(src_spacing), _sp(tgt_spacing)
+    if ss is None and ts is None:
+        lib().orc_pose_matrix(_c(pose, np.float32), _c(src_dims, np.int32), _c(src_origin, np.float32),
+                              _c(tgt_origin, np.float32), M, a)
+    else:
+        ptr = lambda v: None if v is None else v.ctypes.data_as(C.c_void_p)  # noqa: E731
+        lib().orc_pose_matrix_sp(_c(pose, np.float32), _c(src_dims, np.int32), _c(src_origin, np.float32),
+                                 ptr(ss), _c(tgt_origin, np.float32), ptr(ts), M, a)
     return M, a
 
 
-def pose_matrices(poses6xN, src_dims, src_origin, tgt_origin):
+def pose_matrices(poses6xN, src_dims, src_origin, tgt_origin, src_spacing=None, tgt_spacing=None):
     poses6xN = np.asarray(poses6xN, np.float32)
     N = poses6xN.shape[1]
     mats = np.zeros((N, 12), np.float32)
     a = None
     for i in range(N):
-        mats[i], a = pose_matrix(poses6xN[:, i], src_dims, src_origin, tgt_origin)
+        mats[i], a = pose_matrix(poses6xN[:, i], src_dims, src_origin, tgt_origin, src_spacing, tgt_spacing)
     return mats, a
 
 
@@ -226,6 +238,56 @@ def estimate(poses6xN, W):
     return est
 
 
+def _qmul(a, b):
+    """Hamilton product of quaternions (w, x, y, z)."""
+    aw, ax, ay, az = a
+    bw, bx, by, bz = b
+    return np.array([aw * bw - ax * bx - ay * by - az * bz,
+                     aw * bx + ax * bw + ay * bz - az * by,
+                     aw * by - ax * bz + ay * bw + az * bx,
+                     aw * bz + ax * by - ay * bx + az * bw])
+
+
+def quaternion(pose):
+    """Unit quaternion (w, x, y, z) of R = Rz(rz) Rx(rx) Ry(ry): qz * qx * qy,
+    each an axis rotation by its half angle (the oracle's fp64 sin/cos)."""
+    rx, ry, rz = (float(v) for v in pose[:3])
+    qx = np.array([cos(rx / 2), sin(rx / 2), 0.0, 0.0])
+    qy = np.array([cos(ry / 2), 0.0, sin(ry / 2), 0.0])
+    qz = np.array([cos(rz / 2), 0.0, 0.0, sin(rz / 2)])
+    return _qmul(qz, _qmul(qx, qy))
+
+
+def quaternion_matrix(q):
+    """Rotation matrix of a unit quaternion (w, x, y, z)."""
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def estimate_quaternion(poses6xN, W):
+    """Estimate (Fig. 1 "estimation") with the rotation averaged as
+    quaternions: translations are the W-weighted mean (uniform when all W are
+    0); the rotation is the unit eigenvector of the largest eigenvalue of
+    sum_i W_i q_i q_i^T, turned back into (rx, ry, rz) of R = Rz Rx Ry
+    (R21 = sin rx, R20 = -cos rx sin ry, R22 = cos rx cos ry,
+    R01 = -sin rz cos rx, R11 = cos rz cos rx)."""
+    poses6xN = np.asarray(poses6xN, np.float32)
+    est = estimate(poses6xN, W)
+    w = np.asarray(W, np.uint64).astype(np.float64)
+    if w.sum() == 0:
+        w = np.ones_like(w)
+    Q = np.stack([quaternion(poses6xN[:, i]) for i in range(poses6xN.shape[1])])
+    A = (Q * w[:, None]).T @ Q / w.sum()
+    vals, vecs = np.linalg.eigh(A)
+    R = quaternion_matrix(vecs[:, -1] / np.linalg.norm(vecs[:, -1]))
+    est[0] = np.arcsin(np.clip(R[2, 1], -1.0, 1.0))
+    est[1] = np.arctan2(-R[2, 0], R[2, 2])
+    est[2] = np.arctan2(-R[0, 1], R[1, 1])
+    return est
+
+
 def init_particles(N, seed, lim6):
     x = np.zeros((6, N), np.float32)
     lib().orc_init(x, N, int(seed), _c(lim6, np.float32))
@@ -248,10 +310,10 @@ def resample_offset(seed, k):
     return lib().orc_resample_offset(int(seed), int(k))
 
 
-def warp(src, src_origin, tgt_dims, tgt_origin, pose, interp=1):
+def warp(src, src_origin, tgt_dims, tgt_origin, pose, interp=1, src_spacing=None, tgt_spacing=None):
     """Warp one source-grid volume into the target grid with the pose."""
     src = _c(src, np.uint8)
-    M, a = pose_matrix(pose, _dims(src), src_origin, tgt_origin)
+    M, a = pose_matrix(pose, _dims(src), src_origin, tgt_origin, src_spacing, tgt_spacing)
     X, Y, Z = tgt_dims
     out = np.zeros((Z, Y, X), np.uint8)
     lib().orc_warp(src, _dims(src), out, _c(tgt_dims, np.int32), M, a, int(interp))
@@ -275,7 +337,7 @@ DEFAULTS = dict(sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, min_overlap_fra
 def register(mode, src_dims, src_origin, tgt_dims, tgt_origin, n_particles, n_iters,
              rot_limit, trans_limit, seed=0, src=None, tgt=None, src_mask=None, tgt_mask=None,
              sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, min_overlap_frac=0.01,
-             poses=None, k0=0, trace=True):
+             poses=None, k0=0, trace=True, src_spacing=None, tgt_spacing=None):
     """Run the whole filter for ``n_iters`` iterations starting at iteration
     ``k0`` (from ``poses`` [6,N] if given, else the Philox initial cloud).
 
@@ -314,7 +376,8 @@ def register(mode, src_dims, src_origin, tgt_dims, tgt_origin, n_particles, n_it
         tr, trp = {}, [None] * 6
     rc = lib().orc_register(
         mode, *[ptr(v) for v in vols], _c(src_dims, np.int32), _c(src_origin, np.float32),
-        _c(tgt_dims, np.int32), _c(tgt_origin, np.float32), N, K, rl, tl,
+        ptr(_sp(src_spacing)), _c(tgt_dims, np.int32), _c(tgt_origin, np.float32), ptr(_sp(tgt_spacing)),
+        N, K, rl, tl,
         float(sigma0_frac), float(sigma_decay), int(gamma_log2), int(seed),
         float(min_overlap_frac), x, int(have), int(k0), est, *trp)
     if rc != 0:

@@ -113,11 +113,16 @@ double orc_cos(double x)
 
 /* ------------------------------------------------------------------------ */
 /* Pose -> 3x4 matrix (Eq. 3).  R = Rz(rz) * Rx(rx) * Ry(ry) by two plain    */
-/* 3x3 products in fp64, each entry rounded once to fp32.  The map takes a   */
-/* target voxel index p to the source continuous index                       */
-/*     q = R (p - a) + b,   a = c - o_T,   b = c + t - o_S,                  */
-/* c = o_S + (dims_S - 1)/2 the source grid centre (reading: the rotation    */
-/* centre).  M holds [r00 r01 r02 b0 | r10 r11 r12 b1 | r20 r21 r22 b2].     */
+/* 3x3 products in fp64.  World positions (the Euler transform of Sec. 3.3   */
+/* acts in physical space; Table 1 gives the voxel sizes): target voxel p    */
+/* sits at w = o_T + s_T p; it maps to R (w - c) + c + t, which is source    */
+/* voxel q = (R (w - c) + c + t - o_S) / s_S, so                             */
+/*     q = M3 (p - a) + b,   M3_ij = (R_ij s_T,j) / s_S,i,                   */
+/*     a = (c - o_T) / s_T,  b = ((c + t) - o_S) / s_S,                      */
+/* c = o_S + s_S (dims_S - 1)/2 the source grid centre (reading: the         */
+/* rotation centre), each entry computed in fp64 and rounded once to fp32.   */
+/* With unit spacings M3 = R, a = c - o_T, b = c + t - o_S.                  */
+/* M holds [r00 r01 r02 b0 | r10 r11 r12 b1 | r20 r21 r22 b2].               */
 /* ------------------------------------------------------------------------ */
 static void matmul3(const double A[3][3], const double B[3][3], double C[3][3])
 {
@@ -145,20 +150,30 @@ void orc_rotation(const float pose[6], double R[9])
         for (int j = 0; j < 3; ++j) R[3 * i + j] = Rm[i][j];
 }
 
+/* sspacing / tspacing may be NULL (unit spacing). */
+void orc_pose_matrix_sp(const float pose[6], const int32_t sdims[3], const float sorigin[3],
+                        const float sspacing[3], const float torigin[3], const float tspacing[3],
+                        float M[12], float a[3])
+{
+    double R[9], ss[3], ts[3];
+    orc_rotation(pose, R);
+    for (int d = 0; d < 3; ++d) {
+        ss[d] = sspacing ? (double)sspacing[d] : 1.0;
+        ts[d] = tspacing ? (double)tspacing[d] : 1.0;
+    }
+    for (int i = 0; i < 3; ++i) {
+        double c = (double)sorigin[i] + ss[i] * ((double)(sdims[i] - 1) / 2.0);
+        a[i] = (float)((c - (double)torigin[i]) / ts[i]);
+        double b = ((c + (double)pose[3 + i]) - (double)sorigin[i]) / ss[i];
+        for (int j = 0; j < 3; ++j) M[4 * i + j] = (float)((R[3 * i + j] * ts[j]) / ss[i]);
+        M[4 * i + 3] = (float)b;
+    }
+}
+
 void orc_pose_matrix(const float pose[6], const int32_t sdims[3], const float sorigin[3],
                      const float torigin[3], float M[12], float a[3])
 {
-    double R[9];
-    orc_rotation(pose, R);
-    for (int i = 0; i < 3; ++i) {
-        double c = (double)sorigin[i] + (double)(sdims[i] - 1) / 2.0;
-        a[i] = (float)(c - (double)torigin[i]);
-        double b = (c + (double)pose[3 + i]) - (double)sorigin[i];
-        M[4 * i + 0] = (float)R[3 * i + 0];
-        M[4 * i + 1] = (float)R[3 * i + 1];
-        M[4 * i + 2] = (float)R[3 * i + 2];
-        M[4 * i + 3] = (float)b;
-    }
+    orc_pose_matrix_sp(pose, sdims, sorigin, NULL, torigin, NULL, M, a);
 }
 
 /* q for target voxel (x, y, z), in this fixed fp32 order (no FMA):          */
@@ -529,11 +544,11 @@ uint32_t orc_resample_offset(uint64_t seed, int32_t k)
 /* Output: the estimate of the last iteration.  Optional traces (NULL skips): */
 /*   tr_poses [K][6][N] (measured poses), tr_mom [K][N][12], tr_score [K][N], */
 /*   tr_W [K][N], tr_idx [K][N], tr_est [K][6].                              */
-/* Volumes unused by the mode may be NULL.                                    */
+/* Volumes unused by the mode may be NULL; so are the spacings ss, ts (1).  */
 /* ------------------------------------------------------------------------ */
 int32_t orc_register(int32_t mode, const uint8_t *src, const uint8_t *tgt, const uint8_t *src_mask,
-                     const uint8_t *tgt_mask, const int32_t sd[3], const float so[3],
-                     const int32_t td[3], const float to[3], int32_t N, int32_t K,
+                     const uint8_t *tgt_mask, const int32_t sd[3], const float so[3], const float ss[3],
+                     const int32_t td[3], const float to[3], const float ts[3], int32_t N, int32_t K,
                      const float rot_lim[3], const float trans_lim[3], float sigma0_frac,
                      float decay, int32_t gamma_log2, uint64_t seed, float min_overlap_frac,
                      float *poses_inout, int32_t have_poses, int32_t k0, double est_out[6],
@@ -567,7 +582,7 @@ int32_t orc_register(int32_t mode, const uint8_t *src, const uint8_t *tgt, const
         for (int32_t i = 0; i < N; ++i) {
             float pose[6];
             for (int d = 0; d < 6; ++d) pose[d] = x[(int64_t)d * N + i];
-            orc_pose_matrix(pose, sd, so, to, mats + 12 * (int64_t)i, a);
+            orc_pose_matrix_sp(pose, sd, so, ss, to, ts, mats + 12 * (int64_t)i, a);
         }
         memset(mom, 0, sizeof(uint64_t) * 12 * (size_t)N);
         for (int32_t i = 0; i < N; ++i) {

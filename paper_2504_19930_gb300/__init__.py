@@ -46,14 +46,14 @@ class PfError(RuntimeError):
 
 class pf_volume(C.Structure):
     _fields_ = [("data", C.c_void_p), ("dims", C.c_int32 * 3), ("origin", C.c_float * 3),
-                ("is_device", C.c_int32)]
+                ("is_device", C.c_int32), ("spacing", C.c_float * 3)]
 
 
 class pf_config(C.Structure):
     _fields_ = [("mode", C.c_int32), ("n_particles", C.c_int32), ("rot_limit", C.c_float * 3),
                 ("trans_limit", C.c_float * 3), ("sigma0_frac", C.c_float),
                 ("sigma_decay", C.c_float), ("gamma_log2", C.c_int32), ("seed", C.c_uint64),
-                ("min_overlap_frac", C.c_float), ("trace_estimate", C.c_int32)]
+                ("min_overlap_frac", C.c_float), ("trace_estimate", C.c_int32), ("estimator", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -92,13 +92,13 @@ def _declare(L):
     L.pf_step.argtypes = [vp, i32]
     L.pf_estimate.argtypes = [vp, vp, vp]
     L.pf_register_destroy.argtypes = [vp]
-    L.warp_sequence.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32, vp]
+    L.warp_sequence.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]
     L.pf_get_iteration.argtypes = [vp, vp]
     L.pf_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.pf_set_state.argtypes = [vp, vp, i32]
     L.pf_get_log.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.pf_measure_matrices.argtypes = [vp, vp, i32, vp, vp]
-    L.pf_pose_matrix.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pf_pose_matrix.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.pf_philox.argtypes = [vp, vp, vp]
     L.pf_measure_matrices_noalloc.argtypes = [vp, vp, i32, vp, vp]
     L.pf_batch_create.argtypes = [C.POINTER(vp), vp, i32, vp]
@@ -155,8 +155,9 @@ def _stream_handle(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def make_volume(vol, origin=(0.0, 0.0, 0.0), dims=None):
-    """pf_volume from a (Z,Y,X) uint8 numpy array or torch tensor (CPU or CUDA)."""
+def make_volume(vol, origin=(0.0, 0.0, 0.0), dims=None, spacing=(1.0, 1.0, 1.0)):
+    """pf_volume from a (Z,Y,X) uint8 numpy array or torch tensor (CPU or CUDA);
+    origin and spacing (x, y, z) in world units."""
     if vol is None:
         return None
     is_dev = 0
@@ -176,6 +177,7 @@ def make_volume(vol, origin=(0.0, 0.0, 0.0), dims=None):
     v.dims[:] = [int(x) for x in d]
     v.origin[:] = [float(x) for x in origin]
     v.is_device = is_dev
+    v.spacing[:] = [float(x) for x in np.broadcast_to(np.asarray(spacing, np.float32), (3,))]
     return v
 
 
@@ -185,9 +187,12 @@ def pf_config_default() -> pf_config:
     return cfg
 
 
+ESTIMATORS = {"mean": 0, "quaternion": 1}
+
+
 def make_config(mode="mask_dice", n_particles=256, rot_limit=0.2617994, trans_limit=8.0,
                 sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, seed=0, min_overlap_frac=0.01,
-                trace_estimate=False):
+                trace_estimate=False, estimator="mean"):
     cfg = pf_config_default()
     cfg.mode = MODES.get(mode, mode)
     cfg.n_particles = int(n_particles)
@@ -199,6 +204,7 @@ def make_config(mode="mask_dice", n_particles=256, rot_limit=0.2617994, trans_li
     cfg.seed = int(seed)
     cfg.min_overlap_frac = float(min_overlap_frac)
     cfg.trace_estimate = int(bool(trace_estimate))
+    cfg.estimator = ESTIMATORS.get(estimator, estimator)
     return cfg
 
 
@@ -250,18 +256,23 @@ def pf_register_destroy(ctx):
     _check(load().pf_register_destroy(ctx))
 
 
+def _spacing3(sp):
+    return _np(np.broadcast_to(np.asarray(sp, np.float32), (3,)), np.float32)
+
+
 def warp_sequence(frames_in, src_dims, src_origin, frames_out, tgt_dims, tgt_origin, pose,
-                  interp=1, stream=None):
+                  interp=1, stream=None, src_spacing=(1.0, 1.0, 1.0), tgt_spacing=(1.0, 1.0, 1.0)):
     """frames_in / frames_out: sequences of CUDA uint8 tensors (one per frame)."""
     n = len(frames_in)
     if len(frames_out) != n:
         raise ValueError("frames_in and frames_out differ in length")
     fin = (C.c_void_p * max(n, 1))(*[f.data_ptr() for f in frames_in])
     fout = (C.c_void_p * max(n, 1))(*[f.data_ptr() for f in frames_out])
-    sd, so = _np(src_dims, np.int32), _np(src_origin, np.float32)
-    td, to, ps = _np(tgt_dims, np.int32), _np(tgt_origin, np.float32), _np(pose, np.float32)
-    _check(load().warp_sequence(fin, n, _ptr(sd), _ptr(so), fout, _ptr(td), _ptr(to), _ptr(ps), int(interp),
-                                _stream_handle(stream)))
+    sd, so, ss = _np(src_dims, np.int32), _np(src_origin, np.float32), _spacing3(src_spacing)
+    td, to, ts = _np(tgt_dims, np.int32), _np(tgt_origin, np.float32), _spacing3(tgt_spacing)
+    ps = _np(pose, np.float32)
+    _check(load().warp_sequence(fin, n, _ptr(sd), _ptr(so), _ptr(ss), fout, _ptr(td), _ptr(to), _ptr(ts),
+                                _ptr(ps), int(interp), _stream_handle(stream)))
 
 
 def pf_get_iteration(ctx) -> int:
@@ -322,12 +333,14 @@ def pf_measure_matrices_noalloc(ctx, mats, a):
     return out
 
 
-def pf_pose_matrix(pose, src_dims, src_origin, tgt_origin):
+def pf_pose_matrix(pose, src_dims, src_origin, tgt_origin, src_spacing=(1.0, 1.0, 1.0),
+                   tgt_spacing=(1.0, 1.0, 1.0)):
     M = np.zeros(12, np.float32)
     a = np.zeros(3, np.float32)
     ps, sd = _np(pose, np.float32), _np(src_dims, np.int32)
     so, to = _np(src_origin, np.float32), _np(tgt_origin, np.float32)
-    _check(load().pf_pose_matrix(_ptr(ps), _ptr(sd), _ptr(so), _ptr(to),
+    ss, ts = _spacing3(src_spacing), _spacing3(tgt_spacing)
+    _check(load().pf_pose_matrix(_ptr(ps), _ptr(sd), _ptr(so), _ptr(ss), _ptr(to), _ptr(ts),
                                  _ptr(M), _ptr(a)))
     return M, a
 
@@ -363,12 +376,14 @@ class Registration:
     """
 
     def __init__(self, mode, src=None, tgt=None, src_mask=None, tgt_mask=None,
-                 src_origin=(0, 0, 0), tgt_origin=(0, 0, 0), stream=None, **cfg):
+                 src_origin=(0, 0, 0), tgt_origin=(0, 0, 0), stream=None, src_spacing=(1.0, 1.0, 1.0),
+                 tgt_spacing=(1.0, 1.0, 1.0), **cfg):
         self.cfg = make_config(mode, **cfg)
         self.N = self.cfg.n_particles
         self.stream = stream
-        vols = [make_volume(src, src_origin), make_volume(tgt, tgt_origin),
-                make_volume(src_mask, src_origin), make_volume(tgt_mask, tgt_origin)]
+        vols = [make_volume(src, src_origin, spacing=src_spacing), make_volume(tgt, tgt_origin, spacing=tgt_spacing),
+                make_volume(src_mask, src_origin, spacing=src_spacing),
+                make_volume(tgt_mask, tgt_origin, spacing=tgt_spacing)]
         self.ctx = pf_register_init(*vols, self.cfg, stream)
 
     def step(self, n_iters=1):
@@ -436,7 +451,7 @@ def _to_cuda(a, stream=None):
 
 def register_sequence(mode, src=None, tgt=None, frames=(), n_iters=1, src_origin=(0, 0, 0),
                       tgt_origin=(0, 0, 0), src_mask=None, tgt_mask=None, interp=1, out=None,
-                      with_score=False, **cfg):
+                      with_score=False, src_spacing=(1.0, 1.0, 1.0), tgt_spacing=(1.0, 1.0, 1.0), **cfg):
     """Register source to target, then warp every source frame by the estimate.
 
     The whole user-facing path: volumes (host numpy / host or pinned torch /
@@ -450,7 +465,8 @@ def register_sequence(mode, src=None, tgt=None, frames=(), n_iters=1, src_origin
     """
     import torch
     reg = Registration(mode, src=src, tgt=tgt, src_mask=src_mask, tgt_mask=tgt_mask,
-                       src_origin=src_origin, tgt_origin=tgt_origin, **cfg)
+                       src_origin=src_origin, tgt_origin=tgt_origin, src_spacing=src_spacing,
+                       tgt_spacing=tgt_spacing, **cfg)
     try:
         reg.step(n_iters)
         pose, score = reg.estimate(with_score)
@@ -463,7 +479,7 @@ def register_sequence(mode, src=None, tgt=None, frames=(), n_iters=1, src_origin
     fin = [_to_cuda(f) for f in frames]
     fout = [torch.empty(tshape, dtype=torch.uint8, device="cuda") for _ in fin]
     warp_sequence(fin, sdims, src_origin, fout, (tshape[2], tshape[1], tshape[0]), tgt_origin, pose,
-                  interp)
+                  interp, src_spacing=src_spacing, tgt_spacing=tgt_spacing)
     if out is not None:
         for o, f in zip(out, fout):
             o.copy_(f, non_blocking=True)

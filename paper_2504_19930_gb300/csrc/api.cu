@@ -55,14 +55,26 @@ int check_volume(const pf_volume *v, const char *name) {
         if (v->dims[d] < 2 || v->dims[d] > kMaxDim)
             return fail(PF_EINVAL, "%s dims[%d] = %d outside [2, %d]", name, d, v->dims[d], kMaxDim);
     if (!finite3(v->origin)) return fail(PF_EINVAL, "%s origin is not finite", name);
+    for (int d = 0; d < 3; ++d)
+        if (!(v->spacing[d] > 0.0f && v->spacing[d] <= 1e6f))
+            return fail(PF_EINVAL, "%s spacing[%d] = %g outside (0, 1e6]", name, d, (double)v->spacing[d]);
     return PF_OK;
+}
+
+// Spacing argument of the plain-array entry points: NULL means 1.
+bool spacing_ok(const float *s) {
+    if (!s) return true;
+    for (int d = 0; d < 3; ++d)
+        if (!(s[d] > 0.0f && s[d] <= 1e6f)) return false;
+    return true;
 }
 
 size_t nvox(const int32_t d[3]) { return (size_t)d[0] * d[1] * d[2]; }
 
 bool same_grid(const pf_volume *a, const pf_volume *b) {
     for (int d = 0; d < 3; ++d)
-        if (a->dims[d] != b->dims[d] || a->origin[d] != b->origin[d]) return false;
+        if (a->dims[d] != b->dims[d] || a->origin[d] != b->origin[d] || a->spacing[d] != b->spacing[d])
+            return false;
     return true;
 }
 
@@ -82,6 +94,8 @@ int check_config(const pf_config *c) {
     if (c->gamma_log2 < 0 || c->gamma_log2 > 10) return fail(PF_EINVAL, "gamma_log2 outside [0, 10]");
     if (!(c->min_overlap_frac >= 0.0f && c->min_overlap_frac <= 1.0f))
         return fail(PF_EINVAL, "min_overlap_frac outside [0, 1]");
+    if (c->estimator != PF_EST_MEAN && c->estimator != PF_EST_QUATERNION)
+        return fail(PF_EINVAL, "estimator %d unknown", c->estimator);
     return PF_OK;
 }
 
@@ -90,16 +104,19 @@ cudaError_t copy_in(void *dst, const pf_volume *v, size_t n, cudaStream_t s) {
     return cudaMemcpyAsync(dst, v->data, n, v->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
 }
 
-Geometry make_geometry(const int32_t sd[3], const float so[3], const int32_t td[3], const float to[3]) {
+Geometry make_geometry(const int32_t sd[3], const float so[3], const float *ss, const int32_t td[3],
+                       const float to[3], const float *ts) {
     Geometry g;
     for (int d = 0; d < 3; ++d) {
         g.sd[d] = sd[d];
         g.td[d] = td[d];
         g.so[d] = so[d];
         g.to[d] = to[d];
-        // a = c - o_T with c = o_S + (dims_S - 1)/2: fp64 then one rounding
-        const double c = (double)so[d] + (double)(sd[d] - 1) / 2.0;
-        g.a[d] = (float)(c - (double)to[d]);
+        g.ss[d] = ss ? ss[d] : 1.0f;
+        g.ts[d] = ts ? ts[d] : 1.0f;
+        // a = (c - o_T) / s_T with c = o_S + s_S (dims_S - 1)/2: fp64, one rounding
+        const double c = (double)so[d] + (double)g.ss[d] * ((double)(sd[d] - 1) / 2.0);
+        g.a[d] = (float)((c - (double)to[d]) / (double)g.ts[d]);
     }
     return g;
 }
@@ -263,6 +280,7 @@ void pf_config_default(pf_config *cfg) {
     cfg->seed = 0;
     cfg->min_overlap_frac = 0.01f;
     cfg->trace_estimate = 0;
+    cfg->estimator = PF_EST_MEAN;
 }
 
 const char *pf_last_error(void) { return g_err.c_str(); }
@@ -320,7 +338,7 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     c->mask = mask;
     c->trace = cfg->trace_estimate != 0;
     const int N = cfg->n_particles;
-    const Geometry g = make_geometry(S->dims, S->origin, T->dims, T->origin);
+    const Geometry g = make_geometry(S->dims, S->origin, S->spacing, T->dims, T->origin, T->spacing);
     const size_t ns = nvox(S->dims), nt = nvox(T->dims);
 
     FilterParams &P = c->P;
@@ -338,6 +356,7 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     P.n_min = (uint64_t)((double)cfg->min_overlap_frac * (double)nt);
     P.b_full = 0;
     P.log_capacity = kLogCapacity;
+    P.estimator = cfg->estimator;
 
     FilterBuffers &B = c->B;
     CK(c->alloc(&B.poses, 6 * (size_t)N));
@@ -350,6 +369,7 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     CK(c->alloc(&B.idx, (size_t)N));
     CK(c->alloc(&B.k, 1));
     CK(c->alloc(&B.log, (size_t)kLogCapacity));
+    if (P.estimator == PF_EST_QUATERNION) CK(c->alloc(&B.quat, 4 * (size_t)N));
     CK(c->alloc(&c->d_u64, 4));
     CK(c->alloc(&c->d_score, 1));
 
@@ -623,15 +643,17 @@ int pf_register_destroy(pf_ctx *c) {
 }
 
 int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float src_origin[3],
-                   const float tgt_origin[3], float mat_out[12], float a_out[3]) {
+                   const float src_spacing[3], const float tgt_origin[3], const float tgt_spacing[3],
+                   float mat_out[12], float a_out[3]) {
     if (!pose || !src_dims || !src_origin || !tgt_origin || !mat_out || !a_out)
         return fail(PF_EINVAL, "NULL argument");
+    if (!spacing_ok(src_spacing) || !spacing_ok(tgt_spacing)) return fail(PF_EINVAL, "spacing outside (0, 1e6]");
     for (int d = 0; d < 6; ++d)
         if (!std::isfinite(pose[d])) return fail(PF_EINVAL, "pose is not finite");
     for (int d = 0; d < 3; ++d)
         if (!(std::fabs(pose[d]) <= kHalfPi)) return fail(PF_EINVAL, "rotation outside [-pi/2, pi/2]");
     const int32_t td[3] = {2, 2, 2};
-    const Geometry g = make_geometry(src_dims, src_origin, td, tgt_origin);
+    const Geometry g = make_geometry(src_dims, src_origin, src_spacing, td, tgt_origin, tgt_spacing);
     float *d = nullptr;
     CU(cudaMalloc(&d, sizeof(float) * 18));
     cudaError_t e = cudaMemcpy(d, pose, sizeof(float) * 6, cudaMemcpyHostToDevice);
@@ -657,8 +679,9 @@ int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
 }
 
 int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32_t src_dims[3],
-                  const float src_origin[3], uint8_t *const *frames_out, const int32_t tgt_dims[3],
-                  const float tgt_origin[3], const float pose[6], int32_t interp, void *cuda_stream) {
+                  const float src_origin[3], const float src_spacing[3], uint8_t *const *frames_out,
+                  const int32_t tgt_dims[3], const float tgt_origin[3], const float tgt_spacing[3],
+                  const float pose[6], int32_t interp, void *cuda_stream) {
     if (!frames_in || !frames_out || !src_dims || !src_origin || !tgt_dims || !tgt_origin || !pose)
         return fail(PF_EINVAL, "NULL argument");
     if (n_frames < 0) return fail(PF_EINVAL, "n_frames < 0");
@@ -674,7 +697,8 @@ int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32
         if (!(std::fabs(pose[d]) <= kHalfPi)) return fail(PF_EINVAL, "rotation outside [-pi/2, pi/2]");
     for (int32_t f = 0; f < n_frames; ++f)
         if (!frames_in[f] || !frames_out[f]) return fail(PF_EINVAL, "frame %d pointer is NULL", f);
-    const Geometry g = make_geometry(src_dims, src_origin, tgt_dims, tgt_origin);
+    if (!spacing_ok(src_spacing) || !spacing_ok(tgt_spacing)) return fail(PF_EINVAL, "spacing outside (0, 1e6]");
+    const Geometry g = make_geometry(src_dims, src_origin, src_spacing, tgt_dims, tgt_origin, tgt_spacing);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     for (int32_t f0 = 0; f0 < n_frames; f0 += WarpFrames::kMax) {
         WarpFrames wf;

@@ -94,18 +94,23 @@ PF_HD void mat3_mul(const double A[9], const double B[9], double C[9]) {
 struct Geometry {
     int32_t sd[3];      // source dims
     int32_t td[3];      // target dims
-    float so[3];        // source origin
-    float to[3];        // target origin
-    float a[3];         // c - o_T (fp32)
+    float so[3];        // source origin (world)
+    float to[3];        // target origin (world)
+    float ss[3];        // source spacing (world units per voxel)
+    float ts[3];        // target spacing
+    float a[3];         // (c - o_T) / s_T, target voxel units (fp32)
 };
 
-// Source-grid centre c_d and a_d = c_d - o_T,d.
+// Source-grid centre in world units, c_d = o_S,d + s_S,d (dims_S,d - 1)/2.
 PF_HD double grid_centre(const Geometry &g, int d) {
-    return d_add((double)g.so[d], d_div((double)(g.sd[d] - 1), 2.0));
+    return d_add((double)g.so[d], d_mul((double)g.ss[d], d_div((double)(g.sd[d] - 1), 2.0)));
 }
 
 // Per-particle pose -> matrix on the device: sin/cos of the three angles
-// (taylor_sin / taylor_cos), R = Rz Rx Ry, b = (c + t) - o_S.
+// (taylor_sin / taylor_cos), R = Rz Rx Ry; with the spacings, target voxel p
+// maps to source voxel q = diag(1/s_S) (R (o_T + s_T p - c) + c + t - o_S),
+// i.e. M_ij = (R_ij s_T,j) / s_S,i and b_i = ((c_i + t_i) - o_S,i) / s_S,i
+// (fp64, one rounding to fp32 each; with unit spacings M = R, b = c + t - o_S).
 
 PF_HD void matrix_from_sincos(const float pose[6], double sa, double ca, double sb, double cb,
                                double sg, double cg, const Geometry &g, float M[12]) {
@@ -116,10 +121,11 @@ PF_HD void matrix_from_sincos(const float pose[6], double sa, double ca, double 
     mat3_mul(Rx, Ry, XY);
     mat3_mul(Rz, XY, R);
     for (int i = 0; i < 3; ++i) {
-        const double b = d_sub(d_add(grid_centre(g, i), (double)pose[3 + i]), (double)g.so[i]);
-        M[4 * i + 0] = d2f(R[3 * i + 0]);
-        M[4 * i + 1] = d2f(R[3 * i + 1]);
-        M[4 * i + 2] = d2f(R[3 * i + 2]);
+        const double si = (double)g.ss[i];
+        const double b = d_div(d_sub(d_add(grid_centre(g, i), (double)pose[3 + i]), (double)g.so[i]), si);
+        M[4 * i + 0] = d2f(d_div(d_mul(R[3 * i + 0], (double)g.ts[0]), si));
+        M[4 * i + 1] = d2f(d_div(d_mul(R[3 * i + 1], (double)g.ts[1]), si));
+        M[4 * i + 2] = d2f(d_div(d_mul(R[3 * i + 2], (double)g.ts[2]), si));
         M[4 * i + 3] = d2f(b);
     }
 }
@@ -128,6 +134,18 @@ PF_HD void pose_to_matrix(const float pose[6], const Geometry &g, float M[12]) {
     matrix_from_sincos(pose, taylor_sin((double)pose[0]), taylor_cos((double)pose[0]),
                        taylor_sin((double)pose[1]), taylor_cos((double)pose[1]),
                        taylor_sin((double)pose[2]), taylor_cos((double)pose[2]), g, M);
+}
+
+// ---------------------------------------------------------------------------
+// Quaternion estimator.  q = qz(rz) * qx(rx) * qy(ry) is the unit quaternion
+// (w, x, y, z) of R = Rz Rx Ry, from the half-angle cosines and sines
+// (ch = sqrt((1 + cos)/2), sh = sin / (2 ch), stable for |angle| <= pi/2).
+// ---------------------------------------------------------------------------
+PF_HD void quat_from_half(double cx, double sx, double cy, double sy, double cz, double sz, double q[4]) {
+    q[0] = d_sub(d_mul(d_mul(cz, cx), cy), d_mul(d_mul(sz, sx), sy));
+    q[1] = d_sub(d_mul(d_mul(cz, sx), cy), d_mul(d_mul(sz, cx), sy));
+    q[2] = d_add(d_mul(d_mul(cz, cx), sy), d_mul(d_mul(sz, sx), cy));
+    q[3] = d_add(d_mul(d_mul(cz, sx), sy), d_mul(d_mul(sz, cx), cy));
 }
 
 // Per-row hoisted part of the coordinate: K_i = (r_i1*dy + r_i2*dz) + b_i.

@@ -75,6 +75,26 @@ __device__ __forceinline__ void predict_particle(const FilterParams &P, const Fi
 #pragma unroll
         for (int q = 0; q < 12; ++q) B.mats[(size_t)i * 12 + q] = M[q];
     }
+    if (P.estimator == 1) {   // quaternion of the pose for the estimate: half angles on lanes 0-2
+        const double cf = __shfl_sync(gmask, tv, gbase + (j < 3 ? j + 3 : 0));
+        double hc = 0.0, hs = 0.0;
+        if (j < 3) {
+            hc = __dsqrt_rn(__dmul_rn(__dadd_rn(1.0, cf), 0.5));
+            hs = __ddiv_rn(tv, __dmul_rn(2.0, hc));
+        }
+        double h[6];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            h[2 * q] = __shfl_sync(gmask, hc, gbase + q);
+            h[2 * q + 1] = __shfl_sync(gmask, hs, gbase + q);
+        }
+        if (j == 0) {
+            double qv[4];
+            quat_from_half(h[0], h[1], h[2], h[3], h[4], h[5], qv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) B.quat[(size_t)q * P.N + i] = qv[q];
+        }
+    }
     for (int q = j; q < kMomStride; q += kGroup) B.mom[(size_t)i * kMomStride + q] = 0ull;
     if (i == 0 && j == kGroup - 1) {   // accumulators of the score kernel
         B.stats[0] = 0ull;
@@ -89,10 +109,68 @@ __global__ void __launch_bounds__(32) k_predict(const FilterParams P, const Filt
     predict_particle(P, B, g, lane - gbase, 0xFFu << gbase, gbase);
 }
 
+// Weighted quaternion average: the unit eigenvector of the largest
+// eigenvalue of the symmetric 4x4 A (upper triangle, row by row: a00 a01 a02
+// a03 a11 a12 a13 a22 a23 a33) by cyclic Jacobi rotations, then the angles of
+// its rotation matrix: R21 = sin rx, R20 = -cos rx sin ry, R22 = cos rx cos ry,
+// R01 = -sin rz cos rx, R11 = cos rz cos rx.
+__device__ __noinline__ void quat_average_angles(const double A10[10], double rot[3]) {
+    double a[4][4], v[4][4];
+    int t = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = i; j < 4; ++j) {
+            a[i][j] = a[j][i] = A10[t++];
+        }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) v[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            diag += a[i][i] * a[i][i];
+            for (int j = i + 1; j < 4; ++j) off += a[i][j] * a[i][j];
+        }
+        if (off <= 1e-32 * diag) break;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                if (a[p][q] == 0.0) continue;
+                const double theta = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
+                for (int k = 0; k < 4; ++k) {   // columns p, q of A P
+                    const double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 4; ++k) {   // rows p, q of P^T (A P)
+                    const double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 4; ++k) {   // eigenvectors V P
+                    const double vkp = v[k][p], vkq = v[k][q];
+                    v[k][p] = c * vkp - s * vkq;
+                    v[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    int m = 0;
+    for (int i = 1; i < 4; ++i)
+        if (a[i][i] > a[m][m]) m = i;
+    double w = v[0][m], x = v[1][m], y = v[2][m], z = v[3][m];
+    const double n = sqrt(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    const double r21 = 2.0 * (y * z + w * x), r20 = 2.0 * (x * z - w * y), r22 = 1.0 - 2.0 * (x * x + y * y);
+    const double r01 = 2.0 * (x * y - w * z), r11 = 1.0 - 2.0 * (x * x + z * z);
+    rot[0] = asin(fmax(-1.0, fmin(1.0, r21)));
+    rot[1] = atan2(-r20, r22);
+    rot[2] = atan2(-r01, r11);
+}
+
 constexpr int kFinThreads = 1024;
 constexpr int kFinWarps = kFinThreads / 32;
 
 constexpr int kCdfSmem = 12288;            // CDF entries staged in shared memory (96 KiB)
+constexpr int kRed = 17;                   // reduced values: 6 pose sums, sum W^2, 10 of sum W q q^T
 
 // Update, part 1 (one thread per particle, many CTAs): score s_i from the
 // integer moments (Eq. 2 / Eq. 4); the maximum score, kept as the bits of a
@@ -148,10 +226,10 @@ __global__ void __launch_bounds__(128) k_weights(const FilterParams P, const Fil
 //   5. log the iteration and advance k.
 __device__ __forceinline__ void finalise_block(const FilterParams &P, const FilterBuffers &B) {
     extern __shared__ unsigned long long sh_cdf[];
-    __shared__ double sh_d[kFinWarps][7];
+    __shared__ double sh_d[kFinWarps][kRed];
     __shared__ unsigned long long sh_u[kFinWarps];
     __shared__ int sh_i[kFinWarps];
-    __shared__ double sh_est[7];
+    __shared__ double sh_est[kRed];
     __shared__ int sh_best_idx;
     const int N = P.N, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k = *B.k;
@@ -218,13 +296,38 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
         for (int o = 16; o > 0; o >>= 1) acc[d] = __dadd_rn(acc[d], __shfl_xor_sync(0xffffffffu, acc[d], o));
         if (lane == 0) sh_d[warp][d] = acc[d];
     }
+    if (P.estimator == 1) {   // the 10 entries of sum W q q^T (upper triangle, row by row)
+        double aq[10];
+#pragma unroll
+        for (int t = 0; t < 10; ++t) aq[t] = 0.0;
+        for (int i = tid; i < N; i += kFinThreads) {
+            const double w = (double)B.W[i];
+            double q[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) q[a] = B.quat[(size_t)a * N + i];
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = a; b < 4; ++b, ++t) {
+                    const double qq = __dmul_rn(q[a], q[b]);
+                    aq[t] = __dadd_rn(aq[t], S > 0 ? __dmul_rn(w, qq) : qq);
+                }
+        }
+#pragma unroll
+        for (int t = 0; t < 10; ++t) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) aq[t] = __dadd_rn(aq[t], __shfl_xor_sync(0xffffffffu, aq[t], o));
+            if (lane == 0) sh_d[warp][7 + t] = aq[t];
+        }
+    }
     __syncthreads();
     if (warp == 0) {
         int bi = sh_i[lane];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bi = min(bi, __shfl_xor_sync(0xffffffffu, bi, o));
         if (lane == 0) sh_best_idx = bi;
-        if (lane < 7) {
+        if (lane < (P.estimator == 1 ? kRed : 7)) {
             double t = 0.0;
             for (int w = 0; w < kFinWarps; ++w) t = __dadd_rn(t, sh_d[w][lane]);
             sh_est[lane] = t;
@@ -258,6 +361,13 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
         IterLog &L = B.log[k % P.log_capacity];
         for (int d = 0; d < 6; ++d)
             L.est[d] = S > 0 ? __ddiv_rn(sh_est[d], (double)S) : __ddiv_rn(sh_est[d], (double)N);
+        if (P.estimator == 1) {
+            double A10[10], rot[3];
+            const double norm = S > 0 ? (double)S : (double)N;
+            for (int t = 0; t < 10; ++t) A10[t] = __ddiv_rn(sh_est[7 + t], norm);
+            quat_average_angles(A10, rot);
+            for (int d = 0; d < 3; ++d) L.est[d] = rot[d];
+        }
         L.best = __longlong_as_double((long long)smax_bits);
         L.best_idx = sh_best_idx;
         L.evals = B.stats[1];

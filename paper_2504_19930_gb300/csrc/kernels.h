@@ -37,6 +37,7 @@ struct FilterParams {
     uint64_t n_min;             // overlap threshold (voxels)
     uint64_t b_full;            // |T| of the target mask (Dice denominator)
     int log_capacity;
+    int estimator;              // pf_estimator
 };
 
 struct IterLog {
@@ -63,6 +64,7 @@ struct FilterBuffers {
     unsigned long long *stats;  // [2] max score (fp64 bits) and evaluation count of the iteration
     float *trace_mat;           // [12] matrix of the estimate (tracing)
     unsigned long long *trace_mom;   // [12] its mask counts (tracing)
+    double *quat;               // [4][N] unit quaternion of each measured pose (quaternion estimator)
 };
 
 cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream_t s);

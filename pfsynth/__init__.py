@@ -59,6 +59,8 @@ class Pair:
     src_mask: np.ndarray | None = None
     tgt_mask: np.ndarray | None = None
     info: dict = field(default_factory=dict)
+    src_spacing: np.ndarray = field(default_factory=lambda: np.ones(3, np.float32))   # world units per voxel
+    tgt_spacing: np.ndarray = field(default_factory=lambda: np.ones(3, np.float32))
 
     @property
     def src_dims(self):
@@ -75,34 +77,40 @@ def rotation_zxy(pose) -> np.ndarray:
     return Rotation.from_euler("ZXY", [rz, rx, ry]).as_matrix()
 
 
-def _centre(dims, origin):
-    return np.asarray(origin, np.float64) + (np.asarray(dims, np.float64) - 1.0) / 2.0
+def _centre(dims, origin, spacing=(1.0, 1.0, 1.0)):
+    return np.asarray(origin, np.float64) + np.asarray(spacing, np.float64) * \
+        ((np.asarray(dims, np.float64) - 1.0) / 2.0)
 
 
-def map_target_to_source(pose, src_dims, src_origin, tgt_origin, pts_tgt_index):
-    """World-space map of target voxel indices (…,3 as x,y,z) into source world."""
+def map_target_to_source(pose, src_dims, src_origin, tgt_origin, pts_tgt_index,
+                         src_spacing=(1.0, 1.0, 1.0), tgt_spacing=(1.0, 1.0, 1.0)):
+    """World-space map of target voxel indices (…,3 as x,y,z) into source world
+    (voxel p of a grid sits at origin + spacing * p)."""
     R = rotation_zxy(pose)
-    c = _centre(src_dims, src_origin)
-    w = np.asarray(pts_tgt_index, np.float64) + np.asarray(tgt_origin, np.float64)
+    c = _centre(src_dims, src_origin, src_spacing)
+    w = np.asarray(pts_tgt_index, np.float64) * np.asarray(tgt_spacing, np.float64) + \
+        np.asarray(tgt_origin, np.float64)
     return (w - c) @ R.T + c + np.asarray(pose[3:6], np.float64)
 
 
-def _grid(dims, origin, dtype=np.float64):
+def _grid(dims, origin, dtype=np.float64, spacing=(1.0, 1.0, 1.0)):
     X, Y, Z = dims
     z, y, x = np.meshgrid(
         np.arange(Z, dtype=dtype), np.arange(Y, dtype=dtype), np.arange(X, dtype=dtype),
         indexing="ij",
     )
     o = np.asarray(origin, dtype)
-    return x + o[0], y + o[1], z + o[2]
+    sp = np.asarray(spacing, dtype)
+    return x * sp[0] + o[0], y * sp[1] + o[1], z * sp[2] + o[2]
 
 
-def _warp_grid(pose, src_dims, src_origin, tgt_dims, tgt_origin, dtype=np.float64):
+def _warp_grid(pose, src_dims, src_origin, tgt_dims, tgt_origin, dtype=np.float64,
+               src_spacing=(1.0, 1.0, 1.0), tgt_spacing=(1.0, 1.0, 1.0)):
     """Source-world coordinates of every target voxel, each (Zt,Yt,Xt)."""
     R = rotation_zxy(pose).astype(dtype)
-    c = _centre(src_dims, src_origin).astype(dtype)
+    c = _centre(src_dims, src_origin, src_spacing).astype(dtype)
     t = np.asarray(pose[3:6], dtype)
-    wx, wy, wz = _grid(tgt_dims, tgt_origin, dtype)
+    wx, wy, wz = _grid(tgt_dims, tgt_origin, dtype, tgt_spacing)
     dx, dy, dz = wx - c[0], wy - c[1], wz - c[2]
     sx = R[0, 0] * dx + R[0, 1] * dy + R[0, 2] * dz + c[0] + t[0]
     sy = R[1, 0] * dx + R[1, 1] * dy + R[1, 2] * dz + c[1] + t[1]
@@ -128,18 +136,21 @@ def _ellipsoid_indicator(wx, wy, wz, centre, axes, bump=None):
 def ellipsoid_pair(seed: int = 0, src_dims=(64, 64, 64), tgt_dims=(64, 64, 45),
                    tgt_origin=(0.0, 0.0, 19.0), semi_axes=(20.0, 14.0, 14.0),
                    max_rot_deg: float = 10.0, max_trans: float = 5.0,
-                   asymmetric: bool = False, true_pose=None) -> Pair:
+                   asymmetric: bool = False, true_pose=None, src_spacing=(1.0, 1.0, 1.0),
+                   tgt_spacing=(1.0, 1.0, 1.0)) -> Pair:
     """Binary mask pair: an ellipsoid and its rigidly moved, cropped copy.
 
     The source is the ellipsoid sampled on the source grid (origin 0).  The
     target is the same analytic shape evaluated at the ground-truth map of every
     target voxel (no resampling of the source), on a grid whose origin crops
     the field of view.  ``asymmetric`` adds an off-axis sphere so all six
-    degrees of freedom are identifiable.
+    degrees of freedom are identifiable.  Grids may have anisotropic voxel
+    sizes (spacings); centre, semi-axes, origins and translations are then in
+    world units.
     """
     rng = np.random.default_rng(seed)
     src_origin = np.zeros(3, np.float32)
-    centre = (np.asarray(src_dims, np.float64) - 1.0) / 2.0 + rng.uniform(-1, 1, 3)
+    centre = _centre(src_dims, src_origin, src_spacing) + rng.uniform(-1, 1, 3)
     axes = np.asarray(semi_axes, np.float64) + rng.uniform(-1, 1, 3)
     if true_pose is None:
         rot = np.deg2rad(rng.uniform(-max_rot_deg, max_rot_deg, 3))
@@ -149,14 +160,16 @@ def ellipsoid_pair(seed: int = 0, src_dims=(64, 64, 64), tgt_dims=(64, 64, 45),
     bump = None
     if asymmetric:
         bump = (centre + np.array([0.55 * axes[0], 0.75 * axes[1], 0.0]), 0.45 * axes[1])
-    sx, sy, sz = _grid(src_dims, src_origin)
+    sx, sy, sz = _grid(src_dims, src_origin, spacing=src_spacing)
     src = _ellipsoid_indicator(sx, sy, sz, centre, axes, bump)
-    wx, wy, wz = _warp_grid(true_pose, src_dims, src_origin, tgt_dims, tgt_origin)
+    wx, wy, wz = _warp_grid(true_pose, src_dims, src_origin, tgt_dims, tgt_origin,
+                            src_spacing=src_spacing, tgt_spacing=tgt_spacing)
     tgt = _ellipsoid_indicator(wx, wy, wz, centre, axes, bump)
     return Pair(src=src, tgt=tgt, src_origin=src_origin,
                 tgt_origin=np.asarray(tgt_origin, np.float32), true_pose=true_pose,
                 src_mask=src, tgt_mask=tgt,
-                info={"centre": centre, "semi_axes": axes, "bump": bump})
+                info={"centre": centre, "semi_axes": axes, "bump": bump},
+                src_spacing=np.asarray(src_spacing, np.float32), tgt_spacing=np.asarray(tgt_spacing, np.float32))
 
 
 # --------------------------------------------------------------------------

@@ -21,10 +21,12 @@ def target_points(tgt_dims):
     return np.stack([x, y, z], -1).reshape(-1, 3)
 
 
-def source_index_f64(pose, src_dims, src_origin, tgt_dims, tgt_origin):
+def source_index_f64(pose, src_dims, src_origin, tgt_dims, tgt_origin, src_spacing=(1.0, 1.0, 1.0),
+                     tgt_spacing=(1.0, 1.0, 1.0)):
     """Continuous source index of every target voxel (float64, scipy rotation)."""
-    w = pfsynth.map_target_to_source(pose, src_dims, src_origin, tgt_origin, target_points(tgt_dims))
-    return w - np.asarray(src_origin, np.float64)
+    w = pfsynth.map_target_to_source(pose, src_dims, src_origin, tgt_origin, target_points(tgt_dims),
+                                     src_spacing, tgt_spacing)
+    return (w - np.asarray(src_origin, np.float64)) / np.asarray(src_spacing, np.float64)
 
 
 def nn_counts_f64(src, tgt, q):

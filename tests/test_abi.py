@@ -100,7 +100,7 @@ def test_null_arguments_are_rejected(pk):
     assert lib.pf_step(None, 1) == -1
     assert lib.pf_estimate(None, None, None) == -1
     assert lib.pf_register_destroy(None) == 0
-    assert lib.warp_sequence(None, 1, None, None, None, None, None, None, 1, None) == -1
+    assert lib.warp_sequence(None, 1, None, None, None, None, None, None, None, None, 1, None) == -1
     assert lib.pf_measure_matrices(None, None, 1, None, None) == -1
     assert lib.pf_step_measure(None, 0, 1) == -1 and lib.pf_step_update(None) == -1
     assert lib.pf_moments_device(None, None, None) == -1

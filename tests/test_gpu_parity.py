@@ -394,3 +394,75 @@ def test_config4_full_size_sampled(pk, orc):
         idx = orc.resample(W, orc.resample_offset(seed, 0))
         assert np.array_equal(st["resample_idx"], idx)
         assert np.array_equal(st["poses_next"], x[:, idx])
+
+
+# ------------------------------------------------- anisotropic voxels (Table 1)
+
+SP_SRC, SP_TGT = (0.87, 1.08, 0.73), (1.09, 1.30, 0.92)
+
+
+def test_pose_matrix_with_spacing_bit_exact(pk, orc):
+    rng = np.random.default_rng(11)
+    for i in range(100):
+        pose = np.concatenate([rng.uniform(-1.5, 1.5, 3), rng.uniform(-30, 30, 3)]).astype(np.float32)
+        sd = tuple(int(v) for v in rng.integers(2, 300, 3))
+        so, to = rng.uniform(-20, 20, 3).astype(np.float32), rng.uniform(-20, 20, 3).astype(np.float32)
+        ss, ts = rng.uniform(0.3, 3.0, 3).astype(np.float32), rng.uniform(0.3, 3.0, 3).astype(np.float32)
+        Mg, ag = pk.pf_pose_matrix(pose, sd, so, to, ss, ts)
+        Mo, ao = orc.pose_matrix(pose, sd, so, to, ss, ts)
+        assert np.array_equal(Mg, Mo) and np.array_equal(ag, ao), i
+
+
+@pytest.mark.parametrize("mode", ["mask_dice", "image_ncc"])
+def test_trajectory_with_spacing_bit_exact(pk, orc, mode):
+    if mode == "mask_dice":
+        pair = pfsynth.ellipsoid_pair(12, src_dims=(34, 28, 36), tgt_dims=(30, 24, 27), tgt_origin=(0, 0, 6),
+                                      semi_axes=(10, 7, 7), asymmetric=True, max_rot_deg=8, max_trans=3,
+                                      src_spacing=SP_SRC, tgt_spacing=SP_TGT)
+    else:
+        pair = pfsynth.speckle_pair(12, src_dims=(36, 34, 30), tgt_dims=(37, 33, 29), overlap=(0.55, 0.7),
+                                    max_rot_deg=8, max_trans=3)
+    N, K, lr, lt = 160, 4, 0.2, 4.0
+    ref = _oracle_run(orc, mode, pair, N, K, lr, lt, seed=21, src_spacing=SP_SRC, tgt_spacing=SP_TGT)
+    with _reg(pk, mode, pair, N, lr, lt, 21, src_spacing=SP_SRC, tgt_spacing=SP_TGT) as reg:
+        _assert_trajectory(reg, ref, K)
+
+
+def test_warp_with_spacing_bit_exact(pk, orc):
+    import torch
+    sd, td = (37, 30, 23), (29, 25, 20)
+    so, to = np.zeros(3, np.float32), np.array([3.0, -2.0, 2.5], np.float32)
+    frames = [pfsynth.random_image(s, sd) for s in range(3)]
+    fout = [torch.empty((td[2], td[1], td[0]), dtype=torch.uint8, device="cuda") for _ in frames]
+    pose = np.array([0.2, -0.3, 0.25, 2.5, -1.25, 0.75], np.float32)
+    for interp in (0, 1):
+        pk.warp_sequence([_cuda(f) for f in frames], sd, so, fout, td, to, pose, interp, src_spacing=SP_SRC,
+                         tgt_spacing=SP_TGT)
+        torch.cuda.synchronize()
+        for i, f in enumerate(frames):
+            want = orc.warp(f, so, td, to, pose, interp, SP_SRC, SP_TGT)
+            assert np.array_equal(fout[i].cpu().numpy(), want), (interp, i)
+
+
+# ------------------------------------------------------ quaternion estimator
+
+@pytest.mark.parametrize("mode", ["mask_dice", "image_ncc"])
+def test_quaternion_estimator_against_oracle(pk, orc, mode):
+    if mode == "mask_dice":
+        pair = pfsynth.ellipsoid_pair(14, src_dims=(30, 28, 26), tgt_dims=(33, 27, 21), tgt_origin=(0, 0, 6),
+                                      semi_axes=(10, 7, 6), asymmetric=True, max_rot_deg=8, max_trans=3)
+    else:
+        pair = pfsynth.speckle_pair(14, src_dims=(36, 34, 30), tgt_dims=(37, 33, 29), overlap=(0.55, 0.7),
+                                    max_rot_deg=8, max_trans=3)
+    N, K, lr, lt = 300, 5, 0.6, 4.0
+    ref = _oracle_run(orc, mode, pair, N, K, lr, lt, seed=5)
+    with _reg(pk, mode, pair, N, lr, lt, 5, estimator="quaternion") as rq, _reg(pk, mode, pair, N, lr, lt, 5) as rm:
+        rq.step(K)
+        rm.step(K)
+        a, b = rq.state(), rm.state()
+        for key in a:   # the estimator does not touch the cloud
+            assert np.array_equal(a[key], b[key]), key
+        est, _, _, _, _ = rq.log()
+    for k in range(K):
+        want = orc.estimate_quaternion(ref["tr_poses"][k], ref["tr_W"][k])
+        assert np.max(np.abs(est[k] - want)) <= 1e-9, (k, est[k] - want)

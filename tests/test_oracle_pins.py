@@ -112,6 +112,28 @@ def test_pose_matrix_geometry(orc):
         assert np.max(np.abs(q - q_ref)) < 2e-4
 
 
+def test_pose_matrix_geometry_with_spacing(orc):
+    """Anisotropic voxels (Table 1 sizes): the matrix maps target voxels to
+    source voxels through world positions, checked against scipy's rotation
+    applied in world units; unit spacings give the unit-spacing matrix bit
+    for bit."""
+    sd, so, to = (37, 29, 23), np.array([1.5, -2.0, 0.25], np.float32), np.array([4.0, 3.0, -1.0], np.float32)
+    td = (21, 18, 11)
+    ss, ts = np.array([0.87, 1.08, 0.73], np.float32), np.array([1.09, 1.30, 0.92], np.float32)
+    for pose in _rand_poses(20, rot=0.6, tr=5, seed=5).astype(np.float32):
+        M, a = orc.pose_matrix(pose, sd, so, to, ss, ts)
+        Mm = M.reshape(3, 4).astype(np.float64)
+        q = (bf.target_points(td) - a) @ Mm[:, :3].T + Mm[:, 3]
+        q_ref = bf.source_index_f64(pose, sd, so, td, to, ss, ts)
+        assert np.max(np.abs(q - q_ref)) < 2e-4
+        # the 3x3 block is R scaled column-wise by s_T and row-wise by 1/s_S
+        R = pfsynth.rotation_zxy(pose.astype(np.float64))
+        np.testing.assert_allclose(Mm[:, :3], R * ts[None, :].astype(np.float64) / ss[:, None], atol=1e-6)
+        M1, a1 = orc.pose_matrix(pose, sd, so, to, (1, 1, 1), (1, 1, 1))
+        M0, a0 = orc.pose_matrix(pose, sd, so, to)
+        assert np.array_equal(M1, M0) and np.array_equal(a1, a0)
+
+
 # --------------------------------------------------------- measure, mask
 
 def _exact_cases(seed, n=12):
@@ -413,3 +435,51 @@ def test_fixed_point_ncc_weak_correlation(orc):
             if exact > 0:
                 worst = max(worst, abs(fixed - exact) / exact)
     assert worst <= 1e-5, worst
+
+
+# --------------------------------------------------- quaternion estimator
+
+def test_quaternion_of_pose_matches_scipy_and_rotation(orc):
+    from scipy.spatial.transform import Rotation
+    for pose in _rand_poses(30, rot=1.5, tr=5, seed=8):
+        q = orc.quaternion(pose)
+        rx, ry, rz = pose[:3]
+        x, y, z, w = Rotation.from_euler("ZXY", [rz, rx, ry]).as_quat()
+        ref = np.array([w, x, y, z])
+        assert min(np.max(np.abs(q - ref)), np.max(np.abs(q + ref))) < 1e-14
+        np.testing.assert_allclose(orc.quaternion_matrix(q), orc.rotation(pose.astype(np.float32)), atol=1e-6)
+        assert abs(np.linalg.norm(q) - 1.0) < 1e-15
+
+
+def test_quaternion_estimate_closed_forms(orc):
+    # two rotations about z with weights w1, w2: the average turns by
+    # atan2(w1 sin t1 + w2 sin t2, w1 cos t1 + w2 cos t2) about z
+    for t1, t2, w1, w2 in ((0.3, -0.3, 5, 5), (0.1, 0.5, 3, 1), (-0.7, 0.2, 1, 7)):
+        poses = np.zeros((6, 2), np.float32)
+        poses[2] = (t1, t2)
+        poses[3] = (1.0, 3.0)
+        est = orc.estimate_quaternion(poses, np.array([w1, w2], np.uint64))
+        want = math.atan2(w1 * math.sin(np.float32(t1)) + w2 * math.sin(np.float32(t2)),
+                          w1 * math.cos(np.float32(t1)) + w2 * math.cos(np.float32(t2)))
+        assert abs(est[2] - want) < 1e-12 and abs(est[0]) < 1e-12 and abs(est[1]) < 1e-12
+        assert abs(est[3] - (w1 * 1.0 + w2 * 3.0) / (w1 + w2)) < 1e-12
+    # identical rotations give that rotation; all-zero weights average uniformly
+    pose = np.array([0.4, -0.2, 1.1, 0, 0, 0], np.float32)
+    est = orc.estimate_quaternion(np.repeat(pose[:, None], 5, 1), np.zeros(5, np.uint64))
+    np.testing.assert_allclose(est[:3], pose[:3].astype(np.float64), atol=1e-7)
+
+
+def test_quaternion_estimate_matches_scipy_mean(orc):
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(3)
+    centre = np.array([0.3, -0.5, 0.9])
+    poses = np.zeros((6, 400), np.float32)
+    poses[:3] = (centre[:, None] + rng.normal(0, 0.25, (3, 400))).clip(-1.5, 1.5)
+    W = rng.integers(0, 1 << 24, 400).astype(np.uint64)
+    est = orc.estimate_quaternion(poses, W)
+    p64 = poses.astype(np.float64)
+    rot = Rotation.from_euler("ZXY", np.stack([p64[2], p64[0], p64[1]], 1))
+    rz, rx, ry = rot.mean(weights=W.astype(np.float64)).as_euler("ZXY")
+    np.testing.assert_allclose(est[:3], [rx, ry, rz], atol=1e-9)
+    # the angle mean is biased away from it for a wide cloud
+    assert np.max(np.abs(orc.estimate(poses, W)[:3] - est[:3])) > 1e-4
