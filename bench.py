@@ -37,10 +37,10 @@ sys.path.insert(0, ROOT)
 import pfsynth  # noqa: E402
 
 WORKLOADS = {
-    "config1": dict(pfsynth.CONFIG1, kind="image_ncc", dims=(224, 208, 176)),
-    "config0": dict(pfsynth.CONFIG0, kind="mask_dice", dims=(64, 64, 64), n_frames=0),
-    "config2": dict(name="batch64_mixed_96to256_n512to8192_k20to60", kind="batch", n_regs=64),
-    "config4": dict(pfsynth.CONFIG4, kind="combined", dims=(256, 256, 256)),
+    "image224": dict(pfsynth.IMAGE224, kind="image_ncc", dims=(224, 208, 176)),
+    "mask64": dict(pfsynth.MASK64, kind="mask_dice", dims=(64, 64, 64), n_frames=0),
+    "batch64": dict(name="batch64_mixed_96to256_n512to8192_k20to60", kind="batch", n_regs=64),
+    "combined256": dict(pfsynth.COMBINED256, kind="combined", dims=(256, 256, 256)),
 }
 METRIC = "particle-voxel evals/s (dense N*iters*target voxels per registration) and ms per registration"
 UNIT = "particle-voxel evals/s"
@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config1")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="image224")
     ap.add_argument("--batch-regs", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -257,9 +257,9 @@ def oracle_measure_all_cores(w, pair, n_particles, cores):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    if args.workload == "config2":      # a bounded sample of one image-based member
+    if args.workload == "batch64":      # a bounded sample of one image-based member
         m = batch_members(2, 7)[1]
-        w = dict(name=WORKLOADS["config2"]["name"], kind=m["mode"], rot_limit_deg=30.0, trans_limit=25.0, seed=1)
+        w = dict(name=WORKLOADS["batch64"]["name"], kind=m["mode"], rot_limit_deg=30.0, trans_limit=25.0, seed=1)
         pair = m["pair"]
     else:
         w, pair, _ = load_workload(args.workload, 0)
@@ -597,7 +597,7 @@ def run_batch(args, rank, world, local):
         line = {"metric": METRIC, "value": total / tb, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * tb / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOADS["config2"]["name"], "registrations": len(members),
+                "config": {"workload": WORKLOADS["batch64"]["name"], "registrations": len(members),
                            "mask_based": sum(m["mode"] == "mask_dice" for m in members),
                            "particles": [m["N"] for m in members], "iterations": [m["K"] for m in members],
                            "dense_evals_per_step": units,
@@ -615,7 +615,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload == "config2":
+    if args.workload == "batch64":
         run_batch(args, rank, world, local)
         return
     run_ours(args, rank, world, local)

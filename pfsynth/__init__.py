@@ -41,9 +41,9 @@ __all__ = [
     "frame_sequence",
     "random_image",
     "random_mask",
-    "CONFIG0",
-    "CONFIG1",
-    "CONFIG4",
+    "MASK64",
+    "IMAGE224",
+    "COMBINED256",
 ]
 
 
@@ -377,13 +377,13 @@ def random_mask(seed: int, dims, fill: float = 0.5) -> np.ndarray:
 # Named workloads (sizes and PF settings of the three single-GPU cases).
 # --------------------------------------------------------------------------
 
-CONFIG0 = dict(  # mask-based, 64^3 ellipsoid, N=256, 10 iterations
+MASK64 = dict(  # mask-based, 64^3 ellipsoid, N=256, 10 iterations
     name="mask64_dice_n256_k10", mode="mask_dice", n_particles=256, n_iters=10,
     rot_limit_deg=15.0, trans_limit=8.0, seed=0)
-CONFIG1 = dict(  # image-based, 224x208x176 speckle, N=2048, 50 iterations, 20-frame warp
+IMAGE224 = dict(  # image-based, 224x208x176 speckle, N=2048, 50 iterations, 20-frame warp
     name="speckle224x208x176_ncc_n2048_k50_warp20", mode="image_ncc", n_particles=2048,
     n_iters=50, rot_limit_deg=30.0, trans_limit=25.0, seed=0, n_frames=20)
-CONFIG4 = dict(  # combined image+mask, 256^3, N=16384, 40 iterations, 30-frame warp
+COMBINED256 = dict(  # combined image+mask, 256^3, N=16384, 40 iterations, 30-frame warp
     name="stress256_combined_n16384_k40_warp30", mode="combined", n_particles=16384,
     n_iters=40, rot_limit_deg=45.0, trans_limit=32.0, seed=0, n_frames=30)
 

@@ -234,10 +234,10 @@ def test_checkpoint_resume_bit_exact(pk, orc):
     assert np.array_equal(est_full, est_b)
 
 
-def test_config0_full_registration_bit_exact(pk, orc):
+def test_mask64_full_registration_bit_exact(pk, orc):
     """The mask-based workload at full size: 64^3 ellipsoid, 64x64x45 target,
     N=256, 10 iterations, +-15 deg / +-8 voxels, Dice with nearest neighbour."""
-    c = pfsynth.CONFIG0
+    c = pfsynth.MASK64
     pair = pfsynth.ellipsoid_pair(0)
     lr, lt = np.deg2rad(c["rot_limit_deg"]), c["trans_limit"]
     ref = _oracle_run(orc, "mask_dice", pair, c["n_particles"], c["n_iters"], lr, lt, seed=c["seed"])
@@ -254,12 +254,12 @@ def test_config0_full_registration_bit_exact(pk, orc):
         assert evals[-1] == int(ref["tr_mom"][-1][:, 8].sum())
 
 
-def test_config1_full_size_sampled(pk, orc):
+def test_image224_full_size_sampled(pk, orc):
     """The image-based workload at full size (224x208x176 speckle, N=2048):
     two iterations on the GPU; the oracle checks sampled particles' moments and
     re-runs every cheap step (score, weights, resampling, prediction) on the
     GPU's own state, bit for bit."""
-    c = pfsynth.CONFIG1
+    c = pfsynth.IMAGE224
     pair = pfsynth.cached(pfsynth.speckle_pair, 0)
     N, lr, lt, seed = c["n_particles"], np.deg2rad(c["rot_limit_deg"]), c["trans_limit"], c["seed"]
     lim = np.array([lr] * 3 + [lt] * 3, np.float32)
@@ -321,7 +321,7 @@ def test_warp_identity_and_rot90(pk):
     assert np.array_equal(out.cpu().numpy(), v)
 
 
-def test_warp_config1_frame_full_size(pk, orc):
+def test_warp_image224_frame_full_size(pk, orc):
     import torch
     pair = pfsynth.cached(pfsynth.speckle_pair, 0)
     frames = pfsynth.cached(pfsynth.frame_sequence, pair, 3)
@@ -366,12 +366,12 @@ def test_estimate_dice_trace(pk, orc, mode):
         assert dice[k] == orc.dice_from_counts(c[0], c[1], c[3], bfull, 0), k
 
 
-def test_config4_full_size_sampled(pk, orc):
+def test_combined256_full_size_sampled(pk, orc):
     """The combined stress workload at full size (256^3 image + LV mask,
     N=16384, +-45 deg / +-32 voxels, score 0.5 (NCC^2 + Dice)): one iteration
     on the GPU; the oracle re-measures sampled particles (image moments and
     mask counts) and recomputes every cheap step on the GPU's state."""
-    c = pfsynth.CONFIG4
+    c = pfsynth.COMBINED256
     pair = pfsynth.cached(pfsynth.speckle_pair, 0, src_dims=(256, 256, 256), with_masks=True,
                           max_rot_deg=20.0, max_trans=15.0)
     N, lr, lt, seed = c["n_particles"], np.deg2rad(c["rot_limit_deg"]), c["trans_limit"], c["seed"]

@@ -57,7 +57,7 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     import bench
 
     class A:
-        workload, warmup, steps, gpus, cpu_sample_particles = "config0", 0, 1, 2, 1
+        workload, warmup, steps, gpus, cpu_sample_particles = "mask64", 0, 1, 2, 1
     bench.run_reference(A(), rank=1, world=2)
     assert capsys.readouterr().out == ""
 
