@@ -44,7 +44,7 @@ MODES = {"mask_dice": 0, "mask_ncc": 1, "image_ncc": 2, "combined": 3}
 
 
 def build(force: bool = False) -> str:
-    """Compile pf_oracle.c into oracle/_build/libpforacle.so (gcc, no FMA)."""
+    """Compile pf_oracle.c into oracle/_build/libpforacle.so (gcc, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
@@ -107,6 +107,8 @@ def _declare(L):
         _f32p, C.c_int32, C.c_int32, _f64p, _vp, _vp, _vp, _vp, _vp, _vp]
     L.orc_register.restype = C.c_int32
     L.orc_warp.argtypes = [_u8p, _i32p, _u8p, _i32p, _f32p, _f32p, C.c_int32]
+    L.orc_trilinear.argtypes = [_u8p, _i32p, _f32p, _f32p]
+    L.orc_trilinear.restype = C.c_int32
 
 
 def _dims(vol):
@@ -123,6 +125,13 @@ def philox(ctr, key):
     out = np.zeros(4, np.uint32)
     lib().orc_philox4x32_10(_c(ctr, np.uint32), _c(key, np.uint32), out)
     return out
+
+
+def trilinear(src, q):
+    """fp32 trilinear sample of src (Z, Y, X) at q = (qx, qy, qz); None outside."""
+    out = np.zeros(1, np.float32)
+    ok = lib().orc_trilinear(_c(src, np.uint8), _dims(src), _c(q, np.float32), out)
+    return float(out[0]) if ok else None
 
 
 def sin(x):

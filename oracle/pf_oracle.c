@@ -205,10 +205,12 @@ static int nn_inside(const float q[3], const int32_t sd[3], int64_t *index)
 
 /* Trilinear sample (Sec. 3.3).  Inside iff 0 <= q <= dims-1 on every axis   */
 /* (fp32).  Base corner i = min(floor(q), dims-2), fraction f = q - i; lerp  */
-/* along x, then y, then z, each lerp a + f*(b - a) in fp32.                 */
+/* along x, then y, then z, each lerp a + f*(b - a) in fp32 with the         */
+/* difference b - a rounded and then a + f*d rounded once (fused multiply-   */
+/* add: C99 fmaf is correctly rounded on every host).                        */
 static float lerp(float a, float b, float f)
 {
-    return a + f * (b - a);
+    return fmaf(f, b - a, a);
 }
 
 static int tri_sample(const uint8_t *S, const int32_t sd[3], const float q[3], float *out)
@@ -237,6 +239,13 @@ static int tri_sample(const uint8_t *S, const int32_t sd[3], const float q[3], f
     float c1 = lerp(c01, c11, f[1]);
     *out = lerp(c0, c1, f[2]);
     return 1;
+}
+
+/* One trilinear sample (Sec. 3.3) at q, as tri_sample; returns 1 when q is  */
+/* inside, else 0 and *out untouched (test export).                          */
+int orc_trilinear(const uint8_t *S, const int32_t sd[3], const float q[3], float *out)
+{
+    return tri_sample(S, sd, q, out);
 }
 
 /* ------------------------------------------------------------------------ */

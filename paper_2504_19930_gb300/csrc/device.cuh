@@ -154,8 +154,10 @@ __device__ __forceinline__ float row_K(float r1, float r2, float b, float dy, fl
     return __fadd_rn(__fadd_rn(__fmul_rn(r1, dy), __fmul_rn(r2, dz)), b);
 }
 
+// Trilinear lerp a + f*(b - a): the difference rounded, then one fused
+// multiply-add (single rounding of the product and sum).
 __device__ __forceinline__ float lerp_rn(float a, float b, float f) {
-    return __fadd_rn(a, __fmul_rn(f, __fsub_rn(b, a)));
+    return __fmaf_rn(f, __fsub_rn(b, a), a);
 }
 
 // Conservative x-range of one target row whose samples can fall inside

@@ -48,11 +48,13 @@ __device__ __forceinline__ uint32_t int_of(float v) {
 }
 
 // Packed fp32 pairs (Blackwell f32x2): two independent IEEE round-to-nearest
-// adds or subtracts per instruction, lane-wise identical to __fadd_rn /
-// __fsub_rn.  They are used only where no product feeds them: ptxas fuses a
-// single-use packed multiply into a following packed add (an FMA, one rounding
-// instead of two) even under .rn, so every product and every add that consumes
-// a product stays a scalar __fmul_rn / __fadd_rn, which are never contracted.
+// operations per instruction, lane-wise identical to __fadd_rn / __fsub_rn /
+// __fmaf_rn.  Packed adds and subtracts are used only where no separately
+// rounded product feeds them: ptxas fuses a single-use packed multiply into a
+// following packed add (one rounding instead of two) even under .rn, so the
+// coordinate products (which the arithmetic reading keeps unfused) and the
+// adds that consume them stay scalar __fmul_rn / __fadd_rn, which are never
+// contracted.  The trilinear lerps are fused by definition (fma2).
 struct f2 {
     float x, y;
 };
@@ -74,9 +76,10 @@ __device__ __forceinline__ f2 splat(float a) { return f2{a, a}; }
 PF_F32X2(add2, "add")
 PF_F32X2(sub2, "sub")
 #undef PF_F32X2
-// a*b + c, used only on integer-valued operands whose products and sums stay
-// below 2^24, where every rounding is exact (index arithmetic).
-__device__ __forceinline__ f2 fma2_exact(f2 a, f2 b, f2 c) {
+// a*b + c with one rounding per lane (fused, lane-wise identical to
+// __fmaf_rn): the trilinear lerps, and the index arithmetic on integer-valued
+// operands whose products and sums stay below 2^24 (every rounding exact).
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     f2 d;
     asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\tmov.b64 rc, {%6,%7};\n\t"
         "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0,%1}, rd;}"
@@ -87,20 +90,18 @@ __device__ __forceinline__ f2 fma2_exact(f2 a, f2 b, f2 c) {
 #else
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return f2{__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)}; }
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return f2{__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y)}; }
-__device__ __forceinline__ f2 fma2_exact(f2 a, f2 b, f2 c) {
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     return f2{__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)};
 }
 #endif
 
-// a + f*(b - a) for two voxels: packed difference, scalar product and sum.
-__device__ __forceinline__ f2 lerp2(f2 a, f2 b, f2 f) {
-    const f2 d = sub2(b, a);
-    return f2{__fadd_rn(a.x, __fmul_rn(f.x, d.x)), __fadd_rn(a.y, __fmul_rn(f.y, d.y))};
-}
-// the same with biased end points A = 2^23 + a, B = 2^23 + b.
+// a + f*(b - a) for two voxels: the difference rounded, then one fused
+// multiply-add (a single rounding of a + f*d).
+__device__ __forceinline__ f2 lerp2(f2 a, f2 b, f2 f) { return fma2(f, sub2(b, a), a); }
+// the same with biased end points A = 2^23 + a, B = 2^23 + b (a, b bytes, so
+// both differences are exact).
 __device__ __forceinline__ f2 lerp2_biased(f2 A, f2 B, f2 f) {
-    const f2 base = sub2(A, splat(kTwo23)), d = sub2(B, A);
-    return f2{__fadd_rn(base.x, __fmul_rn(f.x, d.x)), __fadd_rn(base.y, __fmul_rn(f.y, d.y))};
+    return fma2(f, sub2(B, A), sub2(A, splat(kTwo23)));
 }
 // q = r*dx + K for two voxels (scalar: a product feeds the add).
 __device__ __forceinline__ f2 coord2(float r, f2 dx, f2 K) {
@@ -115,11 +116,13 @@ struct MaskAcc {
     uint32_t n = 0, A = 0, B = 0, C = 0;
 };
 
-// Two voxels handed to eval_pair: their x as floats, the row offsets K of
-// each voxel's row and their target indices (in bounds even for a voxel
-// that is not taken).
+// Two voxels handed to eval_pair: their x (as floats and as integers, the
+// latter indexing the x-product table), the row offsets K of each voxel's
+// row and their target indices (in bounds even for a voxel that is not
+// taken).
 struct PairIn {
     f2 xf;
+    int x0, x1;
     f2 K0, K1, K2;
     uint32_t t0, t1;
     // FULL: address of the first voxel's target byte (the second is 32
@@ -159,15 +162,27 @@ __device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t 
 // where min(floor q, D - 2) = floor q.  FIDX: the source has at most 2^23
 // voxels and the quad index is formed in fp32 (exact integers below 2^24)
 // as 2^23 + index, read through a base address lowered by 2^23 words.
-template <bool IMG, bool MASK, bool FULL, bool IFULL, bool NOCLAMP, bool FIDX>
-__device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *__restrict__ bits, const float r0x,
-                                          const float r0y, const float r0z, const PairIn &v, bool valid0,
-                                          bool valid1, bool ivalid0, bool ivalid1, ImgAcc &ia, MaskAcc &ma) {
+// XTAB: the products r_i0 * (x - a0) of the particle's matrix come from the
+// warp's shared-memory table (the same fp32 roundings, computed once per
+// particle), so q = product + K is one packed add per axis.
+template <bool IMG, bool MASK, bool FULL, bool IFULL, bool NOCLAMP, bool FIDX, bool XTAB>
+__device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *__restrict__ bits,
+                                          const float4 *__restrict__ tab, const float r0x, const float r0y,
+                                          const float r0z, const PairIn &v, bool valid0, bool valid1,
+                                          bool ivalid0, bool ivalid1, ImgAcc &ia, MaskAcc &ma) {
     if (FULL) valid0 = valid1 = true;
-    const f2 dx = sub2(v.xf, splat(a.g.a[0]));
-    const f2 qx = coord2(r0x, dx, v.K0);
-    const f2 qy = coord2(r0y, dx, v.K1);
-    const f2 qz = coord2(r0z, dx, v.K2);
+    f2 qx, qy, qz;
+    if (XTAB) {
+        const float4 P0 = tab[v.x0], P1 = tab[v.x1];
+        qx = add2(pair(P0.x, P1.x), v.K0);
+        qy = add2(pair(P0.y, P1.y), v.K1);
+        qz = add2(pair(P0.z, P1.z), v.K2);
+    } else {
+        const f2 dx = sub2(v.xf, splat(a.g.a[0]));
+        qx = coord2(r0x, dx, v.K0);
+        qy = coord2(r0y, dx, v.K1);
+        qz = coord2(r0z, dx, v.K2);
+    }
     if (IMG) {
         const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
         const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
@@ -184,8 +199,8 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const uint32_t *qbase;
         uint32_t i0, i1;
         if (FIDX) {
-            const f2 w = fma2_exact(splat((float)SXY), flz,
-                                    fma2_exact(splat((float)SX), fly, add2(flx, splat(kTwo23))));
+            const f2 w = fma2(splat((float)SXY), flz,
+                                    fma2(splat((float)SX), fly, add2(flx, splat(kTwo23))));
             i0 = __float_as_uint(w.x);
             i1 = __float_as_uint(w.y);
             qbase = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(a.src_quad) -
@@ -341,9 +356,9 @@ __device__ __forceinline__ void exact_interval(const float r0[3], const float K[
 // for the image mode) and, combined, the trilinear interval [ib, ie) inside
 // it -- then the warp sweeps the intervals, reduces the moments and adds
 // them to mom[p] with one integer atomic each (S2 is 128-bit).
-template <bool IMG, bool MASK, bool FIDX>
+template <bool IMG, bool MASK, bool FIDX, bool XTAB>
 __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_t *__restrict__ bits,
-                                             long long item, int lane) {
+                                             const float4 *__restrict__ tab, long long item, int lane) {
     constexpr bool BOTH = IMG && MASK;
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
     const int TX = a.g.td[0], TY = a.g.td[1];
@@ -430,23 +445,23 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
         for (;;) {
             const int len0 = end0 - pos;
             if (len0 >= 64) {
-                const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), splat(K0), splat(K1), splat(K2), 0u, 0u,
-                               tgt + toff, a.tgt_mask + toff};
+                const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), pos + lane, pos + lane + 32, splat(K0), splat(K1),
+                               splat(K2), 0u, 0u, tgt + toff, a.tgt_mask + toff};
                 const bool nc = IMG && ((noclamp >> j0) & 1u);
                 if (BOTH && !(pos >= ib0 && pos + 64 <= ie0)) {   // the image interval ends in this pass
                     const int x = pos + lane;
                     const bool iv0 = x >= ib0 && x < ie0, iv1 = x + 32 >= ib0 && x + 32 < ie0;
                     if (nc)
-                        eval_pair<IMG, MASK, true, false, true, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true, true,
+                        eval_pair<IMG, MASK, true, false, true, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true, true,
                                                                       iv0, iv1, ia, ma);
                     else
-                        eval_pair<IMG, MASK, true, false, false, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true,
+                        eval_pair<IMG, MASK, true, false, false, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true,
                                                                        true, iv0, iv1, ia, ma);
                 } else if (nc) {
-                    eval_pair<IMG, MASK, true, true, true, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true, true, true,
+                    eval_pair<IMG, MASK, true, true, true, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true, true, true,
                                                                  true, ia, ma);
                 } else {
-                    eval_pair<IMG, MASK, true, true, false, FIDX>(a, bits, r0[0], r0[1], r0[2], v, true, true,
+                    eval_pair<IMG, MASK, true, true, false, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true, true,
                                                                   true, true, ia, ma);
                 }
                 pos += 64;
@@ -471,11 +486,11 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
             const int x1 = in1a ? pos + e1 : (ok1 ? xb1 + e1 - len0 : 0);
             const bool iv0 = ok0 && (in0a ? x0 >= ib0 && x0 < ie0 : x0 >= ib1 && x0 < ie1);
             const bool iv1 = ok1 && (in1a ? x1 >= ib0 && x1 < ie0 : x1 >= ib1 && x1 < ie1);
-            const PairIn v{pair((float)x0, (float)x1), pair(in0a ? K0 : L0, in1a ? K0 : L0),
+            const PairIn v{pair((float)x0, (float)x1), x0, x1, pair(in0a ? K0 : L0, in1a ? K0 : L0),
                            pair(in0a ? K1 : L1, in1a ? K1 : L1), pair(in0a ? K2 : L2, in1a ? K2 : L2),
                            (in0a || !ok0 ? trow0 : trow1) + (uint32_t)x0,
                            (in1a || !ok1 ? trow0 : trow1) + (uint32_t)x1, nullptr, nullptr};
-            eval_pair<IMG, MASK, false, false, false, FIDX>(a, bits, r0[0], r0[1], r0[2], v, ok0, ok1, iv0, iv1,
+            eval_pair<IMG, MASK, false, false, false, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, ok0, ok1, iv0, iv1,
                                                             ia, ma);
             if (IMG) {
                 ia.S1 += ia.S1row;
@@ -559,24 +574,50 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
 #ifndef PF_MEASURE_MIN_BLOCKS_COMBINED
 #define PF_MEASURE_MIN_BLOCKS_COMBINED 3
 #endif
-template <bool IMG, bool MASK, bool MASK_SMEM, bool FIDX>
+// XTAB: each warp keeps the table of r_i0 * (x - a0), x = 0 .. X-1, of its
+// current particle in shared memory (X float4 per warp, X <= kTabMaxX), in
+// front of the optional mask bits.
+constexpr int kTabMaxX = 512;
+template <bool IMG, bool MASK, bool MASK_SMEM, bool FIDX, bool XTAB>
 __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_COMBINED
                                                         : (IMG ? PF_MEASURE_MIN_BLOCKS_IMG : 4))
     k_measure(const MeasureArgs a) {
-    extern __shared__ uint32_t smem_bits[];
+    extern __shared__ float4 smem_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int TX = a.g.td[0];
+    float4 *tab = XTAB ? smem_dyn + (size_t)warp * TX : nullptr;
     const uint32_t *bits = a.src_bits;
     if (MASK && MASK_SMEM) {
+        uint32_t *sb = reinterpret_cast<uint32_t *>(smem_dyn + (XTAB ? (size_t)kWarps * TX : 0));
         const int nwords = (int)(((size_t)a.g.sd[0] * a.g.sd[1] * a.g.sd[2] + 31) / 32);
-        for (int i = threadIdx.x; i < nwords; i += kThreads) smem_bits[i] = a.src_bits[i];
+        for (int i = threadIdx.x; i < nwords; i += kThreads) sb[i] = a.src_bits[i];
         __syncthreads();
-        bits = smem_bits;
+        bits = sb;
     }
     const int rows = a.g.td[1] * a.g.td[2];
-    const long long items = (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
+    const int nblocks = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
+    const long long items = (long long)a.P * nblocks;
     const long long item0 = ((long long)blockIdx.x * kWarps + warp) * kItemsPerWarp;
     const long long item1 = min(items, item0 + kItemsPerWarp);
-    for (long long item = item0; item < item1; ++item) measure_item<IMG, MASK, FIDX>(a, bits, item, lane);
+    int tab_p = -1;
+    for (long long item = item0; item < item1; ++item) {
+        if (XTAB) {
+            const int p = (int)(item / nblocks);   // warp-uniform
+            if (p != tab_p) {
+                // same roundings as the per-voxel form: fl(r_i0 * fl(x - a0))
+                const float *Mp = a.mats + 12 * (size_t)p;
+                const float r0 = __ldg(Mp + 0), r1 = __ldg(Mp + 4), r2 = __ldg(Mp + 8);
+                __syncwarp();
+                for (int x = lane; x < TX; x += 32) {
+                    const float dx = __fsub_rn((float)x, a.g.a[0]);
+                    tab[x] = make_float4(__fmul_rn(r0, dx), __fmul_rn(r1, dx), __fmul_rn(r2, dx), 0.0f);
+                }
+                __syncwarp();
+                tab_p = p;
+            }
+        }
+        measure_item<IMG, MASK, FIDX, XTAB>(a, bits, tab, item, lane);
+    }
 }
 
 // Measurement of many registrations in one launch: the items of the listed
@@ -600,13 +641,13 @@ __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batc
         }
         const BatchReg &R = regs[list[lo]];
         if (*R.B.k >= R.n_iters) continue;          // warp-uniform
-        measure_item<IMG, MASK, false>(R.ma, R.ma.src_bits, item - offs[lo], lane);
+        measure_item<IMG, MASK, false, false>(R.ma, R.ma.src_bits, nullptr, item - offs[lo], lane);
     }
 }
 
-template <bool IMG, bool MASK, bool SMEM, bool FIDX = false>
+template <bool IMG, bool MASK, bool SMEM, bool FIDX, bool XTAB>
 cudaError_t launch_variant(const MeasureArgs &a, size_t smem, cudaStream_t s) {
-    auto kern = k_measure<IMG, MASK, SMEM, FIDX>;
+    auto kern = k_measure<IMG, MASK, SMEM, FIDX, XTAB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -670,22 +711,36 @@ long long measure_items(const MeasureArgs &a) {
     return (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
 }
 
+#ifndef PF_MEASURE_XTAB
+#define PF_MEASURE_XTAB 1
+#endif
+template <bool IMG, bool MASK, bool SMEM, bool FIDX>
+cudaError_t launch_tab(const MeasureArgs &a, bool xtab, size_t smem_bits, cudaStream_t s) {
+    if (xtab)
+        return launch_variant<IMG, MASK, SMEM, FIDX, true>(
+            a, (size_t)kWarps * a.g.td[0] * sizeof(float4) + (SMEM ? smem_bits : 0), s);
+    return launch_variant<IMG, MASK, SMEM, FIDX, false>(a, SMEM ? smem_bits : 0, s);
+}
+
 cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream_t s) {
     if (a.P <= 0) return cudaSuccess;
     const size_t nvox = (size_t)a.g.sd[0] * a.g.sd[1] * a.g.sd[2];
     const size_t smem_bits = ((nvox + 31) / 32) * 4;
     const bool smem = mask && smem_bits <= 160 * 1024;
     const bool fidx = nvox <= ((size_t)1 << 23);   // quad indices formed in fp32
+    const size_t tab_bytes = (size_t)kWarps * a.g.td[0] * sizeof(float4);
+    const bool xtab = PF_MEASURE_XTAB && a.g.td[0] <= kTabMaxX &&
+                      tab_bytes + (smem ? smem_bits : 0) <= 200 * 1024;
     if (img && mask) {
-        if (smem) return fidx ? launch_variant<true, true, true, true>(a, smem_bits, s)
-                              : launch_variant<true, true, true, false>(a, smem_bits, s);
-        return fidx ? launch_variant<true, true, false, true>(a, 0, s)
-                    : launch_variant<true, true, false, false>(a, 0, s);
+        if (smem) return fidx ? launch_tab<true, true, true, true>(a, xtab, smem_bits, s)
+                              : launch_tab<true, true, true, false>(a, xtab, smem_bits, s);
+        return fidx ? launch_tab<true, true, false, true>(a, xtab, smem_bits, s)
+                    : launch_tab<true, true, false, false>(a, xtab, smem_bits, s);
     }
-    if (img) return fidx ? launch_variant<true, false, false, true>(a, 0, s)
-                         : launch_variant<true, false, false, false>(a, 0, s);
-    return smem ? launch_variant<false, true, true>(a, smem_bits, s)
-                : launch_variant<false, true, false>(a, 0, s);
+    if (img) return fidx ? launch_tab<true, false, false, true>(a, xtab, smem_bits, s)
+                         : launch_tab<true, false, false, false>(a, xtab, smem_bits, s);
+    return smem ? launch_tab<false, true, true, false>(a, xtab, smem_bits, s)
+                : launch_tab<false, true, false, false>(a, xtab, smem_bits, s);
 }
 
 }  // namespace pfreg

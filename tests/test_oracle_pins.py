@@ -483,3 +483,42 @@ def test_quaternion_estimate_matches_scipy_mean(orc):
     np.testing.assert_allclose(est[:3], [rx, ry, rz], atol=1e-9)
     # the angle mean is biased away from it for a wide cloud
     assert np.max(np.abs(orc.estimate(poses, W)[:3] - est[:3])) > 1e-4
+
+
+def _round_f32(x):
+    """Nearest float32 to the exact rational x (ties to even)."""
+    from fractions import Fraction
+    c = np.float32(float(x))
+    best = None
+    for cand in (np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))):
+        err = abs(Fraction(float(cand)) - x)
+        key = (err, int(np.float32(cand).view(np.uint32)) & 1)
+        if best is None or key < best[0]:
+            best = (key, cand)
+    return np.float32(best[1])
+
+
+def test_trilinear_lerp_single_rounding(orc):
+    """Each lerp of the trilinear sample (Sec. 3.3) rounds a + f*(b - a) once:
+    on a volume that varies along x only, the y and z lerps are exact, so the
+    sample must be the exact interpolation a + f*(b - a) rounded to fp32 once.
+    A separately rounded product (two roundings) differs on some of these."""
+    from fractions import Fraction
+    rng = np.random.default_rng(41)
+    X, Y, Z = 40, 3, 3
+    line = rng.integers(0, 256, X).astype(np.uint8)
+    src = np.broadcast_to(line[None, None, :], (Z, Y, X)).copy()
+    twice = 0
+    for _ in range(4000):
+        qx = np.float32(rng.uniform(0, X - 1))
+        q = np.array([qx, rng.uniform(0, Y - 1), rng.uniform(0, Z - 1)], np.float32)
+        got = orc.trilinear(src, q)
+        i = min(int(np.floor(qx)), X - 2)
+        f = Fraction(float(qx)) - i                 # exact: q - floor(q) is representable
+        a, b = int(line[i]), int(line[i + 1])
+        want = _round_f32(a + f * (b - a))
+        assert np.float32(got) == want, (qx, got, want)
+        two = np.float32(np.float32(a) + np.float32(np.float32(f) * np.float32(b - a)))
+        twice += int(two != want)
+    assert twice > 0   # the case set separates one rounding from two
+    assert orc.trilinear(src, np.array([X - 0.5, 1, 1], np.float32)) is None
