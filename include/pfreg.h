@@ -133,6 +133,18 @@ int pf_step(pf_ctx *ctx, int32_t n_iters);
  * pose (one extra measurement).  PF_ESTATE before the first pf_step. */
 int pf_estimate(pf_ctx *ctx, float pose_out[6], double *score_out);
 
+/* Seed the cloud from a proposal (the learned approach named as future work
+ * in Sec. 6: a predicted mean and spread seed and shrink the particle cloud).
+ * Replaces the initial particles by x_id = clamp(mean_d + std_d eps_id, -L_d,
+ * L_d), eps the bounded unit-variance Irwin-Hall draw (u1+u2+u3+u4-2) sqrt 3
+ * of Philox counter (i, 0, 3, d), and makes std the perturbation base:
+ * sigma_kd = std_d * sigma_decay^k (instead of sigma0_frac * L_d).  mean /
+ * std: [rx ry rz tx ty tz] in radians and world units.  Only before the first
+ * pf_step.  Synchronous; re-captures the iteration graph.
+ * Errors: PF_EINVAL (NULL, non-finite mean, std outside (0, 1e6]),
+ * PF_ESTATE (after the first iteration, or while profiling is armed), PF_ECUDA. */
+int pf_seed_gaussian(pf_ctx *ctx, const float mean[6], const float std[6]);
+
 /* Release the context and its device memory (NULL is accepted). */
 int pf_register_destroy(pf_ctx *ctx);
 
@@ -278,6 +290,109 @@ int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
  * device time of those measurement launches (ms) and how many were timed. */
 int pf_profile_begin(pf_ctx *ctx, int32_t capacity);
 int pf_profile_end(pf_ctx *ctx, double *total_ms, int32_t *n_timed);
+
+/* ---- learned proposal network: tensor-core contractions (test exports) ----
+ *
+ * The proposal network (a 3-D CNN that predicts the mean and log-variance of
+ * the 6-DOF pose to seed the particle cloud; the learned approach Sec. 6 names
+ * as future work) is built from strided 3-D convolutions: kernel 4^3, stride 2,
+ * padding 1, 32 output channels.  Tensors are bf16 (uint16_t bit patterns) in
+ * NDHWC layout, x fastest: element (b, z, y, x, c) of a D^3 x C volume sits at
+ * (((b*D + z)*D + y)*D + x)*C + c.  Weights are [32 co][64 taps][Cin], tap =
+ * (kz*4 + ky)*4 + kx.  The contractions run on the tcgen05 tensor cores with
+ * fp32 accumulation.  All pointers are device pointers; calls are asynchronous
+ * on `stream` (a cudaStream_t) and allocate nothing.
+ * Errors: PF_EINVAL (NULL, D odd or outside [2, 512], Cin not 2 or a multiple
+ * of 8 up to 256, sizes beyond int32 indexing), PF_ECUDA. */
+
+/* C[M][32] (fp32) = A[M][K] B[32][K]^T, A and B row-major bf16, K % 8 == 0. */
+int pf_nn_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int32_t M, int32_t K, void *stream);
+
+/* y[b, o, co] = relu(bias[co] + sum_{tap, ci} x[b, 2o + k - 1, ci] w[co][tap][ci])
+ * (per axis, k the tap's offset 0..3; taps outside the input read 0).
+ * x: [batch][D^3][Cin]; y: [batch][(D/2)^3][32] bf16 (rounded to nearest). */
+int pf_nn_conv3d_forward(const uint16_t *x, int32_t batch, int32_t D, int32_t Cin, const uint16_t *w,
+                         const float *bias, uint16_t *y, void *stream);
+
+/* Gradient with respect to the input of a 32-channel layer (Cin = 32):
+ * dx[b, i, ci] = [act[b, i, ci] > 0] * sum over (tap, co) with o = (i + 1 - k)/2
+ * integral and inside of dy[b, o, co] w[co][tap][ci]  (per axis).
+ * dy: [batch][(D/2)^3][32]; w_t: the weights transposed to [ci][tap][co];
+ * act: [batch][D^3][32] ReLU output of the layer below (mask), or NULL for no
+ * mask; dx: [batch][D^3][32] bf16. */
+int pf_nn_conv3d_backward_data(const uint16_t *dy, int32_t batch, int32_t D, const uint16_t *w_t,
+                               const uint16_t *act, uint16_t *dx, void *stream);
+
+/* Gradient with respect to the weights: dw[co][tap][ci] += sum_{b, o}
+ * x[b, 2o + k - 1, ci] dy[b, o, co] (fp32 accumulation into dw; partial sums
+ * of K-slices are added atomically, so the summation order varies). */
+int pf_nn_conv3d_backward_weights(const uint16_t *x, int32_t batch, int32_t D, int32_t Cin, const uint16_t *dy,
+                                  float *dw, void *stream);
+
+/* *gave_up = 1 when a tensor-core kernel's bounded wait on an mbarrier ran
+ * out since the last clear (its tile was then not written); clear != 0
+ * resets the flag.  Synchronous. */
+int pf_nn_status(int32_t clear, int32_t *gave_up);
+
+/* ---- learned proposal network ----
+ *
+ * A 3-D CNN that predicts, from a source/target pair, the mean and the
+ * log-variance of the 6-DOF pose; the mean and spread seed and shrink the
+ * particle cloud (pf_seed_gaussian).  The paper names a learned approach as
+ * future work (Sec. 6); this network is not in the paper.  Architecture:
+ * input 64^3 x 2 (source and target box-averaged, /64, onto one 64^3 grid over
+ * the source's box: the target sits at its own origin), four convolutions
+ * 4^3 / stride 2 / padding 1 / 32 channels with ReLU (bf16 activations, fp32
+ * accumulation on the tcgen05 tensor cores), then fully connected 2048 -> 128
+ * (ReLU) -> 12 in fp32: mean (6) and log-variance (6) in units of the
+ * training limits.  464,652 fp32 parameters, Adam.
+ * Training data: synthetic echo-like pairs generated on the GPU (speckled
+ * left-ventricle shell, per-view gain, random pose within the limits, target
+ * field of view slid along x for 35-60 % overlap), labels = generating pose.
+ * A proposal object belongs to one stream and is not thread-safe. */
+typedef struct pf_proposal pf_proposal;
+
+/* Create a network with parameters drawn from Philox(seed) (uniform, fan-in
+ * scaled) for batches of up to max_batch (1..256) pairs.  Device memory:
+ * about max_batch * 2.5 MB plus 8 MB.  Errors: PF_EINVAL, PF_ENOMEM, PF_ECUDA. */
+int pf_proposal_create(pf_proposal **out, int32_t max_batch, uint64_t seed, void *stream);
+int pf_proposal_destroy(pf_proposal *p);
+
+/* Run n_steps Adam steps (learning rate lr) on fresh synthetic batches of
+ * `batch` pairs of vol_dims volumes with poses uniform in +-rot_limit (rad,
+ * every axis) / +-trans_limit (voxels); batch b of step t is drawn from
+ * Philox(data_seed, b, t).  Each step is one CUDA-graph launch.  loss_out
+ * (host, n_steps floats, may be NULL) receives the mean Gaussian negative
+ * log-likelihood of each step.  The limits are the units of the outputs and
+ * must stay the same across calls.  Synchronous when loss_out is given.
+ * Errors: PF_EINVAL (sizes, lr outside (0, 1), limits), PF_ENOMEM, PF_ECUDA. */
+int pf_proposal_train(pf_proposal *p, int32_t n_steps, int32_t batch, float lr, uint64_t data_seed,
+                      const int32_t vol_dims[3], float rot_limit, float trans_limit, float *loss_out);
+
+/* Predict the pose of a pair: mean_out = mean * limits, std_out =
+ * exp(log-variance / 2) * limits, per DOF [rx ry rz tx ty tz] (radians,
+ * world units).  Volumes as for pf_register_init (host or device).
+ * Synchronous.  Errors: PF_EINVAL, PF_ESTATE (not trained), PF_ECUDA. */
+int pf_proposal_predict(pf_proposal *p, const pf_volume *src, const pf_volume *tgt, float mean_out[6],
+                        float std_out[6]);
+
+/* Checkpoint and inspection (host buffers of *n_params floats, any may be
+ * NULL): theta_in replaces the parameters, then theta_out / grad_out receive
+ * the parameters and the gradient of the last backward pass.  Synchronous. */
+int pf_proposal_params(pf_proposal *p, float *theta_out, float *grad_out, const float *theta_in,
+                       int64_t *n_params);
+
+/* Test exports (device buffers, asynchronous on the stream):
+ *   forward:  x [batch][64^3][2] bf16 -> out [batch][12], hidden [batch][128] (may be NULL);
+ *   backward: gradient of the mean loss for labels y [batch][6] (pose / limits)
+ *             after a forward of the same batch; *loss_out (host) = the loss; synchronous;
+ *   synth:    a synthetic batch (x, y) of step `step` as pf_proposal_train draws it;
+ *   input:    the network input [64^3][2] of one pair, as pf_proposal_predict builds it. */
+int pf_proposal_forward(pf_proposal *p, const uint16_t *x, int32_t batch, float *out, float *hidden);
+int pf_proposal_backward(pf_proposal *p, const float *y, int32_t batch, float *loss_out);
+int pf_proposal_synth(pf_proposal *p, int32_t batch, uint64_t seed, int32_t step, const int32_t vol_dims[3],
+                      float rot_limit, float trans_limit, uint16_t *x_out, float *y_out);
+int pf_proposal_input(pf_proposal *p, const pf_volume *src, const pf_volume *tgt, uint16_t *x_out);
 
 /* Number of this library's kernels launched in this process so far (each
  * graph replay counts its kernels). */

@@ -104,8 +104,9 @@ def _declare(L):
     L.orc_register.argtypes = [
         C.c_int32, _vp, _vp, _vp, _vp, _i32p, _f32p, _vp, _i32p, _f32p, _vp, C.c_int32, C.c_int32,
         _f32p, _f32p, C.c_float, C.c_float, C.c_int32, C.c_uint64, C.c_float,
-        _f32p, C.c_int32, C.c_int32, _f64p, _vp, _vp, _vp, _vp, _vp, _vp]
+        _f32p, C.c_int32, C.c_int32, _f64p, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.orc_register.restype = C.c_int32
+    L.orc_init_gaussian.argtypes = [_f32p, C.c_int32, C.c_uint64, _f32p, _f32p, _f32p]
     L.orc_warp.argtypes = [_u8p, _i32p, _u8p, _i32p, _f32p, _f32p, C.c_int32]
     L.orc_trilinear.argtypes = [_u8p, _i32p, _f32p, _f32p]
     L.orc_trilinear.restype = C.c_int32
@@ -303,6 +304,13 @@ def init_particles(N, seed, lim6):
     return x
 
 
+def init_gaussian(N, seed, mean6, std6, lim6):
+    """Initial cloud around a proposal: clamp(mean + std * eps) per DOF."""
+    x = np.zeros((6, N), np.float32)
+    lib().orc_init_gaussian(x, N, int(seed), _c(mean6, np.float32), _c(std6, np.float32), _c(lim6, np.float32))
+    return x
+
+
 def sigma(sigma0_frac, decay, k, lim6):
     out = np.zeros(6, np.float32)
     lib().orc_sigma(float(sigma0_frac), float(decay), int(k), _c(lim6, np.float32), out)
@@ -346,9 +354,10 @@ DEFAULTS = dict(sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, min_overlap_fra
 def register(mode, src_dims, src_origin, tgt_dims, tgt_origin, n_particles, n_iters,
              rot_limit, trans_limit, seed=0, src=None, tgt=None, src_mask=None, tgt_mask=None,
              sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, min_overlap_frac=0.01,
-             poses=None, k0=0, trace=True, src_spacing=None, tgt_spacing=None):
+             poses=None, k0=0, trace=True, src_spacing=None, tgt_spacing=None, sig_base=None):
     """Run the whole filter for ``n_iters`` iterations starting at iteration
     ``k0`` (from ``poses`` [6,N] if given, else the Philox initial cloud).
+    ``sig_base`` (6 floats) replaces sigma0_frac * limit as the noise base.
 
     Returns a dict: est (fp64[6] of the last iteration), poses (the resampled
     cloud after the last iteration) and, with ``trace``, per-iteration arrays
@@ -388,7 +397,8 @@ def register(mode, src_dims, src_origin, tgt_dims, tgt_origin, n_particles, n_it
         ptr(_sp(src_spacing)), _c(tgt_dims, np.int32), _c(tgt_origin, np.float32), ptr(_sp(tgt_spacing)),
         N, K, rl, tl,
         float(sigma0_frac), float(sigma_decay), int(gamma_log2), int(seed),
-        float(min_overlap_frac), x, int(have), int(k0), est, *trp)
+        float(min_overlap_frac), x, int(have), int(k0), est, *trp,
+        ptr(None if sig_base is None else _c(sig_base, np.float32)))
     if rc != 0:
         raise RuntimeError(f"orc_register failed: {rc}")
     out = dict(est=est, poses=x)

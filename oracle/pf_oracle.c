@@ -65,7 +65,7 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 }
 
 /* Stream identifiers in counter word 2 (reading: one Philox stream per use). */
-enum { ORC_STREAM_INIT = 0, ORC_STREAM_PERTURB = 1, ORC_STREAM_RESAMPLE = 2 };
+enum { ORC_STREAM_INIT = 0, ORC_STREAM_PERTURB = 1, ORC_STREAM_RESAMPLE = 2, ORC_STREAM_SEED = 3 };
 
 static void philox_seeded(uint64_t seed, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
                           uint32_t out[4])
@@ -510,6 +510,26 @@ void orc_init(float *poses, int32_t N, uint64_t seed, const float lim[6])
     }
 }
 
+/* Initial particles drawn around a proposal (the learned approach of Sec. 6,  */
+/* which seeds and shrinks the cloud): x_id = clamp(m_d + s_d eps, -L_d, L_d)  */
+/* with the Irwin-Hall draw eps = (u1+u2+u3+u4 - 2) sqrt(3) of Philox counter  */
+/* (i, 0, SEED, d).  poses: SoA [6][N].                                       */
+void orc_init_gaussian(float *poses, int32_t N, uint64_t seed, const float mean[6], const float std[6],
+                       const float lim[6])
+{
+    const float sqrt3 = 1.7320508075688772f;
+    for (int32_t i = 0; i < N; ++i)
+        for (int d = 0; d < 6; ++d) {
+            uint32_t r[4];
+            philox_seeded(seed, (uint32_t)i, 0u, ORC_STREAM_SEED, (uint32_t)d, r);
+            float e = ((((unit24(r[0]) + unit24(r[1])) + unit24(r[2])) + unit24(r[3])) - 2.0f) * sqrt3;
+            float v = mean[d] + std[d] * e;
+            if (v > lim[d]) v = lim[d];
+            if (v < -lim[d]) v = -lim[d];
+            poses[(int64_t)d * N + i] = v;
+        }
+}
+
 /* Noise scale of iteration k (reading): sigma_kd = sigma0_frac * L_d *       */
 /* decay^k, decay^k by k fp64 products, rounded once to fp32.                */
 void orc_sigma(float sigma0_frac, float decay, int32_t k, const float lim[6], float sigma[6])
@@ -554,6 +574,8 @@ uint32_t orc_resample_offset(uint64_t seed, int32_t k)
 /*   tr_poses [K][6][N] (measured poses), tr_mom [K][N][12], tr_score [K][N], */
 /*   tr_W [K][N], tr_idx [K][N], tr_est [K][6].                              */
 /* Volumes unused by the mode may be NULL; so are the spacings ss, ts (1).  */
+/* sig_base (6 floats or NULL): the per-DOF noise base that replaces         */
+/* sigma0_frac * L_d (a proposal's spread), sigma_kd = sig_base_d * decay^k.  */
 /* ------------------------------------------------------------------------ */
 int32_t orc_register(int32_t mode, const uint8_t *src, const uint8_t *tgt, const uint8_t *src_mask,
                      const uint8_t *tgt_mask, const int32_t sd[3], const float so[3], const float ss[3],
@@ -562,7 +584,7 @@ int32_t orc_register(int32_t mode, const uint8_t *src, const uint8_t *tgt, const
                      float decay, int32_t gamma_log2, uint64_t seed, float min_overlap_frac,
                      float *poses_inout, int32_t have_poses, int32_t k0, double est_out[6],
                      float *tr_poses, uint64_t *tr_mom, double *tr_score, uint64_t *tr_W,
-                     int32_t *tr_idx, double *tr_est)
+                     int32_t *tr_idx, double *tr_est, const float *sig_base)
 {
     const float lim[6] = {rot_lim[0], rot_lim[1], rot_lim[2], trans_lim[0], trans_lim[1], trans_lim[2]};
     int64_t nt = (int64_t)td[0] * td[1] * td[2];
@@ -586,6 +608,11 @@ int32_t orc_register(int32_t mode, const uint8_t *src, const uint8_t *tgt, const
         if (k > 0) {
             float sig[6];
             orc_sigma(sigma0_frac, decay, k, lim, sig);
+            if (sig_base) {
+                double p = 1.0;
+                for (int32_t j = 0; j < k; ++j) p = p * (double)decay;
+                for (int d = 0; d < 6; ++d) sig[d] = (float)((double)sig_base[d] * p);
+            }
             orc_perturb(x, N, seed, k, sig, lim);
         }
         for (int32_t i = 0; i < N; ++i) {

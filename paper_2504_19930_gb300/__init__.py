@@ -114,6 +114,26 @@ def _declare(L):
     L.pf_kernel_launches.restype = u64
     L.pf_last_error.argtypes = []
     L.pf_last_error.restype = C.c_char_p
+    L.pf_nn_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, vp]
+    L.pf_nn_conv3d_forward.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp]
+    L.pf_nn_conv3d_backward_data.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+    L.pf_nn_conv3d_backward_weights.argtypes = [vp, i32, i32, i32, vp, vp, vp]
+    L.pf_nn_status.argtypes = [i32, vp]
+    L.pf_seed_gaussian.argtypes = [vp, vp, vp]
+    L.pf_proposal_create.argtypes = [C.POINTER(vp), i32, u64, vp]
+    L.pf_proposal_destroy.argtypes = [vp]
+    L.pf_proposal_train.argtypes = [vp, i32, i32, C.c_float, u64, vp, C.c_float, C.c_float, vp]
+    L.pf_proposal_predict.argtypes = [vp, C.POINTER(pf_volume), C.POINTER(pf_volume), vp, vp]
+    L.pf_proposal_params.argtypes = [vp, vp, vp, vp, vp]
+    L.pf_proposal_forward.argtypes = [vp, vp, i32, vp, vp]
+    L.pf_proposal_backward.argtypes = [vp, vp, i32, vp]
+    L.pf_proposal_synth.argtypes = [vp, i32, u64, i32, vp, C.c_float, C.c_float, vp, vp]
+    L.pf_proposal_input.argtypes = [vp, C.POINTER(pf_volume), C.POINTER(pf_volume), vp]
+    for name in ("pf_nn_gemm_bf16", "pf_nn_conv3d_forward", "pf_nn_conv3d_backward_data",
+                 "pf_nn_conv3d_backward_weights", "pf_nn_status", "pf_seed_gaussian", "pf_proposal_create",
+                 "pf_proposal_destroy", "pf_proposal_train", "pf_proposal_predict", "pf_proposal_params",
+                 "pf_proposal_forward", "pf_proposal_backward", "pf_proposal_synth", "pf_proposal_input"):
+        getattr(L, name).restype = C.c_int
     for name in ("pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy", "warp_sequence",
                  "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
                  "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_profile_begin",
@@ -390,6 +410,12 @@ class Registration:
         pf_step(self.ctx, n_iters)
         return self
 
+    def seed_gaussian(self, mean, std):
+        """Seed the cloud around a proposal (before the first step)."""
+        m, sd = _np(mean, np.float32), _np(std, np.float32)
+        _check(load().pf_seed_gaussian(self.ctx, _ptr(m), _ptr(sd)))
+        return self
+
     def estimate(self, with_score=True):
         return pf_estimate(self.ctx, with_score)
 
@@ -534,6 +560,135 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ proposal network contractions
+# Thin wrappers over the pf_nn_* exports (tensor-core kernels); tensors are
+# torch CUDA tensors, bf16 in NDHWC layout, shapes as in include/pfreg.h.
+
+def _need(t, dtype, shape=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA tensor of {dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+def nn_gemm_bf16(A, B, C, stream=None):
+    """C[M][32] = A[M][K] @ B[32][K]^T on the tensor cores (fp32 out)."""
+    import torch
+    M, K = A.shape
+    _need(A, torch.bfloat16), _need(B, torch.bfloat16, (32, K)), _need(C, torch.float32, (M, 32))
+    _check(load().pf_nn_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(K), _stream_handle(stream)))
+
+
+def nn_conv3d_forward(x, w, bias, y, stream=None):
+    """y = relu(conv3d(x, w, stride 2, padding 1) + bias); x (B,D,D,D,Cin), y (B,D/2,D/2,D/2,32)."""
+    import torch
+    Bn, D, _, _, Cin = x.shape
+    _need(x, torch.bfloat16), _need(w, torch.bfloat16, (32, 64, Cin)), _need(bias, torch.float32, (32,))
+    _need(y, torch.bfloat16, (Bn, D // 2, D // 2, D // 2, 32))
+    _check(load().pf_nn_conv3d_forward(_ptr(x), int(Bn), int(D), int(Cin), _ptr(w), _ptr(bias), _ptr(y),
+                                       _stream_handle(stream)))
+
+
+def nn_conv3d_backward_data(dy, w_t, act, dx, stream=None):
+    """dx = mask(act) * conv3d-transpose(dy, w); w_t is w as [ci][tap][co]; act may be None."""
+    import torch
+    Bn, D = dx.shape[0], dx.shape[1]
+    _need(dy, torch.bfloat16, (Bn, D // 2, D // 2, D // 2, 32)), _need(w_t, torch.bfloat16, (32, 64, 32))
+    _need(dx, torch.bfloat16, (Bn, D, D, D, 32))
+    if act is not None:
+        _need(act, torch.bfloat16, (Bn, D, D, D, 32))
+    _check(load().pf_nn_conv3d_backward_data(_ptr(dy), int(Bn), int(D), _ptr(w_t), _ptr(act), _ptr(dx),
+                                             _stream_handle(stream)))
+
+
+def nn_conv3d_backward_weights(x, dy, dw, stream=None):
+    """dw[co][tap][ci] += sum_{b,o} x[b, 2o+k-1, ci] dy[b, o, co] (fp32)."""
+    import torch
+    Bn, D, _, _, Cin = x.shape
+    _need(x, torch.bfloat16), _need(dy, torch.bfloat16, (Bn, D // 2, D // 2, D // 2, 32))
+    _need(dw, torch.float32, (32, 64, Cin))
+    _check(load().pf_nn_conv3d_backward_weights(_ptr(x), int(Bn), int(D), int(Cin), _ptr(dy), _ptr(dw),
+                                                _stream_handle(stream)))
+
+
+def nn_status(clear=True) -> int:
+    """1 when a tensor-core kernel's bounded wait ran out since the last clear."""
+    v = C.c_int32(0)
+    _check(load().pf_nn_status(1 if clear else 0, C.byref(v)))
+    return int(v.value)
+
+
+# ------------------------------------------------------------------ learned proposal network
+
+class Proposal:
+    """The learned proposal network (pf_proposal_*): trains on synthetic
+    pairs generated on the GPU and predicts a pose mean and spread that seed
+    a registration's particle cloud."""
+
+    N_PARAMS = 464652
+
+    def __init__(self, max_batch=32, seed=0, stream=None):
+        self.stream = stream
+        h = C.c_void_p()
+        _check(load().pf_proposal_create(C.byref(h), int(max_batch), int(seed), _stream_handle(stream)))
+        self.h = h
+        self.max_batch = int(max_batch)
+
+    def train(self, n_steps, batch=32, lr=1e-3, data_seed=1, vol_dims=(224, 208, 176),
+              rot_limit=0.5235988, trans_limit=25.0, with_loss=True):
+        loss = np.zeros(max(int(n_steps), 1), np.float32) if with_loss else None
+        dims = _np(vol_dims, np.int32)
+        _check(load().pf_proposal_train(self.h, int(n_steps), int(batch), float(lr), int(data_seed), _ptr(dims),
+                                        float(rot_limit), float(trans_limit), _ptr(loss)))
+        return loss[:int(n_steps)] if with_loss else None
+
+    def predict(self, src, tgt, src_origin=(0, 0, 0), tgt_origin=(0, 0, 0), src_spacing=(1, 1, 1),
+                tgt_spacing=(1, 1, 1)):
+        vs, vt = make_volume(src, src_origin, spacing=src_spacing), make_volume(tgt, tgt_origin, spacing=tgt_spacing)
+        mean, std = np.zeros(6, np.float32), np.zeros(6, np.float32)
+        _check(load().pf_proposal_predict(self.h, C.byref(vs), C.byref(vt), _ptr(mean), _ptr(std)))
+        return mean, std
+
+    def params(self, theta_in=None, with_grad=False):
+        n = C.c_int64(0)
+        _check(load().pf_proposal_params(self.h, None, None, None, C.byref(n)))
+        theta = np.zeros(n.value, np.float32)
+        grad = np.zeros(n.value, np.float32) if with_grad else None
+        tin = None if theta_in is None else _np(theta_in, np.float32)
+        _check(load().pf_proposal_params(self.h, _ptr(theta), _ptr(grad), _ptr(tin), C.byref(n)))
+        return (theta, grad) if with_grad else theta
+
+    def forward(self, x, out, hidden=None):
+        _check(load().pf_proposal_forward(self.h, _ptr(x), int(x.shape[0]), _ptr(out), _ptr(hidden)))
+
+    def backward(self, y):
+        loss = C.c_float(0.0)
+        _check(load().pf_proposal_backward(self.h, _ptr(y), int(y.shape[0]), C.byref(loss)))
+        return float(loss.value)
+
+    def synth(self, x, y, seed, step, vol_dims=(224, 208, 176), rot_limit=0.5235988, trans_limit=25.0):
+        dims = _np(vol_dims, np.int32)
+        _check(load().pf_proposal_synth(self.h, int(x.shape[0]), int(seed), int(step), _ptr(dims),
+                                        float(rot_limit), float(trans_limit), _ptr(x), _ptr(y)))
+
+    def input(self, src, tgt, x, src_origin=(0, 0, 0), tgt_origin=(0, 0, 0), src_spacing=(1, 1, 1),
+              tgt_spacing=(1, 1, 1)):
+        vs, vt = make_volume(src, src_origin, spacing=src_spacing), make_volume(tgt, tgt_origin, spacing=tgt_spacing)
+        _check(load().pf_proposal_input(self.h, C.byref(vs), C.byref(vt), _ptr(x)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load().pf_proposal_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -255,6 +255,22 @@ int build_graph(pf_ctx *c) {
     return PF_OK;
 }
 
+// Re-capture the iteration graph after the filter parameters changed.
+int rebuild_graph(pf_ctx *c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->ev_before) cudaEventDestroy(c->ev_before);
+    if (c->ev_after) cudaEventDestroy(c->ev_after);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    c->ev_before = c->ev_after = nullptr;
+    c->cap_stream = nullptr;
+    c->node_before = c->node_after = nullptr;
+    c->prof_default = true;
+    return build_graph(c);
+}
+
 int set_record_events(pf_ctx *c, cudaEvent_t before, cudaEvent_t after) {
     CU(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_before, before));
     CU(cudaGraphExecEventRecordNodeSetEvent(c->exec, c->node_after, after));
@@ -350,6 +366,7 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
         P.lim[3 + d] = cfg->trans_limit[d];
     }
     P.sigma0_frac = cfg->sigma0_frac;
+    for (int d = 0; d < 6; ++d) P.sig0[d] = (double)cfg->sigma0_frac * (double)P.lim[d];   // exact product
     P.sigma_decay = cfg->sigma_decay;
     P.gamma_log2 = cfg->gamma_log2;
     P.seed = cfg->seed;
@@ -437,6 +454,23 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
 #undef CK
     *out = c;
     return PF_OK;
+}
+
+int pf_seed_gaussian(pf_ctx *c, const float mean[6], const float std[6]) {
+    if (!c || !mean || !std) return fail(PF_EINVAL, "NULL argument");
+    for (int d = 0; d < 6; ++d) {
+        if (!std::isfinite(mean[d])) return fail(PF_EINVAL, "mean[%d] is not finite", d);
+        if (!(std[d] > 0.0f && std[d] <= 1e6f)) return fail(PF_EINVAL, "std[%d] outside (0, 1e6]", d);
+    }
+    int32_t k = 0;
+    CU(cudaMemcpyAsync(&k, c->B.k, sizeof k, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (k != 0) return fail(PF_ESTATE, "pf_seed_gaussian after the first iteration (k = %d)", k);
+    if (c->prof_events.size()) return fail(PF_ESTATE, "pf_seed_gaussian while profiling is armed");
+    for (int d = 0; d < 6; ++d) c->P.sig0[d] = (double)std[d];
+    CU(launch_seed_gaussian(c->P, c->B, mean, std, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return rebuild_graph(c);
 }
 
 int pf_step(pf_ctx *c, int32_t n_iters) {

@@ -41,7 +41,7 @@ __device__ __forceinline__ u32x4 philox10(u32x4 c, uint32_t k0, uint32_t k1) {
 }
 
 // Philox stream ids (counter word 2): one per use of randomness.
-enum : uint32_t { kStreamInit = 0, kStreamPerturb = 1, kStreamResample = 2 };
+enum : uint32_t { kStreamInit = 0, kStreamPerturb = 1, kStreamResample = 2, kStreamSeed = 3 };
 
 __device__ __forceinline__ u32x4 philox_seeded(uint64_t seed, uint32_t w0, uint32_t w1,
                                                uint32_t w2, uint32_t w3) {

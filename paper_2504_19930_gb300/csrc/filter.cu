@@ -26,6 +26,29 @@ __global__ void k_init(const FilterParams P, float *poses) {
         poses[(size_t)d * P.N + i] = __fmul_rn(P.lim[d], __fsub_rn(__fmul_rn(2.0f, unit24(u[d])), 1.0f));
 }
 
+// Initial particles around a proposal (the learned approach of Sec. 6 seeds
+// and shrinks the cloud): x_id = clamp(m_d + s_d eps, -L_d, L_d), eps the
+// Irwin-Hall draw of Philox counter (i, 0, SEED, d).
+struct Seed6 {
+    float m[6], s[6];
+};
+__global__ void k_seed_gaussian(const FilterParams P, float *poses, const Seed6 sd) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const float sqrt3 = 1.7320508075688772f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const u32x4 r = philox_seeded(P.seed, (uint32_t)i, 0u, kStreamSeed, (uint32_t)d);
+        const float e = __fmul_rn(
+            __fsub_rn(__fadd_rn(__fadd_rn(__fadd_rn(unit24(r.x), unit24(r.y)), unit24(r.z)), unit24(r.w)), 2.0f),
+            sqrt3);
+        float v = __fadd_rn(sd.m[d], __fmul_rn(sd.s[d], e));
+        if (v > P.lim[d]) v = P.lim[d];
+        if (v < -P.lim[d]) v = -P.lim[d];
+        poses[(size_t)d * P.N + i] = v;
+    }
+}
+
 // Prediction for k > 0 (reading: bounded Irwin-Hall noise of unit variance,
 // eps = (u1+u2+u3+u4 - 2) sqrt(3) from Philox counter (i, k, PERTURB, d),
 // scale sigma_kd = sigma0_frac * L_d * decay^k, clamped to the limits), then
@@ -46,7 +69,7 @@ __device__ __forceinline__ void predict_particle(const FilterParams &P, const Fi
         double pk = 1.0;
         for (int q = 0; q < k; ++q) pk = __dmul_rn(pk, (double)P.sigma_decay);
         const float sqrt3 = 1.7320508075688772f;
-        const float sig = __double2float_rn(__dmul_rn(__dmul_rn((double)P.sigma0_frac, (double)P.lim[j]), pk));
+        const float sig = __double2float_rn(__dmul_rn(P.sig0[j], pk));
         const u32x4 r = philox_seeded(P.seed, (uint32_t)i, (uint32_t)k, kStreamPerturb, (uint32_t)j);
         const float e = __fmul_rn(
             __fsub_rn(__fadd_rn(__fadd_rn(__fadd_rn(unit24(r.x), unit24(r.y)), unit24(r.z)), unit24(r.w)), 2.0f),
@@ -538,6 +561,18 @@ uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_init_particles(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
     k_init<<<blocks_for(p.N, 256), 256, 0, s>>>(p, b.poses);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_gaussian(const FilterParams &p, const FilterBuffers &b, const float mean[6],
+                                 const float std[6], cudaStream_t s) {
+    Seed6 sd;
+    for (int d = 0; d < 6; ++d) {
+        sd.m[d] = mean[d];
+        sd.s[d] = std[d];
+    }
+    k_seed_gaussian<<<blocks_for(p.N, 256), 256, 0, s>>>(p, b.poses, sd);
     count_launches(1);
     return cudaGetLastError();
 }

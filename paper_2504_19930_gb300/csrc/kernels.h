@@ -38,6 +38,8 @@ struct FilterParams {
     uint64_t b_full;            // |T| of the target mask (Dice denominator)
     int log_capacity;
     int estimator;              // pf_estimator
+    double sig0[6];             // perturbation base: sigma_kd = sig0_d * decay^k (default
+                                // sigma0_frac * L_d; a proposal's spread after pf_seed_gaussian)
 };
 
 struct IterLog {
@@ -72,6 +74,8 @@ long long measure_items(const MeasureArgs &a);   // work items of one measuremen
 cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_t *quad, cudaStream_t s);
 int rows_per_item_for(int target_x);
 cudaError_t launch_init_particles(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
+cudaError_t launch_seed_gaussian(const FilterParams &p, const FilterBuffers &b, const float mean[6],
+                                 const float std[6], cudaStream_t s);
 cudaError_t launch_predict(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
 cudaError_t launch_finalise(const FilterParams &p, const FilterBuffers &b, cudaStream_t s);
 // Tracing of the estimate (Sec. 3.2: the masks are warped with the estimate

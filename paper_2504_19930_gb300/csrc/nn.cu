@@ -1,0 +1,914 @@
+// nn.cu -- tensor-core contractions of the learned proposal network.
+//
+// The proposal network (a 3-D CNN that predicts the 6-DOF mean and
+// log-variance used to seed the particle cloud; future work of Sec. 6) is
+// four strided 3-D convolutions (kernel 4, stride 2, padding 1, 32 output
+// channels, ReLU) on bf16 activations in NDHWC layout, then two small fully
+// connected layers.  The convolutions and their two gradients are implicit
+// GEMMs on the tcgen05 tensor cores (bf16 operands, fp32 accumulators in
+// tensor memory):
+//   forward  D[o][co]        = sum_{tap,ci} X[o*2+tap-1][ci] W[co][tap][ci]
+//   data     dX[i][ci]       = sum_{tap,co} dY[(i+1-tap)/2][co] W[co][tap][ci]
+//   weights  dW[(tap,ci)][co] = sum_{o}     X[o*2+tap-1][ci] dY[o][co]
+// (per axis; taps outside the volume and, for the data gradient, taps whose
+// (i + 1 - tap) is odd or out of range contribute zero).
+//
+// One CTA (four warps) owns a tile of 128 rows x 32 columns whose
+// accumulator lives in 32 tensor-memory columns; thread t stages row t of
+// the A operand (64 K elements per chunk) into shared memory in the
+// canonical no-swizzle K-major layout (umma.cuh), the 32 B rows are staged
+// by all threads, and one thread issues four K = 16 MMAs per chunk.  Two
+// shared-memory stages alternate: the loads of chunk c overlap the MMAs of
+// chunk c - 1, and a stage is rewritten only after the mbarrier of the
+// commit that last read it has completed.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+#include "nn.h"
+#include "umma.cuh"
+
+namespace pfreg {
+namespace nn {
+
+constexpr int kTileM = 128;
+constexpr int kTileN = 32;
+constexpr int kChunkK = 64;   // K elements staged per chunk (4 MMAs)
+constexpr int kStageA = kTileM * kChunkK * 2;   // bytes
+constexpr int kStageB = kTileN * kChunkK * 2;
+constexpr uint32_t kIdesc = umma::idesc_bf16_f32(kTileM, kTileN);
+
+__device__ unsigned int g_nn_error;   // set when a bounded wait gave up
+
+__device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+
+__device__ __forceinline__ void st16(uint8_t *tile, int r, int k, uint4 v) {
+    *reinterpret_cast<uint4 *>(tile + umma::tile_offset(r, k, kChunkK)) = v;
+}
+
+// ---------------------------------------------------------------------------
+// Operand loaders.  load_a(tile, m0, chunk, t): thread t (0..127) writes row t
+// of the 128 x 64 A tile; load_b(tile, chunk, t): the 32 x 64 B tile, two
+// 8-element groups per thread; epilogue(row, acc[32]).
+// ---------------------------------------------------------------------------
+
+// Plain GEMM C[M][32] = A[M][K] B[32][K]^T (row-major bf16, K % 8 == 0).
+struct GemmOp {
+    const uint16_t *A, *B;
+    float *C;
+    int M, K;
+    __device__ int chunks() const { return (K + kChunkK - 1) / kChunkK; }
+    __device__ void load_a(uint8_t *tile, int m0, int c, int t) const {
+        const int r = m0 + t;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = c * kChunkK + 8 * j;
+            uint4 v = zero4();
+            if (r < M && k < K) v = __ldg(reinterpret_cast<const uint4 *>(A + (size_t)r * K + k));
+            st16(tile, t, 8 * j, v);
+        }
+    }
+    __device__ void load_b(uint8_t *tile, int c, int t) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int g = t + 128 * i, n = g >> 3, j = g & 7, k = c * kChunkK + 8 * j;
+            uint4 v = zero4();
+            if (k < K) v = __ldg(reinterpret_cast<const uint4 *>(B + (size_t)n * K + k));
+            st16(tile, n, 8 * j, v);
+        }
+    }
+    __device__ void epilogue(int row, const float *acc) const {
+        if (row >= M) return;
+        float4 *dst = reinterpret_cast<float4 *>(C + (size_t)row * kTileN);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dst[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+    }
+};
+
+// Geometry of one strided convolution: input D^3 x Cin, output (D/2)^3 x 32.
+struct ConvGeom {
+    int batch, D, Cin;   // Cin in {2, 8, 16, 32, ...}: a multiple of 2, and of 8 when >= 8
+    __device__ int Do() const { return D >> 1; }
+};
+
+// Input element offset of voxel (b, z, y, x) channel 0, or -1 outside.
+__device__ __forceinline__ long long vox(const ConvGeom &g, int b, int z, int y, int x, int C) {
+    if ((unsigned)z >= (unsigned)g.D || (unsigned)y >= (unsigned)g.D || (unsigned)x >= (unsigned)g.D) return -1;
+    return ((((long long)b * g.D + z) * g.D + y) * g.D + x) * C;
+}
+
+// Forward: rows = output voxels (b, oz, oy, ox), K = tap * Cin + ci,
+// tap = (kz * 4 + ky) * 4 + kx.  Epilogue: y = relu(acc + bias) as bf16.
+struct ConvFwdOp {
+    ConvGeom g;
+    const uint16_t *X;      // [B][D][D][D][Cin]
+    const uint16_t *W;      // [32][64][Cin]
+    const float *bias;      // [32]
+    uint16_t *Y;            // [B][Do][Do][Do][32]
+    __device__ int M() const { const int d = g.Do(); return g.batch * d * d * d; }
+    __device__ int chunks() const { return (64 * g.Cin + kChunkK - 1) / kChunkK; }
+    __device__ void load_a(uint8_t *tile, int m0, int c, int t) const {
+        const int r = m0 + t, Do = g.Do();
+        const bool live = r < M();
+        const int ox = r % Do, oy = (r / Do) % Do, oz = (r / (Do * Do)) % Do, b = r / (Do * Do * Do);
+        const int K = 64 * g.Cin;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k0 = c * kChunkK + 8 * j;
+            uint4 v = zero4();
+            if (live && k0 < K) {
+                if (g.Cin >= 8) {
+                    const int tap = k0 / g.Cin, ci = k0 - tap * g.Cin;
+                    const int kz = tap >> 4, ky = (tap >> 2) & 3, kx = tap & 3;
+                    const long long e = vox(g, b, 2 * oz + kz - 1, 2 * oy + ky - 1, 2 * ox + kx - 1, g.Cin);
+                    if (e >= 0) v = __ldg(reinterpret_cast<const uint4 *>(X + e + ci));
+                } else {   // Cin == 2: the group spans four taps of two channels
+                    uint32_t w[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int tap = (k0 >> 1) + q;
+                        const int kz = tap >> 4, ky = (tap >> 2) & 3, kx = tap & 3;
+                        const long long e = vox(g, b, 2 * oz + kz - 1, 2 * oy + ky - 1, 2 * ox + kx - 1, 2);
+                        w[q] = e >= 0 ? __ldg(reinterpret_cast<const uint32_t *>(X + e)) : 0u;
+                    }
+                    v = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            st16(tile, t, 8 * j, v);
+        }
+    }
+    __device__ void load_b(uint8_t *tile, int c, int t) const {
+        const int K = 64 * g.Cin;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = t + 128 * i, n = q >> 3, j = q & 7, k = c * kChunkK + 8 * j;
+            uint4 v = zero4();
+            if (k < K) v = __ldg(reinterpret_cast<const uint4 *>(W + (size_t)n * K + k));
+            st16(tile, n, 8 * j, v);
+        }
+    }
+    __device__ void epilogue(int row, const float *acc) const {
+        if (row >= M()) return;
+        uint32_t packed[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const float a = fmaxf(acc[2 * i] + bias[2 * i], 0.0f), b = fmaxf(acc[2 * i + 1] + bias[2 * i + 1], 0.0f);
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            packed[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(Y + (size_t)row * kTileN);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+    }
+};
+
+// Data gradient: rows = input voxels (b, iz, iy, ix), columns = ci (Cin = 32),
+// K = tap * 32 + co.  Wt = W transposed to [ci][tap][co].  Epilogue: the
+// gradient times the ReLU mask of the layer below (act > 0), as bf16; with
+// act == nullptr no mask.
+struct ConvDgradOp {
+    ConvGeom g;             // the forward layer's geometry (input D, Cin = 32)
+    const uint16_t *dY;     // [B][Do^3][32] gradient wrt the pre-activation of this layer
+    const uint16_t *Wt;     // [32 ci][64][32 co]
+    const uint16_t *act;    // [B][D^3][32] this layer's input (ReLU output below), or nullptr
+    uint16_t *dX;           // [B][D^3][32]
+    __device__ int M() const { return g.batch * g.D * g.D * g.D; }
+    __device__ int chunks() const { return (64 * 32) / kChunkK; }
+    __device__ void load_a(uint8_t *tile, int m0, int c, int t) const {
+        const int r = m0 + t, D = g.D, Do = g.Do();
+        const bool live = r < M();
+        const int ix = r % D, iy = (r / D) % D, iz = (r / (D * D)) % D, b = r / (D * D * D);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k0 = c * kChunkK + 8 * j, tap = k0 >> 5, co = k0 & 31;
+            const int kz = tap >> 4, ky = (tap >> 2) & 3, kx = tap & 3;
+            const int nz = iz + 1 - kz, ny = iy + 1 - ky, nx = ix + 1 - kx;
+            uint4 v = zero4();
+            if (live && !((nz | ny | nx) & 1)) {
+                const int oz = nz >> 1, oy = ny >> 1, ox = nx >> 1;
+                if ((unsigned)oz < (unsigned)Do && (unsigned)oy < (unsigned)Do && (unsigned)ox < (unsigned)Do) {
+                    const long long e = ((((long long)b * Do + oz) * Do + oy) * Do + ox) * 32 + co;
+                    v = __ldg(reinterpret_cast<const uint4 *>(dY + e));
+                }
+            }
+            st16(tile, t, 8 * j, v);
+        }
+    }
+    __device__ void load_b(uint8_t *tile, int c, int t) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = t + 128 * i, n = q >> 3, j = q & 7, k = c * kChunkK + 8 * j;
+            st16(tile, n, 8 * j, __ldg(reinterpret_cast<const uint4 *>(Wt + (size_t)n * 2048 + k)));
+        }
+    }
+    __device__ void epilogue(int row, const float *acc) const {
+        if (row >= M()) return;
+        uint32_t mask[16];
+        if (act) {
+            const uint4 *a4 = reinterpret_cast<const uint4 *>(act + (size_t)row * 32);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint4 u = a4[i];
+                mask[4 * i] = u.x; mask[4 * i + 1] = u.y; mask[4 * i + 2] = u.z; mask[4 * i + 3] = u.w;
+            }
+        }
+        uint32_t packed[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float a = acc[2 * i], b = acc[2 * i + 1];
+            if (act) {
+                // bf16 activations are >= 0 (ReLU): positive iff a nonzero bit pattern
+                a = (mask[i] & 0xFFFFu) ? a : 0.0f;
+                b = (mask[i] >> 16) ? b : 0.0f;
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            packed[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(dX + (size_t)row * 32);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+    }
+};
+
+// Weight gradient: rows = (tap, ci) (64 Cin rows), columns = co, K = output
+// positions (b, o), split over blockIdx.y; partial sums are added to dW
+// (fp32, [32][64][Cin]) atomically.
+struct ConvWgradOp {
+    ConvGeom g;
+    const uint16_t *X;      // [B][D^3][Cin]
+    const uint16_t *dY;     // [B][Do^3][32]
+    float *dW;              // [32][64][Cin], accumulated
+    int chunks_per_split;
+    __device__ int M() const { return 64 * g.Cin; }
+    __device__ int positions() const { const int d = g.Do(); return g.batch * d * d * d; }
+    __device__ int chunks() const { return (positions() + kChunkK - 1) / kChunkK; }
+    __device__ void load_a(uint8_t *tile, int m0, int c, int t) const {
+        const int r = m0 + t, Do = g.Do();
+        const bool live = r < M();
+        const int tap = r / g.Cin, ci = r - tap * g.Cin;
+        const int kz = tap >> 4, ky = (tap >> 2) & 3, kx = tap & 3;
+        const int P = positions();
+#pragma unroll 1
+        for (int j = 0; j < 8; ++j) {
+            uint32_t w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t lohi[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int p = c * kChunkK + 8 * j + 2 * q + h;
+                    uint32_t val = 0u;
+                    if (live && p < P) {
+                        const int ox = p % Do, oy = (p / Do) % Do, oz = (p / (Do * Do)) % Do, b = p / (Do * Do * Do);
+                        const long long e = vox(g, b, 2 * oz + kz - 1, 2 * oy + ky - 1, 2 * ox + kx - 1, g.Cin);
+                        if (e >= 0) val = __ldg(X + e + ci);
+                    }
+                    lohi[h] = val;
+                }
+                w[q] = lohi[0] | (lohi[1] << 16);
+            }
+            st16(tile, t, 8 * j, make_uint4(w[0], w[1], w[2], w[3]));
+        }
+    }
+    __device__ void load_b(uint8_t *tile, int c, int t) const {
+        const int P = positions();
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = t + 128 * i, n = q >> 3, j = q & 7;
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p0 = c * kChunkK + 8 * j + 2 * u;
+                const uint32_t lo = p0 < P ? __ldg(dY + (size_t)p0 * 32 + n) : 0u;
+                const uint32_t hi = p0 + 1 < P ? __ldg(dY + (size_t)(p0 + 1) * 32 + n) : 0u;
+                w[u] = lo | (hi << 16);
+            }
+            st16(tile, n, 8 * j, make_uint4(w[0], w[1], w[2], w[3]));
+        }
+    }
+    __device__ void epilogue(int row, const float *acc) const {
+        if (row >= M()) return;
+        const int tap = row / g.Cin, ci = row - tap * g.Cin;
+#pragma unroll
+        for (int co = 0; co < 32; ++co)
+            if (acc[co] != 0.0f) atomicAdd(dW + ((size_t)co * 64 + tap) * g.Cin + ci, acc[co]);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The tile kernel.  blockIdx.x: 128-row tile; blockIdx.y: K split (chunks
+// [y * per, min((y + 1) * per, chunks))).
+// ---------------------------------------------------------------------------
+template <class Op>
+__global__ void __launch_bounds__(128) k_umma_tile(const Op op, int chunks_per_split) {
+    __shared__ __align__(1024) uint8_t sA[2][kStageA];
+    __shared__ __align__(1024) uint8_t sB[2][kStageB];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ uint32_t tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int m0 = blockIdx.x * kTileM;
+    const int nch = op.chunks();
+    const int c0 = blockIdx.y * chunks_per_split;
+    const int c1 = min(nch, c0 + chunks_per_split);
+
+    if (warp == 0) umma::tmem_alloc(&tmem_slot, kTileN);
+    if (t == 0) {
+        umma::mbar_init(umma::smem_u32(&mbar[0]), 1);
+        umma::mbar_init(umma::smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    // every wait's outcome is agreed by the whole CTA (__syncthreads_and), so
+    // all threads leave the loop together
+    bool ok = true;
+    for (int c = c0; c < c1; ++c) {
+        const int s = (c - c0) & 1, use = (c - c0) >> 1;
+        if (use > 0 && !__syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[s]), (uint32_t)((use - 1) & 1)))) {
+            ok = false;
+            break;
+        }
+        op.load_a(sA[s], m0, c, t);
+        op.load_b(sB[s], c, t);
+        umma::fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            umma::fence_after_sync();
+            const uint32_t a = umma::smem_u32(sA[s]), b = umma::smem_u32(sB[s]);
+#pragma unroll
+            for (int kk = 0; kk < kChunkK / 16; ++kk)
+                umma::mma_bf16(tmem, umma::smem_desc(a + 256 * kk, 128, 16 * kChunkK),
+                               umma::smem_desc(b + 256 * kk, 128, 16 * kChunkK), kIdesc, c > c0 || kk > 0);
+            umma::commit(umma::smem_u32(&mbar[s]));
+        }
+    }
+    const int n = c1 - c0;
+    if (ok && n > 0)
+        ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[(n - 1) & 1]), (uint32_t)(((n - 1) >> 1) & 1)));
+    if (!ok) {
+        if (t == 0) atomicExch(&g_nn_error, 1u);
+    } else if (n > 0) {
+        umma::fence_after_sync();
+        float acc[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
+        op.epilogue(m0 + t, acc);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, kTileN);
+}
+
+template <class Op>
+cudaError_t launch_tile(const Op &op, int M, int chunks, int splits, cudaStream_t s) {
+    if (M <= 0 || chunks <= 0) return cudaSuccess;
+    if (splits < 1) splits = 1;
+    if (splits > chunks) splits = chunks;
+    const int per = (chunks + splits - 1) / splits;
+    splits = (chunks + per - 1) / per;
+    dim3 grid((unsigned)((M + kTileM - 1) / kTileM), (unsigned)splits);
+    k_umma_tile<Op><<<grid, 128, 0, s>>>(op, per);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// W [32][64][Cin] -> Wt [Cin][64][32] (bf16), for the data gradient.
+__global__ void k_transpose_w(const uint16_t *W, int Cin, uint16_t *Wt) {
+    const int n = 32 * 64 * Cin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int ci = i % Cin, tap = (i / Cin) % 64, co = i / (64 * Cin);
+        Wt[((size_t)ci * 64 + tap) * 32 + co] = W[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core parts of the network: fully connected layers, bias gradients,
+// the loss, Adam, input preparation and the synthetic training pairs.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    return *reinterpret_cast<const uint16_t *>(&h);
+}
+
+// out[b][n] = act(b_n + sum_k in[b][k] W[n][k]); one warp per output.
+template <class T>
+__global__ void k_fc_forward(const T *__restrict__ in, int B, int K, const float *__restrict__ W,
+                             const float *__restrict__ bias, int N, float *__restrict__ out, int relu) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= B * N) return;
+    const int b = w / N, n = w - b * N;
+    float acc = 0.0f;
+    for (int k = lane; k < K; k += 32) acc += to_f(in[(size_t)b * K + k]) * W[(size_t)n * K + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        acc += bias[n];
+        out[(size_t)b * N + n] = relu ? fmaxf(acc, 0.0f) : acc;
+    }
+}
+
+// din[b][k] = [act[b][k] > 0] * sum_n dout[b][n] W[n][k]  (T = float or bf16 out).
+template <class TA, class TO>
+__global__ void k_fc_backward_input(const float *__restrict__ dout, int B, int N, const float *__restrict__ W,
+                                    int K, const TA *__restrict__ act, TO *__restrict__ din) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * K) return;
+    const int b = i / K, k = i - b * K;
+    float acc = 0.0f;
+    for (int n = 0; n < N; ++n) acc += dout[(size_t)b * N + n] * W[(size_t)n * K + k];
+    if (!(to_f(act[i]) > 0.0f)) acc = 0.0f;
+    if constexpr (sizeof(TO) == 2) din[i] = bf16_bits(acc);
+    else din[i] = acc;
+}
+
+// dW[n][k] += sum_b dout[b][n] in[b][k];  db[n] += sum_b dout[b][n] (k == 0 threads).
+template <class T>
+__global__ void k_fc_backward_weight(const float *__restrict__ dout, int B, int N, const T *__restrict__ in, int K,
+                                     float *__restrict__ dW, float *__restrict__ db) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N * K) return;
+    const int n = i / K, k = i - n * K;
+    float acc = 0.0f, accb = 0.0f;
+    for (int b = 0; b < B; ++b) {
+        const float g = dout[(size_t)b * N + n];
+        acc += g * to_f(in[(size_t)b * K + k]);
+        accb += g;
+    }
+    dW[i] += acc;
+    if (k == 0) db[n] += accb;
+}
+
+// db[c] += sum_rows dY[row][c] (32 channels, bf16 rows).
+__global__ void k_bias_grad(const uint16_t *__restrict__ dY, long long rows, float *__restrict__ db) {
+    __shared__ float part[8][32];
+    const int c = threadIdx.x & 31, r0 = threadIdx.x >> 5;   // 256 threads: 8 row lanes
+    float acc = 0.0f;
+    for (long long r = (long long)blockIdx.x * 8 + r0; r < rows; r += (long long)gridDim.x * 8)
+        acc += to_f(dY[r * 32 + c]);
+    part[r0][c] = acc;
+    __syncthreads();
+    if (r0 == 0) {
+        float s = 0.0f;
+        for (int q = 0; q < 8; ++q) s += part[q][c];
+        atomicAdd(db + c, s);
+    }
+}
+
+// Gaussian negative log-likelihood of the labels y under N(mu, exp(s)) per
+// DOF, out = [mu(6) | s(6)], averaged over the batch; writes d loss / d out
+// and adds the loss into *loss.
+__global__ void k_nll(const float *__restrict__ out, const float *__restrict__ y, int B, float *__restrict__ dout,
+                      float *__restrict__ loss_log, const int *__restrict__ step) {
+    float *loss = loss_log + *step;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (i < B * 6) {
+        const int b = i / 6, d = i - b * 6;
+        const float mu = out[b * 12 + d], sv = out[b * 12 + 6 + d];
+        const float r = y[b * 6 + d] - mu, e = __expf(-sv);
+        dout[b * 12 + d] = -r * e / (float)B;
+        dout[b * 12 + 6 + d] = 0.5f * (1.0f - r * r * e) / (float)B;
+        l = 0.5f * (r * r * e + sv) / (float)B;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss, l);
+}
+
+// Adam (Kingma & Ba, Algorithm 1) with the step count t = *step + 1.
+__global__ void k_adam(float *__restrict__ theta, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, long long n, float lr, const int *__restrict__ step) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const int t = *step + 1;
+    const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi, vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void k_step_inc(int *step) { *step += 1; }
+
+// bf16 copies of fp32 parameters (conv weights) and their [ci][tap][co] transposes.
+__global__ void k_to_bf16(const float *__restrict__ a, long long n, uint16_t *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = bf16_bits(a[i]);
+}
+
+// Uniform initialisation U(-a, a), a = sqrt(6 / fan_in), from Philox(seed).
+__global__ void k_init_uniform(float *p, long long n, float a, uint64_t seed, uint32_t tensor) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const u32x4 r = philox_seeded(seed, (uint32_t)i, tensor, 0x6E6E0000u, 0u);
+        p[i] = a * (2.0f * ((float)(r.x >> 8) * 5.9604644775390625e-08f) - 1.0f);
+    }
+}
+
+// Network input: the box-average of a uint8 volume over each cell of a
+// G^3 grid covering the box [box_o, box_o + G h) (world units), scaled by
+// 1/64, into channel c of a [G^3][2] bf16 input; cells with no voxel get 0.
+struct DownArgs {
+    const uint8_t *vol;
+    int dims[3];
+    float origin[3], spacing[3];
+    float box_o[3], h[3];
+    int G, c;
+    uint16_t *x;
+};
+__global__ void k_downsample(const DownArgs a) {
+    const int G = a.G;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= G * G * G) return;
+    const int gx = i % G, gy = (i / G) % G, gz = i / (G * G);
+    const int g[3] = {gx, gy, gz};
+    int lo[3], hi[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        // voxel p sits at origin + spacing * p; the cell covers [b0, b1)
+        const float b0 = a.box_o[d] + a.h[d] * g[d], b1 = a.box_o[d] + a.h[d] * (g[d] + 1);
+        lo[d] = max(0, (int)ceilf((b0 - a.origin[d]) / a.spacing[d]));
+        hi[d] = min(a.dims[d], (int)ceilf((b1 - a.origin[d]) / a.spacing[d]));
+    }
+    unsigned sum = 0, cnt = 0;
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y) {
+            const uint8_t *row = a.vol + ((size_t)z * a.dims[1] + y) * a.dims[0];
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                sum += row[x];
+                ++cnt;
+            }
+        }
+    const float v = cnt ? (float)sum / (float)cnt * (1.0f / 64.0f) : 0.0f;
+    a.x[(size_t)i * 2 + a.c] = bf16_bits(v);
+}
+
+// Synthetic training pairs: echo-like source and target views of a random
+// left-ventricle shell (myocardium 1.0, blood pool 0.15, background 0.3,
+// cut open at the valve plane), Rayleigh speckle (sigma 40) hashed from the
+// rounded world voxel, a smooth multiplicative gain per view, a random rigid
+// pose within the training limits and a target field of view slid along x
+// for 35-60 % overlap -- the recipe of the image workload's pairs -- each
+// voxel computed at full resolution (X, Y, Z) and box-averaged into the G^3
+// input exactly as k_downsample does for real volumes.
+struct SynthSample {
+    float R[9], t[3], c[3];          // pose about the source centre c
+    float hc[3], outer[3], inner[3]; // heart centre and shell semi-axes
+    float base_x;
+    float gf[2][3][3], gph[2][3];    // gain frequencies / phases per view
+    int shift;                       // target origin x (voxels)
+    uint32_t speckle;
+};
+struct SynthArgs {
+    int X, Y, Z, G;
+    float rot_lim, trans_lim;
+    uint64_t seed;
+    int step;                // used when step_ptr is NULL
+    const int *step_ptr;     // the optimiser's step counter (graph replays)
+    SynthSample *samples;
+    uint16_t *x;   // [B][G^3][2]
+    float *y;      // [B][6] pose / limits
+};
+
+__device__ __forceinline__ float u01(uint32_t r) { return (float)(r >> 8) * 5.9604644775390625e-08f; }
+
+__global__ void k_synth_params(const SynthArgs a, int B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const uint32_t step = (uint32_t)(a.step_ptr ? *a.step_ptr : a.step);
+    uint32_t w[24];
+    for (int q = 0; q < 6; ++q) {
+        const u32x4 r = philox_seeded(a.seed, (uint32_t)b, step, 0x53594E00u, (uint32_t)q);
+        w[4 * q] = r.x; w[4 * q + 1] = r.y; w[4 * q + 2] = r.z; w[4 * q + 3] = r.w;
+    }
+    SynthSample s;
+    const float dims[3] = {(float)a.X, (float)a.Y, (float)a.Z};
+    float ang[3], tr[3];
+    for (int d = 0; d < 3; ++d) {
+        ang[d] = a.rot_lim * (2.0f * u01(w[d]) - 1.0f);
+        tr[d] = a.trans_lim * (2.0f * u01(w[3 + d]) - 1.0f);
+        s.c[d] = 0.5f * (dims[d] - 1.0f);
+        s.hc[d] = s.c[d] + 8.0f * u01(w[6 + d]) - 4.0f;
+    }
+    const float fr[3] = {0.36f, 0.26f, 0.28f};
+    for (int d = 0; d < 3; ++d) s.outer[d] = fr[d] * dims[d] * (0.95f + 0.1f * u01(w[9 + d]));
+    const float th = 0.055f * dims[0];
+    for (int d = 0; d < 3; ++d) s.inner[d] = s.outer[d] - th;
+    s.base_x = 0.55f * s.outer[0];
+    // R = Rz Rx Ry
+    float sx, cx, sy, cy, sz, cz;
+    sincosf(ang[0], &sx, &cx);
+    sincosf(ang[1], &sy, &cy);
+    sincosf(ang[2], &sz, &cz);
+    const float Rz[9] = {cz, -sz, 0, sz, cz, 0, 0, 0, 1};
+    const float Rx[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};
+    const float Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};
+    float T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.0f;
+            for (int k = 0; k < 3; ++k) acc += Rz[3 * i + k] * Rx[3 * k + j];
+            T[3 * i + j] = acc;
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            float acc = 0.0f;
+            for (int k = 0; k < 3; ++k) acc += T[3 * i + k] * Ry[3 * k + j];
+            s.R[3 * i + j] = acc;
+        }
+    for (int d = 0; d < 3; ++d) s.t[d] = tr[d];
+    s.shift = (int)rintf((0.40f + 0.25f * u01(w[12])) * dims[0]);
+    for (int v = 0; v < 2; ++v)
+        for (int q = 0; q < 3; ++q) {
+            for (int d = 0; d < 3; ++d) {
+                const u32x4 r = philox_seeded(a.seed, (uint32_t)b, step, 0x53594E01u, (uint32_t)(9 * v + 3 * q + d));
+                s.gf[v][q][d] = 0.3f + 0.9f * u01(r.x);
+            }
+            s.gph[v][q] = 6.2831853f * u01(w[13 + 3 * v + q]);
+        }
+    s.speckle = w[20];
+    a.samples[b] = s;
+    for (int d = 0; d < 3; ++d) {
+        a.y[b * 6 + d] = ang[d] / a.rot_lim;
+        a.y[b * 6 + 3 + d] = tr[d] / a.trans_lim;
+    }
+}
+
+__device__ __forceinline__ uint32_t hash3(int x, int y, int z, uint32_t seed) {
+    uint32_t h = (uint32_t)x * 0x8DA6B343u ^ (uint32_t)y * 0xD8163841u ^ (uint32_t)z * 0xCB1AB31Fu ^ seed;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+
+// One view's voxel value at world point w (source frame) and grid fraction u.
+__device__ __forceinline__ float synth_voxel(const SynthSample &s, int view, const float w[3], const float u[3]) {
+    const float ux = w[0] - s.hc[0], uy = w[1] - s.hc[1], uz = w[2] - s.hc[2];
+    const float eo = (ux / s.outer[0]) * (ux / s.outer[0]) + (uy / s.outer[1]) * (uy / s.outer[1]) +
+                     (uz / s.outer[2]) * (uz / s.outer[2]);
+    const float ei = (ux / s.inner[0]) * (ux / s.inner[0]) + (uy / s.inner[1]) * (uy / s.inner[1]) +
+                     (uz / s.inner[2]) * (uz / s.inner[2]);
+    float tissue = 0.3f;
+    if (ux <= s.base_x) {
+        if (ei <= 1.0f) tissue = 0.15f;
+        else if (eo <= 1.0f) tissue = 1.0f;
+    }
+    const uint32_t h = hash3((int)rintf(w[0]), (int)rintf(w[1]), (int)rintf(w[2]), s.speckle);
+    const float uu = ((float)(h >> 8) + 0.5f) * 5.9604644775390625e-08f;
+    const float speck = 40.0f * sqrtf(-2.0f * __logf(uu));
+    float gsum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        gsum += __cosf(6.2831853f * (s.gf[view][q][0] * u[0] + s.gf[view][q][1] * u[1] + s.gf[view][q][2] * u[2]) +
+                       s.gph[view][q]);
+    const float gain = 1.0f + 0.3f * gsum / 3.0f;
+    return fminf(fmaxf(rintf(tissue * speck * gain), 0.0f), 255.0f);
+}
+
+// blockIdx.y = sample, threads over the G^3 cells; both channels.
+__global__ void k_synth_views(const SynthArgs a) {
+    const int G = a.G, b = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= G * G * G) return;
+    const SynthSample &s = a.samples[b];
+    const int g[3] = {i % G, (i / G) % G, i / (G * G)};
+    const int dims[3] = {a.X, a.Y, a.Z};
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        const float h = (float)dims[d] / (float)G;
+        lo[d] = (int)ceilf(h * g[d]);
+        hi[d] = min(dims[d], (int)ceilf(h * (g[d] + 1)));
+    }
+    const float inv[3] = {1.0f / a.X, 1.0f / a.Y, 1.0f / a.Z};
+    float sum_s = 0.0f, sum_t = 0.0f;
+    int cnt_s = 0, cnt_t = 0;
+    for (int z = lo[2]; z < hi[2]; ++z)
+        for (int y = lo[1]; y < hi[1]; ++y)
+            for (int x = lo[0]; x < hi[0]; ++x) {
+                // source view: voxel (x, y, z) at world (x, y, z)
+                const float ws[3] = {(float)x, (float)y, (float)z};
+                const float us[3] = {x * inv[0], y * inv[1], z * inv[2]};
+                sum_s += synth_voxel(s, 0, ws, us);
+                ++cnt_s;
+                // target view: target voxel p = (x - shift, y, z) sits here at identity;
+                // its tissue is at R (p + o_T - c) + c + t
+                const int px = x - s.shift;
+                if (px >= 0 && px < a.X) {
+                    const float q[3] = {(float)x - s.c[0], (float)y - s.c[1], (float)z - s.c[2]};
+                    float wt[3];
+                    for (int r = 0; r < 3; ++r)
+                        wt[r] = s.R[3 * r] * q[0] + s.R[3 * r + 1] * q[1] + s.R[3 * r + 2] * q[2] + s.c[r] + s.t[r];
+                    const float ut[3] = {px * inv[0], y * inv[1], z * inv[2]};
+                    sum_t += synth_voxel(s, 1, wt, ut);
+                    ++cnt_t;
+                }
+            }
+    uint16_t *xo = a.x + ((size_t)b * G * G * G + i) * 2;
+    xo[0] = bf16_bits(cnt_s ? sum_s / cnt_s * (1.0f / 64.0f) : 0.0f);
+    xo[1] = bf16_bits(cnt_t ? sum_t / cnt_t * (1.0f / 64.0f) : 0.0f);
+}
+
+}  // namespace nn
+
+cudaError_t nn_error_flag(unsigned int *out, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, nn::g_nn_error, sizeof(unsigned int));
+    if (e != cudaSuccess || !clear) return e;
+    const unsigned int z = 0;
+    return cudaMemcpyToSymbol(nn::g_nn_error, &z, sizeof(z));
+}
+
+cudaError_t nn_gemm(const uint16_t *A, const uint16_t *B, float *C, int M, int K, cudaStream_t s) {
+    nn::GemmOp op{A, B, C, M, K};
+    return nn::launch_tile(op, M, (K + nn::kChunkK - 1) / nn::kChunkK, 1, s);
+}
+
+cudaError_t nn_conv_fwd(const uint16_t *X, int batch, int D, int Cin, const uint16_t *W, const float *bias,
+                        uint16_t *Y, cudaStream_t s) {
+    nn::ConvFwdOp op{{batch, D, Cin}, X, W, bias, Y};
+    const int Do = D / 2;
+    return nn::launch_tile(op, batch * Do * Do * Do, (64 * Cin + nn::kChunkK - 1) / nn::kChunkK, 1, s);
+}
+
+cudaError_t nn_conv_dgrad(const uint16_t *dY, int batch, int D, const uint16_t *Wt, const uint16_t *act,
+                          uint16_t *dX, cudaStream_t s) {
+    nn::ConvDgradOp op{{batch, D, 32}, dY, Wt, act, dX};
+    return nn::launch_tile(op, batch * D * D * D, 2048 / nn::kChunkK, 1, s);
+}
+
+cudaError_t nn_transpose_w(const uint16_t *W, int Cin, uint16_t *Wt, cudaStream_t s) {
+    nn::k_transpose_w<<<64, 256, 0, s>>>(W, Cin, Wt);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t nn_conv_wgrad(const uint16_t *X, int batch, int D, int Cin, const uint16_t *dY, float *dW,
+                          cudaStream_t s) {
+    const int Do = D / 2;
+    const int P = batch * Do * Do * Do;
+    const int chunks = (P + nn::kChunkK - 1) / nn::kChunkK;
+    const int mtiles = (64 * Cin + nn::kTileM - 1) / nn::kTileM;
+    int splits = (4 * 152 + mtiles - 1) / mtiles;   // about four CTAs per SM in all
+    nn::ConvWgradOp op{{batch, D, Cin}, X, dY, dW, 0};
+    return nn::launch_tile(op, 64 * Cin, chunks, splits, s);
+}
+
+}  // namespace pfreg
+
+namespace pfreg {
+
+namespace {
+unsigned grid_for(long long n, int threads, long long cap = 4096) {
+    long long g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+}  // namespace
+
+#define NNCK(call)                             \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) return e_;      \
+    } while (0)
+#define NNLAUNCH(n) (count_launches(n), cudaGetLastError())
+
+cudaError_t net_forward(const NetPtrs &n, int B, cudaStream_t s) {
+    const uint16_t *in = n.x;
+    for (int l = 0; l < 4; ++l) {
+        NNCK(nn_conv_fwd(in, B, net_din(l), net_cin(l), n.wbf[l], n.theta + n.L.cb[l], n.a[l], s));
+        in = n.a[l];
+    }
+    const int t = 256;
+    nn::k_fc_forward<uint16_t><<<grid_for((long long)B * kNetHidden * 32, t, 1 << 20), t, 0, s>>>(
+        n.a[3], B, kNetFlat, n.theta + n.L.f1w, n.theta + n.L.f1b, kNetHidden, n.h, 1);
+    NNCK(NNLAUNCH(1));
+    nn::k_fc_forward<float><<<grid_for((long long)B * kNetOut * 32, t, 1 << 20), t, 0, s>>>(
+        n.h, B, kNetHidden, n.theta + n.L.f2w, n.theta + n.L.f2b, kNetOut, n.out, 0);
+    return NNLAUNCH(1);
+}
+
+// Gradients of the mean loss over the batch into n.grad (zeroed here) and the
+// loss into n.loss[*n.step].
+cudaError_t net_backward(const NetPtrs &n, int B, cudaStream_t s) {
+    NNCK(cudaMemsetAsync(n.grad, 0, sizeof(float) * n.L.total, s));
+    float *g = n.grad;
+    const int t = 256;
+    nn::k_nll<<<grid_for((long long)B * 6, t), t, 0, s>>>(n.out, n.y, B, n.dout, n.loss, n.step);
+    NNCK(NNLAUNCH(1));
+    nn::k_fc_backward_weight<float><<<grid_for((long long)kNetOut * kNetHidden, t), t, 0, s>>>(
+        n.dout, B, kNetOut, n.h, kNetHidden, g + n.L.f2w, g + n.L.f2b);
+    NNCK(NNLAUNCH(1));
+    nn::k_fc_backward_input<float, float><<<grid_for((long long)B * kNetHidden, t), t, 0, s>>>(
+        n.dout, B, kNetOut, n.theta + n.L.f2w, kNetHidden, n.h, n.dh);
+    NNCK(NNLAUNCH(1));
+    nn::k_fc_backward_weight<uint16_t><<<grid_for((long long)kNetHidden * kNetFlat, t, 1 << 20), t, 0, s>>>(
+        n.dh, B, kNetHidden, n.a[3], kNetFlat, g + n.L.f1w, g + n.L.f1b);
+    NNCK(NNLAUNCH(1));
+    nn::k_fc_backward_input<uint16_t, uint16_t><<<grid_for((long long)B * kNetFlat, t, 1 << 20), t, 0, s>>>(
+        n.dh, B, kNetHidden, n.theta + n.L.f1w, kNetFlat, n.a[3], n.d[3]);
+    NNCK(NNLAUNCH(1));
+    for (int l = 3; l >= 0; --l) {
+        const int D = net_din(l), Do = D / 2;
+        const uint16_t *X = l == 0 ? n.x : n.a[l - 1];
+        NNCK(nn_conv_wgrad(X, B, D, net_cin(l), n.d[l], g + n.L.cw[l], s));
+        const long long rows = (long long)B * Do * Do * Do;
+        nn::k_bias_grad<<<grid_for(rows, 8, 1024), 256, 0, s>>>(n.d[l], rows, g + n.L.cb[l]);
+        NNCK(NNLAUNCH(1));
+        if (l > 0) NNCK(nn_conv_dgrad(n.d[l], B, D, n.wt[l], n.a[l - 1], n.d[l - 1], s));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t net_refresh_bf16(const NetPtrs &n, cudaStream_t s) {
+    for (int l = 0; l < 4; ++l) {
+        const long long cnt = 32LL * 64 * net_cin(l);
+        nn::k_to_bf16<<<grid_for(cnt, 256), 256, 0, s>>>(n.theta + n.L.cw[l], cnt, n.wbf[l]);
+        NNCK(NNLAUNCH(1));
+        if (l > 0) NNCK(nn_transpose_w(n.wbf[l], net_cin(l), n.wt[l], s));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t net_adam(const NetPtrs &n, float lr, cudaStream_t s) {
+    nn::k_adam<<<grid_for(n.L.total, 256, 2048), 256, 0, s>>>(n.theta, n.m, n.v, n.grad, n.L.total, lr, n.step);
+    NNCK(NNLAUNCH(1));
+    nn::k_step_inc<<<1, 1, 0, s>>>(n.step);
+    NNCK(NNLAUNCH(1));
+    return net_refresh_bf16(n, s);
+}
+
+cudaError_t net_init(const NetPtrs &n, uint64_t seed, cudaStream_t s) {
+    NNCK(cudaMemsetAsync(n.theta, 0, sizeof(float) * n.L.total, s));
+    NNCK(cudaMemsetAsync(n.m, 0, sizeof(float) * n.L.total, s));
+    NNCK(cudaMemsetAsync(n.v, 0, sizeof(float) * n.L.total, s));
+    NNCK(cudaMemsetAsync(n.step, 0, sizeof(int), s));
+    struct T {
+        long long off, cnt;
+        int fan_in;
+    } ts[6] = {{n.L.cw[0], 32LL * 64 * 2, 64 * 2},      {n.L.cw[1], 32LL * 64 * 32, 64 * 32},
+               {n.L.cw[2], 32LL * 64 * 32, 64 * 32},    {n.L.cw[3], 32LL * 64 * 32, 64 * 32},
+               {n.L.f1w, (long long)kNetHidden * kNetFlat, kNetFlat}, {n.L.f2w, (long long)kNetOut * kNetHidden, kNetHidden}};
+    for (int i = 0; i < 6; ++i) {
+        const float a = sqrtf(6.0f / (float)ts[i].fan_in) * (i == 5 ? 0.1f : 1.0f);   // small output layer
+        nn::k_init_uniform<<<grid_for(ts[i].cnt, 256), 256, 0, s>>>(n.theta + ts[i].off, ts[i].cnt, a, seed, (uint32_t)i);
+        NNCK(NNLAUNCH(1));
+    }
+    return net_refresh_bf16(n, s);
+}
+
+cudaError_t net_synth(const NetPtrs &n, int B, uint64_t seed, int step, float rot_lim, float trans_lim,
+                      const int dims[3], bool step_from_counter, cudaStream_t s) {
+    nn::SynthArgs a{};
+    a.X = dims[0];
+    a.Y = dims[1];
+    a.Z = dims[2];
+    a.G = kNetG;
+    a.rot_lim = rot_lim;
+    a.trans_lim = trans_lim;
+    a.seed = seed;
+    a.step = step;
+    a.step_ptr = step_from_counter ? n.step : nullptr;
+    a.samples = static_cast<nn::SynthSample *>(n.samples);
+    a.x = n.x;
+    a.y = n.y;
+    nn::k_synth_params<<<grid_for(B, 64), 64, 0, s>>>(a, B);
+    NNCK(NNLAUNCH(1));
+    const int cells = kNetG * kNetG * kNetG;
+    nn::k_synth_views<<<dim3((unsigned)((cells + 127) / 128), (unsigned)B), 128, 0, s>>>(a);
+    return NNLAUNCH(1);
+}
+
+size_t net_sample_bytes() { return sizeof(nn::SynthSample); }
+
+cudaError_t net_downsample(const NetPtrs &n, const uint8_t *vol, const int dims[3], const float origin[3],
+                           const float spacing[3], const float box_o[3], const float box_h[3], int channel,
+                           cudaStream_t s) {
+    nn::DownArgs a{};
+    a.vol = vol;
+    for (int d = 0; d < 3; ++d) {
+        a.dims[d] = dims[d];
+        a.origin[d] = origin[d];
+        a.spacing[d] = spacing[d];
+        a.box_o[d] = box_o[d];
+        a.h[d] = box_h[d];
+    }
+    a.G = kNetG;
+    a.c = channel;
+    a.x = n.x;
+    const int cells = kNetG * kNetG * kNetG;
+    nn::k_downsample<<<(cells + 255) / 256, 256, 0, s>>>(a);
+    return NNLAUNCH(1);
+}
+
+#undef NNCK
+#undef NNLAUNCH
+
+}  // namespace pfreg

@@ -1,0 +1,155 @@
+"""The learned proposal network on the GPU against its float64 oracle
+(oracle/nn.py), and the proposal-seeded filter against the C oracle."""
+import numpy as np
+import pytest
+
+from oracle import nn as onn
+
+pytestmark = pytest.mark.gpu
+
+ROT, TRANS = 0.5235988, 25.0
+DIMS = (96, 80, 72)   # small synthetic volumes keep the generator quick
+
+
+@pytest.fixture(scope="module")
+def torch_():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import paper_2504_19930_gb300 as pk
+    pk.build()
+    pk.load()
+    return pk
+
+
+def _bf16_host(torch, t):
+    return onn.from_bf16_bits(t.view(torch.int16).cpu().numpy().view(np.uint16))
+
+
+def _batch(torch, pk, net, B, seed=3, step=0):
+    x = torch.zeros((B, 64, 64, 64, 2), dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros((B, 6), dtype=torch.float32, device="cuda")
+    net.synth(x, y, seed, step, DIMS, ROT, TRANS)
+    torch.cuda.synchronize()
+    return x, y
+
+
+def test_synthetic_batch_is_well_formed(torch_, pk):
+    torch = torch_
+    net = pk.Proposal(max_batch=4, seed=1)
+    x, y = _batch(torch, pk, net, 4)
+    xs, ys = _bf16_host(torch, x), y.cpu().numpy()
+    assert np.all(np.abs(ys) <= 1.0) and np.std(ys) > 0.2
+    assert np.all(xs >= 0) and np.all(np.isfinite(xs))
+    # the source channel covers the whole box; the target channel, slid along
+    # +x by 40-65 % of X, is empty over the first 40 % of the cells in x
+    assert np.all(xs[..., 0].mean(axis=(1, 2, 3)) > 0.05)
+    assert np.all(xs[:, :, :, : int(0.39 * 64), 1] == 0.0)
+    assert np.all(xs[:, :, :, -8:, 1].mean(axis=(1, 2, 3)) > 0.05)
+    x2, y2 = _batch(torch, pk, net, 4)
+    assert torch.equal(x, x2) and torch.equal(y, y2)           # seeded
+    x3, _ = _batch(torch, pk, net, 4, step=1)
+    assert not torch.equal(x, x3)
+
+
+def test_forward_matches_oracle(torch_, pk):
+    torch = torch_
+    B = 2
+    net = pk.Proposal(max_batch=B, seed=5)
+    theta = net.params()
+    x, _ = _batch(torch, pk, net, B, seed=11)
+    out = torch.zeros((B, 12), dtype=torch.float32, device="cuda")
+    hid = torch.zeros((B, 128), dtype=torch.float32, device="cuda")
+    net.forward(x, out, hid)
+    torch.cuda.synchronize()
+    want, h_want, _ = onn.net_forward(theta, _bf16_host(torch, x))
+    got = out.cpu().numpy()
+    scale = np.abs(want).max()
+    assert np.max(np.abs(got - want)) <= 2e-2 * scale, (got, want)
+    assert np.max(np.abs(hid.cpu().numpy() - h_want)) <= 2e-2 * np.abs(h_want).max()
+
+
+def test_backward_matches_oracle(torch_, pk):
+    torch = torch_
+    B = 2
+    net = pk.Proposal(max_batch=B, seed=6)
+    x, y = _batch(torch, pk, net, B, seed=12)
+    out = torch.zeros((B, 12), dtype=torch.float32, device="cuda")
+    net.forward(x, out)
+    loss = net.backward(y)
+    theta, grad = net.params(with_grad=True)
+    want_loss, want = onn.net_backward(theta, _bf16_host(torch, x), y.cpu().numpy())
+    assert abs(loss - want_loss) <= 2e-2 * abs(want_loss)
+    off, _ = onn.layout()
+    for k, (o, sh) in off.items():
+        n = int(np.prod(sh))
+        g, w = grad[o:o + n].astype(np.float64), want[o:o + n]
+        rel = np.linalg.norm(g - w) / max(np.linalg.norm(w), 1e-30)
+        assert rel < 5e-2, f"{k}: relative gradient error {rel:.3g}"
+
+
+def test_input_matches_box_average(torch_, pk):
+    torch = torch_
+    import pfsynth
+    src = pfsynth.random_image(5, (70, 66, 67))
+    tgt = pfsynth.random_image(6, (60, 72, 50))
+    so, to = np.array([0.0, 0.0, 0.0], np.float32), np.array([20.0, -5.0, 3.0], np.float32)
+    net = pk.Proposal(max_batch=1, seed=1)
+    x = torch.zeros((1, 64, 64, 64, 2), dtype=torch.bfloat16, device="cuda")
+    net.input(torch.from_numpy(src).cuda(), tgt, x, so, to)
+    torch.cuda.synchronize()
+    got = _bf16_host(torch, x)[0]
+    h = np.array([70, 66, 67], np.float64) / 64.0
+    for c, (v, o) in enumerate(((src, so), (tgt, to))):
+        want = onn.box_average(v, o.astype(np.float64), np.ones(3), so.astype(np.float64), h)
+        assert np.all(np.abs(got[..., c] - want) <= 2.0 ** -7 * np.abs(want) + 1e-6)   # fp32 mean, then bf16
+
+
+def test_training_reduces_the_loss(torch_, pk):
+    net = pk.Proposal(max_batch=16, seed=7)
+    loss = net.train(300, batch=16, lr=1e-3, data_seed=5, vol_dims=DIMS, rot_limit=ROT, trans_limit=TRANS)
+    assert np.all(np.isfinite(loss))
+    assert pk.nn_status() == 0
+    assert loss[-30:].mean() < loss[:30].mean() - 0.5, (loss[:30].mean(), loss[-30:].mean())
+
+
+def test_seeded_filter_matches_oracle(torch_, pk):
+    """pf_seed_gaussian + pf_step follow the oracle bit for bit: the seeded
+    cloud, its perturbation scale and every iteration."""
+    import oracle
+    import pfsynth
+    p = pfsynth.ellipsoid_pair(4, src_dims=(26, 24, 22), tgt_dims=(24, 22, 16), tgt_origin=(0, 0, 5),
+                               semi_axes=(8, 6, 5), asymmetric=True, max_rot_deg=8, max_trans=2)
+    N, K, lr_, lt = 128, 4, 0.3, 4.0
+    mean = np.array([0.02, -0.03, 0.01, 0.5, -0.4, 0.2], np.float32)
+    std = np.array([0.05, 0.04, 0.06, 1.0, 0.8, 1.2], np.float32)
+    reg = pk.Registration("mask_dice", src_mask=p.src, tgt_mask=p.tgt, src_origin=p.src_origin,
+                          tgt_origin=p.tgt_origin, n_particles=N, rot_limit=lr_, trans_limit=lt, seed=9)
+    reg.seed_gaussian(mean, std)
+    lim = np.array([lr_] * 3 + [lt] * 3, np.float32)
+    x0 = oracle.init_gaussian(N, 9, mean, std, lim)
+    ref = oracle.register("mask_dice", p.src_dims, p.src_origin, p.tgt_dims, p.tgt_origin, N, K, lr_, lt,
+                          seed=9, src_mask=p.src, tgt_mask=p.tgt, poses=x0, sig_base=std)
+    for k in range(K):
+        reg.step(1)
+        st = reg.state()
+        assert np.array_equal(st["poses_measured"], ref["tr_poses"][k]), f"poses differ at k={k}"
+        assert np.array_equal(st["moments"], ref["tr_mom"][k]), f"counts differ at k={k}"
+        assert np.array_equal(st["resample_idx"], ref["tr_idx"][k]), f"indices differ at k={k}"
+    with pytest.raises(Exception):
+        reg.seed_gaussian(mean, std)        # only before the first iteration
+    reg.close()
+
+
+def test_predict_returns_a_finite_proposal(torch_, pk):
+    import pfsynth
+    net = pk.Proposal(max_batch=8, seed=8)
+    net.train(20, batch=8, lr=1e-3, data_seed=2, vol_dims=DIMS, rot_limit=ROT, trans_limit=TRANS)
+    p = pfsynth.speckle_pair(3, src_dims=DIMS)
+    mean, std = net.predict(p.src, p.tgt, p.src_origin, p.tgt_origin)
+    assert np.all(np.isfinite(mean)) and np.all(std > 0)

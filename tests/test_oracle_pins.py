@@ -522,3 +522,23 @@ def test_trilinear_lerp_single_rounding(orc):
         twice += int(two != want)
     assert twice > 0   # the case set separates one rounding from two
     assert orc.trilinear(src, np.array([X - 0.5, 1, 1], np.float32)) is None
+
+
+def test_init_gaussian_statistics(orc):
+    """The proposal-seeded cloud: bounded Irwin-Hall draws (|eps| <= 2 sqrt 3)
+    of unit variance around the mean, clamped to the limits."""
+    N = 20000
+    lim = np.array([0.5, 0.5, 0.5, 20, 20, 20], np.float32)
+    mean = np.array([0.1, -0.2, 0.05, 3.0, -4.0, 1.0], np.float32)
+    std = np.array([0.02, 0.03, 0.01, 1.0, 2.0, 0.5], np.float32)
+    x = orc.init_gaussian(N, 7, mean, std, lim)
+    eps = (x.astype(np.float64) - mean[:, None]) / std[:, None]
+    assert np.all(np.abs(eps) <= 2 * np.sqrt(3) + 1e-4)
+    assert np.allclose(eps.mean(1), 0.0, atol=0.03)
+    assert np.allclose(eps.std(1), 1.0, atol=0.03)
+    assert np.array_equal(x, orc.init_gaussian(N, 7, mean, std, lim))
+    assert not np.array_equal(x, orc.init_gaussian(N, 8, mean, std, lim))
+    # clamping: a mean outside the limits puts every particle on the limit
+    far = mean.copy()
+    far[3] = 40.0
+    assert np.all(orc.init_gaussian(100, 7, far, std, lim)[3] == 20.0)
