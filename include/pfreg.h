@@ -88,6 +88,10 @@ typedef struct {
                                  the masks validate image-based registration after each
                                  iteration); needs both masks, also in image mode */
     int32_t estimator;        /* pf_estimator: how the estimate's rotation is averaged */
+    int32_t autotune;         /* 1: pick the measurement's tile shape (work items per warp)
+                                 by timing the candidates on the initial cloud at creation,
+                                 cached per (mode, dims, N) for the process; results are
+                                 identical for every shape.  0: the default shape */
 } pf_config;
 
 /* Estimate of an iteration (Fig. 1 "estimation"), from the measured cloud
@@ -103,7 +107,7 @@ typedef enum { PF_EST_MEAN = 0, PF_EST_QUATERNION = 1 } pf_estimator;
 
 /* Fill cfg with the defaults: PF_MASK_DICE, N = 256, limits 15 deg / 8 voxels,
  * sigma0_frac 0.25, sigma_decay 0.8, gamma_log2 5, seed 0,
- * min_overlap_frac 0.01, trace_estimate 0, estimator PF_EST_MEAN. */
+ * min_overlap_frac 0.01, trace_estimate 0, estimator PF_EST_MEAN, autotune 0. */
 void pf_config_default(pf_config *cfg);
 
 /* Create a registration context (Sec. 3.1 problem statement: source and target
@@ -183,6 +187,11 @@ int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32
  * devices or streams, negative count), PF_ENOMEM, PF_ECUDA. */
 typedef struct pf_batch pf_batch;
 int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_t *n_iters);
+/* When every member was created with autotune = 1 and none has run yet,
+ * pf_batch_create also picks the tile shape of the batch's measurement
+ * launches by timing the candidates on the members' initial clouds.
+ * pf_batch_tile_shape reports it (work items per warp). */
+int pf_batch_tile_shape(pf_batch *b, int32_t *items_per_warp);
 /* Launch n_iters batch iterations (asynchronous on the contexts' stream). */
 int pf_batch_step(pf_batch *b, int32_t n_iters);
 /* Launch as many batch iterations as the longest remaining registration needs. */
@@ -280,6 +289,10 @@ int pf_measure_matrices_noalloc(pf_ctx *ctx, const float *mats, int32_t M, const
 int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float src_origin[3],
                    const float src_spacing[3], const float tgt_origin[3], const float tgt_spacing[3],
                    float mat_out[12], float a_out[3]);
+
+/* The measurement's tile shape: target rows per work item (one warp's rows)
+ * and consecutive work items per warp (the autotuned parameter). */
+int pf_tile_shape(pf_ctx *ctx, int32_t *rows_per_item, int32_t *items_per_warp);
 
 /* Philox4x32-10 of (ctr, key) computed on the device (tests of the generator). */
 int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

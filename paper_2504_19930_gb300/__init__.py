@@ -53,7 +53,8 @@ class pf_config(C.Structure):
     _fields_ = [("mode", C.c_int32), ("n_particles", C.c_int32), ("rot_limit", C.c_float * 3),
                 ("trans_limit", C.c_float * 3), ("sigma0_frac", C.c_float),
                 ("sigma_decay", C.c_float), ("gamma_log2", C.c_int32), ("seed", C.c_uint64),
-                ("min_overlap_frac", C.c_float), ("trace_estimate", C.c_int32), ("estimator", C.c_int32)]
+                ("min_overlap_frac", C.c_float), ("trace_estimate", C.c_int32), ("estimator", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -120,6 +121,8 @@ def _declare(L):
     L.pf_nn_conv3d_backward_weights.argtypes = [vp, i32, i32, i32, vp, vp, vp]
     L.pf_nn_status.argtypes = [i32, vp]
     L.pf_seed_gaussian.argtypes = [vp, vp, vp]
+    L.pf_tile_shape.argtypes = [vp, vp, vp]
+    L.pf_batch_tile_shape.argtypes = [vp, vp]
     L.pf_proposal_create.argtypes = [C.POINTER(vp), i32, u64, vp]
     L.pf_proposal_destroy.argtypes = [vp]
     L.pf_proposal_train.argtypes = [vp, i32, i32, C.c_float, u64, vp, C.c_float, C.c_float, vp]
@@ -132,7 +135,8 @@ def _declare(L):
     for name in ("pf_nn_gemm_bf16", "pf_nn_conv3d_forward", "pf_nn_conv3d_backward_data",
                  "pf_nn_conv3d_backward_weights", "pf_nn_status", "pf_seed_gaussian", "pf_proposal_create",
                  "pf_proposal_destroy", "pf_proposal_train", "pf_proposal_predict", "pf_proposal_params",
-                 "pf_proposal_forward", "pf_proposal_backward", "pf_proposal_synth", "pf_proposal_input"):
+                 "pf_proposal_forward", "pf_proposal_backward", "pf_proposal_synth", "pf_proposal_input",
+                 "pf_tile_shape", "pf_batch_tile_shape"):
         getattr(L, name).restype = C.c_int
     for name in ("pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy", "warp_sequence",
                  "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
@@ -212,7 +216,7 @@ ESTIMATORS = {"mean": 0, "quaternion": 1}
 
 def make_config(mode="mask_dice", n_particles=256, rot_limit=0.2617994, trans_limit=8.0,
                 sigma0_frac=0.25, sigma_decay=0.8, gamma_log2=5, seed=0, min_overlap_frac=0.01,
-                trace_estimate=False, estimator="mean"):
+                trace_estimate=False, estimator="mean", autotune=False):
     cfg = pf_config_default()
     cfg.mode = MODES.get(mode, mode)
     cfg.n_particles = int(n_particles)
@@ -225,6 +229,7 @@ def make_config(mode="mask_dice", n_particles=256, rot_limit=0.2617994, trans_li
     cfg.min_overlap_frac = float(min_overlap_frac)
     cfg.trace_estimate = int(bool(trace_estimate))
     cfg.estimator = ESTIMATORS.get(estimator, estimator)
+    cfg.autotune = int(bool(autotune))
     return cfg
 
 
@@ -410,6 +415,12 @@ class Registration:
         pf_step(self.ctx, n_iters)
         return self
 
+    def tile_shape(self):
+        """(rows per work item, work items per warp) of the measurement."""
+        r, i = C.c_int32(0), C.c_int32(0)
+        _check(load().pf_tile_shape(self.ctx, C.byref(r), C.byref(i)))
+        return r.value, i.value
+
     def seed_gaussian(self, mean, std):
         """Seed the cloud around a proposal (before the first step)."""
         m, sd = _np(mean, np.float32), _np(std, np.float32)
@@ -545,6 +556,12 @@ class Batch:
     def run(self):
         pf_batch_run(self.handle)
         return self
+
+    def tile_shape(self):
+        """Work items per warp of the batch's measurement launches."""
+        i = C.c_int32(0)
+        _check(load().pf_batch_tile_shape(self.handle, C.byref(i)))
+        return i.value
 
     def step(self, n_iters=1):
         pf_batch_step(self.handle, n_iters)

@@ -11,6 +11,7 @@
 #include <vector>
 #include <algorithm>
 #include <map>
+#include <mutex>
 
 #include "../../include/pfreg.h"
 #include "kernels.h"
@@ -96,6 +97,7 @@ int check_config(const pf_config *c) {
         return fail(PF_EINVAL, "min_overlap_frac outside [0, 1]");
     if (c->estimator != PF_EST_MEAN && c->estimator != PF_EST_QUATERNION)
         return fail(PF_EINVAL, "estimator %d unknown", c->estimator);
+    if (c->autotune != 0 && c->autotune != 1) return fail(PF_EINVAL, "autotune must be 0 or 1");
     return PF_OK;
 }
 
@@ -252,6 +254,87 @@ int build_graph(pf_ctx *c) {
     }
     if (!c->node_before || !c->node_after) return fail(PF_ECUDA, "timing nodes not found in the graph");
     CU(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the measurement's tile shape (work items per warp).  Every
+// candidate gives the same moments bit for bit (integer atomics), so the
+// choice only moves time: each candidate measures the context's current
+// cloud (one warm-up and two timed launches, CUDA events) and the fastest
+// wins.  Results are cached per (mode, source dims, target dims, N) for the
+// process, so contexts of a repeated shape pay the search once.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+
+std::string tune_key(const pf_ctx *c) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "%d%d|%d,%d,%d|%d,%d,%d|%d", (int)c->img, (int)c->mask, c->MA.g.sd[0], c->MA.g.sd[1],
+             c->MA.g.sd[2], c->MA.g.td[0], c->MA.g.td[1], c->MA.g.td[2], c->P.N);
+    return buf;
+}
+
+// Time `launch(ipw)` for every candidate; returns the fastest (ms in *best_ms).
+template <class F>
+int time_candidates(cudaStream_t s, F launch, int *best, float *best_ms) {
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    *best = kDefaultItemsPerWarp;
+    *best_ms = 1e30f;
+    int rc = PF_OK;
+    for (int cand : kTileCandidates) {
+        cudaError_t e = launch(cand);   // warm-up
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) e = launch(cand);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && ms < tmin) tmin = ms;
+        }
+        if (e != cudaSuccess) {
+            rc = fail(PF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (tmin < *best_ms) {
+            *best_ms = tmin;
+            *best = cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+// Pick the context's tile shape (iteration 0: the prediction only builds the
+// matrices of the initial cloud and zeroes the moments, so it can run here).
+int autotune_ctx(pf_ctx *c) {
+    const std::string key = tune_key(c);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c->MA.items_per_warp = it->second;
+            return PF_OK;
+        }
+    }
+    CU(launch_predict(c->P, c->B, c->stream));
+    int best = kDefaultItemsPerWarp;
+    float ms = 0.0f;
+    int rc = time_candidates(c->stream, [&](int ipw) {
+        MeasureArgs ma = c->MA;
+        ma.items_per_warp = ipw;
+        return launch_measure(ma, c->img, c->mask, c->stream);
+    }, &best, &ms);
+    if (rc) return rc;
+    CU(cudaMemsetAsync(c->B.mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)c->P.N, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->MA.items_per_warp = best;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
     return PF_OK;
 }
 
@@ -444,11 +527,16 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     MA.P = N;
     MA.rows_per_item = rows_per_item_for(g.td[0]);
     MA.n_rowblocks = (g.td[1] * g.td[2] + MA.rows_per_item - 1) / MA.rows_per_item;
+    MA.items_per_warp = kDefaultItemsPerWarp;
 
     CK(cudaMemsetAsync(B.k, 0, sizeof(int32_t), c->stream));
     CK(cudaMemsetAsync(B.mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)N, c->stream));
     CK(launch_init_particles(P, B, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (cfg->autotune) {
+        rc = autotune_ctx(c);
+        if (rc) return bail(rc);
+    }
     rc = build_graph(c);
     if (rc) return bail(rc);
 #undef CK
@@ -783,6 +871,7 @@ struct pf_batch {
     std::vector<int32_t> list_h[3];            // members of each list (batch positions)
     std::vector<long long> offs_h[3], poffs_h, poffs32_h;
     std::map<int, cudaGraphExec_t> phase;      // graph per number of active members
+    int ipw = kDefaultItemsPerWarp;            // tile shape of the measurement launches
     ~pf_batch() {
         for (auto &kv : phase) cudaGraphExecDestroy(kv.second);
         for (cudaStream_t s : {cap, side[0], side[1]})
@@ -823,11 +912,12 @@ int batch_phase_graph(pf_batch *b, int active, cudaGraphExec_t *out) {
         es[1] = cudaEventRecord(b->fork, b->cap);
         es[2] = cudaStreamWaitEvent(b->side[0], b->fork, 0);
         es[3] = cudaStreamWaitEvent(b->side[1], b->fork, 0);
-        es[4] = launch_measure_batch(b->regs, b->lptr[0], b->optr[0], nl[0], b->offs_h[0][nl[0]], true, false, b->cap);
+        es[4] = launch_measure_batch(b->regs, b->lptr[0], b->optr[0], nl[0], b->offs_h[0][nl[0]], true, false,
+                                     b->ipw, b->cap);
         es[5] = launch_measure_batch(b->regs, b->lptr[1], b->optr[1], nl[1], b->offs_h[1][nl[1]], false, true,
-                                     b->side[0]);
+                                     b->ipw, b->side[0]);
         es[6] = launch_measure_batch(b->regs, b->lptr[2], b->optr[2], nl[2], b->offs_h[2][nl[2]], true, true,
-                                     b->side[1]);
+                                     b->ipw, b->side[1]);
         es[7] = cudaEventRecord(b->join[0], b->side[0]);
         es[8] = cudaEventRecord(b->join[1], b->side[1]);
         es[9] = cudaStreamWaitEvent(b->cap, b->join[0], 0);
@@ -942,7 +1032,56 @@ int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_
     BK(cudaEventCreateWithFlags(&b->join[0], cudaEventDisableTiming));
     BK(cudaEventCreateWithFlags(&b->join[1], cudaEventDisableTiming));
 #undef BK
+    // Tile shape of the batch's measurement launches: tuned when every member
+    // asked for it and none has run yet (the members' iteration-0 prediction
+    // is repeatable, so the search can measure the real clouds).
+    bool tune = true;
+    for (int32_t r = 0; r < n; ++r) {
+        int32_t k = 0;
+        int rc = pf_get_iteration(ctxs[r], &k);
+        if (rc) return bail(rc);
+        tune = tune && ctxs[r]->cfg.autotune && k == 0;
+    }
+    if (tune) {
+        for (pf_ctx *c : b->ctxs) {
+            cudaError_t e = launch_predict(c->P, c->B, b->stream);
+            if (e != cudaSuccess) return bail(fail(PF_ECUDA, "autotune: %s", cudaGetErrorString(e)));
+        }
+        int best = kDefaultItemsPerWarp;
+        float ms = 0.0f;
+        int rc = time_candidates(b->stream, [&](int ipw) {
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+                const int nk = (int)b->list_h[k].size();
+                e = launch_measure_batch(b->regs, b->lptr[k], b->optr[k], nk, b->offs_h[k][nk], k != 1, k != 0, ipw,
+                                         b->stream);
+            }
+            return e;
+        }, &best, &ms);
+        if (rc) return bail(rc);
+        for (pf_ctx *c : b->ctxs) {
+            cudaError_t e = cudaMemsetAsync(c->B.mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)c->P.N,
+                                            b->stream);
+            if (e != cudaSuccess) return bail(fail(PF_ECUDA, "autotune: %s", cudaGetErrorString(e)));
+        }
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bail(fail(PF_ECUDA, "autotune: %s", cudaGetErrorString(e)));
+        b->ipw = best;
+    }
     *out = b;
+    return PF_OK;
+}
+
+int pf_batch_tile_shape(pf_batch *b, int32_t *items_per_warp) {
+    if (!b || !items_per_warp) return fail(PF_EINVAL, "NULL argument");
+    *items_per_warp = b->ipw;
+    return PF_OK;
+}
+
+int pf_tile_shape(pf_ctx *c, int32_t *rows_per_item, int32_t *items_per_warp) {
+    if (!c) return fail(PF_EINVAL, "ctx is NULL");
+    if (rows_per_item) *rows_per_item = c->MA.rows_per_item;
+    if (items_per_warp) *items_per_warp = c->MA.items_per_warp;
     return PF_OK;
 }
 

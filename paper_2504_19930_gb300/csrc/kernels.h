@@ -23,6 +23,7 @@ struct MeasureArgs {
     int P;
     int rows_per_item;          // target rows per work item
     int n_rowblocks;            // ceil(rows / rows_per_item)
+    int items_per_warp;         // tile shape: consecutive work items per warp (0 = default)
 };
 
 // Filter parameters shared by the per-iteration kernels.
@@ -116,7 +117,10 @@ struct BatchReg {
 // one CTA per registration.
 // Registrations whose iteration counter has reached n_iters are skipped.
 cudaError_t launch_measure_batch(const BatchReg *regs, const int32_t *list, const long long *offs, int nlist,
-                                 long long total_items, bool img, bool mask, cudaStream_t s);
+                                 long long total_items, bool img, bool mask, int items_per_warp, cudaStream_t s);
+constexpr int kDefaultItemsPerWarp = 8;
+// Candidate tile shapes (work items per warp) of the autotuner.
+constexpr int kTileCandidates[] = {1, 2, 4, 8, 16, 32};
 cudaError_t launch_predict_batch(const BatchReg *regs, const long long *poffs, int nregs, long long total,
                                  cudaStream_t s);
 cudaError_t launch_finalise_batch(const BatchReg *regs, const long long *poffs32, int nregs, long long total32,

@@ -260,7 +260,10 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
 }
 
 constexpr int kRowsPerWarp = 32;
-constexpr int kItemsPerWarp = 8;   // consecutive items: one particle, adjacent row blocks
+// consecutive items per warp (one particle, adjacent row blocks): the tile
+// shape the autotuner picks; this is the default
+constexpr int kItemsPerWarp = kDefaultItemsPerWarp;
+__host__ __device__ __forceinline__ int ipw_of(int v) { return v > 0 ? v : kItemsPerWarp; }
 
 // Coordinate q_d(x) of target voxel x of a row (fixed order, no FMA).
 __device__ __forceinline__ float coord1(float r, float K, float a0, int x) {
@@ -597,8 +600,9 @@ __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_
     const int rows = a.g.td[1] * a.g.td[2];
     const int nblocks = (rows + kRowsPerWarp - 1) / kRowsPerWarp;
     const long long items = (long long)a.P * nblocks;
-    const long long item0 = ((long long)blockIdx.x * kWarps + warp) * kItemsPerWarp;
-    const long long item1 = min(items, item0 + kItemsPerWarp);
+    const int ipw = ipw_of(a.items_per_warp);
+    const long long item0 = ((long long)blockIdx.x * kWarps + warp) * ipw;
+    const long long item1 = min(items, item0 + ipw);
     int tab_p = -1;
     for (long long item = item0; item < item1; ++item) {
         if (XTAB) {
@@ -628,11 +632,12 @@ __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_
 template <bool IMG, bool MASK>
 __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batch(const BatchReg *__restrict__ regs,
                                                             const int32_t *__restrict__ list,
-                                                            const long long *__restrict__ offs, int nlist) {
+                                                            const long long *__restrict__ offs, int nlist,
+                                                            int ipw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long total = offs[nlist];
-    const long long item0 = ((long long)blockIdx.x * kWarps + warp) * kItemsPerWarp;
-    const long long item1 = min(total, item0 + kItemsPerWarp);
+    const long long item0 = ((long long)blockIdx.x * kWarps + warp) * ipw;
+    const long long item1 = min(total, item0 + ipw);
     for (long long item = item0; item < item1; ++item) {
         int lo = 0, hi = nlist - 1;                  // last r with offs[r] <= item
         while (lo < hi) {
@@ -654,7 +659,7 @@ cudaError_t launch_variant(const MeasureArgs &a, size_t smem, cudaStream_t s) {
     }
     const int rows = a.g.td[1] * a.g.td[2];
     const long long items = (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
-    const long long per_cta = (long long)kWarps * kItemsPerWarp;
+    const long long per_cta = (long long)kWarps * ipw_of(a.items_per_warp);
     long long grid = (items + per_cta - 1) / per_cta;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, kThreads, smem, s>>>(a);
@@ -695,13 +700,14 @@ cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_
 }
 
 cudaError_t launch_measure_batch(const BatchReg *regs, const int32_t *list, const long long *offs, int nlist,
-                                 long long total_items, bool img, bool mask, cudaStream_t s) {
+                                 long long total_items, bool img, bool mask, int items_per_warp, cudaStream_t s) {
     if (nlist <= 0 || total_items <= 0) return cudaSuccess;
-    const long long per_cta = (long long)kWarps * kItemsPerWarp;
+    const int ipw = ipw_of(items_per_warp);
+    const long long per_cta = (long long)kWarps * ipw;
     const unsigned grid = (unsigned)((total_items + per_cta - 1) / per_cta);
-    if (img && mask) k_measure_batch<true, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist);
-    else if (img) k_measure_batch<true, false><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist);
-    else k_measure_batch<false, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist);
+    if (img && mask) k_measure_batch<true, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist, ipw);
+    else if (img) k_measure_batch<true, false><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist, ipw);
+    else k_measure_batch<false, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist, ipw);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -66,7 +66,7 @@ def _init_rc(pk, cfg, vols):
 
 @pytest.mark.parametrize("field,value", [
     ("n_particles", 0), ("n_particles", 65537), ("mode", 7), ("gamma_log2", 11),
-    ("sigma0_frac", 0.0), ("sigma_decay", 1.5), ("min_overlap_frac", -0.1)])
+    ("sigma0_frac", 0.0), ("sigma_decay", 1.5), ("min_overlap_frac", -0.1), ("autotune", 2)])
 def test_invalid_config_is_rejected(pk, field, value):
     cfg = pk.make_config("mask_dice")
     setattr(cfg, field, value)

@@ -44,14 +44,14 @@ def _members():
     ]
 
 
-def _make(pk, mode, pair, N, seed):
+def _make(pk, mode, pair, N, seed, **cfg):
     vols = {}
     if mode in ("image_ncc", "combined"):
         vols.update(src=_cuda(pair.src), tgt=_cuda(pair.tgt))
     if mode != "image_ncc":
         vols.update(src_mask=_cuda(pair.src_mask), tgt_mask=_cuda(pair.tgt_mask))
     return pk.Registration(mode, src_origin=pair.src_origin, tgt_origin=pair.tgt_origin, n_particles=N,
-                           rot_limit=0.2, trans_limit=3.0, seed=seed, **vols)
+                           rot_limit=0.2, trans_limit=3.0, seed=seed, **vols, **cfg)
 
 
 def _snapshot(reg):
@@ -117,3 +117,32 @@ def test_batch_rejects_bad_membership(pk):
     with pytest.raises(pk.PfError):
         pk.pf_batch_create([r.ctx], [-1])
     r.close()
+
+
+CANDIDATES = (1, 2, 4, 8, 16, 32)
+
+
+def test_autotuned_tile_shape_changes_no_result(pk):
+    """The autotuner only picks how work items are spread over warps; every
+    registration and every batch member gives the same bits as with the
+    default tile shape."""
+    members = _members()
+    singles = []
+    for mode, pair, N, K, seed in members:
+        with _make(pk, mode, pair, N, seed) as r:
+            assert r.tile_shape() == (32, 8)
+            r.step(K)
+            singles.append(_snapshot(r))
+    for i, (mode, pair, N, K, seed) in enumerate(members):
+        with _make(pk, mode, pair, N, seed, autotune=True) as r:
+            assert r.tile_shape()[1] in CANDIDATES
+            assert r.iteration == 0 and not r.state()["moments"].any()
+            r.step(K)
+            _assert_same(_snapshot(r), singles[i], f"tuned member {i}")
+    regs = [_make(pk, mode, pair, N, seed, autotune=True) for mode, pair, N, K, seed in members]
+    with pk.Batch(regs, [m[3] for m in members]) as b:
+        assert b.tile_shape() in CANDIDATES
+        b.run()
+    for i, r in enumerate(regs):
+        _assert_same(_snapshot(r), singles[i], f"tuned batch member {i} ({members[i][0]})")
+        r.close()
