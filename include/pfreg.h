@@ -290,6 +290,12 @@ int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float s
                    const float src_spacing[3], const float tgt_origin[3], const float tgt_spacing[3],
                    float mat_out[12], float a_out[3]);
 
+/* Host-side fault injection for tests (no counterpart in the paper): cap the
+ * device bytes any context created afterwards may allocate (0 = no cap);
+ * pf_register_init then fails with PF_ENOMEM, releasing what it allocated.
+ * Process-wide.  Errors: PF_EINVAL (bytes < 0). */
+int pf_debug_alloc_limit(int64_t bytes);
+
 /* The measurement's tile shape: target rows per work item (one warp's rows)
  * and consecutive work items per warp (the autotuned parameter). */
 int pf_tile_shape(pf_ctx *ctx, int32_t *rows_per_item, int32_t *items_per_warp);
@@ -315,8 +321,8 @@ int pf_profile_end(pf_ctx *ctx, double *total_ms, int32_t *n_timed);
  * (kz*4 + ky)*4 + kx.  The contractions run on the tcgen05 tensor cores with
  * fp32 accumulation.  All pointers are device pointers; calls are asynchronous
  * on `stream` (a cudaStream_t) and allocate nothing.
- * Errors: PF_EINVAL (NULL, D odd or outside [2, 512], Cin not 2 or a multiple
- * of 8 up to 256, sizes beyond int32 indexing), PF_ECUDA. */
+ * Errors: PF_EINVAL (NULL, D odd or outside [2, 512], Cin not one of 2, 8, 16,
+ * 32, 64, 128, 256, sizes beyond int32 indexing), PF_ECUDA. */
 
 /* C[M][32] (fp32) = A[M][K] B[32][K]^T, A and B row-major bf16, K % 8 == 0. */
 int pf_nn_gemm_bf16(const uint16_t *A, const uint16_t *B, float *C, int32_t M, int32_t K, void *stream);
@@ -346,6 +352,13 @@ int pf_nn_conv3d_backward_weights(const uint16_t *x, int32_t batch, int32_t D, i
  * out since the last clear (its tile was then not written); clear != 0
  * resets the flag.  Synchronous. */
 int pf_nn_status(int32_t clear, int32_t *gave_up);
+
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * thread that waits on an mbarrier nothing arrives on, with the same kind of
+ * bounded wait the tensor-core kernels use (2^16 polls); when the wait runs
+ * out it sets the flag pf_nn_status reports.  Nothing faults or hangs: the
+ * kernel returns and the context stays usable.  Asynchronous on `stream`. */
+int pf_nn_wait_selftest(void *stream);
 
 /* ---- learned proposal network ----
  *

@@ -122,6 +122,8 @@ def _declare(L):
     L.pf_nn_status.argtypes = [i32, vp]
     L.pf_seed_gaussian.argtypes = [vp, vp, vp]
     L.pf_tile_shape.argtypes = [vp, vp, vp]
+    L.pf_debug_alloc_limit.argtypes = [C.c_int64]
+    L.pf_nn_wait_selftest.argtypes = [vp]
     L.pf_batch_tile_shape.argtypes = [vp, vp]
     L.pf_proposal_create.argtypes = [C.POINTER(vp), i32, u64, vp]
     L.pf_proposal_destroy.argtypes = [vp]
@@ -136,7 +138,7 @@ def _declare(L):
                  "pf_nn_conv3d_backward_weights", "pf_nn_status", "pf_seed_gaussian", "pf_proposal_create",
                  "pf_proposal_destroy", "pf_proposal_train", "pf_proposal_predict", "pf_proposal_params",
                  "pf_proposal_forward", "pf_proposal_backward", "pf_proposal_synth", "pf_proposal_input",
-                 "pf_tile_shape", "pf_batch_tile_shape"):
+                 "pf_tile_shape", "pf_batch_tile_shape", "pf_debug_alloc_limit", "pf_nn_wait_selftest"):
         getattr(L, name).restype = C.c_int
     for name in ("pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy", "warp_sequence",
                  "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
@@ -712,3 +714,13 @@ class Proposal:
             self.close()
         except Exception:
             pass
+
+
+def pf_debug_alloc_limit(nbytes):
+    """Cap the device bytes a context may allocate (0 = no cap); test fault injection."""
+    _check(load().pf_debug_alloc_limit(int(nbytes)))
+
+
+def nn_wait_selftest(stream=None):
+    """Run the bounded-wait self-test kernel (sets the nn_status flag)."""
+    _check(load().pf_nn_wait_selftest(_stream_handle(stream)))

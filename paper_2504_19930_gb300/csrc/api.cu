@@ -11,6 +11,7 @@
 #include <vector>
 #include <algorithm>
 #include <map>
+#include <atomic>
 #include <mutex>
 
 #include "../../include/pfreg.h"
@@ -129,6 +130,11 @@ namespace pfreg {
 bool capturing() { return g_capturing; }
 }  // namespace pfreg
 
+// Host-side fault injection: a cap on the device bytes one context may
+// allocate (pf_debug_alloc_limit); beyond it the allocation reports
+// cudaErrorMemoryAllocation without calling cudaMalloc.  0 = no cap.
+static std::atomic<long long> g_alloc_limit{0};
+
 struct pf_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -158,12 +164,18 @@ struct pf_ctx {
     int x_cap = 0;
     std::vector<void *> allocs;
 
+    long long alloc_bytes = 0;
+
     template <class T>
     cudaError_t alloc(T **p, size_t count) {
+        const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 1;
+        const long long cap = g_alloc_limit.load();
+        if (cap > 0 && alloc_bytes + (long long)bytes > cap) return cudaErrorMemoryAllocation;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+        cudaError_t e = cudaMalloc(&q, bytes);
         if (e == cudaSuccess) {
             allocs.push_back(q);
+            alloc_bytes += (long long)bytes;
             *p = static_cast<T *>(q);
         }
         return e;
@@ -872,6 +884,7 @@ struct pf_batch {
     std::vector<long long> offs_h[3], poffs_h, poffs32_h;
     std::map<int, cudaGraphExec_t> phase;      // graph per number of active members
     int ipw = kDefaultItemsPerWarp;            // tile shape of the measurement launches
+    int max_tx[3] = {0, 0, 0};                 // longest target row of each list
     ~pf_batch() {
         for (auto &kv : phase) cudaGraphExecDestroy(kv.second);
         for (cudaStream_t s : {cap, side[0], side[1]})
@@ -913,11 +926,11 @@ int batch_phase_graph(pf_batch *b, int active, cudaGraphExec_t *out) {
         es[2] = cudaStreamWaitEvent(b->side[0], b->fork, 0);
         es[3] = cudaStreamWaitEvent(b->side[1], b->fork, 0);
         es[4] = launch_measure_batch(b->regs, b->lptr[0], b->optr[0], nl[0], b->offs_h[0][nl[0]], true, false,
-                                     b->ipw, b->cap);
+                                     b->ipw, b->max_tx[0], b->cap);
         es[5] = launch_measure_batch(b->regs, b->lptr[1], b->optr[1], nl[1], b->offs_h[1][nl[1]], false, true,
-                                     b->ipw, b->side[0]);
+                                     b->ipw, b->max_tx[1], b->side[0]);
         es[6] = launch_measure_batch(b->regs, b->lptr[2], b->optr[2], nl[2], b->offs_h[2][nl[2]], true, true,
-                                     b->ipw, b->side[1]);
+                                     b->ipw, b->max_tx[2], b->side[1]);
         es[7] = cudaEventRecord(b->join[0], b->side[0]);
         es[8] = cudaEventRecord(b->join[1], b->side[1]);
         es[9] = cudaStreamWaitEvent(b->cap, b->join[0], 0);
@@ -1001,6 +1014,7 @@ int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_
         regs[pos].mask = c->mask;
         const int kind = (c->img && c->mask) ? 2 : (c->img ? 0 : 1);
         b->list_h[kind].push_back(pos);
+        b->max_tx[kind] = std::max(b->max_tx[kind], (int)c->MA.g.td[0]);
         b->offs_h[kind].push_back(b->offs_h[kind].back() + measure_items(c->MA));
         b->poffs_h.push_back(b->poffs_h.back() + c->P.N);
         b->poffs32_h.push_back(b->poffs32_h.back() + (c->P.N + 31) / 32 * 32);
@@ -1054,7 +1068,7 @@ int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_
             for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
                 const int nk = (int)b->list_h[k].size();
                 e = launch_measure_batch(b->regs, b->lptr[k], b->optr[k], nk, b->offs_h[k][nk], k != 1, k != 0, ipw,
-                                         b->stream);
+                                         b->max_tx[k], b->stream);
             }
             return e;
         }, &best, &ms);
@@ -1075,6 +1089,12 @@ int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_
 int pf_batch_tile_shape(pf_batch *b, int32_t *items_per_warp) {
     if (!b || !items_per_warp) return fail(PF_EINVAL, "NULL argument");
     *items_per_warp = b->ipw;
+    return PF_OK;
+}
+
+int pf_debug_alloc_limit(int64_t bytes) {
+    if (bytes < 0) return fail(PF_EINVAL, "bytes < 0");
+    g_alloc_limit.store(bytes);
     return PF_OK;
 }
 

@@ -117,7 +117,8 @@ struct BatchReg {
 // one CTA per registration.
 // Registrations whose iteration counter has reached n_iters are skipped.
 cudaError_t launch_measure_batch(const BatchReg *regs, const int32_t *list, const long long *offs, int nlist,
-                                 long long total_items, bool img, bool mask, int items_per_warp, cudaStream_t s);
+                                 long long total_items, bool img, bool mask, int items_per_warp, int max_tx,
+                                 cudaStream_t s);
 constexpr int kDefaultItemsPerWarp = 8;
 // Candidate tile shapes (work items per warp) of the autotuner.
 constexpr int kTileCandidates[] = {1, 2, 4, 8, 16, 32};

@@ -581,6 +581,9 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
 // current particle in shared memory (X float4 per warp, X <= kTabMaxX), in
 // front of the optional mask bits.
 constexpr int kTabMaxX = 512;
+#ifndef PF_MEASURE_XTAB
+#define PF_MEASURE_XTAB 1
+#endif
 template <bool IMG, bool MASK, bool MASK_SMEM, bool FIDX, bool XTAB>
 __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_COMBINED
                                                         : (IMG ? PF_MEASURE_MIN_BLOCKS_IMG : 4))
@@ -627,17 +630,27 @@ __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_
 // Measurement of many registrations in one launch: the items of the listed
 // registrations are concatenated (offs = prefix of their item counts); each
 // item finds its registration by binary search, and registrations that have
-// run all their iterations are skipped.
+// run all their iterations are skipped.  With tab_x > 0 (every listed
+// registration's target rows are at most tab_x <= kTabMaxX long) each warp
+// keeps the x-product table of its current (registration, particle) in
+// shared memory, as the single-registration kernel does; image sources of at
+// most 2^23 voxels take the fp32 quad index.  Each warp copies its current
+// registration's measurement arguments into shared memory, so the sweep
+// reads them there rather than from the global registration table.
 // (The registration lookup costs registers: tighter bounds than these spill.)
 template <bool IMG, bool MASK>
 __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batch(const BatchReg *__restrict__ regs,
                                                             const int32_t *__restrict__ list,
                                                             const long long *__restrict__ offs, int nlist,
-                                                            int ipw) {
+                                                            int ipw, int tab_x) {
+    extern __shared__ float4 smem_dyn[];
+    __shared__ MeasureArgs sma[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *tab = tab_x > 0 ? smem_dyn + (size_t)warp * tab_x : nullptr;
     const long long total = offs[nlist];
     const long long item0 = ((long long)blockIdx.x * kWarps + warp) * ipw;
     const long long item1 = min(total, item0 + ipw);
+    int tab_r = -1, tab_p = -1, arg_r = -1;
     for (long long item = item0; item < item1; ++item) {
         int lo = 0, hi = nlist - 1;                  // last r with offs[r] <= item
         while (lo < hi) {
@@ -646,7 +659,39 @@ __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batc
         }
         const BatchReg &R = regs[list[lo]];
         if (*R.B.k >= R.n_iters) continue;          // warp-uniform
-        measure_item<IMG, MASK, false, false>(R.ma, R.ma.src_bits, nullptr, item - offs[lo], lane);
+        if (lo != arg_r) {
+            const int *src = reinterpret_cast<const int *>(&R.ma);
+            int *dst = reinterpret_cast<int *>(&sma[warp]);
+            __syncwarp();
+            for (int i = lane; i < (int)(sizeof(MeasureArgs) / sizeof(int)); i += 32) dst[i] = src[i];
+            __syncwarp();
+            arg_r = lo;
+        }
+        const MeasureArgs &A = sma[warp];
+        const long long local = item - offs[lo];
+        const bool fidx = IMG && (size_t)A.g.sd[0] * A.g.sd[1] * A.g.sd[2] <= ((size_t)1 << 23);
+        if (tab) {
+            const int rows = A.g.td[1] * A.g.td[2];
+            const int p = (int)(local / ((rows + kRowsPerWarp - 1) / kRowsPerWarp));   // warp-uniform
+            if (lo != tab_r || p != tab_p) {
+                const float *Mp = A.mats + 12 * (size_t)p;
+                const float r0 = __ldg(Mp + 0), r1 = __ldg(Mp + 4), r2 = __ldg(Mp + 8);
+                const float a0 = A.g.a[0];
+                __syncwarp();
+                for (int x = lane; x < A.g.td[0]; x += 32) {
+                    const float dx = __fsub_rn((float)x, a0);
+                    tab[x] = make_float4(__fmul_rn(r0, dx), __fmul_rn(r1, dx), __fmul_rn(r2, dx), 0.0f);
+                }
+                __syncwarp();
+                tab_r = lo;
+                tab_p = p;
+            }
+            if (fidx) measure_item<IMG, MASK, true, true>(A, A.src_bits, tab, local, lane);
+            else measure_item<IMG, MASK, false, true>(A, A.src_bits, tab, local, lane);
+        } else {
+            if (fidx) measure_item<IMG, MASK, true, false>(A, A.src_bits, nullptr, local, lane);
+            else measure_item<IMG, MASK, false, false>(A, A.src_bits, nullptr, local, lane);
+        }
     }
 }
 
@@ -700,14 +745,20 @@ cudaError_t launch_pack_quads(const uint8_t *src, const int32_t dims[3], uint32_
 }
 
 cudaError_t launch_measure_batch(const BatchReg *regs, const int32_t *list, const long long *offs, int nlist,
-                                 long long total_items, bool img, bool mask, int items_per_warp, cudaStream_t s) {
+                                 long long total_items, bool img, bool mask, int items_per_warp, int max_tx,
+                                 cudaStream_t s) {
     if (nlist <= 0 || total_items <= 0) return cudaSuccess;
     const int ipw = ipw_of(items_per_warp);
     const long long per_cta = (long long)kWarps * ipw;
     const unsigned grid = (unsigned)((total_items + per_cta - 1) / per_cta);
-    if (img && mask) k_measure_batch<true, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist, ipw);
-    else if (img) k_measure_batch<true, false><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist, ipw);
-    else k_measure_batch<false, true><<<grid, kThreads, 0, s>>>(regs, list, offs, nlist, ipw);
+    const int tab_x = (PF_MEASURE_XTAB && max_tx > 0 && max_tx <= kTabMaxX) ? max_tx : 0;
+    const size_t smem = (size_t)kWarps * tab_x * sizeof(float4);
+    auto kern = img && mask ? k_measure_batch<true, true> : (img ? k_measure_batch<true, false> : k_measure_batch<false, true>);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kThreads, smem, s>>>(regs, list, offs, nlist, ipw, tab_x);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -717,9 +768,6 @@ long long measure_items(const MeasureArgs &a) {
     return (long long)a.P * ((rows + kRowsPerWarp - 1) / kRowsPerWarp);
 }
 
-#ifndef PF_MEASURE_XTAB
-#define PF_MEASURE_XTAB 1
-#endif
 template <bool IMG, bool MASK, bool SMEM, bool FIDX>
 cudaError_t launch_tab(const MeasureArgs &a, bool xtab, size_t smem_bits, cudaStream_t s) {
     if (xtab)

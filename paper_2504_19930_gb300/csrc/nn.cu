@@ -39,11 +39,31 @@ constexpr uint32_t kIdesc = umma::idesc_bf16_f32(kTileM, kTileN);
 
 __device__ unsigned int g_nn_error;   // set when a bounded wait gave up
 
+#ifndef PF_NN_ASYNC
+#define PF_NN_ASYNC 1   // forward / data-gradient / GEMM tiles fed by the cp.async pipeline
+#endif
+
 __device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
 
 __device__ __forceinline__ void st16(uint8_t *tile, int r, int k, uint4 v) {
     *reinterpret_cast<uint4 *>(tile + umma::tile_offset(r, k, kChunkK)) = v;
 }
+
+// Asynchronous global -> shared copies (cp.async): 16 or 4 bytes, written as
+// zeros when !valid (source size 0: nothing is read, the address is only a
+// placeholder and is always a valid one).
+__device__ __forceinline__ void cp16(uint32_t tile, int r, int k, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tile + umma::tile_offset(r, k, kChunkK)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp4(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------------------
 // Operand loaders.  load_a(tile, m0, chunk, t): thread t (0..127) writes row t
@@ -76,6 +96,26 @@ struct GemmOp {
             st16(tile, n, 8 * j, v);
         }
     }
+    struct Row {
+        int r;
+    };
+    __device__ Row row(int r) const { return Row{r}; }
+    __device__ void issue_a(uint32_t tile, const Row &rw, int c, int t) const {
+        const int r = rw.r;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = c * kChunkK + 8 * j;
+            const bool ok = r < M && k < K;
+            cp16(tile, t, 8 * j, ok ? (const void *)(A + (size_t)r * K + k) : (const void *)A, ok);
+        }
+    }
+    __device__ void issue_b(uint32_t tile, int c, int t) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int g = t + 128 * i, n = g >> 3, j = g & 7, k = c * kChunkK + 8 * j;
+            cp16(tile, n, 8 * j, k < K ? (const void *)(B + (size_t)n * K + k) : (const void *)B, k < K);
+        }
+    }
     __device__ void epilogue(int row, const float *acc) const {
         if (row >= M) return;
         float4 *dst = reinterpret_cast<float4 *>(C + (size_t)row * kTileN);
@@ -86,7 +126,7 @@ struct GemmOp {
 
 // Geometry of one strided convolution: input D^3 x Cin, output (D/2)^3 x 32.
 struct ConvGeom {
-    int batch, D, Cin;   // Cin in {2, 8, 16, 32, ...}: a multiple of 2, and of 8 when >= 8
+    int batch, D, Cin;   // Cin in {2, 8, 16, 32, 64, 128, 256}
     __device__ int Do() const { return D >> 1; }
 };
 
@@ -146,6 +186,64 @@ struct ConvFwdOp {
             st16(tile, n, 8 * j, v);
         }
     }
+    // Per-thread row context, decoded once: the input corner 2o - 1 of the
+    // output voxel's 4^3 window and the batch offset.
+    struct Row {
+        long long bbase;   // element offset of (b, 0, 0, 0)
+        int iz, iy, ix;    // 2 o - 1 per axis
+        bool live;
+    };
+    __device__ Row row(int r) const {
+        const int Do = g.Do();
+        Row w;
+        w.live = r < M();
+        const int rr = w.live ? r : 0;
+        const int ox = rr % Do, oy = (rr / Do) % Do, oz = (rr / (Do * Do)) % Do, b = rr / (Do * Do * Do);
+        w.bbase = (long long)b * g.D * g.D * g.D * g.Cin;
+        w.iz = 2 * oz - 1;
+        w.iy = 2 * oy - 1;
+        w.ix = 2 * ox - 1;
+        return w;
+    }
+    // input element offset of tap (kz, ky, kx), or -1 outside the volume
+    __device__ long long tap_off(const Row &w, int tap) const {
+        const int z = w.iz + (tap >> 4), y = w.iy + ((tap >> 2) & 3), x = w.ix + (tap & 3);
+        if (!w.live || (unsigned)z >= (unsigned)g.D || (unsigned)y >= (unsigned)g.D || (unsigned)x >= (unsigned)g.D)
+            return -1;
+        return w.bbase + (((long long)z * g.D + y) * g.D + x) * g.Cin;
+    }
+    __device__ void issue_a(uint32_t tile, const Row &w, int c, int t) const {
+        if (g.Cin >= 8) {
+            // the chunk's 64 K elements: 64 / Cin whole taps (Cin <= 64) or a
+            // slice of one tap; one offset per tap, Cin / 8 copies of 16 bytes
+            const int tpc = g.Cin >= 64 ? 1 : 64 / g.Cin;          // taps in this chunk
+            const int gpt = g.Cin >= 64 ? 8 : g.Cin / 8;           // 16-byte groups per tap here
+            for (int q = 0; q < tpc; ++q) {
+                const int k0 = c * kChunkK + q * 8 * gpt;
+                const int tap = k0 / g.Cin, ci0 = k0 - tap * g.Cin;
+                const long long e = tap < 64 ? tap_off(w, tap) : -1;
+                for (int j = 0; j < gpt; ++j)
+                    cp16(tile, t, 8 * (q * gpt + j), e >= 0 ? (const void *)(X + e + ci0 + 8 * j) : (const void *)X,
+                         e >= 0);
+            }
+        } else {   // Cin == 2: 32 taps of two channels per chunk, 4 bytes each
+#pragma unroll 4
+            for (int q = 0; q < 32; ++q) {
+                const int tap = c * 32 + q;
+                const long long e = tap < 64 ? tap_off(w, tap) : -1;
+                cp4(tile + umma::tile_offset(t, 2 * q, kChunkK), e >= 0 ? (const void *)(X + e) : (const void *)X,
+                    e >= 0);
+            }
+        }
+    }
+    __device__ void issue_b(uint32_t tile, int c, int t) const {
+        const int K = 64 * g.Cin;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = t + 128 * i, n = q >> 3, j = q & 7, k = c * kChunkK + 8 * j;
+            cp16(tile, n, 8 * j, k < K ? (const void *)(W + (size_t)n * K + k) : (const void *)W, k < K);
+        }
+    }
     __device__ void epilogue(int row, const float *acc) const {
         if (row >= M()) return;
         uint32_t packed[16];
@@ -200,6 +298,44 @@ struct ConvDgradOp {
             st16(tile, n, 8 * j, __ldg(reinterpret_cast<const uint4 *>(Wt + (size_t)n * 2048 + k)));
         }
     }
+    struct Row {
+        long long bbase;   // element offset of (b, 0, 0, 0) in dY
+        int z1, y1, x1;    // i + 1 per axis
+        bool live;
+    };
+    __device__ Row row(int r) const {
+        const int D = g.D, Do = g.Do();
+        Row w;
+        w.live = r < M();
+        const int rr = w.live ? r : 0;
+        const int ix = rr % D, iy = (rr / D) % D, iz = (rr / (D * D)) % D, b = rr / (D * D * D);
+        w.bbase = (long long)b * Do * Do * Do * 32;
+        w.z1 = iz + 1;
+        w.y1 = iy + 1;
+        w.x1 = ix + 1;
+        return w;
+    }
+    __device__ void issue_a(uint32_t tile, const Row &w, int c, int t) const {
+        const int Do = g.Do();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {   // two taps of 32 output channels per chunk
+            const int tap = 2 * c + q;
+            const int nz = w.z1 - (tap >> 4), ny = w.y1 - ((tap >> 2) & 3), nx = w.x1 - (tap & 3);
+            const int oz = nz >> 1, oy = ny >> 1, ox = nx >> 1;
+            const bool ok = w.live && !((nz | ny | nx) & 1) && (unsigned)oz < (unsigned)Do &&
+                            (unsigned)oy < (unsigned)Do && (unsigned)ox < (unsigned)Do;
+            const long long e = ok ? w.bbase + (((long long)oz * Do + oy) * Do + ox) * 32 : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cp16(tile, t, 8 * (4 * q + j), dY + e + 8 * j, ok);
+        }
+    }
+    __device__ void issue_b(uint32_t tile, int c, int t) const {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = t + 128 * i, n = q >> 3, j = q & 7, k = c * kChunkK + 8 * j;
+            cp16(tile, n, 8 * j, Wt + (size_t)n * 2048 + k, true);
+        }
+    }
     __device__ void epilogue(int row, const float *acc) const {
         if (row >= M()) return;
         uint32_t mask[16];
@@ -242,11 +378,14 @@ struct ConvWgradOp {
     __device__ int positions() const { const int d = g.Do(); return g.batch * d * d * d; }
     __device__ int chunks() const { return (positions() + kChunkK - 1) / kChunkK; }
     __device__ void load_a(uint8_t *tile, int m0, int c, int t) const {
-        const int r = m0 + t, Do = g.Do();
+        const int r = m0 + t, Do = g.Do(), D = g.D;
         const bool live = r < M();
         const int tap = r / g.Cin, ci = r - tap * g.Cin;
         const int kz = tap >> 4, ky = (tap >> 2) & 3, kx = tap & 3;
         const int P = positions();
+        // the chunk's 64 consecutive positions, decoded once and then stepped
+        int p = c * kChunkK;
+        int ox = p % Do, oy = (p / Do) % Do, oz = (p / (Do * Do)) % Do, b = p / (Do * Do * Do);
 #pragma unroll 1
         for (int j = 0; j < 8; ++j) {
             uint32_t w[4];
@@ -255,14 +394,23 @@ struct ConvWgradOp {
                 uint32_t lohi[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int p = c * kChunkK + 8 * j + 2 * q + h;
                     uint32_t val = 0u;
-                    if (live && p < P) {
-                        const int ox = p % Do, oy = (p / Do) % Do, oz = (p / (Do * Do)) % Do, b = p / (Do * Do * Do);
-                        const long long e = vox(g, b, 2 * oz + kz - 1, 2 * oy + ky - 1, 2 * ox + kx - 1, g.Cin);
-                        if (e >= 0) val = __ldg(X + e + ci);
-                    }
+                    const int z = 2 * oz + kz - 1, y = 2 * oy + ky - 1, x = 2 * ox + kx - 1;
+                    if (live && p < P && (unsigned)z < (unsigned)D && (unsigned)y < (unsigned)D &&
+                        (unsigned)x < (unsigned)D)
+                        val = __ldg(X + ((((long long)b * D + z) * D + y) * D + x) * g.Cin + ci);
                     lohi[h] = val;
+                    ++p;
+                    if (++ox == Do) {
+                        ox = 0;
+                        if (++oy == Do) {
+                            oy = 0;
+                            if (++oz == Do) {
+                                oz = 0;
+                                ++b;
+                            }
+                        }
+                    }
                 }
                 w[q] = lohi[0] | (lohi[1] << 16);
             }
@@ -369,6 +517,103 @@ cudaError_t launch_tile(const Op &op, int M, int chunks, int splits, cudaStream_
     splits = (chunks + per - 1) / per;
     dim3 grid((unsigned)((M + kTileM - 1) / kTileM), (unsigned)splits);
     k_umma_tile<Op><<<grid, 128, 0, s>>>(op, per);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// The same tile with an S-stage cp.async pipeline: chunk i's copies are
+// issued P = S - 2 chunks ahead; before the MMAs of chunk i every thread waits
+// for its own copies of that chunk (cp.async.wait_group), makes them visible
+// to the tensor core (fence.proxy.async) and the CTA synchronises.  The stage
+// refilled at iteration i is the one chunk i - 2 used, so the wait on that
+// commit's mbarrier leaves the tensor core a whole iteration of slack.
+constexpr int kAsyncStages = 5;
+constexpr int kAsyncSmem = kAsyncStages * (kStageA + kStageB) + 64;
+
+template <class Op>
+__global__ void __launch_bounds__(128) k_umma_async(const Op op) {
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    uint8_t *sA = dsm;                                   // [S][kStageA]
+    uint8_t *sB = dsm + kAsyncStages * kStageA;          // [S][kStageB]
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sB + kAsyncStages * kStageB);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + kAsyncStages);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int m0 = blockIdx.x * kTileM;
+    const int n = op.chunks();
+    constexpr int S = kAsyncStages;
+
+    if (warp == 0) umma::tmem_alloc(tmem_slot, kTileN);
+    if (t == 0) {
+        for (int q = 0; q < S; ++q) umma::mbar_init(umma::smem_u32(&mbar[q]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t a0 = umma::smem_u32(sA), b0 = umma::smem_u32(sB);
+    const typename Op::Row rw = op.row(m0 + t);
+
+    constexpr int P = S - 2;           // prefetch distance
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        if (i < n) {
+            op.issue_a(a0 + i * kStageA, rw, i, t);
+            op.issue_b(b0 + i * kStageB, i, t);
+        }
+        cp_commit();
+    }
+    bool ok = true;
+    for (int i = 0; i < n; ++i) {
+        const int s = i % S;
+        cp_wait<P - 1>();              // this thread's copies of chunk i have landed
+        umma::fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            umma::fence_after_sync();
+            const uint32_t a = a0 + s * kStageA, b = b0 + s * kStageB;
+#pragma unroll
+            for (int kk = 0; kk < kChunkK / 16; ++kk)
+                umma::mma_bf16(tmem, umma::smem_desc(a + 256 * kk, 128, 16 * kChunkK),
+                               umma::smem_desc(b + 256 * kk, 128, 16 * kChunkK), kIdesc, i > 0 || kk > 0);
+            umma::commit(umma::smem_u32(&mbar[s]));
+        }
+        const int j = i + P;           // refill the stage chunk i - 2 used
+        if (j < n) {
+            if (i >= 2) {
+                const int sp = (i - 2) % S;
+                if (!__syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[sp]), (uint32_t)(((i - 2) / S) & 1)))) {
+                    ok = false;
+                    break;
+                }
+            }
+            op.issue_a(a0 + (j % S) * kStageA, rw, j, t);
+            op.issue_b(b0 + (j % S) * kStageB, j, t);
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    if (ok && n > 0)
+        ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[(n - 1) % S]), (uint32_t)(((n - 1) / S) & 1)));
+    if (!ok) {
+        if (t == 0) atomicExch(&g_nn_error, 1u);
+    } else if (n > 0) {
+        umma::fence_after_sync();
+        float acc[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
+        op.epilogue(m0 + t, acc);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, kTileN);
+}
+
+template <class Op>
+cudaError_t launch_async(const Op &op, int M, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_umma_async<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, kAsyncSmem);
+    if (e != cudaSuccess) return e;
+    k_umma_async<Op><<<(unsigned)((M + kTileM - 1) / kTileM), 128, kAsyncSmem, s>>>(op);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -718,6 +963,37 @@ __global__ void k_synth_views(const SynthArgs a) {
 
 }  // namespace nn
 
+namespace nn {
+// Failure-detection self-test: one thread waits on an mbarrier that nothing
+// arrives on, with a short bounded wait; when it gives up it sets the error
+// flag the host reads (pf_nn_status), exactly as the tensor-core kernels do.
+__global__ void k_wait_timeout_selftest(uint32_t polls) {
+    __shared__ __align__(8) unsigned long long mbar;
+    const uint32_t a = umma::smem_u32(&mbar);
+    umma::mbar_init(a, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool done = false;
+    for (uint32_t i = 0; i < polls && !done; ++i) {
+        uint32_t r;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(r)
+            : "r"(a), "r"(0u)
+            : "memory");
+        done = r != 0;
+    }
+    if (!done) atomicExch(&g_nn_error, 1u);
+}
+}  // namespace nn
+
+cudaError_t nn_wait_selftest(cudaStream_t s) {
+    nn::k_wait_timeout_selftest<<<1, 1, 0, s>>>(1u << 16);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t nn_error_flag(unsigned int *out, bool clear) {
     cudaError_t e = cudaMemcpyFromSymbol(out, nn::g_nn_error, sizeof(unsigned int));
     if (e != cudaSuccess || !clear) return e;
@@ -727,20 +1003,32 @@ cudaError_t nn_error_flag(unsigned int *out, bool clear) {
 
 cudaError_t nn_gemm(const uint16_t *A, const uint16_t *B, float *C, int M, int K, cudaStream_t s) {
     nn::GemmOp op{A, B, C, M, K};
+#if PF_NN_ASYNC
+    return nn::launch_async(op, M, s);
+#else
     return nn::launch_tile(op, M, (K + nn::kChunkK - 1) / nn::kChunkK, 1, s);
+#endif
 }
 
 cudaError_t nn_conv_fwd(const uint16_t *X, int batch, int D, int Cin, const uint16_t *W, const float *bias,
                         uint16_t *Y, cudaStream_t s) {
     nn::ConvFwdOp op{{batch, D, Cin}, X, W, bias, Y};
     const int Do = D / 2;
+#if PF_NN_ASYNC
+    return nn::launch_async(op, batch * Do * Do * Do, s);
+#else
     return nn::launch_tile(op, batch * Do * Do * Do, (64 * Cin + nn::kChunkK - 1) / nn::kChunkK, 1, s);
+#endif
 }
 
 cudaError_t nn_conv_dgrad(const uint16_t *dY, int batch, int D, const uint16_t *Wt, const uint16_t *act,
                           uint16_t *dX, cudaStream_t s) {
     nn::ConvDgradOp op{{batch, D, 32}, dY, Wt, act, dX};
+#if PF_NN_ASYNC
+    return nn::launch_async(op, batch * D * D * D, s);
+#else
     return nn::launch_tile(op, batch * D * D * D, 2048 / nn::kChunkK, 1, s);
+#endif
 }
 
 cudaError_t nn_transpose_w(const uint16_t *W, int Cin, uint16_t *Wt, cudaStream_t s) {

@@ -15,6 +15,7 @@
 namespace pfreg {
 int set_error(int code, const char *msg);
 cudaError_t nn_error_flag(unsigned int *out, bool clear);
+cudaError_t nn_wait_selftest(cudaStream_t s);
 cudaError_t nn_gemm(const uint16_t *A, const uint16_t *B, float *C, int M, int K, cudaStream_t s);
 cudaError_t nn_conv_fwd(const uint16_t *X, int batch, int D, int Cin, const uint16_t *W, const float *bias,
                         uint16_t *Y, cudaStream_t s);
@@ -57,8 +58,8 @@ int cuda_fail(cudaError_t e, const char *what) {
 // Rows of a conv's implicit GEMM must stay within int32, and D must halve.
 int check_conv(int batch, int D, int Cin) {
     if (batch < 1 || D < 2 || (D & 1) || D > 512) return set_error(PF_EINVAL, "conv: batch >= 1, D even in [2, 512]");
-    if (!(Cin == 2 || (Cin >= 8 && Cin <= 256 && Cin % 8 == 0)))
-        return set_error(PF_EINVAL, "conv: Cin must be 2 or a multiple of 8 up to 256");
+    if (!(Cin == 2 || Cin == 8 || Cin == 16 || Cin == 32 || Cin == 64 || Cin == 128 || Cin == 256))
+        return set_error(PF_EINVAL, "conv: Cin must be 2, 8, 16, 32, 64, 128 or 256");
     if ((long long)batch * D * D * D >= (1ll << 31) / 64) return set_error(PF_EINVAL, "conv: volume too large");
     return PF_OK;
 }
@@ -95,6 +96,11 @@ int pf_nn_conv3d_backward_weights(const uint16_t *x, int32_t batch, int32_t D, i
     if (!x || !dy || !dw) return set_error(PF_EINVAL, "conv backward weights: NULL pointer");
     if (int r = check_conv(batch, D, Cin)) return r;
     CUP(nn_conv_wgrad(x, batch, D, Cin, dy, dw, static_cast<cudaStream_t>(stream)));
+    return PF_OK;
+}
+
+int pf_nn_wait_selftest(void *stream) {
+    CUP(nn_wait_selftest(static_cast<cudaStream_t>(stream)));
     return PF_OK;
 }
 

@@ -1,0 +1,26 @@
+"""Host-side helpers of bench.py (no GPU)."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_settled_iteration():
+    f = bench.settled_iteration
+    assert f([0.5, 0.9, 0.99, 0.99], 0.985) == 3          # first iteration of the final run above target
+    assert f([0.99, 0.95, 0.99, 0.99], 0.985) == 3        # a dip resets the count
+    assert f([0.99, 0.99], 0.985) == 1
+    assert f([0.99, 0.97], 0.985) is None                 # never settles: the last one is below
+    assert f([], 0.5) is None
+    assert f(np.array([0.2, 0.6]), 0.6) == 2              # >= target counts
+
+
+def test_workloads_name_sizes_not_indices():
+    for key, w in bench.WORKLOADS.items():
+        assert not key.startswith("config"), key
+        assert "name" in w

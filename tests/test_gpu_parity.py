@@ -3,7 +3,7 @@ oracle on the same seeded inputs.
 
 Bars (element by element):
   * Philox words, pose matrices, mask counts, image moments (samples rounded
-    to 1/1024), scores, quantised weights, resampled indices, particle clouds
+    to 2^-15), scores, quantised weights, resampled indices, particle clouds
     and warped voxels: bit-exact;
   * image NCC^2 against the fp64 two-pass oracle: within 1e-5 relative;
   * final estimates: within 1e-4 rad and 1e-3 voxel (the fp64 weighted sums
@@ -138,6 +138,9 @@ def test_integer_maps_exact(pk, mode):
     ("mask_dice", (130, 118, 97), (61, 50, 40)),        # bit mask too large for shared memory
     ("image_ncc", (40, 37, 29), (45, 33, 27)),
     ("image_ncc", (70, 66, 60), (97, 31, 20)),          # rows longer than 3 warps, few rows
+    ("image_ncc", (30, 40, 36), (20, 45, 40)),          # every row shorter than a pass of 64
+    ("image_ncc", (70, 30, 26), (64, 33, 30)),          # rows of exactly one pass at the centre
+    ("image_ncc", (300, 40, 20), (290, 36, 16)),        # > 8192 entries per work item
     ("combined", (44, 39, 31), (41, 35, 30)),
 ])
 def test_measure_random_poses_bit_exact(pk, orc, mode, sdims, tdims):
@@ -466,3 +469,38 @@ def test_quaternion_estimator_against_oracle(pk, orc, mode):
     for k in range(K):
         want = orc.estimate_quaternion(ref["tr_poses"][k], ref["tr_W"][k])
         assert np.max(np.abs(est[k] - want)) <= 1e-9, (k, est[k] - want)
+
+
+# ------------------------------------------------------------- fault paths
+
+def test_allocation_failure_is_reported_and_released(pk):
+    """Host-side fault injection: with a cap on a context's device bytes,
+    creation fails with PF_ENOMEM (no fault, nothing leaked), and works again
+    once the cap is lifted."""
+    import torch
+    src = pfsynth.random_mask(3, (40, 40, 40), 0.4)
+    free0 = torch.cuda.mem_get_info()[0]
+    pk.pf_debug_alloc_limit(4096)
+    try:
+        with pytest.raises(pk.PfError) as ei:
+            pk.Registration("mask_dice", src_mask=src, tgt_mask=src, n_particles=256)
+        assert ei.value.code == -2
+    finally:
+        pk.pf_debug_alloc_limit(0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (8 << 20)
+    with pk.Registration("mask_dice", src_mask=src, tgt_mask=src, n_particles=256) as r:
+        r.step(1)
+
+
+def test_bounded_wait_reports_instead_of_hanging(pk):
+    """A device-side wait that nothing satisfies gives up after its bound and
+    sets the flag the host reads; the context stays usable."""
+    import torch
+    assert pk.nn_status(clear=True) == 0
+    pk.nn_wait_selftest()
+    torch.cuda.synchronize()
+    assert pk.nn_status(clear=True) == 1
+    assert pk.nn_status(clear=True) == 0
+    x = torch.ones(4, device="cuda")
+    assert float((x * 2).sum()) == 8.0
