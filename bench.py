@@ -40,6 +40,7 @@ WORKLOADS = {
     "image224": dict(pfsynth.IMAGE224, kind="image_ncc", dims=(224, 208, 176)),
     "mask64": dict(pfsynth.MASK64, kind="mask_dice", dims=(64, 64, 64), n_frames=0),
     "batch64": dict(name="batch64_mixed_96to256_n512to8192_k20to60", kind="batch", n_regs=64),
+    "batch64_small": dict(name="batch64_mixed_40to80_n128to1024_k8to16", kind="batch", n_regs=64, small=True),
     "combined256": dict(pfsynth.COMBINED256, kind="combined", dims=(256, 256, 256)),
     "conv32": dict(name="conv3d_b32_32x32x32x32_to_16x16x16x32_bf16", kind="conv"),
     "proposal": dict(name="proposal_speckle224x208x176_learned_n512_vs_plain_n2048_k50", kind="proposal",
@@ -63,8 +64,8 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of one measurement launch from an ncu capture (profiles/), with
 # the hash of the kernel source it was taken on; reported as null once the
 # kernel changes.
-NCU_TRAFFIC = {"measure_cu_sha1": "ae37878f55c07fadcf70e131661a7792823e64b9",
-               "bytes_per_launch": 36112128}   # the ncu capture summarised under profiles/
+NCU_TRAFFIC = {"measure_cu_sha1": "3d97c7469f8e4eff292ac1e31b76707a0eb7a4e4",
+               "bytes_per_launch": 36134912}   # the ncu capture summarised under profiles/
 
 
 def parse():
@@ -273,10 +274,13 @@ def oracle_measure_all_cores(w, pair, n_particles, cores):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    if args.workload == "batch64":      # a bounded sample of one image-based member
-        m = batch_members(2, 7)[1]
-        w = dict(name=WORKLOADS["batch64"]["name"], kind=m["mode"], rot_limit_deg=30.0, trans_limit=25.0, seed=1)
+    if WORKLOADS[args.workload]["kind"] == "batch":      # a bounded sample of one image-based member
+        m = batch_members(2, 7, small=WORKLOADS[args.workload].get("small", False))[1]
+        w = dict(name=WORKLOADS[args.workload]["name"], kind=m["mode"], rot_limit_deg=30.0, trans_limit=25.0,
+                 seed=1)
         pair = m["pair"]
+    elif WORKLOADS[args.workload]["kind"] in ("proposal", "conv"):
+        w, pair, _ = load_workload("image224", 0)   # the filter the proposal seeds: the image workload's pair
     else:
         w, pair, _ = load_workload(args.workload, 0)
     n, k = args.cpu_sample_particles, 1
@@ -532,17 +536,24 @@ def run_ours(args, rank, world, local):
     dist.close()
 
 
-def batch_members(n_regs, seed):
+def batch_members(n_regs, seed, small=False):
     """The batched workload: registration r draws its grid (each axis 96..256),
     particle count {512, 1024, 4096, 8192}, iteration count 20..60 and mode
     (even r: mask Dice on an ellipsoid mask pair, odd r: image NCC on a speckle
-    pair), all from one seeded generator."""
+    pair), all from one seeded generator.  small: grids 40..80, particle
+    counts {128, 256, 512, 1024}, 8..16 iterations -- registrations too small
+    to fill the GPU on their own."""
     rng = np.random.default_rng(seed)
     out = []
     for r in range(n_regs):
-        dims = tuple(int(v) for v in rng.integers(96, 257, 3))
-        N = int(rng.choice([512, 1024, 4096, 8192]))
-        K = int(rng.integers(20, 61))
+        if small:
+            dims = tuple(int(v) for v in rng.integers(40, 81, 3))
+            N = int(rng.choice([128, 256, 512, 1024]))
+            K = int(rng.integers(8, 17))
+        else:
+            dims = tuple(int(v) for v in rng.integers(96, 257, 3))
+            N = int(rng.choice([512, 1024, 4096, 8192]))
+            K = int(rng.integers(20, 61))
         if r % 2 == 0:
             pair = pfsynth.cached(pfsynth.ellipsoid_pair, seed * 1000 + r, src_dims=dims, tgt_dims=dims,
                                   tgt_origin=(0.0, 0.0, float(int(0.2 * dims[2]))),
@@ -568,7 +579,8 @@ def run_batch(args, rank, world, local):
     pk.build()
     pk.load()
     dist = Dist(world)
-    members = batch_members(args.batch_regs, 7 + rank)
+    wname = args.workload
+    members = batch_members(args.batch_regs, 7 + rank, small=WORKLOADS[wname].get("small", False))
     dev = torch.device("cuda", local)
     dev_vols = []
     for m in members:
@@ -617,7 +629,7 @@ def run_batch(args, rank, world, local):
         line = {"metric": METRIC, "value": total / tb, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * tb / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOADS["batch64"]["name"], "registrations": len(members),
+                "config": {"workload": WORKLOADS[wname]["name"], "registrations": len(members),
                            "mask_based": sum(m["mode"] == "mask_dice" for m in members),
                            "particles": [m["N"] for m in members], "iterations": [m["K"] for m in members],
                            "dense_evals_per_step": units,
@@ -801,7 +813,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload == "batch64":
+    if args.workload in ("batch64", "batch64_small"):
         run_batch(args, rank, world, local)
         return
     if args.workload == "proposal":

@@ -634,9 +634,9 @@ __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_
 // registration's target rows are at most tab_x <= kTabMaxX long) each warp
 // keeps the x-product table of its current (registration, particle) in
 // shared memory, as the single-registration kernel does; image sources of at
-// most 2^23 voxels take the fp32 quad index.  Each warp copies its current
-// registration's measurement arguments into shared memory, so the sweep
-// reads them there rather than from the global registration table.
+// most 2^23 voxels take the fp32 quad index.  (A per-warp shared-memory copy
+// of the current member's arguments measured slower than reading them
+// through the read-only path of the registration table.)
 // (The registration lookup costs registers: tighter bounds than these spill.)
 template <bool IMG, bool MASK>
 __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batch(const BatchReg *__restrict__ regs,
@@ -644,13 +644,12 @@ __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batc
                                                             const long long *__restrict__ offs, int nlist,
                                                             int ipw, int tab_x) {
     extern __shared__ float4 smem_dyn[];
-    __shared__ MeasureArgs sma[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4 *tab = tab_x > 0 ? smem_dyn + (size_t)warp * tab_x : nullptr;
     const long long total = offs[nlist];
     const long long item0 = ((long long)blockIdx.x * kWarps + warp) * ipw;
     const long long item1 = min(total, item0 + ipw);
-    int tab_r = -1, tab_p = -1, arg_r = -1;
+    int tab_r = -1, tab_p = -1;
     for (long long item = item0; item < item1; ++item) {
         int lo = 0, hi = nlist - 1;                  // last r with offs[r] <= item
         while (lo < hi) {
@@ -659,15 +658,7 @@ __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batc
         }
         const BatchReg &R = regs[list[lo]];
         if (*R.B.k >= R.n_iters) continue;          // warp-uniform
-        if (lo != arg_r) {
-            const int *src = reinterpret_cast<const int *>(&R.ma);
-            int *dst = reinterpret_cast<int *>(&sma[warp]);
-            __syncwarp();
-            for (int i = lane; i < (int)(sizeof(MeasureArgs) / sizeof(int)); i += 32) dst[i] = src[i];
-            __syncwarp();
-            arg_r = lo;
-        }
-        const MeasureArgs &A = sma[warp];
+        const MeasureArgs &A = R.ma;
         const long long local = item - offs[lo];
         const bool fidx = IMG && (size_t)A.g.sd[0] * A.g.sd[1] * A.g.sd[2] <= ((size_t)1 << 23);
         if (tab) {

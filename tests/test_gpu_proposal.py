@@ -153,3 +153,30 @@ def test_predict_returns_a_finite_proposal(torch_, pk):
     p = pfsynth.speckle_pair(3, src_dims=DIMS)
     mean, std = net.predict(p.src, p.tgt, p.src_origin, p.tgt_origin)
     assert np.all(np.isfinite(mean)) and np.all(std > 0)
+
+
+def test_checkpoint_round_trip_and_continued_training(torch_, pk):
+    """Parameters saved from one network and loaded into another give the
+    same outputs; training continues across calls with the step counter."""
+    torch = torch_
+    a = pk.Proposal(max_batch=4, seed=21)
+    l1 = a.train(10, batch=4, lr=1e-3, data_seed=3, vol_dims=DIMS, rot_limit=ROT, trans_limit=TRANS)
+    l2 = a.train(10, batch=4, lr=1e-3, data_seed=3, vol_dims=DIMS, rot_limit=ROT, trans_limit=TRANS)
+    assert len(l1) == len(l2) == 10 and np.all(np.isfinite(l2))
+    assert not np.array_equal(l1, l2)                  # new batches (the step counter moved on)
+    theta = a.params()
+    b = pk.Proposal(max_batch=4, seed=99)
+    assert not np.array_equal(b.params(), theta)
+    b.params(theta_in=theta)
+    assert np.array_equal(b.params(), theta)
+    x, _ = _batch(torch, pk, a, 4, seed=13)
+    oa = torch.zeros((4, 12), dtype=torch.float32, device="cuda")
+    ob = torch.zeros((4, 12), dtype=torch.float32, device="cuda")
+    a.forward(x, oa)
+    b.forward(x, ob)
+    torch.cuda.synchronize()
+    assert torch.equal(oa, ob)
+    with pytest.raises(pk.PfError):                    # the output units are the training limits
+        a.train(1, batch=4, lr=1e-3, data_seed=3, vol_dims=DIMS, rot_limit=ROT / 2, trans_limit=TRANS)
+    with pytest.raises(pk.PfError):
+        a.train(1, batch=5, lr=1e-3, data_seed=3, vol_dims=DIMS, rot_limit=ROT, trans_limit=TRANS)
