@@ -24,6 +24,7 @@ import hashlib
 import json
 import os
 import platform
+import re
 import statistics
 import subprocess
 import sys
@@ -64,8 +65,25 @@ FP32_LANES_PER_SM = 128
 # DRAM traffic of one measurement launch from an ncu capture (profiles/), with
 # the hash of the kernel source it was taken on; reported as null once the
 # kernel changes.
-NCU_TRAFFIC = {"measure_cu_sha1": "3d97c7469f8e4eff292ac1e31b76707a0eb7a4e4",
-               "bytes_per_launch": 36134912}   # the ncu capture summarised under profiles/
+NCU_TRAFFIC = {"measure_code_sha1": "0b5fa053fc4720104dc58fc59983ad3ffc2722c2",
+               "bytes_per_launch": 36114944}   # the ncu capture summarised under profiles/
+
+
+# the measurement kernel's translation unit (its source and the headers it includes)
+MEASURE_SOURCES = [os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", f)
+                   for f in ("measure.cu", "kernels.h", "device.cuh")]
+
+
+def kernel_code_hash(paths):
+    """sha1 of CUDA sources with their comments and whitespace removed, so that
+    it names the kernel's code (a comment edit leaves it unchanged)."""
+    h = hashlib.sha1()
+    for path in paths:
+        src = open(path).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode() + b"\0")
+    return h.hexdigest()
 
 
 def parse():
@@ -403,9 +421,8 @@ def run_ours(args, rank, world, local):
     meas_s = rec["measure_ms"] / 1e3
     ops = OPS_PER_EVAL_MODE[kind]
     achieved = rec["evals"] * ops / meas_s if meas_s > 0 else 0.0
-    sha = hashlib.sha1(open(os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "measure.cu"), "rb")
-                       .read()).hexdigest()
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["measure_cu_sha1"] == sha else None
+    sha = kernel_code_hash(MEASURE_SOURCES)
+    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["measure_code_sha1"] == sha else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TOP/s",
                 "frac": achieved / peak_ops if peak_ops else None, "traffic": traffic,
                 "kernel": {"image_ncc": "k_measure<image>", "mask_dice": "k_measure<mask>",

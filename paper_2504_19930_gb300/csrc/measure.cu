@@ -1,13 +1,15 @@
 // measure.cu -- the measurement step (Fig. 1 caption: the similarity of the
 // source warped by each particle's transform is the particle's measurement).
 //
-// One work item = (particle p, block of target rows); a persistent grid
-// strides over the items, consecutive items sharing a particle.  Each warp
-// sweeps one target row at a time, lane = x offset, so a warp's gathers follow
-// the rotated row through the L2-resident source.  Per row the x-range that
-// can map inside the source is computed first (row_interval) and only that
-// range is visited; every visited voxel still takes the exact fp32 inside
-// test, so the result equals the full sweep.
+// One work item = (particle p, 32 consecutive target rows), one warp; a warp
+// takes a few consecutive items (one particle) and the grid covers all items
+// in several waves.  Lane l first finds the exact inside interval of row
+// first + l (each coordinate is monotone along a row, so the interval where
+// all six bounds hold is found by probing and bisection on the same fp32
+// coordinates the samples use); then the warp sweeps the 32 intervals as one
+// sequence, lane = x offset, so its gathers follow the rotated row through
+// the L2-resident source.  No voxel is tested for inside-ness and the result
+// equals the full sweep of the target grid.
 //
 // Image mode (trilinear, Sec. 3.3): the source is read in a quad-packed copy
 // Q[x,y,z] = S[x,y,z] | S[x+1,y,z]<<8 | S[x,y+1,z]<<16 | S[x+1,y+1,z]<<24, so
@@ -29,6 +31,21 @@ constexpr int kThreads = kWarps * 32;
 constexpr float kTwo23 = 8388608.0f;
 constexpr uint32_t kTwo23Bits = 0x4B000000u;   // bits of 2^23
 constexpr uint32_t k256Bits = 0x43800000u;     // bits of 256.0f
+
+// Per-mode forms of the sweep (each gives the same bits; each mode takes the
+// form that timed faster for it):
+// paired table (image only): the x-product table holds the products of x and
+// x + 32 side by side, so a pass inside one row reads both voxels' products
+// as ready-made pairs (the combined kernel, which also gathers mask bits
+// through L1, was slower with the larger table);
+// crossing without clamp (combined only): the per-row clamp flag is kept
+// across passes and a row-crossing pass whose two rows need no y/z clamp
+// skips it (the image kernel was slower with it).
+#ifndef PF_MEASURE_NNPACK
+#define PF_MEASURE_NNPACK 1
+#endif
+template <bool IMG, bool MASK> __host__ __device__ constexpr bool paired_tab() { return IMG && !MASK; }
+template <bool IMG, bool MASK> __host__ __device__ constexpr bool crossing_noclamp() { return IMG && MASK; }
 
 __device__ __forceinline__ unsigned long long warp_sum64(unsigned long long v) {
 #pragma unroll
@@ -76,6 +93,17 @@ __device__ __forceinline__ f2 splat(float a) { return f2{a, a}; }
 PF_F32X2(add2, "add")
 PF_F32X2(sub2, "sub")
 #undef PF_F32X2
+// a + b rounded toward -infinity, per lane.  With b = 2^23 and 0 <= a < 2^23
+// the exact sum lies in [2^23, 2^24), where the floats are the integers, so
+// the result is 2^23 + floor(a) exactly.
+__device__ __forceinline__ f2 addrm2(f2 a, f2 b) {
+    f2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2,%3};\n\tmov.b64 rb, {%4,%5};\n\t"
+        "add.rm.f32x2 rd, ra, rb;\n\tmov.b64 {%0,%1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
 // a*b + c with one rounding per lane (fused, lane-wise identical to
 // __fmaf_rn): the trilinear lerps, and the index arithmetic on integer-valued
 // operands whose products and sums stay below 2^24 (every rounding exact).
@@ -93,6 +121,7 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return f2{__fsub_rn(a.x, b.x), 
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     return f2{__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y)};
 }
+__device__ __forceinline__ f2 addrm2(f2 a, f2 b) { return f2{__fadd_rd(a.x, b.x), __fadd_rd(a.y, b.y)}; }
 #endif
 
 // a + f*(b - a) for two voxels: the difference rounded, then one fused
@@ -167,16 +196,32 @@ __device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t 
 // particle), so q = product + K is one packed add per axis.
 template <bool IMG, bool MASK, bool FULL, bool IFULL, bool NOCLAMP, bool FIDX, bool XTAB>
 __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *__restrict__ bits,
-                                          const float4 *__restrict__ tab, const float r0x, const float r0y,
-                                          const float r0z, const PairIn &v, bool valid0, bool valid1,
-                                          bool ivalid0, bool ivalid1, ImgAcc &ia, MaskAcc &ma) {
+                                          const float4 *__restrict__ tab, const float2 *__restrict__ tabz,
+                                          const float r0x, const float r0y, const float r0z, const PairIn &v,
+                                          bool valid0, bool valid1, bool ivalid0, bool ivalid1, ImgAcc &ia,
+                                          MaskAcc &ma) {
     if (FULL) valid0 = valid1 = true;
     f2 qx, qy, qz;
     if (XTAB) {
-        const float4 P0 = tab[v.x0], P1 = tab[v.x1];
-        qx = add2(pair(P0.x, P1.x), v.K0);
-        qy = add2(pair(P0.y, P1.y), v.K1);
-        qz = add2(pair(P0.z, P1.z), v.K2);
+        if (paired_tab<IMG, MASK>() && FULL) {
+            // entry x holds the products of x and x + 32 (= x1) side by side
+            const float4 P = tab[v.x0];
+            const float2 Z = tabz[v.x0];
+            qx = add2(pair(P.x, P.y), v.K0);
+            qy = add2(pair(P.z, P.w), v.K1);
+            qz = add2(pair(Z.x, Z.y), v.K2);
+        } else if (paired_tab<IMG, MASK>()) {
+            const float4 P0 = tab[v.x0], P1 = tab[v.x1];
+            const float Z0 = tabz[v.x0].x, Z1 = tabz[v.x1].x;
+            qx = add2(pair(P0.x, P1.x), v.K0);
+            qy = add2(pair(P0.z, P1.z), v.K1);
+            qz = add2(pair(Z0, Z1), v.K2);
+        } else {
+            const float4 P0 = tab[v.x0], P1 = tab[v.x1];
+            qx = add2(pair(P0.x, P1.x), v.K0);
+            qy = add2(pair(P0.y, P1.y), v.K1);
+            qz = add2(pair(P0.z, P1.z), v.K2);
+        }
     } else {
         const f2 dx = sub2(v.xf, splat(a.g.a[0]));
         qx = coord2(r0x, dx, v.K0);
@@ -190,17 +235,20 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const bool in1 = IFULL || (MASK ? ivalid1 : valid1);
         // base corner min(floor q, D-2) and fraction q - base
         const float Dm2y = (float)(SY - 2), Dm2z = (float)(SZ - 2);
-        const f2 flx = pair(floorf(qx.x), floorf(qx.y));
-        const f2 fly = NOCLAMP ? pair(floorf(qy.x), floorf(qy.y))
-                               : pair(fminf(floorf(qy.x), Dm2y), fminf(floorf(qy.y), Dm2y));
-        const f2 flz = NOCLAMP ? pair(floorf(qz.x), floorf(qz.y))
-                               : pair(fminf(floorf(qz.x), Dm2z), fminf(floorf(qz.y), Dm2z));
+        // floors by rounding 2^23 + q down, two voxels per instruction (every
+        // voxel taken has q >= 0; the others get their index replaced below);
+        // bx = 2^23 + floor(qx) is also the biased x term of the quad index
+        const f2 bx = addrm2(qx, splat(kTwo23));
+        const f2 flx = sub2(bx, splat(kTwo23));
+        const f2 fly0 = sub2(addrm2(qy, splat(kTwo23)), splat(kTwo23));
+        const f2 flz0 = sub2(addrm2(qz, splat(kTwo23)), splat(kTwo23));
+        const f2 fly = NOCLAMP ? fly0 : pair(fminf(fly0.x, Dm2y), fminf(fly0.y, Dm2y));
+        const f2 flz = NOCLAMP ? flz0 : pair(fminf(flz0.x, Dm2z), fminf(flz0.y, Dm2z));
         const f2 fx = sub2(qx, flx), fy = sub2(qy, fly), fz = sub2(qz, flz);
         const uint32_t *qbase;
         uint32_t i0, i1;
         if (FIDX) {
-            const f2 w = fma2(splat((float)SXY), flz,
-                                    fma2(splat((float)SX), fly, add2(flx, splat(kTwo23))));
+            const f2 w = fma2(splat((float)SXY), flz, fma2(splat((float)SX), fly, bx));
             i0 = __float_as_uint(w.x);
             i1 = __float_as_uint(w.y);
             qbase = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(a.src_quad) -
@@ -211,8 +259,7 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
             }
         } else {
             const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY);   // folds the three int_of
-            const f2 bxv = add2(flx, splat(kTwo23)), byv = add2(fly, splat(kTwo23)),
-                     bzv = add2(flz, splat(kTwo23));
+            const f2 bxv = bx, byv = add2(fly, splat(kTwo23)), bzv = add2(flz, splat(kTwo23));
             i0 = __float_as_uint(bxv.x) + (uint32_t)SX * __float_as_uint(byv.x) + SXY * __float_as_uint(bzv.x) + bias;
             i1 = __float_as_uint(bxv.y) + (uint32_t)SX * __float_as_uint(byv.y) + SXY * __float_as_uint(bzv.y) + bias;
             qbase = a.src_quad;
@@ -254,8 +301,39 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
     }
     if (MASK) {
         const uint8_t *tm = IMG ? v.tpm : v.tp;   // FULL: the mask target's address
+#if PF_MEASURE_NNPACK
+        // nearest-neighbour voxel floor(q + 0.5) for both voxels at once:
+        // h = q + 0.5 (rounded), then 2^23 + floor(h) by a rounding-down add
+        // (every voxel taken has h >= 0); the three biases fold into one
+        // constant of the integer index
+        const int SX = a.g.sd[0], SY = a.g.sd[1];
+        const uint32_t SXY = (uint32_t)SX * (uint32_t)SY;
+        const f2 bxn = addrm2(add2(qx, splat(0.5f)), splat(kTwo23));
+        const f2 byn = addrm2(add2(qy, splat(0.5f)), splat(kTwo23));
+        const f2 bzn = addrm2(add2(qz, splat(0.5f)), splat(kTwo23));
+        const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY);
+        if (valid0) {
+            const uint32_t si = __float_as_uint(bxn.x) + (uint32_t)SX * __float_as_uint(byn.x) +
+                                SXY * __float_as_uint(bzn.x) + bias;
+            const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
+            const uint32_t tb = __ldg(FULL ? tm : a.tgt_mask + v.t0);
+            ma.A += sb;
+            ma.B += tb;
+            ma.C += sb & tb;
+        }
+        if (valid1) {
+            const uint32_t si = __float_as_uint(bxn.y) + (uint32_t)SX * __float_as_uint(byn.y) +
+                                SXY * __float_as_uint(bzn.y) + bias;
+            const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
+            const uint32_t tb = __ldg(FULL ? tm + 32 : a.tgt_mask + v.t1);
+            ma.A += sb;
+            ma.B += tb;
+            ma.C += sb & tb;
+        }
+#else
         mask_voxel(a, bits, qx.x, qy.x, qz.x, FULL ? tm : a.tgt_mask + v.t0, valid0, ma);
         mask_voxel(a, bits, qx.y, qy.y, qz.y, FULL ? tm + 32 : a.tgt_mask + v.t1, valid1, ma);
+#endif
     }
 }
 
@@ -361,7 +439,8 @@ __device__ __forceinline__ void exact_interval(const float r0[3], const float K[
 // them to mom[p] with one integer atomic each (S2 is 128-bit).
 template <bool IMG, bool MASK, bool FIDX, bool XTAB>
 __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_t *__restrict__ bits,
-                                             const float4 *__restrict__ tab, long long item, int lane) {
+                                             const float4 *__restrict__ tab, const float2 *__restrict__ tabz,
+                                             long long item, int lane) {
     constexpr bool BOTH = IMG && MASK;
     const int SX = a.g.sd[0], SY = a.g.sd[1], SZ = a.g.sd[2];
     const int TX = a.g.td[0], TY = a.g.td[1];
@@ -445,26 +524,27 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
         uint32_t trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
         float xf = (float)(pos + lane);
         uint32_t toff = trow0 + (uint32_t)(pos + lane);
+        bool nc0 = IMG && ((noclamp >> j0) & 1u);   // row j0 needs no y/z clamp
         for (;;) {
             const int len0 = end0 - pos;
             if (len0 >= 64) {
                 const PairIn v{pair(xf, __fadd_rn(xf, 32.0f)), pos + lane, pos + lane + 32, splat(K0), splat(K1),
                                splat(K2), 0u, 0u, tgt + toff, a.tgt_mask + toff};
-                const bool nc = IMG && ((noclamp >> j0) & 1u);
+                const bool nc = crossing_noclamp<IMG, MASK>() ? nc0 : IMG && ((noclamp >> j0) & 1u);
                 if (BOTH && !(pos >= ib0 && pos + 64 <= ie0)) {   // the image interval ends in this pass
                     const int x = pos + lane;
                     const bool iv0 = x >= ib0 && x < ie0, iv1 = x + 32 >= ib0 && x + 32 < ie0;
                     if (nc)
-                        eval_pair<IMG, MASK, true, false, true, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true, true,
+                        eval_pair<IMG, MASK, true, false, true, FIDX, XTAB>(a, bits, tab, tabz, r0[0], r0[1], r0[2], v, true, true,
                                                                       iv0, iv1, ia, ma);
                     else
-                        eval_pair<IMG, MASK, true, false, false, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true,
+                        eval_pair<IMG, MASK, true, false, false, FIDX, XTAB>(a, bits, tab, tabz, r0[0], r0[1], r0[2], v, true,
                                                                        true, iv0, iv1, ia, ma);
                 } else if (nc) {
-                    eval_pair<IMG, MASK, true, true, true, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true, true, true,
+                    eval_pair<IMG, MASK, true, true, true, FIDX, XTAB>(a, bits, tab, tabz, r0[0], r0[1], r0[2], v, true, true, true,
                                                                  true, ia, ma);
                 } else {
-                    eval_pair<IMG, MASK, true, true, false, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, true, true,
+                    eval_pair<IMG, MASK, true, true, false, FIDX, XTAB>(a, bits, tab, tabz, r0[0], r0[1], r0[2], v, true, true,
                                                                   true, true, ia, ma);
                 }
                 pos += 64;
@@ -493,8 +573,14 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
                            pair(in0a ? K1 : L1, in1a ? K1 : L1), pair(in0a ? K2 : L2, in1a ? K2 : L2),
                            (in0a || !ok0 ? trow0 : trow1) + (uint32_t)x0,
                            (in1a || !ok1 ? trow0 : trow1) + (uint32_t)x1, nullptr, nullptr};
-            eval_pair<IMG, MASK, false, false, false, FIDX, XTAB>(a, bits, tab, r0[0], r0[1], r0[2], v, ok0, ok1, iv0, iv1,
-                                                            ia, ma);
+            // with j1 = j0 when no row follows
+            const bool nc1 = IMG && ((noclamp >> j1) & 1u);
+            if (crossing_noclamp<IMG, MASK>() && nc0 && nc1)   // both rows' taken voxels need no y/z clamp
+                eval_pair<IMG, MASK, false, false, true, FIDX, XTAB>(a, bits, tab, tabz, r0[0], r0[1], r0[2], v, ok0, ok1,
+                                                                   iv0, iv1, ia, ma);
+            else
+                eval_pair<IMG, MASK, false, false, false, FIDX, XTAB>(a, bits, tab, tabz, r0[0], r0[1], r0[2], v, ok0, ok1,
+                                                                    iv0, iv1, ia, ma);
             if (IMG) {
                 ia.S1 += ia.S1row;
                 ia.S1row = 0;
@@ -512,6 +598,7 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
                 K1 = L1;
                 K2 = L2;
                 trow0 = trow1;
+                nc0 = nc1;
             } else {
                 if (!live) break;
                 j0 = __ffs(live) - 1;
@@ -524,6 +611,7 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
                 K1 = __shfl_sync(0xffffffffu, myK1, j0);
                 K2 = __shfl_sync(0xffffffffu, myK2, j0);
                 trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
+                nc0 = IMG && ((noclamp >> j0) & 1u);
             }
             xf = (float)(pos + lane);
             toff = trow0 + (uint32_t)(pos + lane);
@@ -578,12 +666,34 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
 #define PF_MEASURE_MIN_BLOCKS_COMBINED 3
 #endif
 // XTAB: each warp keeps the table of r_i0 * (x - a0), x = 0 .. X-1, of its
-// current particle in shared memory (X float4 per warp, X <= kTabMaxX), in
-// front of the optional mask bits.
+// current particle in shared memory (X <= kTabMaxX), in front of the optional
+// mask bits.  Paired layout: float4 {r_00 dx, r_00 dx', r_10 dx, r_10 dx'} per
+// x, then float2 {r_20 dx, r_20 dx'} per x, with dx = x - a0, dx' = x + 32 - a0;
+// otherwise float4 {r_00 dx, r_10 dx, r_20 dx, 0} per x.
 constexpr int kTabMaxX = 512;
 #ifndef PF_MEASURE_XTAB
 #define PF_MEASURE_XTAB 1
 #endif
+// float4 slots of one warp's table (a multiple of 16 bytes)
+__host__ __device__ __forceinline__ int tab_slots(int X, bool paired) { return paired ? X + (X + 1) / 2 : X; }
+
+// Table of one particle, same roundings as the per-voxel form: fl(r_i0 * fl(x - a0)).
+template <bool PAIRED>
+__device__ __forceinline__ void build_xtab(float4 *tab, float2 *tabz, int X, float a0, const float *Mp, int lane) {
+    const float r0 = __ldg(Mp + 0), r1 = __ldg(Mp + 4), r2 = __ldg(Mp + 8);
+    __syncwarp();
+    for (int x = lane; x < X; x += 32) {
+        const float dx = __fsub_rn((float)x, a0);
+        if (PAIRED) {
+            const float dx2 = __fsub_rn((float)(x + 32), a0);
+            tab[x] = make_float4(__fmul_rn(r0, dx), __fmul_rn(r0, dx2), __fmul_rn(r1, dx), __fmul_rn(r1, dx2));
+            tabz[x] = make_float2(__fmul_rn(r2, dx), __fmul_rn(r2, dx2));
+        } else {
+            tab[x] = make_float4(__fmul_rn(r0, dx), __fmul_rn(r1, dx), __fmul_rn(r2, dx), 0.0f);
+        }
+    }
+    __syncwarp();
+}
 template <bool IMG, bool MASK, bool MASK_SMEM, bool FIDX, bool XTAB>
 __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_COMBINED
                                                         : (IMG ? PF_MEASURE_MIN_BLOCKS_IMG : 4))
@@ -591,10 +701,12 @@ __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_
     extern __shared__ float4 smem_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int TX = a.g.td[0];
-    float4 *tab = XTAB ? smem_dyn + (size_t)warp * TX : nullptr;
+    constexpr bool PAIRED = paired_tab<IMG, MASK>();
+    float4 *tab = XTAB ? smem_dyn + (size_t)warp * tab_slots(TX, PAIRED) : nullptr;
+    float2 *tabz = XTAB ? reinterpret_cast<float2 *>(tab + TX) : nullptr;
     const uint32_t *bits = a.src_bits;
     if (MASK && MASK_SMEM) {
-        uint32_t *sb = reinterpret_cast<uint32_t *>(smem_dyn + (XTAB ? (size_t)kWarps * TX : 0));
+        uint32_t *sb = reinterpret_cast<uint32_t *>(smem_dyn + (XTAB ? (size_t)kWarps * tab_slots(TX, PAIRED) : 0));
         const int nwords = (int)(((size_t)a.g.sd[0] * a.g.sd[1] * a.g.sd[2] + 31) / 32);
         for (int i = threadIdx.x; i < nwords; i += kThreads) sb[i] = a.src_bits[i];
         __syncthreads();
@@ -611,19 +723,11 @@ __global__ void __launch_bounds__(kThreads, IMG && MASK ? PF_MEASURE_MIN_BLOCKS_
         if (XTAB) {
             const int p = (int)(item / nblocks);   // warp-uniform
             if (p != tab_p) {
-                // same roundings as the per-voxel form: fl(r_i0 * fl(x - a0))
-                const float *Mp = a.mats + 12 * (size_t)p;
-                const float r0 = __ldg(Mp + 0), r1 = __ldg(Mp + 4), r2 = __ldg(Mp + 8);
-                __syncwarp();
-                for (int x = lane; x < TX; x += 32) {
-                    const float dx = __fsub_rn((float)x, a.g.a[0]);
-                    tab[x] = make_float4(__fmul_rn(r0, dx), __fmul_rn(r1, dx), __fmul_rn(r2, dx), 0.0f);
-                }
-                __syncwarp();
+                build_xtab<PAIRED>(tab, tabz, TX, a.g.a[0], a.mats + 12 * (size_t)p, lane);
                 tab_p = p;
             }
         }
-        measure_item<IMG, MASK, FIDX, XTAB>(a, bits, tab, item, lane);
+        measure_item<IMG, MASK, FIDX, XTAB>(a, bits, tab, tabz, item, lane);
     }
 }
 
@@ -645,7 +749,8 @@ __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batc
                                                             int ipw, int tab_x) {
     extern __shared__ float4 smem_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float4 *tab = tab_x > 0 ? smem_dyn + (size_t)warp * tab_x : nullptr;
+    constexpr bool PAIRED = paired_tab<IMG, MASK>();
+    float4 *tab = tab_x > 0 ? smem_dyn + (size_t)warp * tab_slots(tab_x, PAIRED) : nullptr;
     const long long total = offs[nlist];
     const long long item0 = ((long long)blockIdx.x * kWarps + warp) * ipw;
     const long long item1 = min(total, item0 + ipw);
@@ -664,24 +769,18 @@ __global__ void __launch_bounds__(kThreads, IMG && !MASK ? 3 : 1) k_measure_batc
         if (tab) {
             const int rows = A.g.td[1] * A.g.td[2];
             const int p = (int)(local / ((rows + kRowsPerWarp - 1) / kRowsPerWarp));   // warp-uniform
+            // this member's table: its own row length, in the warp's tab_x slots
+            float2 *tabz = reinterpret_cast<float2 *>(tab + A.g.td[0]);
             if (lo != tab_r || p != tab_p) {
-                const float *Mp = A.mats + 12 * (size_t)p;
-                const float r0 = __ldg(Mp + 0), r1 = __ldg(Mp + 4), r2 = __ldg(Mp + 8);
-                const float a0 = A.g.a[0];
-                __syncwarp();
-                for (int x = lane; x < A.g.td[0]; x += 32) {
-                    const float dx = __fsub_rn((float)x, a0);
-                    tab[x] = make_float4(__fmul_rn(r0, dx), __fmul_rn(r1, dx), __fmul_rn(r2, dx), 0.0f);
-                }
-                __syncwarp();
+                build_xtab<PAIRED>(tab, tabz, A.g.td[0], A.g.a[0], A.mats + 12 * (size_t)p, lane);
                 tab_r = lo;
                 tab_p = p;
             }
-            if (fidx) measure_item<IMG, MASK, true, true>(A, A.src_bits, tab, local, lane);
-            else measure_item<IMG, MASK, false, true>(A, A.src_bits, tab, local, lane);
+            if (fidx) measure_item<IMG, MASK, true, true>(A, A.src_bits, tab, tabz, local, lane);
+            else measure_item<IMG, MASK, false, true>(A, A.src_bits, tab, tabz, local, lane);
         } else {
-            if (fidx) measure_item<IMG, MASK, true, false>(A, A.src_bits, nullptr, local, lane);
-            else measure_item<IMG, MASK, false, false>(A, A.src_bits, nullptr, local, lane);
+            if (fidx) measure_item<IMG, MASK, true, false>(A, A.src_bits, nullptr, nullptr, local, lane);
+            else measure_item<IMG, MASK, false, false>(A, A.src_bits, nullptr, nullptr, local, lane);
         }
     }
 }
@@ -743,7 +842,7 @@ cudaError_t launch_measure_batch(const BatchReg *regs, const int32_t *list, cons
     const long long per_cta = (long long)kWarps * ipw;
     const unsigned grid = (unsigned)((total_items + per_cta - 1) / per_cta);
     const int tab_x = (PF_MEASURE_XTAB && max_tx > 0 && max_tx <= kTabMaxX) ? max_tx : 0;
-    const size_t smem = (size_t)kWarps * tab_x * sizeof(float4);
+    const size_t smem = (size_t)kWarps * tab_slots(tab_x, img && !mask) * sizeof(float4);
     auto kern = img && mask ? k_measure_batch<true, true> : (img ? k_measure_batch<true, false> : k_measure_batch<false, true>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -763,7 +862,8 @@ template <bool IMG, bool MASK, bool SMEM, bool FIDX>
 cudaError_t launch_tab(const MeasureArgs &a, bool xtab, size_t smem_bits, cudaStream_t s) {
     if (xtab)
         return launch_variant<IMG, MASK, SMEM, FIDX, true>(
-            a, (size_t)kWarps * a.g.td[0] * sizeof(float4) + (SMEM ? smem_bits : 0), s);
+            a, (size_t)kWarps * tab_slots(a.g.td[0], paired_tab<IMG, MASK>()) * sizeof(float4) + (SMEM ? smem_bits : 0),
+            s);
     return launch_variant<IMG, MASK, SMEM, FIDX, false>(a, SMEM ? smem_bits : 0, s);
 }
 
@@ -773,7 +873,7 @@ cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream
     const size_t smem_bits = ((nvox + 31) / 32) * 4;
     const bool smem = mask && smem_bits <= 160 * 1024;
     const bool fidx = nvox <= ((size_t)1 << 23);   // quad indices formed in fp32
-    const size_t tab_bytes = (size_t)kWarps * a.g.td[0] * sizeof(float4);
+    const size_t tab_bytes = (size_t)kWarps * tab_slots(a.g.td[0], img && !mask) * sizeof(float4);
     const bool xtab = PF_MEASURE_XTAB && a.g.td[0] <= kTabMaxX &&
                       tab_bytes + (smem ? smem_bits : 0) <= 200 * 1024;
     if (img && mask) {

@@ -24,3 +24,17 @@ def test_workloads_name_sizes_not_indices():
     for key, w in bench.WORKLOADS.items():
         assert not key.startswith("config"), key
         assert "name" in w
+
+
+def test_kernel_code_hash_ignores_comments_only(tmp_path):
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text("// header\n__global__ void k(int *p) {\n    p[0] = 1;   // store\n}\n")
+    b.write_text("/* another\n header */\n__global__ void k(int *p) {\n  p[0] = 1;\n}\n")
+    c.write_text("__global__ void k(int *p) {\n    p[0] = 2;\n}\n")
+    h = bench.kernel_code_hash
+    assert h([str(a)]) == h([str(b)])
+    assert h([str(a)]) != h([str(c)])
+    assert h([str(a), str(c)]) != h([str(c), str(a)])   # file order and boundaries count
+
