@@ -173,7 +173,10 @@ int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32
  * counts) together.  One batch iteration is one CUDA-graph launch: prediction
  * of every particle of every running registration, their measurements (image,
  * mask and combined registrations as three concurrent launches over their
- * concatenated work items) and one update/resampling block per registration.
+ * concatenated work items; a registration with at least 120000 measurement
+ * work items -- 32 target rows of one particle each, enough to fill the GPU
+ * for several waves -- gets its own launch in the same graph instead) and one
+ * update/resampling block per registration.
  * n_iters[r] is registration r's total iteration count.  Members are ordered
  * by remaining iterations, so the running ones are a prefix; one graph is
  * captured per such prefix (on first use) and its grids cover only the

@@ -41,7 +41,23 @@ def _members():
                                            max_trans=2), 200, 0, 5),
         ("mask_dice", pfsynth.ellipsoid_pair(26, src_dims=(70, 66, 60), tgt_dims=(68, 60, 50),
                                              tgt_origin=(0, 0, 10), semi_axes=(22, 15, 14)), 128, 2, 6),
+        # members large enough for their own measurement launch inside the batch graph
+        ("mask_dice", pfsynth.ellipsoid_pair(27, src_dims=(40, 38, 36), tgt_dims=(40, 38, 30),
+                                             tgt_origin=(0, 0, 6), semi_axes=(13, 9, 8), asymmetric=True),
+         4096, 3, 7),
+        ("combined", pfsynth.speckle_pair(28, src_dims=(40, 36, 34), overlap=(0.6, 0.7), max_rot_deg=6,
+                                          max_trans=2, with_masks=True), 4096, 2, 8),
     ]
+
+
+# a member with at least this many measurement work items (32 target rows of
+# one particle each) is measured by its own launch in the batch graph
+SOLO_ITEMS = 120000
+
+
+def _items(pair, N):
+    rows = pair.tgt.shape[0] * pair.tgt.shape[1]
+    return (rows + 31) // 32 * N
 
 
 def _make(pk, mode, pair, N, seed, **cfg):
@@ -72,6 +88,8 @@ def _assert_same(a, b, tag):
 
 def test_batch_equals_individual_registrations(pk):
     members = _members()
+    sizes = [_items(pair, N) for mode, pair, N, K, seed in members]
+    assert any(n >= SOLO_ITEMS for n in sizes) and any(n < SOLO_ITEMS for n in sizes)   # both launch forms
     singles = []
     for mode, pair, N, K, seed in members:
         with _make(pk, mode, pair, N, seed) as r:
