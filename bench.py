@@ -46,7 +46,7 @@ WORKLOADS = {
     "conv32": dict(name="conv3d_b32_32x32x32x32_to_16x16x16x32_bf16", kind="conv"),
     "proposal": dict(name="proposal_speckle224x208x176_learned_n512_vs_plain_n2048_k50", kind="proposal",
                      n_particles=512, plain_particles=2048, n_iters=50, rot_limit_deg=30.0, trans_limit=25.0,
-                     seed=0, train_steps=1500, train_batch=32, lr=1e-3, n_eval=6, std_inflate=1.5),
+                     seed=0, train_steps=1500, train_batch=32, lr=1e-3, std_inflate=1.5),
 }
 METRIC = "particle-voxel evals/s (dense N*iters*target voxels per registration) and ms per registration"
 UNIT = "particle-voxel evals/s"
@@ -94,6 +94,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="image224")
     ap.add_argument("--batch-regs", type=int, default=64)
+    ap.add_argument("--proposal-eval-pairs", type=int, default=32,
+                    help="held-out pairs of the learned-proposal comparison (seeds 5000 + 1000 rank + i)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-particles", type=int, default=32)
@@ -708,6 +710,12 @@ def run_conv(args, rank, world, local):
                           "config": {"workload": WORKLOADS["conv32"]["name"]}, "roofline": r}), flush=True)
 
 
+def _held_out_pair(seed):
+    """Pool worker: one held-out speckle pair with masks, into the disk cache."""
+    pfsynth.cached(pfsynth.speckle_pair, seed, with_masks=True)
+    return seed
+
+
 def run_proposal(args, rank, world, local):
     """Learned proposal against the plain filter: train the network on
     synthetic pairs (GPU generator), then on held-out seeded speckle pairs
@@ -743,13 +751,18 @@ def run_proposal(args, rank, world, local):
 
     roofline = conv_roofline(pk, torch, dev, stream, w["train_batch"])
 
-    # --- held-out pairs
+    # --- held-out pairs (generated on the host cores by spawned processes first)
+    n_eval = args.proposal_eval_pairs
+    seeds = [5000 + 1000 * rank + i for i in range(n_eval)]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(len(seeds), os.cpu_count() or 1))) as pool:
+        pool.map(_held_out_pair, seeds)
     rows = []
     units_learned, secs_learned = 0, 0.0
     launches0 = pk.pf_kernel_launches()
     with ClockSampler(local) as clocks:
-        for i in range(w["n_eval"]):
-            pair = pfsynth.cached(pfsynth.speckle_pair, 5000 + 100 * rank + i, with_masks=True)
+        for seed in seeds:
+            pair = pfsynth.cached(pfsynth.speckle_pair, seed, with_masks=True)
             vols = dict(src=torch.from_numpy(pair.src).to(dev), tgt=torch.from_numpy(pair.tgt).to(dev),
                         src_mask=torch.from_numpy(pair.src_mask).to(dev),
                         tgt_mask=torch.from_numpy(pair.tgt_mask).to(dev))
@@ -805,7 +818,7 @@ def run_proposal(args, rank, world, local):
     value = dist.sum(units_learned) / t_max if t_max > 0 else 0.0
     if rank == 0:
         med = lambda k: float(np.median([r[k] for r in rows]))   # noqa: E731
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": w["n_eval"],
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_eval,
                 "warmup": 0, "ms_per_step": 1e3 * secs_learned / max(len(rows), 1), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network / f32 filter", "data": "synthetic",
                 "config": {"workload": w["name"], "n_eval_pairs": len(rows),
