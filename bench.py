@@ -98,8 +98,10 @@ def parse():
                     help="held-out pairs of the learned-proposal comparison (seeds 5000 + 1000 rank + i)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-particles", type=int, default=32)
-    ap.add_argument("--cpu-sample-iters", type=int, default=2)
+    ap.add_argument("--cpu-sample-particles", type=int, default=None,
+                    help="oracle sample: particles (default: 64, or the whole cloud of the 64^3 mask workload)")
+    ap.add_argument("--cpu-sample-iters", type=int, default=None,
+                    help="oracle sample: iterations (default: 2, or all of the 64^3 mask workload's)")
     ap.add_argument("--cpu-all-cores-particles", type=int, default=512)
     return ap.parse_args()
 
@@ -303,7 +305,7 @@ def run_reference(args, rank, world):
         w, pair, _ = load_workload("image224", 0)   # the filter the proposal seeds: the image workload's pair
     else:
         w, pair, _ = load_workload(args.workload, 0)
-    n, k = args.cpu_sample_particles, 1
+    n, k = cpu_sample_size(args, w)[0], 1
     times, units = [], 0
     for i in range(args.warmup + args.steps):
         dt, u = oracle_sample(w, pair, n, k)
@@ -515,7 +517,7 @@ def run_ours(args, rank, world, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, k = args.cpu_sample_particles, args.cpu_sample_iters
+        n, k = cpu_sample_size(args, w)
         dt, u = oracle_sample(w, pair, n, k)
         ncpu = os.cpu_count() or 1
         cpu = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -708,6 +710,17 @@ def run_conv(args, rank, world, local):
                           "value": r["achieved"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
                           "warmup": 3, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
                           "config": {"workload": WORKLOADS["conv32"]["name"]}, "roofline": r}), flush=True)
+
+
+def cpu_sample_size(args, w):
+    """(particles, iterations) of the oracle's bounded sample: about 10-30 s of
+    single-threaded work on the 16-core Arm host for the image and combined
+    workloads (64 particles x 2 iterations), the whole registration for the
+    small mask workload (a few seconds)."""
+    small = w["kind"] == "mask_dice"
+    n = getattr(args, "cpu_sample_particles", None) or (w["n_particles"] if small else 64)
+    k = getattr(args, "cpu_sample_iters", None) or (w["n_iters"] if small else 2)
+    return n, k
 
 
 def _held_out_pair(seed):

@@ -38,3 +38,15 @@ def test_kernel_code_hash_ignores_comments_only(tmp_path):
     assert h([str(a)]) != h([str(c)])
     assert h([str(a), str(c)]) != h([str(c), str(a)])   # file order and boundaries count
 
+
+
+def test_cpu_sample_size():
+    import types
+    f = bench.cpu_sample_size
+    none = types.SimpleNamespace(cpu_sample_particles=None, cpu_sample_iters=None)
+    assert f(none, bench.WORKLOADS["image224"]) == (64, 2)
+    assert f(none, bench.WORKLOADS["combined256"]) == (64, 2)
+    assert f(none, bench.WORKLOADS["mask64"]) == (256, 10)            # the whole small registration
+    given = types.SimpleNamespace(cpu_sample_particles=8, cpu_sample_iters=1)
+    assert f(given, bench.WORKLOADS["image224"]) == (8, 1)
+    assert f(types.SimpleNamespace(), bench.WORKLOADS["mask64"]) == (256, 10)
