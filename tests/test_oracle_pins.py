@@ -155,6 +155,26 @@ def test_mask_counts_integer_maps_exact(orc):
         assert got.tolist() == want.tolist()
 
 
+def test_mask_counts_half_voxel_ties_round_up(orc):
+    # q = P p + b + h with h_d in {0, 1/2}: every coordinate with h_d = 1/2 sits
+    # exactly on a tie of the nearest-neighbour rounding; the reading takes
+    # voxel floor(q + 1/2), i.e. rounds the tie up, which is the integer map
+    # with b + 1 on those axes (round-half-even or half-down would differ)
+    src = pfsynth.random_mask(13, (17, 15, 13), 0.45)
+    tgt = pfsynth.random_mask(14, (14, 16, 12), 0.45)
+    a0 = np.zeros(3, np.float32)
+    rng = np.random.default_rng(8)
+    for P, b in _exact_cases(7, 24):
+        h = rng.integers(0, 2, 3)
+        if not h.any():
+            h[rng.integers(3)] = 1
+        M = bf.exact_matrix(P, b)
+        M[[3, 7, 11]] += 0.5 * h
+        got = orc.measure_mask(src, tgt, M, a0)[0]
+        want = bf.integer_map_counts(src, tgt, P, b + h)
+        assert got.tolist() == want.tolist(), (P.tolist(), b.tolist(), h.tolist())
+
+
 def test_mask_identity_gives_dice_one(orc):
     m = pfsynth.random_mask(3, (16, 15, 14), 0.35)
     sd = (16, 15, 14)
