@@ -84,6 +84,43 @@ def integer_map_counts(src, tgt, P, b, image=False):
                     dtype=np.uint64)
 
 
+def dyadic_map_moments(src, tgt, P, b, h4):
+    """Exact image moments for q = P p + b + h4/4 (integer P, b, h4; a = 0).
+
+    Every fraction is a multiple of 1/4, so each trilinear weight, corner
+    product and sample is a dyadic rational with at most 6 fractional bits:
+    the samples, their 15-bit fixed point values and all sums are exact
+    (Python integers in units of 2^-6 for the samples)."""
+    sd = np.array([src.shape[2], src.shape[1], src.shape[0]], np.int64)
+    tgt_dims = (tgt.shape[2], tgt.shape[1], tgt.shape[0])
+    p = target_points(tgt_dims).astype(np.int64)
+    q4 = 4 * (p @ P.T + b) + h4                       # 4 q, exact integers
+    ok = np.all((q4 >= 0) & (q4 <= 4 * (sd - 1)), axis=1)
+    i0 = np.minimum(q4 // 4, sd - 2)                  # min(floor q, D - 2)
+    f4 = q4 - 4 * i0                                  # 4 f, in 0..4
+    t = tgt.reshape(-1).astype(np.int64)
+    srci = src.astype(np.int64)
+    n = S1 = S2 = ST = T1 = T2 = 0
+    for k in np.nonzero(ok)[0]:
+        x0, y0, z0 = (int(v) for v in i0[k])
+        fx, fy, fz = (int(v) for v in f4[k])
+        acc = 0                                       # 64 s (weights in quarters per axis)
+        for dz, wz in ((0, 4 - fz), (1, fz)):
+            for dy, wy in ((0, 4 - fy), (1, fy)):
+                for dx, wx in ((0, 4 - fx), (1, fx)):
+                    if wx and wy and wz:
+                        acc += wx * wy * wz * int(srci[z0 + dz, y0 + dy, x0 + dx])
+        sq = acc * 512                                # 2^15 s = 2^15 acc / 64
+        tk = int(t[k])
+        n += 1
+        S1 += sq
+        S2 += sq * sq
+        ST += sq * tk
+        T1 += tk
+        T2 += tk * tk
+    return np.array([n, S1, S2 & (2**64 - 1), S2 >> 64, ST, T1, T2], dtype=np.uint64)
+
+
 def integer_map_warp(src, tgt_dims, P, b):
     sd = np.array([src.shape[2], src.shape[1], src.shape[0]])
     p = target_points(tgt_dims)

@@ -231,6 +231,29 @@ def _ramp(dims, g, c0):
     return v.astype(np.uint8)
 
 
+def test_image_moments_dyadic_shifts_exact(orc):
+    # axis maps shifted by multiples of a quarter voxel: every trilinear
+    # fraction is 0, 1/4, 1/2 or 3/4, so the samples and the 15-bit moments
+    # are exact rationals -- an exact check of the interpolation (corner
+    # order, lerp direction) that integer maps, whose fractions are all 0,
+    # cannot give
+    src = pfsynth.random_image(43, (13, 12, 11))
+    tgt = pfsynth.random_image(44, (11, 12, 10))
+    a0 = np.zeros(3, np.float32)
+    rng = np.random.default_rng(12)
+    cases = 0
+    for P, b in _exact_cases(9, 40):
+        b = rng.integers(-3, 8, 3)
+        h4 = rng.integers(0, 4, 3)
+        M = bf.exact_matrix(P, b)
+        M[[3, 7, 11]] += 0.25 * h4
+        got = orc.measure_image(src, tgt, M, a0)[0][:7]
+        want = bf.dyadic_map_moments(src, tgt, P, b, h4)
+        assert got.tolist() == want.tolist(), (P.tolist(), b.tolist(), h4.tolist())
+        cases += int(want[0]) > 0
+    assert cases >= 20   # most cases overlap
+
+
 def test_image_ncc_linear_ramp_closed_form(orc):
     """Trilinear interpolation reproduces an affine field exactly, so for a
     target box wholly inside the source, NCC^2 = (u.V.h)^2 / (u.V.u h.V.h)
