@@ -121,6 +121,40 @@ def dyadic_map_moments(src, tgt, P, b, h4):
     return np.array([n, S1, S2 & (2**64 - 1), S2 >> 64, ST, T1, T2], dtype=np.uint64)
 
 
+def dyadic_map_warp(src, tgt_dims, P, b, h4, interp):
+    """Exact warp for q = P p + b + h4/4 (integer P, b, h4): trilinear samples
+    are exact multiples of 1/64, rounded half to even into uint8; nearest
+    neighbour takes voxel floor(q + 1/2); 0 outside the source."""
+    sd = np.array([src.shape[2], src.shape[1], src.shape[0]], np.int64)
+    p = target_points(tgt_dims).astype(np.int64)
+    q4 = 4 * (p @ P.T + b) + h4
+    out = np.zeros(len(p), np.uint8)
+    srci = src.astype(np.int64)
+    if interp == 0:
+        i = (q4 + 2) // 4                             # floor(q + 1/2)
+        ok = np.all((i >= 0) & (i < sd), axis=1)
+        ii = i[ok]
+        out[ok] = src[ii[:, 2], ii[:, 1], ii[:, 0]]
+    else:
+        ok = np.all((q4 >= 0) & (q4 <= 4 * (sd - 1)), axis=1)
+        i0 = np.minimum(q4 // 4, sd - 2)
+        f4 = q4 - 4 * i0
+        for k in np.nonzero(ok)[0]:
+            x0, y0, z0 = (int(v) for v in i0[k])
+            fx, fy, fz = (int(v) for v in f4[k])
+            acc = 0                                   # 64 s
+            for dz, wz in ((0, 4 - fz), (1, fz)):
+                for dy, wy in ((0, 4 - fy), (1, fy)):
+                    for dx, wx in ((0, 4 - fx), (1, fx)):
+                        if wx and wy and wz:
+                            acc += wx * wy * wz * int(srci[z0 + dz, y0 + dy, x0 + dx])
+            v, r = divmod(acc, 64)
+            v += 1 if (r > 32 or (r == 32 and v % 2 == 1)) else 0
+            out[k] = min(v, 255)
+    X, Y, Z = tgt_dims
+    return out.reshape(Z, Y, X)
+
+
 def integer_map_warp(src, tgt_dims, P, b):
     sd = np.array([src.shape[2], src.shape[1], src.shape[0]])
     p = target_points(tgt_dims)

@@ -439,6 +439,28 @@ def test_warp_identity_and_integer_maps(orc):
             assert np.array_equal(got, bf.integer_map_warp(src, (9, 14, 10), P, b))
 
 
+def test_warp_dyadic_shifts_exact(orc):
+    # quarter-voxel shifts of the axis maps: the trilinear samples are exact
+    # multiples of 1/64, so the uint8 output is pinned exactly, ties (odd
+    # multiples of 1/2 at half-voxel shifts) included: rounded half to even;
+    # nearest neighbour rounds its half-voxel ties up
+    src = pfsynth.random_image(94, (12, 11, 10))
+    a0 = np.zeros(3, np.float32)
+    rng = np.random.default_rng(14)
+    ties = 0
+    for P, b in _exact_cases(10, 24):
+        b = rng.integers(-3, 7, 3)
+        h4 = rng.integers(0, 4, 3)
+        M = bf.exact_matrix(P, b)
+        M[[3, 7, 11]] += 0.25 * h4
+        for interp in (0, 1):
+            got = orc.warp_matrix(src, (10, 12, 9), M, a0, interp)
+            want = bf.dyadic_map_warp(src, (10, 12, 9), P, b, h4, interp)
+            assert np.array_equal(got, want), (P.tolist(), b.tolist(), h4.tolist(), interp)
+        ties += int((h4 == 2).any())
+    assert ties >= 8
+
+
 def test_warp_rot90_equals_numpy(orc):
     src = pfsynth.random_image(92, (11, 9, 7))
     X, Y, Z = 11, 9, 7
