@@ -669,9 +669,10 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
 #ifndef PF_MEASURE_MIN_BLOCKS_COMBINED
 #define PF_MEASURE_MIN_BLOCKS_COMBINED 3
 #endif
-// XTAB: each warp keeps the table of r_i0 * (x - a0), x = 0 .. X-1, of its
-// current particle in shared memory (X <= kTabMaxX), in front of the optional
-// mask bits.  Paired layout: float4 {r_00 dx, r_00 dx', r_10 dx, r_10 dx'} per
+// XTAB: the table of r_i0 * (x - a0), x = 0 .. X-1, of a particle sits in
+// shared memory (X <= kTabMaxX), in front of the optional mask bits: one per
+// warp for its current particle, or (CTAB) two per CTA for the particles of
+// the CTA's items.  Paired layout: float4 {r_00 dx, r_00 dx', r_10 dx, r_10 dx'} per
 // x, then float2 {r_20 dx, r_20 dx'} per x, with dx = x - a0, dx' = x + 32 - a0;
 // otherwise float4 {r_00 dx, r_10 dx, r_20 dx, 0} per x.
 constexpr int kTabMaxX = 512;
