@@ -344,6 +344,47 @@ def test_image_identity_ncc_one(orc):
     assert abs(orc.ncc2_from_moments(m) - 1.0) < 1e-15
 
 
+def test_mask_ncc_and_combined_scores_against_scipy(orc):
+    # mask NCC^2 from the four counts is the squared Pearson correlation of
+    # the binary samples over the overlap; the combined score is half the sum
+    # of the image NCC^2 (Pearson of the image samples) and the mask Dice
+    # over the whole target grid -- each computed here from exact integer-map
+    # samples with scipy / numpy
+    src = pfsynth.random_image(45, (15, 14, 13))
+    tgt = pfsynth.random_image(46, (13, 14, 12))
+    smask = pfsynth.random_mask(47, (15, 14, 13), 0.45)
+    tmask = pfsynth.random_mask(48, (13, 14, 12), 0.45)
+    a0 = np.zeros(3, np.float32)
+    sd = np.array([15, 14, 13])
+    checked = 0
+    for P, b in _exact_cases(11, 30):
+        b = np.random.default_rng(int(np.abs(b).sum())).integers(-2, 4, 3)
+        p = bf.target_points((13, 14, 12))
+        q = p @ P.T + b
+        ok = np.all((q >= 0) & (q < sd), axis=1)
+        if ok.sum() < 50:
+            continue
+        qq = q[ok]
+        s_img = src[qq[:, 2], qq[:, 1], qq[:, 0]].astype(np.float64)
+        t_img = tgt.reshape(-1)[ok].astype(np.float64)
+        s_m = (smask[qq[:, 2], qq[:, 1], qq[:, 0]] != 0).astype(np.float64)
+        t_m = (tmask.reshape(-1)[ok] != 0).astype(np.float64)
+        M = bf.exact_matrix(P, b)
+        mom = np.zeros(12, np.uint64)
+        mom[:7] = orc.measure_image(src, tgt, M, a0)[0]
+        mom[8:] = orc.measure_mask(smask, tmask, M, a0)[0]
+        b_full = int((tmask != 0).sum())
+        if s_m.std() > 0 and t_m.std() > 0:
+            r_m = stats.pearsonr(s_m, t_m)[0]
+            assert abs(orc.score("mask_ncc", mom, b_full) - r_m ** 2) < 1e-12
+        r_i = stats.pearsonr(s_img, t_img)[0]
+        dice = 2.0 * np.sum(s_m * t_m) / (s_m.sum() + b_full)
+        assert abs(orc.score("combined", mom, b_full) - 0.5 * (r_i ** 2 + dice)) < 1e-12
+        assert abs(orc.score("mask_dice", mom, b_full) - dice) < 1e-15
+        checked += 1
+    assert checked >= 10
+
+
 def test_score_zero_cases(orc):
     # overlap below n_min, empty overlap, constant target
     assert orc.ncc2_from_moments([5, 10, 30, 0, 20, 2, 4], n_min=6) == 0.0
