@@ -127,3 +127,25 @@ def test_batch_arguments_are_validated(pk):
     assert lib.pf_batch_create(C.byref(out), None, 0, None) == -1 and out.value is None
     assert lib.pf_batch_step(None, 1) == -1 and lib.pf_batch_run(None) == -1
     assert lib.pf_batch_destroy(None) == 0
+
+
+def test_volume_and_config_marshalling(pk):
+    # (Z, Y, X) arrays become pf_volume dims {X, Y, Z}; origin and spacing are
+    # passed through per axis; malformed arrays are refused before any C call
+    vol = np.zeros((5, 6, 7), np.uint8)
+    v = pk.make_volume(vol, origin=(1.5, -2.0, 3.0), spacing=(0.8, 1.0, 1.2))
+    assert list(v.dims) == [7, 6, 5] and v.is_device == 0 and v.data == vol.ctypes.data
+    assert list(v.origin) == [1.5, -2.0, 3.0]
+    np.testing.assert_allclose(list(v.spacing), [0.8, 1.0, 1.2], rtol=1e-7)
+    assert list(pk.make_volume(vol, spacing=2.0).spacing) == [2.0, 2.0, 2.0]
+    assert pk.make_volume(None) is None
+    for bad in (np.zeros((5, 6, 7), np.float32), np.zeros((5, 6), np.uint8),
+                np.zeros((7, 6, 5), np.uint8).transpose(2, 1, 0)):
+        with pytest.raises(ValueError):
+            pk.make_volume(bad)
+    cfg = pk.make_config("combined", n_particles=100, rot_limit=(0.1, 0.2, 0.3), trans_limit=4.0,
+                         seed=2**40 + 3, trace_estimate=True, estimator="quaternion", autotune=True)
+    assert cfg.mode == pk.PF_COMBINED and cfg.n_particles == 100 and cfg.seed == 2**40 + 3
+    np.testing.assert_allclose(list(cfg.rot_limit), [0.1, 0.2, 0.3], rtol=1e-7)
+    assert list(cfg.trans_limit) == [4.0, 4.0, 4.0]
+    assert (cfg.trace_estimate, cfg.estimator, cfg.autotune) == (1, 1, 1)
