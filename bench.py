@@ -39,7 +39,7 @@ import pfsynth  # noqa: E402
 
 WORKLOADS = {
     "image224": dict(pfsynth.IMAGE224, kind="image_ncc", dims=(224, 208, 176)),
-    "mask64": dict(pfsynth.MASK64, kind="mask_dice", dims=(64, 64, 64), n_frames=0),
+    "mask64": dict(pfsynth.MASK64, kind="mask_dice", dims=(64, 64, 64), n_frames=0, default_steps=1500),
     "batch64": dict(name="batch64_mixed_96to256_n512to8192_k20to60", kind="batch", n_regs=64),
     "batch64_small": dict(name="batch64_mixed_40to80_n128to1024_k8to16", kind="batch", n_regs=64, small=True),
     "combined256": dict(pfsynth.COMBINED256, kind="combined", dims=(256, 256, 256)),
@@ -62,11 +62,12 @@ OPS_PER_EVAL = 27
 OPS_PER_EVAL_MODE = {"image_ncc": OPS_PER_EVAL, "mask_dice": 12, "combined": OPS_PER_EVAL + 6}
 FP32_LANES_PER_SM = 128
 
-# DRAM traffic of one measurement launch from an ncu capture (profiles/), with
-# the hash of the kernel source it was taken on; reported as null once the
-# kernel changes.
-NCU_TRAFFIC = {"measure_code_sha1": "61cff5f9de83cd7024fefa688a46cd4454d28356",
-               "bytes_per_launch": 36115712}   # the ncu capture summarised under profiles/
+# Counters of one measurement launch from an ncu capture of each workload
+# (summarised under profiles/), keyed by workload and tied to the hash of the
+# kernel source they were taken on: DRAM bytes (read + write) per launch and
+# L2 -> L1 bytes per visited evaluation.  A workload without its own capture,
+# or whose kernel changed since, reports null.
+NCU_COUNTERS = {}
 
 
 # the measurement kernel's translation unit (its source and the headers it includes)
@@ -89,7 +90,9 @@ def kernel_code_hash(paths):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 3; 1500 for the 64^3 mask workload, whose registration takes "
+                         "~2 ms, so that the clock sampler sees the timed region)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="image224")
@@ -103,7 +106,10 @@ def parse():
     ap.add_argument("--cpu-sample-iters", type=int, default=None,
                     help="oracle sample: iterations (default: 2, or all of the 64^3 mask workload's)")
     ap.add_argument("--cpu-all-cores-particles", type=int, default=512)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:   # the oracle arm's steps are bounded samples: 3 by default everywhere
+        args.steps = WORKLOADS[args.workload].get("default_steps", 3) if args.impl == "ours" else 3
+    return args
 
 
 def dist_info():
@@ -207,6 +213,26 @@ def measured_peaks():
             return json.load(f)
     except (OSError, ValueError):
         return {}
+
+
+def l2_read_peak(pk, torch, dev, stream):
+    """L2 -> SM read bandwidth (GB/s) measured with the library's probe: a
+    48 MiB buffer (resident in the 129 MB L2) read 20 times with 16-byte loads
+    that bypass L1, timed with CUDA events on the launching stream."""
+    buf = torch.ones(48 << 20, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    reps = 20
+    pk.pf_probe_read(buf, 2, sink, stream=stream)            # warm-up: brings the buffer into L2
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pk.pf_probe_read(buf, reps, sink, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        gbs = buf.numel() * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+        best = gbs if best is None else max(best, gbs)
+    return best
 
 
 def load_workload(name, rank):
@@ -392,6 +418,8 @@ def run_ours(args, rank, world, local):
     for i in range(args.warmup):
         step(i, False)
     torch.cuda.synchronize()
+    l2_peak = l2_read_peak(pk, torch, dev, stream)
+    torch.cuda.synchronize()
     gpu_id = local
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -426,7 +454,9 @@ def run_ours(args, rank, world, local):
     ops = OPS_PER_EVAL_MODE[kind]
     achieved = rec["evals"] * ops / meas_s if meas_s > 0 else 0.0
     sha = kernel_code_hash(MEASURE_SOURCES)
-    traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["measure_code_sha1"] == sha else None
+    ncu = NCU_COUNTERS.get(args.workload)
+    ncu = ncu if ncu and ncu["measure_code_sha1"] == sha else None
+    traffic = ncu["dram_bytes_per_launch"] if ncu else None
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "TOP/s",
                 "frac": achieved / peak_ops if peak_ops else None, "traffic": traffic,
                 "kernel": {"image_ncc": "k_measure<image>", "mask_dice": "k_measure<mask>",
@@ -435,6 +465,18 @@ def run_ours(args, rank, world, local):
                 "avg_launch_ms": rec["measure_ms"] / max(rec["measure_launches"], 1),
                 "share_of_step": rec["measure_ms"] / sum(step_ms),
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} fp32 lanes x {mhz:.0f} MHz (median SM clock sampled during the timed steps)"}
+    # the L2 roof of the same kernel: L2 -> L1 bytes per visited evaluation
+    # (ncu capture of this workload and kernel) x the live evaluation rate,
+    # against the L2 read bandwidth the probe measured on this GPU
+    l2_bpe = ncu["l2_to_l1_bytes_per_eval"] if ncu else None
+    l2_ach = l2_bpe * rec["evals"] / meas_s / 1e9 if (l2_bpe and meas_s > 0) else None
+    roofline["l2"] = {"achieved": l2_ach, "peak": l2_peak, "unit": "GB/s",
+                      "frac": l2_ach / l2_peak if (l2_ach and l2_peak) else None,
+                      "bytes_per_eval": l2_bpe,
+                      "peak_basis": "pf_probe_read: 48 MiB L2-resident buffer, 16-byte loads bypassing L1, "
+                                    "best of 3 x 20 passes (CUDA events)",
+                      "bytes_basis": "ncu l1tex__m_xbar2l1tex_read_bytes.sum / visited evaluations of one launch "
+                                     "of this workload (null without a capture of the current kernel)"}
 
     # the sequence warp: algorithmic bytes (each frame read once, each output
     # written once) against the measured HBM copy rate

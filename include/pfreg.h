@@ -6,7 +6,7 @@
  * rigid transform that aligns a source volume or binary mask with a target
  * (Eq. 1, Sec. 3.1), and the warp of every frame of the source sequence by
  * the estimate (Abstract; Sec. 3.3).  Each particle is a 6-DOF pose
- * [rx, ry, rz, tx, ty, tz] (radians, voxels; Eq. 3) drawn within the given
+ * [rx, ry, rz, tx, ty, tz] (radians, world units; Eq. 3) drawn within the given
  * rotation and translation limits; every iteration runs the cycle of the
  * Fig. 1 caption: prediction (perturbation), measurement (each particle's
  * transform warps the source into the target grid and a similarity is
@@ -14,11 +14,16 @@
  *
  * Conventions
  *   Volumes: uint8, x fastest, index = x + X*(y + Y*z); dims = {X, Y, Z},
- *   each >= 2 and <= 2048.  A grid's origin is the world position of voxel
- *   (0,0,0) in voxel units (spacing 1).  A pose maps target voxel p to the
- *   source continuous index q = R (p + o_T - c) + c + t - o_S with
- *   R = Rz(rz) Rx(rx) Ry(ry) and c = o_S + (dims_S - 1)/2 the source centre.
- *   Masks: nonzero voxels are 1.
+ *   each >= 2 and <= 2048.  Every grid carries an origin o (the world
+ *   position of voxel (0,0,0)) and a voxel size s per axis (spacing; Table 1
+ *   lists anisotropic ones), both in world units (mm; spacing 1 makes world
+ *   units voxels).  Voxel p of a grid sits at o + s * p.  Translations and
+ *   their limits are in the same world units, rotations in radians.  A pose
+ *   maps target voxel p to the source continuous index
+ *     q = (R (o_T + s_T * p - c) + c + t - o_S) / s_S
+ *   (element-wise products and quotients by the spacings) with
+ *   R = Rz(rz) Rx(rx) Ry(ry) and c = o_S + s_S * (dims_S - 1)/2 the world
+ *   position of the source centre.  Masks: nonzero voxels are 1.
  *
  * Errors: every call returns PF_OK (0) or a negative PF_E* code and never
  * aborts; pf_last_error() gives the calling thread's last message.
@@ -39,6 +44,8 @@ extern "C" {
 #define PF_EINVAL (-1)   /* bad argument: NULL, dims, limits, sizes, non-finite values */
 #define PF_ENOMEM (-2)   /* a device or pinned-host allocation failed */
 #define PF_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define PF_ETIMEOUT (-4) /* a bounded device-side wait gave up (the tensor-core kernels'
+                            mbarrier waits; the registration kernels wait on nothing) */
 #define PF_ESTATE (-5)   /* call not valid in the context's current state */
 
 typedef struct pf_ctx pf_ctx;
@@ -277,11 +284,14 @@ int pf_measure_matrices(pf_ctx *ctx, const float *mats, int32_t M, const float a
  * PF_EINVAL.  It calls no cudaMalloc or cudaFree: the uploaded matrices and
  * the moment accumulators live in one fixed library-wide device array
  * (PF_NOALLOC_MAX_MATRICES x 144 bytes, 576 KiB) that every GPU loading the
- * library holds until the process exits.  The first call on a device looks up
- * that array's device address (once per device); make that first call before
- * any CUDA stream capture.  All calls share the one array: calls that overlap
- * on the GPU (different streams or contexts at the same time) race; the
- * accumulators are cleared at the start of every call.  Synchronous. */
+ * library holds until the process exits.  The device the context was created
+ * on must be the calling thread's current device (else PF_EINVAL, before
+ * anything is copied): the array has one copy per device.  The first call on
+ * a device looks up that array's device address (once per device); make that
+ * first call before any CUDA stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (different streams or contexts at the same
+ * time) race; the accumulators are cleared at the start of every call.
+ * Synchronous. */
 #define PF_NOALLOC_MAX_MATRICES 4096
 int pf_measure_matrices_noalloc(pf_ctx *ctx, const float *mats, int32_t M, const float a[3],
                                 uint64_t *moments_out);
@@ -353,7 +363,10 @@ int pf_nn_conv3d_backward_weights(const uint16_t *x, int32_t batch, int32_t D, i
 
 /* *gave_up = 1 when a tensor-core kernel's bounded wait on an mbarrier ran
  * out since the last clear (its tile was then not written); clear != 0
- * resets the flag.  Synchronous. */
+ * resets the flag.  Synchronous.  The synchronous proposal calls
+ * (pf_proposal_train with loss_out, pf_proposal_predict,
+ * pf_proposal_backward) check the same flag when they finish: if it is set
+ * they return PF_ETIMEOUT and clear it. */
 int pf_nn_status(int32_t clear, int32_t *gave_up);
 
 /* Failure-detection self-test (no counterpart in the paper): launches one
@@ -426,6 +439,21 @@ int pf_proposal_input(pf_proposal *p, const pf_volume *src, const pf_volume *tgt
 /* Number of this library's kernels launched in this process so far (each
  * graph replay counts its kernels). */
 uint64_t pf_kernel_launches(void);
+
+/* Read-bandwidth probe (no counterpart in the paper; the L2 roof the
+ * measurement's gathers are reported against): launches one kernel that reads
+ * the device buffer buf (16-byte aligned, `bytes` a multiple of 16) `reps`
+ * times with 16-byte loads that bypass L1, so every byte comes from L2 when
+ * the buffer fits there (from HBM otherwise).  The caller times it with CUDA
+ * events on `stream`; bytes * reps were read.  sink: one device uint64 the
+ * kernel may write (it keeps the loads).  Asynchronous.
+ * Errors: PF_EINVAL (NULL, size, alignment, reps outside [1, 100000]), PF_ECUDA. */
+int pf_probe_read(const void *buf, int64_t bytes, int32_t reps, uint64_t *sink, void *stream);
+
+/* Number of device allocations (cudaMalloc / cudaMallocAsync calls that
+ * succeeded) this library has made in this process so far; a test hook that
+ * shows which calls allocate (no counterpart in the paper). */
+uint64_t pf_debug_device_allocs(void);
 
 /* The calling thread's last error message ("" if none). */
 const char *pf_last_error(void);

@@ -27,7 +27,7 @@ __all__ = [
     "warp_sequence", "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
     "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_kernel_launches", "pf_last_error",
     "pf_profile_begin", "pf_profile_end", "register_sequence", "pf_measure_matrices_noalloc",
-    "pf_step_measure", "pf_step_update", "pf_moments_device",
+    "pf_step_measure", "pf_step_update", "pf_moments_device", "pf_debug_device_allocs", "pf_probe_read",
     "Batch", "pf_batch_create", "pf_batch_step", "pf_batch_run", "pf_batch_destroy",
     "Registration", "MODES", "build", "library_path",
 ]
@@ -35,7 +35,7 @@ __all__ = [
 PF_MASK_DICE, PF_MASK_NCC, PF_IMAGE_NCC, PF_COMBINED = 0, 1, 2, 3
 MODES = {"mask_dice": 0, "mask_ncc": 1, "image_ncc": 2, "combined": 3}
 MOM_STRIDE = 12   # [n S1 S2lo S2hi ST T1 T2 0 | n_nn A B C]
-_ERRORS = {-1: "PF_EINVAL", -2: "PF_ENOMEM", -3: "PF_ECUDA", -5: "PF_ESTATE"}
+_ERRORS = {-1: "PF_EINVAL", -2: "PF_ENOMEM", -3: "PF_ECUDA", -4: "PF_ETIMEOUT", -5: "PF_ESTATE"}
 
 
 class PfError(RuntimeError):
@@ -113,6 +113,10 @@ def _declare(L):
     L.pf_moments_device.argtypes = [vp, vp, vp]
     L.pf_kernel_launches.argtypes = []
     L.pf_kernel_launches.restype = u64
+    L.pf_debug_device_allocs.argtypes = []
+    L.pf_debug_device_allocs.restype = u64
+    L.pf_probe_read.argtypes = [vp, C.c_int64, i32, vp, vp]
+    L.pf_probe_read.restype = C.c_int
     L.pf_last_error.argtypes = []
     L.pf_last_error.restype = C.c_char_p
     L.pf_nn_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -393,6 +397,18 @@ def pf_profile_end(ctx):
 
 def pf_kernel_launches() -> int:
     return int(load().pf_kernel_launches())
+
+
+def pf_debug_device_allocs() -> int:
+    """Device allocations the library has made in this process (test hook)."""
+    return int(load().pf_debug_device_allocs())
+
+
+def pf_probe_read(buf, reps, sink, stream=None):
+    """Launch the read-bandwidth probe over the device tensor ``buf`` (L1
+    bypassed); the caller times it.  ``sink``: a device uint64/int64 tensor."""
+    _check(load().pf_probe_read(_ptr(buf), int(buf.numel() * buf.element_size()), int(reps), _ptr(sink),
+                                _stream_handle(stream)))
 
 
 class Registration:

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpfreg.so")
-SOURCES = ["api.cu", "measure.cu", "filter.cu", "warp.cu", "noalloc.cu", "nn.cu", "proposal.cu"]
+SOURCES = ["api.cu", "measure.cu", "filter.cu", "warp.cu", "noalloc.cu", "nn.cu", "proposal.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-I" + INCLUDE]

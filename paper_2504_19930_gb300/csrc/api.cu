@@ -172,7 +172,7 @@ struct pf_ctx {
         const long long cap = g_alloc_limit.load();
         if (cap > 0 && alloc_bytes + (long long)bytes > cap) return cudaErrorMemoryAllocation;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, bytes);
+        cudaError_t e = dev_malloc(&q, bytes);
         if (e == cudaSuccess) {
             allocs.push_back(q);
             alloc_bytes += (long long)bytes;
@@ -202,8 +202,8 @@ int ensure_scratch(pf_ctx *c, int M) {
     c->x_mats = nullptr;
     c->x_mom = nullptr;
     c->x_cap = 0;
-    CU(cudaMalloc(&c->x_mats, sizeof(float) * 12 * (size_t)M));
-    CU(cudaMalloc(&c->x_mom, sizeof(unsigned long long) * kMomStride * (size_t)M));
+    CU(dev_malloc(&c->x_mats, sizeof(float) * 12 * (size_t)M));
+    CU(dev_malloc(&c->x_mom, sizeof(unsigned long long) * kMomStride * (size_t)M));
     c->x_cap = M;
     return PF_OK;
 }
@@ -398,6 +398,8 @@ const char *pf_last_error(void) { return g_err.c_str(); }
 
 uint64_t pf_kernel_launches(void) { return launches(); }
 
+uint64_t pf_debug_device_allocs(void) { return device_allocs(); }
+
 int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, const pf_volume *src_mask,
                      const pf_volume *tgt_mask, const pf_config *cfg, void *cuda_stream) {
     if (!out) return fail(PF_EINVAL, "out is NULL");
@@ -491,7 +493,7 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
         CK(c->alloc(&c->tgt_img, nt));
         const uint8_t *sp = static_cast<const uint8_t *>(src->data);
         if (!src->is_device) {
-            CK(cudaMallocAsync(&raw, ns, c->stream));
+            CK(dev_malloc_async(&raw, ns, c->stream));
             CK(copy_in(raw, src, ns, c->stream));
             sp = raw;
         }
@@ -789,7 +791,7 @@ int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float s
     const int32_t td[3] = {2, 2, 2};
     const Geometry g = make_geometry(src_dims, src_origin, src_spacing, td, tgt_origin, tgt_spacing);
     float *d = nullptr;
-    CU(cudaMalloc(&d, sizeof(float) * 18));
+    CU(dev_malloc(&d, sizeof(float) * 18));
     cudaError_t e = cudaMemcpy(d, pose, sizeof(float) * 6, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_pose_matrix(d, g, d + 6, nullptr);
     if (e == cudaSuccess) e = cudaMemcpy(mat_out, d + 6, sizeof(float) * 12, cudaMemcpyDeviceToHost);
@@ -803,7 +805,7 @@ int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
     if (!ctr || !key || !out) return fail(PF_EINVAL, "NULL argument");
     uint32_t h[6] = {ctr[0], ctr[1], ctr[2], ctr[3], key[0], key[1]};
     uint32_t *d = nullptr;
-    CU(cudaMalloc(&d, sizeof(uint32_t) * 10));
+    CU(dev_malloc(&d, sizeof(uint32_t) * 10));
     cudaError_t e = cudaMemcpy(d, h, sizeof h, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = launch_philox(d, d + 6, nullptr);
     if (e == cudaSuccess) e = cudaMemcpy(out, d + 6, sizeof(uint32_t) * 4, cudaMemcpyDeviceToHost);
@@ -851,12 +853,13 @@ int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32
 namespace pfreg {
 
 // Measurement set-up of a context, for entry points defined in other files.
-int ctx_measure_setup(pf_ctx *c, MeasureArgs *ma, bool *img, bool *mask, cudaStream_t *stream) {
+int ctx_measure_setup(pf_ctx *c, MeasureArgs *ma, bool *img, bool *mask, cudaStream_t *stream, int *device) {
     if (!c) return fail(PF_EINVAL, "ctx is NULL");
     *ma = c->MA;
     *img = c->img;
     *mask = c->mask;
     *stream = c->stream;
+    *device = c->device;
     return PF_OK;
 }
 
@@ -1049,11 +1052,11 @@ int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_
         b->poffs_h.push_back(b->poffs_h.back() + c->P.N);
         b->poffs32_h.push_back(b->poffs32_h.back() + (c->P.N + 31) / 32 * 32);
     }
-    BK(cudaMalloc(&b->regs, sizeof(BatchReg) * n));
-    BK(cudaMalloc(&b->lists, sizeof(int32_t) * (size_t)n + 4));
-    BK(cudaMalloc(&b->offs, sizeof(long long) * (size_t)(n + 3)));
-    BK(cudaMalloc(&b->poffs, sizeof(long long) * (size_t)(n + 1)));
-    BK(cudaMalloc(&b->poffs32, sizeof(long long) * (size_t)(n + 1)));
+    BK(dev_malloc(&b->regs, sizeof(BatchReg) * n));
+    BK(dev_malloc(&b->lists, sizeof(int32_t) * (size_t)n + 4));
+    BK(dev_malloc(&b->offs, sizeof(long long) * (size_t)(n + 3)));
+    BK(dev_malloc(&b->poffs, sizeof(long long) * (size_t)(n + 1)));
+    BK(dev_malloc(&b->poffs32, sizeof(long long) * (size_t)(n + 1)));
     BK(cudaMemcpy(b->regs, regs.data(), sizeof(BatchReg) * n, cudaMemcpyHostToDevice));
     BK(cudaMemcpy(b->poffs, b->poffs_h.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));
     BK(cudaMemcpy(b->poffs32, b->poffs32_h.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice));

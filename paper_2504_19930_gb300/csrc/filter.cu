@@ -559,6 +559,21 @@ void count_launches(uint64_t n) {
 }
 uint64_t launches() { return g_launches.load(std::memory_order_relaxed); }
 
+// Every device allocation the library makes goes through these two calls,
+// which count the successful ones process-wide (pf_debug_device_allocs).
+static std::atomic<uint64_t> g_device_allocs{0};
+cudaError_t dev_malloc_bytes(void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_device_allocs.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+cudaError_t dev_malloc_async_bytes(void **p, size_t bytes, cudaStream_t s) {
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) g_device_allocs.fetch_add(1, std::memory_order_relaxed);
+    return e;
+}
+uint64_t device_allocs() { return g_device_allocs.load(std::memory_order_relaxed); }
+
 cudaError_t launch_init_particles(const FilterParams &p, const FilterBuffers &b, cudaStream_t s) {
     k_init<<<blocks_for(p.N, 256), 256, 0, s>>>(p, b.poses);
     count_launches(1);

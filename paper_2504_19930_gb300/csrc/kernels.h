@@ -134,4 +134,18 @@ bool capturing();
 void count_launches(uint64_t n);
 uint64_t launches();
 
+// Device allocations: every cudaMalloc / cudaMallocAsync of the library goes
+// through these, which count the successful ones process-wide.
+cudaError_t dev_malloc_bytes(void **p, size_t bytes);
+cudaError_t dev_malloc_async_bytes(void **p, size_t bytes, cudaStream_t s);
+template <class T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
+template <class T>
+cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t s) {
+    return dev_malloc_async_bytes(reinterpret_cast<void **>(p), bytes, s);
+}
+uint64_t device_allocs();
+
 }  // namespace pfreg

@@ -17,7 +17,7 @@
 
 namespace pfreg {
 // Measurement set-up of a context (defined with the context in api.cu).
-int ctx_measure_setup(pf_ctx *c, MeasureArgs *ma, bool *img, bool *mask, cudaStream_t *stream);
+int ctx_measure_setup(pf_ctx *c, MeasureArgs *ma, bool *img, bool *mask, cudaStream_t *stream, int *device);
 int set_error(int code, const char *msg);
 }  // namespace pfreg
 
@@ -36,21 +36,19 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 // In host code g_noalloc_scratch names a host-side stand-in, not device
-// memory; the device address is looked up once per device (with that device
-// current) and cached here.
+// memory.  Its device address differs per device; it is looked up once per
+// device, with that device current (the caller has checked that the
+// context's device is the current one), and cached here.
 constexpr int kMaxDevices = 256;
 std::mutex g_mu;
 NoAllocScratch *g_scratch_addr[kMaxDevices] = {};
 
-int scratch_for_current_device(NoAllocScratch **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_error(PF_ECUDA, cudaGetErrorString(e));
+int scratch_for_device(int dev, NoAllocScratch **out) {
     if (dev < 0 || dev >= kMaxDevices) return set_error(PF_EINVAL, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return set_error(PF_ECUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
         g_scratch_addr[dev] = static_cast<NoAllocScratch *>(p);
     }
@@ -81,10 +79,19 @@ extern "C" int pf_measure_matrices_noalloc(pf_ctx *c, const float *mats, int32_t
     MeasureArgs ma;
     bool img = false, mask = false;
     cudaStream_t s = nullptr;
-    int rc = ctx_measure_setup(c, &ma, &img, &mask, &s);
+    int ctx_dev = -1;
+    int rc = ctx_measure_setup(c, &ma, &img, &mask, &s, &ctx_dev);
     if (rc) return rc;
+    // The scratch is per device and the context's stream belongs to its
+    // device: the symbol address is only valid with that device current.
+    int cur = -1;
+    const cudaError_t ed = cudaGetDevice(&cur);
+    if (ed != cudaSuccess) return set_error(PF_ECUDA, cudaGetErrorString(ed));
+    if (cur != ctx_dev)
+        return set_error(PF_EINVAL, "the current device is not the context's device: make the device the context "
+                                    "was created on current (cudaSetDevice) before calling");
     NoAllocScratch *scr = nullptr;
-    if ((rc = scratch_for_current_device(&scr))) return rc;
+    if ((rc = scratch_for_device(ctx_dev, &scr))) return rc;
     cudaError_t e = cudaMemcpyAsync(scr->mats, mats, sizeof(float) * 12 * (size_t)M, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(scr->mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)M, s);
     if (e == cudaSuccess) {

@@ -55,6 +55,17 @@ int cuda_fail(cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
     } while (0)
 
+// After a synchronising call: a tensor-core kernel whose bounded mbarrier
+// wait ran out left its tile unwritten.  Report that as PF_ETIMEOUT (and
+// clear the flag, so that the next call starts clean).
+int check_waits() {
+    unsigned int f = 0;
+    CUP(nn_error_flag(&f, false));
+    if (!f) return PF_OK;
+    CUP(nn_error_flag(&f, true));
+    return set_error(PF_ETIMEOUT, "a tensor-core kernel's bounded wait ran out; its output tile was not written");
+}
+
 // Rows of a conv's implicit GEMM must stay within int32, and D must halve.
 int check_conv(int batch, int D, int Cin) {
     if (batch < 1 || D < 2 || (D & 1) || D > 512) return set_error(PF_EINVAL, "conv: batch >= 1, D even in [2, 512]");
@@ -134,7 +145,7 @@ struct pf_proposal {
     template <class T>
     cudaError_t alloc(T **p, size_t count) {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
+        cudaError_t e = dev_malloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 1);
         if (e == cudaSuccess) {
             allocs.push_back(q);
             *p = static_cast<T *>(q);
@@ -167,7 +178,7 @@ int copy_volume_to_device(const pf_volume *v, const uint8_t **dev, uint8_t **own
         *dev = static_cast<const uint8_t *>(v->data);
         return PF_OK;
     }
-    CUP(cudaMallocAsync(owned, n, s));
+    CUP(dev_malloc_async(owned, n, s));
     CUP(cudaMemcpyAsync(*owned, v->data, n, cudaMemcpyHostToDevice, s));
     *dev = *owned;
     return PF_OK;
@@ -265,7 +276,7 @@ int pf_proposal_train(pf_proposal *p, int32_t n_steps, int32_t batch, float lr, 
     const int need = step0 + n_steps;
     if (need > p->loss_cap) {
         float *nl = nullptr;
-        CUP(cudaMalloc(&nl, sizeof(float) * (size_t)need));
+        CUP(dev_malloc(&nl, sizeof(float) * (size_t)need));
         CUP(cudaMemsetAsync(nl, 0, sizeof(float) * (size_t)need, s));
         if (p->loss_log && step0 > 0) CUP(cudaMemcpyAsync(nl, p->loss_log, sizeof(float) * step0, cudaMemcpyDeviceToDevice, s));
         CUP(cudaStreamSynchronize(s));
@@ -312,6 +323,7 @@ int pf_proposal_train(pf_proposal *p, int32_t n_steps, int32_t batch, float lr, 
     if (loss_out) {
         CUP(cudaMemcpyAsync(loss_out, p->loss_log + step0, sizeof(float) * (size_t)n_steps, cudaMemcpyDeviceToHost, s));
         CUP(cudaStreamSynchronize(s));
+        return check_waits();
     }
     return PF_OK;
 }
@@ -342,6 +354,7 @@ int pf_proposal_predict(pf_proposal *p, const pf_volume *src, const pf_volume *t
     if (rc) return rc;
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return cuda_fail(e, "proposal forward");
+    if ((rc = check_waits())) return rc;
     for (int d = 0; d < 6; ++d) {
         const float unit = d < 3 ? p->rot_lim : p->trans_lim;
         mean_out[d] = out[d] * unit;
@@ -384,12 +397,12 @@ int pf_proposal_backward(pf_proposal *p, const float *y, int32_t batch, float *l
     CUP(cudaMemcpyAsync(p->n.y, y, sizeof(float) * (size_t)batch * 6, cudaMemcpyDeviceToDevice, s));
     // the loss of this call goes to a scratch slot: the log entry of the current step
     float *scratch = nullptr;
-    CUP(cudaMallocAsync(&scratch, sizeof(float), s));
+    CUP(dev_malloc_async(&scratch, sizeof(float), s));
     CUP(cudaMemsetAsync(scratch, 0, sizeof(float), s));
     NetPtrs n = p->n;
     n.loss = scratch;
     int *zero = nullptr;
-    CUP(cudaMallocAsync(&zero, sizeof(int), s));
+    CUP(dev_malloc_async(&zero, sizeof(int), s));
     CUP(cudaMemsetAsync(zero, 0, sizeof(int), s));
     n.step = zero;
     cudaError_t e = net_backward(n, batch, s);
@@ -401,7 +414,7 @@ int pf_proposal_backward(pf_proposal *p, const float *y, int32_t batch, float *l
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return cuda_fail(e, "proposal backward");
     if (loss_out) *loss_out = l;
-    return PF_OK;
+    return check_waits();
 }
 
 int pf_proposal_synth(pf_proposal *p, int32_t batch, uint64_t seed, int32_t step, const int32_t vol_dims[3],

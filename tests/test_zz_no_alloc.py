@@ -2,14 +2,16 @@
 cannot allocate device memory while they run (a loop that must not stall on
 the allocator or fail midway, or a fixed memory budget after start-up).
 
-Its output must equal pf_measure_matrices' output bit for bit (the tolerance
-the other moment tests use), on consecutive calls that share the fixed
-scratch array, and it must reject batches larger than that array.  This file
-sorts last so a run that stops at the first failure has run every other test.
+Its output must equal pf_measure_matrices' output and the oracle's moments
+bit for bit (the tolerance the other moment tests use), on consecutive calls
+that share the fixed scratch array; it must make no device allocation, and it
+must reject batches larger than that array.  This file sorts last so a run
+that stops at the first failure has run every other test.
 """
 import numpy as np
 import pytest
 
+import oracle as orc
 import pfsynth
 
 pytestmark = pytest.mark.gpu
@@ -53,12 +55,34 @@ def test_noalloc_matches_allocating_entry_point(pk, mode):
         want_a = pk.pf_measure_matrices(reg.ctx, mats_a, a)
         want_b = pk.pf_measure_matrices(reg.ctx, mats_b, a)
         got_a1 = pk.pf_measure_matrices_noalloc(reg.ctx, mats_a, a)
+        allocs = pk.pf_debug_device_allocs()
         got_a2 = pk.pf_measure_matrices_noalloc(reg.ctx, mats_a, a)      # second call, same scratch
         got_b = pk.pf_measure_matrices_noalloc(reg.ctx, mats_b, a)       # fewer matrices after more
+        assert pk.pf_debug_device_allocs() == allocs, "the no-alloc entry point allocated device memory"
         assert np.any(want_a != 0)
         assert np.array_equal(got_a1, want_a)
         assert np.array_equal(got_a2, want_a)
         assert np.array_equal(got_b, want_b)
+    # the moments themselves, against the oracle (not only against the other entry point)
+    if mode in ("image_ncc", "combined"):
+        assert np.array_equal(got_a2[:, 0:7], orc.measure_image(img_s, img_t, mats_a, a))
+        assert np.array_equal(got_b[:, 0:7], orc.measure_image(img_s, img_t, mats_b, a))
+    if mode in ("mask_dice", "combined"):
+        assert np.array_equal(got_a2[:, 8:12], orc.measure_mask(msk_s, msk_t, mats_a, a))
+        assert np.array_equal(got_b[:, 8:12], orc.measure_mask(msk_s, msk_t, mats_b, a))
+
+
+def test_allocating_calls_are_counted(pk):
+    """The allocation counter the no-alloc test relies on does see allocations:
+    the allocating entry point grows its scratch for a larger batch."""
+    import torch
+    v = torch.from_numpy(pfsynth.random_mask(8, (12, 11, 10), 0.4)).cuda()
+    with pk.Registration("mask_dice", src_mask=v, tgt_mask=v, n_particles=4) as reg:
+        eye = np.array([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0], np.float32)
+        pk.pf_measure_matrices(reg.ctx, np.tile(eye, (2, 1)), np.zeros(3, np.float32))
+        before = pk.pf_debug_device_allocs()
+        pk.pf_measure_matrices(reg.ctx, np.tile(eye, (64, 1)), np.zeros(3, np.float32))
+        assert pk.pf_debug_device_allocs() > before
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch(pk):
