@@ -450,6 +450,18 @@ uint64_t pf_kernel_launches(void);
  * Errors: PF_EINVAL (NULL, size, alignment, reps outside [1, 100000]), PF_ECUDA. */
 int pf_probe_read(const void *buf, int64_t bytes, int32_t reps, uint64_t *sink, void *stream);
 
+/* Bounds checks of the debug build (no counterpart in the paper).  The
+ * library built with -DPF_DEBUG=1 (libpfreg_debug.so) checks every gather
+ * index of the measurement and warp kernels against its buffer before the
+ * load; an index outside is counted, the first one is kept and the load is
+ * skipped (the value reads 0) -- nothing traps, the context stays usable.
+ * Synchronises the device, then *checks_on = 1 in the debug build (0 in the
+ * release build, where *hits is always 0), *hits = out-of-bounds indices seen
+ * since the last clear, *first_bad = the first of them (an element index of
+ * the buffer).  clear != 0 resets the counters.  Errors: PF_EINVAL (NULL),
+ * PF_ECUDA. */
+int pf_debug_bounds(int32_t clear, int32_t *checks_on, uint64_t *hits, int64_t *first_bad);
+
 /* Number of device allocations (cudaMalloc / cudaMallocAsync calls that
  * succeeded) this library has made in this process so far; a test hook that
  * shows which calls allocate (no counterpart in the paper). */

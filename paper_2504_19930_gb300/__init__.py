@@ -18,8 +18,13 @@ import threading
 
 import numpy as np
 
-from ._build import LIB as _LIB_PATH
+from ._build import LIB as _LIB_RELEASE
+from ._build import LIB_DEBUG as _LIB_DEBUG
 from ._build import build as _build_lib
+
+# PFREG_DEBUG=1 loads the bounds-checked build (libpfreg_debug.so) instead.
+_DEBUG = os.environ.get("PFREG_DEBUG", "0") == "1"
+_LIB_PATH = _LIB_DEBUG if _DEBUG else _LIB_RELEASE
 
 __all__ = [
     "PF_MASK_DICE", "PF_MASK_NCC", "PF_IMAGE_NCC", "PF_COMBINED", "PfError", "load",
@@ -27,7 +32,7 @@ __all__ = [
     "warp_sequence", "pf_get_iteration", "pf_get_state", "pf_set_state", "pf_get_log",
     "pf_measure_matrices", "pf_pose_matrix", "pf_philox", "pf_kernel_launches", "pf_last_error",
     "pf_profile_begin", "pf_profile_end", "register_sequence", "pf_measure_matrices_noalloc",
-    "pf_step_measure", "pf_step_update", "pf_moments_device", "pf_debug_device_allocs", "pf_probe_read",
+    "pf_step_measure", "pf_step_update", "pf_moments_device", "pf_debug_device_allocs", "pf_probe_read", "pf_debug_bounds",
     "Batch", "pf_batch_create", "pf_batch_step", "pf_batch_run", "pf_batch_destroy",
     "Registration", "MODES", "build", "library_path",
 ]
@@ -65,8 +70,11 @@ def library_path() -> str:
     return _LIB_PATH
 
 
-def build(force: bool = False) -> str:
-    return _build_lib(force=force)
+def build(force: bool = False, debug: bool = None) -> str:
+    """Build the release library (and the debug one when debug is True or the
+    process runs with PFREG_DEBUG=1); returns the path this process loads."""
+    _build_lib(force=force, debug=_DEBUG if debug is None else debug)
+    return _LIB_PATH
 
 
 def load():
@@ -76,7 +84,7 @@ def load():
         if _lib is None:
             if not os.path.exists(_LIB_PATH):
                 raise RuntimeError(
-                    f"libpfreg.so not found at {_LIB_PATH}; build it with "
+                    f"{os.path.basename(_LIB_PATH)} not found at {_LIB_PATH}; build it with "
                     "`python -c 'import __graft_entry__ as g; g.build()'`")
             L = C.CDLL(_LIB_PATH)
             _declare(L)
@@ -117,6 +125,8 @@ def _declare(L):
     L.pf_debug_device_allocs.restype = u64
     L.pf_probe_read.argtypes = [vp, C.c_int64, i32, vp, vp]
     L.pf_probe_read.restype = C.c_int
+    L.pf_debug_bounds.argtypes = [i32, vp, vp, vp]
+    L.pf_debug_bounds.restype = C.c_int
     L.pf_last_error.argtypes = []
     L.pf_last_error.restype = C.c_char_p
     L.pf_nn_gemm_bf16.argtypes = [vp, vp, vp, i32, i32, vp]
@@ -409,6 +419,14 @@ def pf_probe_read(buf, reps, sink, stream=None):
     bypassed); the caller times it.  ``sink``: a device uint64/int64 tensor."""
     _check(load().pf_probe_read(_ptr(buf), int(buf.numel() * buf.element_size()), int(reps), _ptr(sink),
                                 _stream_handle(stream)))
+
+
+def pf_debug_bounds(clear=True):
+    """(checks_on, hits, first_bad) of the debug build's gather bounds checks
+    (synchronises the device; checks_on is False in the release build)."""
+    on, hits, first = C.c_int32(0), C.c_uint64(0), C.c_int64(0)
+    _check(load().pf_debug_bounds(1 if clear else 0, C.byref(on), C.byref(hits), C.byref(first)))
+    return bool(on.value), int(hits.value), int(first.value)
 
 
 class Registration:

@@ -14,10 +14,23 @@
 #include <atomic>
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/pfreg.h"
 #include "kernels.h"
 
 using namespace pfreg;
+
+namespace {
+// NVTX range around a host call (shows the library's steps on a profiler's
+// timeline; costs nothing when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -400,8 +413,23 @@ uint64_t pf_kernel_launches(void) { return launches(); }
 
 uint64_t pf_debug_device_allocs(void) { return device_allocs(); }
 
+int pf_debug_bounds(int32_t clear, int32_t *checks_on, uint64_t *hits, int64_t *first_bad) {
+    if (!checks_on || !hits || !first_bad) return fail(PF_EINVAL, "NULL argument");
+    CU(cudaDeviceSynchronize());
+    unsigned long long h1 = 0, h2 = 0;
+    long long f1 = 0, f2 = 0;
+    bool on1 = false, on2 = false;
+    CU(measure_debug_bounds(clear != 0, &h1, &f1, &on1));
+    CU(warp_debug_bounds(clear != 0, &h2, &f2, &on2));
+    *checks_on = (on1 && on2) ? 1 : 0;
+    *hits = h1 + h2;
+    *first_bad = h1 ? f1 : f2;
+    return PF_OK;
+}
+
 int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, const pf_volume *src_mask,
                      const pf_volume *tgt_mask, const pf_config *cfg, void *cuda_stream) {
+    NvtxRange nvtx("pf_register_init");
     if (!out) return fail(PF_EINVAL, "out is NULL");
     *out = nullptr;
     int rc = check_config(cfg);
@@ -576,6 +604,7 @@ int pf_seed_gaussian(pf_ctx *c, const float mean[6], const float std[6]) {
 }
 
 int pf_step(pf_ctx *c, int32_t n_iters) {
+    NvtxRange nvtx("pf_step");
     if (!c) return fail(PF_EINVAL, "ctx is NULL");
     if (n_iters < 0) return fail(PF_EINVAL, "n_iters < 0");
     for (int32_t i = 0; i < n_iters; ++i) {
@@ -597,6 +626,7 @@ int pf_step(pf_ctx *c, int32_t n_iters) {
 }
 
 int pf_step_measure(pf_ctx *c, int32_t p_begin, int32_t p_end) {
+    NvtxRange nvtx("pf_step_measure");
     if (!c) return fail(PF_EINVAL, "ctx is NULL");
     if (p_begin < 0 || p_end < p_begin || p_end > c->P.N)
         return fail(PF_EINVAL, "slice [%d, %d) outside [0, %d]", p_begin, p_end, c->P.N);
@@ -612,6 +642,7 @@ int pf_step_measure(pf_ctx *c, int32_t p_begin, int32_t p_end) {
 }
 
 int pf_step_update(pf_ctx *c) {
+    NvtxRange nvtx("pf_step_update");
     if (!c) return fail(PF_EINVAL, "ctx is NULL");
     CU(launch_finalise(c->P, c->B, c->stream));
     if (c->trace) {
@@ -673,6 +704,7 @@ int pf_get_iteration(pf_ctx *c, int32_t *k_out) {
 }
 
 int pf_estimate(pf_ctx *c, float pose_out[6], double *score_out) {
+    NvtxRange nvtx("pf_estimate");
     if (!c || !pose_out) return fail(PF_EINVAL, "NULL argument");
     int32_t k = 0;
     int rc = pf_get_iteration(c, &k);
@@ -818,6 +850,7 @@ int warp_sequence(const uint8_t *const *frames_in, int32_t n_frames, const int32
                   const float src_origin[3], const float src_spacing[3], uint8_t *const *frames_out,
                   const int32_t tgt_dims[3], const float tgt_origin[3], const float tgt_spacing[3],
                   const float pose[6], int32_t interp, void *cuda_stream) {
+    NvtxRange nvtx("warp_sequence");
     if (!frames_in || !frames_out || !src_dims || !src_origin || !tgt_dims || !tgt_origin || !pose)
         return fail(PF_EINVAL, "NULL argument");
     if (n_frames < 0) return fail(PF_EINVAL, "n_frames < 0");
@@ -1139,6 +1172,7 @@ int pf_tile_shape(pf_ctx *c, int32_t *rows_per_item, int32_t *items_per_warp) {
 }
 
 int pf_batch_step(pf_batch *b, int32_t n_iters) {
+    NvtxRange nvtx("pf_batch_step");
     if (!b) return fail(PF_EINVAL, "batch is NULL");
     if (n_iters < 0) return fail(PF_EINVAL, "n_iters < 0");
     for (int32_t i = 0; i < n_iters; ++i) {

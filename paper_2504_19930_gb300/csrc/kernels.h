@@ -100,6 +100,12 @@ struct WarpFrames {
 cudaError_t launch_warp(const WarpFrames &f, int n, const float pose[6], Geometry g, int interp,
                         cudaStream_t s);
 
+// Bounds checks of the debug build (-DPF_DEBUG=1) of the measurement and warp
+// kernels: out-of-bounds gather indices seen (the load was skipped), the first
+// bad index, whether the checks are compiled in; clear resets the counters.
+cudaError_t measure_debug_bounds(bool clear, unsigned long long *hits, long long *first, bool *on);
+cudaError_t warp_debug_bounds(bool clear, unsigned long long *hits, long long *first, bool *on);
+
 // One registration of a batch (device table entry): its measurement
 // arguments, filter parameters and buffers, and its iteration count.
 struct BatchReg {

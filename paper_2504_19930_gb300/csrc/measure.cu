@@ -20,11 +20,30 @@
 // exact integers, so the atomics give order-free, deterministic bits.
 // Mask mode (nearest neighbour): counts n, A, B, C; the source mask is one
 // bit per voxel, in shared memory when it fits.
+//
+// Debug build (-DPF_DEBUG=1): every gather index is checked against its
+// buffer before the load; an index outside sets a device flag, records the
+// first bad index and skips the load (the value reads 0) -- nothing traps.
 #include "kernels.h"
+
+#ifndef PF_DEBUG
+#define PF_DEBUG 0
+#endif
 
 namespace pfreg {
 
 namespace {
+
+#if PF_DEBUG
+__device__ unsigned long long g_dbg_hits;
+__device__ long long g_dbg_first;
+// true when idx < limit; otherwise counts the hit, keeps the first bad index
+__device__ __forceinline__ bool dbg_ok(unsigned long long idx, unsigned long long limit) {
+    if (idx < limit) return true;
+    if (atomicAdd(&g_dbg_hits, 1ull) == 0ull) g_dbg_first = (long long)idx;
+    return false;
+}
+#endif
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
@@ -173,7 +192,12 @@ __device__ __forceinline__ void mask_voxel(const MeasureArgs &a, const uint32_t 
     if (valid) {
         const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
         const uint32_t si = int_of(floorf(hx)) + (uint32_t)SX * int_of(floorf(hy)) + SXY * int_of(floorf(hz));
+#if PF_DEBUG
+        const bool ok = dbg_ok(si, (unsigned long long)SXY * a.g.sd[2]);
+        const uint32_t sb = ok ? (bits[si >> 5] >> (si & 31)) & 1u : 0u;
+#else
         const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
+#endif
         const uint32_t tb = __ldg(tptr);
         ma.A += sb;
         ma.B += tb;
@@ -272,10 +296,26 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
                 i1 = in1 ? i1 : 0u;
             }
         }
+#if PF_DEBUG
+        const unsigned long long nq = (unsigned long long)SXY * SZ;
+        const unsigned long long ntgt = (unsigned long long)a.g.td[0] * a.g.td[1] * a.g.td[2];
+        const uint32_t ioff = FIDX ? kTwo23Bits : 0u;   // the fp32 index is biased by 2^23
+        const bool ok0 = dbg_ok((unsigned long long)(uint32_t)(i0 - ioff) + SXY, nq);
+        const bool ok1 = dbg_ok((unsigned long long)(uint32_t)(i1 - ioff) + SXY, nq);
+        const uint8_t *tp0 = FULL ? v.tp : a.tgt_img + v.t0;
+        const uint8_t *tp1 = FULL ? v.tp + 32 : a.tgt_img + v.t1;
+        const bool okt0 = dbg_ok((unsigned long long)(tp0 - a.tgt_img), ntgt);
+        const bool okt1 = dbg_ok((unsigned long long)(tp1 - a.tgt_img), ntgt);
+        const uint32_t w00 = ok0 ? __ldg(qbase + i0) : 0u, w01 = ok0 ? __ldg(qbase + i0 + SXY) : 0u;
+        const uint32_t w10 = ok1 ? __ldg(qbase + i1) : 0u, w11 = ok1 ? __ldg(qbase + i1 + SXY) : 0u;
+        const uint32_t t0 = okt0 ? __ldg(tp0) : 0u;
+        const uint32_t t1 = okt1 ? __ldg(tp1) : 0u;
+#else
         const uint32_t w00 = __ldg(qbase + i0), w01 = __ldg(qbase + i0 + SXY);
         const uint32_t w10 = __ldg(qbase + i1), w11 = __ldg(qbase + i1 + SXY);
         const uint32_t t0 = FULL ? __ldg(v.tp) : __ldg(a.tgt_img + v.t0);
         const uint32_t t1 = FULL ? __ldg(v.tp + 32) : __ldg(a.tgt_img + v.t1);
+#endif
         const f2 c00 = lerp2_biased(pair(byte_biased(w00, 0), byte_biased(w10, 0)),
                                     pair(byte_biased(w00, 1), byte_biased(w10, 1)), fx);
         const f2 c10 = lerp2_biased(pair(byte_biased(w00, 2), byte_biased(w10, 2)),
@@ -316,11 +356,21 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const f2 byn = addrm2(add2(qy, splat(0.5f)), splat(kTwo23));
         const f2 bzn = addrm2(add2(qz, splat(0.5f)), splat(kTwo23));
         const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY);
+#if PF_DEBUG
+        const unsigned long long nvx = (unsigned long long)SXY * a.g.sd[2];
+        const unsigned long long ntm = (unsigned long long)a.g.td[0] * a.g.td[1] * a.g.td[2];
+#endif
         if (valid0) {
             const uint32_t si = __float_as_uint(bxn.x) + (uint32_t)SX * __float_as_uint(byn.x) +
                                 SXY * __float_as_uint(bzn.x) + bias;
+#if PF_DEBUG
+            const uint8_t *tq = FULL ? tm : a.tgt_mask + v.t0;
+            const uint32_t sb = dbg_ok(si, nvx) ? (bits[si >> 5] >> (si & 31)) & 1u : 0u;
+            const uint32_t tb = dbg_ok((unsigned long long)(tq - a.tgt_mask), ntm) ? __ldg(tq) : 0u;
+#else
             const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
             const uint32_t tb = __ldg(FULL ? tm : a.tgt_mask + v.t0);
+#endif
             ma.A += sb;
             ma.B += tb;
             ma.C += sb & tb;
@@ -328,8 +378,14 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         if (valid1) {
             const uint32_t si = __float_as_uint(bxn.y) + (uint32_t)SX * __float_as_uint(byn.y) +
                                 SXY * __float_as_uint(bzn.y) + bias;
+#if PF_DEBUG
+            const uint8_t *tq = FULL ? tm + 32 : a.tgt_mask + v.t1;
+            const uint32_t sb = dbg_ok(si, nvx) ? (bits[si >> 5] >> (si & 31)) & 1u : 0u;
+            const uint32_t tb = dbg_ok((unsigned long long)(tq - a.tgt_mask), ntm) ? __ldg(tq) : 0u;
+#else
             const uint32_t sb = (bits[si >> 5] >> (si & 31)) & 1u;
             const uint32_t tb = __ldg(FULL ? tm + 32 : a.tgt_mask + v.t1);
+#endif
             ma.A += sb;
             ma.B += tb;
             ma.C += sb & tb;
@@ -933,6 +989,28 @@ cudaError_t launch_measure(const MeasureArgs &a, bool img, bool mask, cudaStream
                          : launch_tab<true, false, false, false>(a, xtab, ctab, smem_bits, s);
     return smem ? launch_tab<false, true, true, false>(a, xtab, ctab, smem_bits, s)
                 : launch_tab<false, true, false, false>(a, xtab, ctab, smem_bits, s);
+}
+
+// Bounds-check counters of the debug build (all zero otherwise).
+cudaError_t measure_debug_bounds(bool clear, unsigned long long *hits, long long *first, bool *on) {
+#if PF_DEBUG
+    *on = true;
+    cudaError_t e = cudaMemcpyFromSymbol(hits, g_dbg_hits, sizeof *hits);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(first, g_dbg_first, sizeof *first);
+    if (e == cudaSuccess && clear) {
+        const unsigned long long z = 0;
+        const long long zf = 0;
+        e = cudaMemcpyToSymbol(g_dbg_hits, &z, sizeof z);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_dbg_first, &zf, sizeof zf);
+    }
+    return e;
+#else
+    *on = false;
+    *hits = 0;
+    *first = 0;
+    (void)clear;
+    return cudaSuccess;
+#endif
 }
 
 }  // namespace pfreg

@@ -9,15 +9,34 @@
 // first builds the pose's matrix in shared memory (six lanes take the fp64
 // sin/cos in parallel), so a launch covers up to 64 frames with one pose
 // passed by value.
+//
+// Debug build (-DPF_DEBUG=1): every gather index is checked against the
+// frame before the load; an index outside sets a device flag, records the
+// first bad index and skips the load (the voxel reads 0) -- nothing traps.
 #include <type_traits>
 
 #include "kernels.h"
+
+#ifndef PF_DEBUG
+#define PF_DEBUG 0
+#endif
 
 namespace pfreg {
 
 namespace {
 
 constexpr int kWarpThreads = 256;
+
+#if PF_DEBUG
+__device__ unsigned long long g_wdbg_hits;
+__device__ long long g_wdbg_first;
+// true when idx < limit; otherwise counts the hit, keeps the first bad index
+__device__ __forceinline__ bool wdbg_ok(unsigned long long idx, unsigned long long limit) {
+    if (idx < limit) return true;
+    if (atomicAdd(&g_wdbg_hits, 1ull) == 0ull) g_wdbg_first = (long long)idx;
+    return false;
+}
+#endif
 
 struct WarpArgs {
     WarpFrames f;
@@ -47,8 +66,11 @@ __device__ __forceinline__ uint8_t warp_voxel(const uint8_t *__restrict__ S, con
         const float hx = __fadd_rn(qx, 0.5f), hy = __fadd_rn(qy, 0.5f), hz = __fadd_rn(qz, 0.5f);
         if (!(hx >= 0.0f && hx < (float)SX && hy >= 0.0f && hy < (float)SY && hz >= 0.0f && hz < (float)SZ))
             return 0;
-        return __ldg(S + (idx_t)uint_of(floorf(hx)) + sx * (idx_t)uint_of(floorf(hy)) +
-                     sxy * (idx_t)uint_of(floorf(hz)));
+        const idx_t i = (idx_t)uint_of(floorf(hx)) + sx * (idx_t)uint_of(floorf(hy)) + sxy * (idx_t)uint_of(floorf(hz));
+#if PF_DEBUG
+        if (!wdbg_ok((unsigned long long)i, (unsigned long long)sxy * (unsigned long long)SZ)) return 0;
+#endif
+        return __ldg(S + i);
     }
     if (!(qx >= 0.0f && qx <= (float)(SX - 1) && qy >= 0.0f && qy <= (float)(SY - 1) && qz >= 0.0f &&
           qz <= (float)(SZ - 1)))
@@ -57,7 +79,12 @@ __device__ __forceinline__ uint8_t warp_voxel(const uint8_t *__restrict__ S, con
     const float fy0 = fminf(floorf(qy), (float)(SY - 2));
     const float fz0 = fminf(floorf(qz), (float)(SZ - 2));
     const float fx = __fsub_rn(qx, fx0), fy = __fsub_rn(qy, fy0), fz = __fsub_rn(qz, fz0);
-    const uint8_t *p = S + (idx_t)uint_of(fx0) + sx * (idx_t)uint_of(fy0) + sxy * (idx_t)uint_of(fz0);
+    const idx_t i0 = (idx_t)uint_of(fx0) + sx * (idx_t)uint_of(fy0) + sxy * (idx_t)uint_of(fz0);
+#if PF_DEBUG
+    // the farthest corner read is i0 + sxy + sx + 1
+    if (!wdbg_ok((unsigned long long)i0 + sxy + sx + 1, (unsigned long long)sxy * (unsigned long long)SZ)) return 0;
+#endif
+    const uint8_t *p = S + i0;
     const float v000 = __ldg(p), v100 = __ldg(p + 1);
     const float v010 = __ldg(p + sx), v110 = __ldg(p + sx + 1);
     const float v001 = __ldg(p + sxy), v101 = __ldg(p + sxy + 1);
@@ -141,6 +168,28 @@ cudaError_t launch_warp(const WarpFrames &f, int n, const float pose[6], Geometr
         k_warp<false><<<(unsigned)grid, kWarpThreads, 0, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
+}
+
+// Bounds-check counters of the debug build (all zero otherwise).
+cudaError_t warp_debug_bounds(bool clear, unsigned long long *hits, long long *first, bool *on) {
+#if PF_DEBUG
+    *on = true;
+    cudaError_t e = cudaMemcpyFromSymbol(hits, g_wdbg_hits, sizeof *hits);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(first, g_wdbg_first, sizeof *first);
+    if (e == cudaSuccess && clear) {
+        const unsigned long long z = 0;
+        const long long zf = 0;
+        e = cudaMemcpyToSymbol(g_wdbg_hits, &z, sizeof z);
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_wdbg_first, &zf, sizeof zf);
+    }
+    return e;
+#else
+    *on = false;
+    *hits = 0;
+    *first = 0;
+    (void)clear;
+    return cudaSuccess;
+#endif
 }
 
 }  // namespace pfreg

@@ -18,3 +18,16 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(autouse=True)
+def _bounds_checked(request):
+    """Under PFREG_DEBUG=1 (the bounds-checked library) every GPU test must
+    end with no out-of-bounds gather index recorded by the kernels."""
+    yield
+    if os.environ.get("PFREG_DEBUG") != "1" or request.node.get_closest_marker("gpu") is None:
+        return
+    import paper_2504_19930_gb300 as pk
+    on, hits, first = pk.pf_debug_bounds(clear=True)
+    assert on, "PFREG_DEBUG=1 but the loaded library has no bounds checks"
+    assert hits == 0, f"{hits} out-of-bounds gather indices (first: {first})"

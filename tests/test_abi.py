@@ -110,7 +110,7 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     import paper_2504_19930_gb300 as pk
     monkeypatch.setattr(pk, "_LIB_PATH", str(tmp_path / "missing.so"))
     monkeypatch.setattr(pk, "_lib", None)
-    with pytest.raises(RuntimeError, match="libpfreg.so not found"):
+    with pytest.raises(RuntimeError, match="missing.so not found at"):
         pk.load()
 
 

@@ -102,12 +102,14 @@ def test_pose_matrix_bit_exact(pk, orc):
 
 # ------------------------------------------------------------- measurement
 
-def _measure_ctx(pk, mode, src, tgt, N=1):
+def _measure_ctx(pk, mode, src, tgt, N=1, src_mask=None, tgt_mask=None):
     s, t = _cuda(src), _cuda(tgt)
     if mode == "image_ncc":
         return pk.Registration(mode, src=s, tgt=t, n_particles=N)
     if mode == "combined":
-        return pk.Registration(mode, src=s, tgt=t, src_mask=s, tgt_mask=t, n_particles=N)
+        sm = s if src_mask is None else _cuda(src_mask)
+        tm = t if tgt_mask is None else _cuda(tgt_mask)
+        return pk.Registration(mode, src=s, tgt=t, src_mask=sm, tgt_mask=tm, n_particles=N)
     return pk.Registration(mode, src_mask=s, tgt_mask=t, n_particles=N)
 
 
@@ -167,6 +169,62 @@ def test_measure_random_poses_bit_exact(pk, orc, mode, sdims, tdims):
         for i in range(len(mats)):
             s = orc.ncc2_from_moments(got[i, 0:7])
             assert abs(s - f64[i]) <= NCC_RTOL * f64[i], (i, s, f64[i])
+
+
+@pytest.mark.parametrize("mode,sdims,tdims,P", [
+    # combined mode with masks drawn independently of the image (not image != 0)
+    ("combined", (44, 39, 31), (41, 35, 30), 40),
+    # targets of 64 x 40 rows = 80 work items per particle, more than the 64 a
+    # CTA takes, so the CTA shares two x-product tables (the per-CTA form) and
+    # CTAs straddle two particles; P = 37 leaves the last CTA partial
+    ("combined", (50, 46, 40), (41, 64, 40), 37),           # mask bits in shared memory
+    ("mask_dice", (130, 118, 97), (41, 64, 40), 37),        # mask bits too large: read from L2
+    ("combined", (130, 118, 97), (41, 64, 40), 37),
+])
+def test_measure_independent_masks_and_cta_tables_bit_exact(pk, orc, mode, sdims, tdims, P):
+    src_m, tgt_m = pfsynth.random_mask(21, sdims, 0.45), pfsynth.random_mask(22, tdims, 0.45)
+    src_i, tgt_i = pfsynth.random_image(23, sdims), pfsynth.random_image(24, tdims)
+    so = np.array([1.0, -2.0, 0.5], np.float32)
+    to = np.array([-3.0, 2.0, 1.0], np.float32)
+    rng = np.random.default_rng(31)
+    poses = np.concatenate([rng.uniform(-0.6, 0.6, (P, 3)), rng.uniform(-9, 9, (P, 3))], 1).astype(np.float32)
+    mats, a = orc.pose_matrices(poses.T, sdims, so, to)
+    if mode == "combined":
+        with _measure_ctx(pk, mode, src_i, tgt_i, src_mask=src_m, tgt_mask=tgt_m) as reg:
+            got = reg.measure(mats, a)
+        assert np.array_equal(got[:, 0:7], orc.measure_image(src_i, tgt_i, mats, a))
+    else:
+        with _measure_ctx(pk, mode, src_m, tgt_m) as reg:
+            got = reg.measure(mats, a)
+    want = orc.measure_mask(src_m, tgt_m, mats, a)
+    assert np.array_equal(got[:, 8:12], want)
+    # the masks are not trivially full: the counts carry information
+    assert np.all(want[:, 1] <= want[:, 0]) and np.any(want[:, 1] < want[:, 0]) and np.any(want[:, 3] < want[:, 1])
+
+
+def test_image_source_beyond_2p23_voxels_bit_exact(pk, orc):
+    """A source of more than 2^23 voxels (256 x 256 x 160): the kernel forms
+    the quad index with integer arithmetic instead of fp32 (exact only below
+    2^24).  The target sits near the source's far corner, so the indices
+    themselves exceed 2^23 (every sample at z >= 128)."""
+    sdims, tdims = (256, 256, 160), (60, 50, 40)
+    assert np.prod(sdims) > (1 << 23)
+    src, tgt = pfsynth.random_image(51, sdims, smooth=False), pfsynth.random_image(52, tdims)
+    so = np.zeros(3, np.float32)
+    to = np.array([150.0, 180.0, 110.0], np.float32)
+    rng = np.random.default_rng(53)
+    poses = np.concatenate([rng.uniform(-0.4, 0.4, (24, 3)), rng.uniform(-10, 10, (24, 3))], 1).astype(np.float32)
+    mats, a = orc.pose_matrices(poses.T, sdims, so, to)
+    with _measure_ctx(pk, "image_ncc", src, tgt) as reg:
+        got = reg.measure(mats, a)
+    want = orc.measure_image(src, tgt, mats, a)
+    assert np.array_equal(got[:, 0:7], want)
+    assert np.all(want[:, 0] > 0)
+    # samples come from source planes z >= 128, whose voxel indices exceed 2^23
+    corners = np.array([[x, y, z] for x in (0, tdims[0] - 1) for y in (0, tdims[1] - 1)
+                        for z in (0, tdims[2] - 1)], np.float64) - a
+    qz = corners @ mats[:, 8:11].T.astype(np.float64) + mats[:, 11]
+    assert np.any((qz >= 129) & (qz <= sdims[2] - 1))
 
 
 def test_measure_degenerate_cases(pk, orc):
@@ -258,18 +316,22 @@ def test_mask64_full_registration_bit_exact(pk, orc):
 
 
 def test_image224_full_size_sampled(pk, orc):
-    """The image-based workload at full size (224x208x176 speckle, N=2048):
-    two iterations on the GPU; the oracle checks sampled particles' moments and
-    re-runs every cheap step (score, weights, resampling, prediction) on the
-    GPU's own state, bit for bit."""
+    """The image-based workload at full size and in the launch configuration
+    the bench times (224x208x176 speckle, N=2048, all 50 iterations, tuned
+    tile shape): every cheap step (score, weights, resampling, prediction) is
+    recomputed by the oracle on the GPU's own state at every iteration, bit
+    for bit; at k = 0 and at the last iteration 32 sampled particles are
+    re-measured by the oracle (spawned processes), moments bit for bit and
+    NCC^2 within 1e-5 of the fp64 oracle."""
+    from tests.oracle_pool import measure_image_parallel
     c = pfsynth.IMAGE224
-    pair = pfsynth.cached(pfsynth.speckle_pair, 0)
-    N, lr, lt, seed = c["n_particles"], np.deg2rad(c["rot_limit_deg"]), c["trans_limit"], c["seed"]
+    pair = pfsynth.cached(pfsynth.speckle_pair, 0, with_masks=True)
+    N, K, lr, lt, seed = c["n_particles"], c["n_iters"], np.deg2rad(c["rot_limit_deg"]), c["trans_limit"], c["seed"]
     lim = np.array([lr] * 3 + [lt] * 3, np.float32)
     nmin = int(float(np.float32(0.01)) * pair.tgt.size)
-    with _reg(pk, "image_ncc", pair, N, lr, lt, seed) as reg:
+    with _reg(pk, "image_ncc", pair, N, lr, lt, seed, autotune=True) as reg:
         prev_next = None
-        for k in range(2):
+        for k in range(K):
             reg.step(1)
             st = reg.state()
             x = st["poses_measured"]
@@ -277,12 +339,13 @@ def test_image224_full_size_sampled(pk, orc):
                 assert np.array_equal(x, orc.init_particles(N, seed, lim))
             else:
                 assert np.array_equal(x, orc.perturb(prev_next, seed, k, orc.sigma(0.25, 0.8, k, lim), lim))
-            sample = np.random.default_rng(k).choice(N, 3, replace=False)
-            mats, a = orc.pose_matrices(x[:, sample], pair.src_dims, pair.src_origin, pair.tgt_origin)
-            assert np.array_equal(st["moments"][sample, 0:7], orc.measure_image(pair.src, pair.tgt, mats, a))
-            f64 = orc.ncc2_f64(pair.src, pair.tgt, mats, a)
-            for j, i in enumerate(sample):
-                assert abs(st["scores"][i] - f64[j]) <= NCC_RTOL * f64[j]
+            if k in (0, K - 1):
+                sample = np.sort(np.random.default_rng(k).choice(N, 32, replace=False))
+                mats, a = orc.pose_matrices(x[:, sample], pair.src_dims, pair.src_origin, pair.tgt_origin)
+                mom, f64 = measure_image_parallel(pair.src, pair.tgt, mats, a)
+                assert np.array_equal(st["moments"][sample, 0:7], mom), f"moments differ at k={k}"
+                for j, i in enumerate(sample):
+                    assert abs(st["scores"][i] - f64[j]) <= NCC_RTOL * f64[j], (k, i)
             s = np.array([orc.score("image_ncc", m, 0, nmin) for m in st["moments"]])
             assert np.array_equal(st["scores"], s)
             W = orc.weights(s, 5)
@@ -295,6 +358,19 @@ def test_image224_full_size_sampled(pk, orc):
             assert log_evals[-1] == int(st["moments"][:, 0].sum())
             assert np.all(np.abs(log_est[-1] - est) <= np.array([ROT_TOL] * 3 + [TRANS_TOL] * 3))
             prev_next = st["poses_next"]
+
+
+def test_image224_small_cloud_trajectory_bit_exact(pk, orc):
+    """The whole filter on the full 224x208x176 pair against the oracle's own
+    run (N = 64, 3 iterations, +-30 deg / +-25 voxels, tuned tile shape):
+    particles, moments, scores, weights and resampled indices bit for bit at
+    every iteration, the estimate within 1e-4 rad / 1e-3 voxel."""
+    c = pfsynth.IMAGE224
+    pair = pfsynth.cached(pfsynth.speckle_pair, 0, with_masks=True)
+    N, K, lr, lt, seed = 64, 3, np.deg2rad(c["rot_limit_deg"]), c["trans_limit"], c["seed"]
+    ref = _oracle_run(orc, "image_ncc", pair, N, K, lr, lt, seed)
+    with _reg(pk, "image_ncc", pair, N, lr, lt, seed, autotune=True) as reg:
+        _assert_trajectory(reg, ref, K)
 
 
 # ------------------------------------------------------------------- warp

@@ -180,3 +180,23 @@ def test_checkpoint_round_trip_and_continued_training(torch_, pk):
         a.train(1, batch=4, lr=1e-3, data_seed=3, vol_dims=DIMS, rot_limit=ROT / 2, trans_limit=TRANS)
     with pytest.raises(pk.PfError):
         a.train(1, batch=5, lr=1e-3, data_seed=3, vol_dims=DIMS, rot_limit=ROT, trans_limit=TRANS)
+
+
+def test_gave_up_wait_is_returned_as_timeout(torch_, pk):
+    """A bounded device wait that ran out is reported by the next synchronous
+    proposal call as PF_ETIMEOUT (and the flag is cleared): the self-test
+    kernel waits on an mbarrier nothing arrives on, gives up and sets the flag
+    -- nothing faults or hangs."""
+    torch = torch_
+    net = pk.Proposal(max_batch=2, seed=5)
+    x, y = _batch(torch, pk, net, 2)
+    out = torch.zeros((2, 12), dtype=torch.float32, device="cuda")
+    net.forward(x, out)
+    assert pk.nn_status(clear=True) == 0
+    pk.nn_wait_selftest()
+    with pytest.raises(pk.PfError) as err:
+        net.backward(y)
+    assert err.value.code == -4 and "PF_ETIMEOUT" in str(err.value)
+    assert pk.nn_status(clear=False) == 0        # cleared by the call that reported it
+    assert np.isfinite(net.backward(y))          # the next call succeeds
+    net.close()
