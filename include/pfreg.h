@@ -436,6 +436,18 @@ int pf_proposal_synth(pf_proposal *p, int32_t batch, uint64_t seed, int32_t step
                       float rot_limit, float trans_limit, uint16_t *x_out, float *y_out);
 int pf_proposal_input(pf_proposal *p, const pf_volume *src, const pf_volume *tgt, uint16_t *x_out);
 
+/* Test export: copy one of the network's device tensors of the last forward /
+ * backward pass to host memory (host_out), for layer-by-layer checks:
+ *   which 0..3   conv layer l's output after ReLU, a_l, bf16 bits [batch][(32 >> l)^3][32];
+ *   which 4..7   the gradient with respect to conv layer (which - 4)'s
+ *                pre-activation, d_l, bf16 bits, same shape;
+ *   which 8 / 10 the hidden layer's output h / the gradient dh with respect
+ *                to its pre-activation, fp32 [batch][128];
+ *   which 9 / 11 the output (mean, log-variance) / the loss gradient with
+ *                respect to it, fp32 [batch][12].
+ * Synchronous.  Errors: PF_EINVAL (NULL, which, batch outside [1, max_batch]), PF_ECUDA. */
+int pf_proposal_tensor(pf_proposal *p, int32_t which, int32_t batch, void *host_out);
+
 /* Number of this library's kernels launched in this process so far (each
  * graph replay counts its kernels). */
 uint64_t pf_kernel_launches(void);

@@ -148,10 +148,12 @@ def _declare(L):
     L.pf_proposal_backward.argtypes = [vp, vp, i32, vp]
     L.pf_proposal_synth.argtypes = [vp, i32, u64, i32, vp, C.c_float, C.c_float, vp, vp]
     L.pf_proposal_input.argtypes = [vp, C.POINTER(pf_volume), C.POINTER(pf_volume), vp]
+    L.pf_proposal_tensor.argtypes = [vp, i32, i32, vp]
     for name in ("pf_nn_gemm_bf16", "pf_nn_conv3d_forward", "pf_nn_conv3d_backward_data",
                  "pf_nn_conv3d_backward_weights", "pf_nn_status", "pf_seed_gaussian", "pf_proposal_create",
                  "pf_proposal_destroy", "pf_proposal_train", "pf_proposal_predict", "pf_proposal_params",
                  "pf_proposal_forward", "pf_proposal_backward", "pf_proposal_synth", "pf_proposal_input",
+                 "pf_proposal_tensor",
                  "pf_tile_shape", "pf_batch_tile_shape", "pf_debug_alloc_limit", "pf_nn_wait_selftest"):
         getattr(L, name).restype = C.c_int
     for name in ("pf_register_init", "pf_step", "pf_estimate", "pf_register_destroy", "warp_sequence",
@@ -737,6 +739,20 @@ class Proposal:
               tgt_spacing=(1, 1, 1)):
         vs, vt = make_volume(src, src_origin, spacing=src_spacing), make_volume(tgt, tgt_origin, spacing=tgt_spacing)
         _check(load().pf_proposal_input(self.h, C.byref(vs), C.byref(vt), _ptr(x)))
+
+    def tensor(self, which, batch):
+        """Host copy of a device tensor of the last pass (pf_proposal_tensor):
+        0..3 conv outputs a_l, 4..7 pre-activation gradients d_l (bf16 bit
+        patterns, uint16), 8 h, 9 out, 10 dh, 11 dout (float32)."""
+        if 0 <= which < 8:
+            D = 64 >> ((which & 3) + 1)
+            out = np.zeros((batch, D, D, D, 32), np.uint16)
+        elif which in (8, 10):
+            out = np.zeros((batch, 128), np.float32)
+        else:
+            out = np.zeros((batch, 12), np.float32)
+        _check(load().pf_proposal_tensor(self.h, int(which), int(batch), _ptr(out)))
+        return out
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -570,6 +570,10 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     MA.rows_per_item = rows_per_item_for(g.td[0]);
     MA.n_rowblocks = (g.td[1] * g.td[2] + MA.rows_per_item - 1) / MA.rows_per_item;
     MA.items_per_warp = kDefaultItemsPerWarp;
+    MA.fdims[0] = (float)g.sd[0];
+    MA.fdims[1] = (float)((int64_t)g.sd[0] * g.sd[1]);
+    MA.fdims[2] = (float)(g.sd[1] - 2);
+    MA.fdims[3] = (float)(g.sd[2] - 2);
 
     CK(cudaMemsetAsync(B.k, 0, sizeof(int32_t), c->stream));
     CK(cudaMemsetAsync(B.mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)N, c->stream));

@@ -24,6 +24,7 @@ struct MeasureArgs {
     int rows_per_item;          // target rows per work item
     int n_rowblocks;            // ceil(rows / rows_per_item)
     int items_per_warp;         // tile shape: consecutive work items per warp (0 = default)
+    float fdims[4];             // source SX, SX * SY, SY - 2, SZ - 2 as floats (host-filled)
 };
 
 // Filter parameters shared by the per-iteration kernels.

@@ -82,6 +82,12 @@ __device__ __forceinline__ float byte_biased(uint32_t w, uint32_t k) {
 }
 
 
+// x as a float for 0 <= x < 2^23 (exact), by an integer add and an fp32
+// subtract instead of a conversion instruction.
+__device__ __forceinline__ float float_of(int x) {
+    return __fsub_rn(__uint_as_float(kTwo23Bits + (uint32_t)x), kTwo23);
+}
+
 // Integer value of an integral float v in [0, 2^22).
 __device__ __forceinline__ uint32_t int_of(float v) {
     return __float_as_uint(__fadd_rn(v, kTwo23)) - kTwo23Bits;
@@ -262,7 +268,7 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const bool in0 = IFULL || (MASK ? ivalid0 : valid0);
         const bool in1 = IFULL || (MASK ? ivalid1 : valid1);
         // base corner min(floor q, D-2) and fraction q - base
-        const float Dm2y = (float)(SY - 2), Dm2z = (float)(SZ - 2);
+        const float Dm2y = a.fdims[2], Dm2z = a.fdims[3];
         // floors by rounding 2^23 + q down, two voxels per instruction (every
         // voxel taken has q >= 0; the others get their index replaced below);
         // bx = 2^23 + floor(qx) is also the biased x term of the quad index
@@ -276,7 +282,7 @@ __device__ __forceinline__ void eval_pair(const MeasureArgs &a, const uint32_t *
         const uint32_t *qbase;
         uint32_t i0, i1;
         if (FIDX) {
-            const f2 w = fma2(splat((float)SXY), flz, fma2(splat((float)SX), fly, bx));
+            const f2 w = fma2(splat(a.fdims[1]), flz, fma2(splat(a.fdims[0]), fly, bx));
             i0 = __float_as_uint(w.x);
             i1 = __float_as_uint(w.y);
             qbase = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(a.src_quad) -
@@ -582,7 +588,7 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
         float K0 = __shfl_sync(0xffffffffu, myK0, j0), K1 = __shfl_sync(0xffffffffu, myK1, j0),
               K2 = __shfl_sync(0xffffffffu, myK2, j0);
         uint32_t trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
-        float xf = (float)(pos + lane);
+        float xf = float_of(pos + lane);
         uint32_t toff = trow0 + (uint32_t)(pos + lane);
         bool nc0 = IMG && ((noclamp >> j0) & 1u);   // row j0 needs no y/z clamp
         for (;;) {
@@ -629,7 +635,7 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
             const int x1 = in1a ? pos + e1 : (ok1 ? xb1 + e1 - len0 : 0);
             const bool iv0 = ok0 && (in0a ? x0 >= ib0 && x0 < ie0 : x0 >= ib1 && x0 < ie1);
             const bool iv1 = ok1 && (in1a ? x1 >= ib0 && x1 < ie0 : x1 >= ib1 && x1 < ie1);
-            const PairIn v{pair((float)x0, (float)x1), x0, x1, pair(in0a ? K0 : L0, in1a ? K0 : L0),
+            const PairIn v{pair(float_of(x0), float_of(x1)), x0, x1, pair(in0a ? K0 : L0, in1a ? K0 : L0),
                            pair(in0a ? K1 : L1, in1a ? K1 : L1), pair(in0a ? K2 : L2, in1a ? K2 : L2),
                            (in0a || !ok0 ? trow0 : trow1) + (uint32_t)x0,
                            (in1a || !ok1 ? trow0 : trow1) + (uint32_t)x1, nullptr, nullptr};
@@ -673,7 +679,7 @@ __device__ __forceinline__ void measure_item(const MeasureArgs &a, const uint32_
                 trow0 = (uint32_t)(first + j0) * (uint32_t)TX;
                 nc0 = IMG && ((noclamp >> j0) & 1u);
             }
-            xf = (float)(pos + lane);
+            xf = float_of(pos + lane);
             toff = trow0 + (uint32_t)(pos + lane);
         }
         if (IMG) {

@@ -417,6 +417,30 @@ int pf_proposal_backward(pf_proposal *p, const float *y, int32_t batch, float *l
     return check_waits();
 }
 
+int pf_proposal_tensor(pf_proposal *p, int32_t which, int32_t batch, void *host_out) {
+    if (!p || !host_out) return set_error(PF_EINVAL, "NULL argument");
+    if (batch < 1 || batch > p->n.max_batch) return set_error(PF_EINVAL, "batch outside [1, max_batch]");
+    const void *src = nullptr;
+    size_t bytes = 0;
+    if (which >= 0 && which < 8) {
+        const int l = which & 3;
+        const long long D = kNetG >> (l + 1);
+        src = which < 4 ? (const void *)p->n.a[l] : (const void *)p->n.d[l];
+        bytes = sizeof(uint16_t) * (size_t)batch * D * D * D * 32;
+    } else if (which == 8 || which == 10) {
+        src = which == 8 ? p->n.h : p->n.dh;
+        bytes = sizeof(float) * (size_t)batch * kNetHidden;
+    } else if (which == 9 || which == 11) {
+        src = which == 9 ? p->n.out : p->n.dout;
+        bytes = sizeof(float) * (size_t)batch * kNetOut;
+    } else {
+        return set_error(PF_EINVAL, "which outside [0, 11]");
+    }
+    CUP(cudaMemcpyAsync(host_out, src, bytes, cudaMemcpyDeviceToHost, p->stream));
+    CUP(cudaStreamSynchronize(p->stream));
+    return PF_OK;
+}
+
 int pf_proposal_synth(pf_proposal *p, int32_t batch, uint64_t seed, int32_t step, const int32_t vol_dims[3],
                       float rot_limit, float trans_limit, uint16_t *x_out, float *y_out) {
     if (!p || !vol_dims || !x_out || !y_out) return set_error(PF_EINVAL, "NULL argument");

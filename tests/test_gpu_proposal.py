@@ -200,3 +200,97 @@ def test_gave_up_wait_is_returned_as_timeout(torch_, pk):
     assert pk.nn_status(clear=False) == 0        # cleared by the call that reported it
     assert np.isfinite(net.backward(y))          # the next call succeeds
     net.close()
+
+
+U32 = 2.0 ** -23   # fp32 unit roundoff, doubled: a tensor-core accumulator need not round to nearest
+
+
+def _bf16_ok(got, ref, bound, what):
+    """got = bf16 rounding of an fp32 value within `bound` of ref."""
+    tol = 2.0 ** -8 * (np.abs(ref) + bound) + bound + 1e-30
+    err = np.abs(np.asarray(got, np.float64) - ref)
+    bad = err > tol
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} outside the bound, worst {err.max():.3g}"
+
+
+def _f32_ok(got, ref, bound, what):
+    err = np.abs(np.asarray(got, np.float64) - ref)
+    bad = err > bound + 1e-30
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} outside the bound, worst {err.max():.3g}"
+
+
+def test_backward_layer_by_layer_element_by_element(torch_, pk):
+    """Every tensor of one forward and backward pass, element by element: each
+    layer is recomputed in float64 from the GPU's own inputs to that layer
+    (so a bf16 rounding that went the other way upstream does not spread),
+    against the bound that fp32 arithmetic guarantees for it: a sum of K
+    terms accumulated in fp32, in any order, is within (K - 1) u sum|terms| of
+    the exact sum (one more u per product rounding and bias add; u = 2^-23,
+    doubled for the tensor core), and a bf16 output within half an ulp
+    (2^-8 relative) of that.  The loss gradient's bound adds the documented
+    error of __expf (2 + 1.16 |x| ulp)."""
+    torch = torch_
+    B = 2
+    net = pk.Proposal(max_batch=B, seed=9)
+    x, y = _batch(torch, pk, net, B, seed=13)
+    out_t = torch.zeros((B, 12), dtype=torch.float32, device="cuda")
+    net.forward(x, out_t)
+    net.backward(y)
+    theta, grad = net.params(with_grad=True)
+    P = onn.unpack(theta)
+    off, _ = onn.layout()
+    G = {k: np.asarray(grad[o:o + int(np.prod(sh))], np.float64).reshape(sh) for k, (o, sh) in off.items()}
+    xin = _bf16_host(torch, x).astype(np.float64)
+    yv = y.cpu().numpy().astype(np.float64)
+    a = [onn.from_bf16_bits(net.tensor(l, B)).astype(np.float64) for l in range(4)]
+    d = [onn.from_bf16_bits(net.tensor(4 + l, B)).astype(np.float64) for l in range(4)]
+    h, out, dh, dout = (net.tensor(k, B).astype(np.float64) for k in (8, 9, 10, 11))
+    ins = [xin] + a[:3]
+    Wb = [onn.bf16_round(P[f"cw{l}"].astype(np.float32)).astype(np.float64) for l in range(4)]
+
+    # forward: the four convolutions (bf16 x bf16 products are exact in fp32)
+    for l in range(4):
+        K = 64 * onn.CIN[l] + 1
+        ref = onn.relu(onn.conv3d_pre(ins[l], Wb[l], P[f"cb{l}"]))
+        bound = K * U32 * (onn.conv3d_abs_bound(ins[l], Wb[l]) + np.abs(P[f"cb{l}"]))
+        _bf16_ok(a[l], ref, bound, f"conv {l} output")
+    flat = a[3].reshape(B, -1)
+    _f32_ok(h, onn.relu(flat @ P["f1w"].T + P["f1b"]),
+            (2048 + 2) * U32 * (np.abs(flat) @ np.abs(P["f1w"]).T + np.abs(P["f1b"])), "hidden")
+    _f32_ok(out, h @ P["f2w"].T + P["f2b"], (128 + 2) * U32 * (np.abs(h) @ np.abs(P["f2w"]).T + np.abs(P["f2b"])),
+            "output")
+
+    # the loss gradient from the GPU's output
+    mu, s = out[:, :6], out[:, 6:]
+    r = yv - mu
+    e = np.exp(-s)
+    de = (2.0 + 1.16 * np.abs(s) + 2.0) * U32          # __expf, plus its argument's rounding
+    want = np.concatenate([-r * e / B, 0.5 * (1.0 - r * r * e) / B], 1)
+    bound = np.concatenate([np.abs(r * e / B) * (de + 4 * U32),
+                            0.5 * (r * r * e * (de + 4 * U32) + 4 * U32 * (1.0 + r * r * e)) / B], 1)
+    _f32_ok(dout, want, bound, "loss gradient")
+
+    # fully connected layers' gradients
+    _f32_ok(G["f2w"], dout.T @ h, (B + 1) * U32 * (np.abs(dout).T @ np.abs(h)), "fc2 weight gradient")
+    _f32_ok(G["f2b"], dout.sum(0), B * U32 * np.abs(dout).sum(0), "fc2 bias gradient")
+    _f32_ok(dh, (dout @ P["f2w"]) * (h > 0), (12 + 1) * U32 * (np.abs(dout) @ np.abs(P["f2w"])), "hidden gradient")
+    _f32_ok(G["f1w"], dh.T @ flat, (B + 1) * U32 * (np.abs(dh).T @ np.abs(flat)), "fc1 weight gradient")
+    _f32_ok(G["f1b"], dh.sum(0), B * U32 * np.abs(dh).sum(0), "fc1 bias gradient")
+    ref = ((dh @ P["f1w"]) * (flat > 0)).reshape(d[3].shape)
+    bound = ((128 + 1) * U32 * (np.abs(dh) @ np.abs(P["f1w"]))).reshape(d[3].shape)
+    _bf16_ok(d[3], ref, bound, "conv 3 pre-activation gradient")
+
+    # the convolutions' gradients, top down
+    for l in range(3, -1, -1):
+        Kw = B * (32 >> l) ** 3
+        _f32_ok(G[f"cw{l}"], onn.conv3d_backward_weights(ins[l], d[l]),
+                (Kw + 1) * U32 * onn.conv3d_backward_weights(np.abs(ins[l]), np.abs(d[l])),
+                f"conv {l} weight gradient")
+        _f32_ok(G[f"cb{l}"], d[l].reshape(-1, 32).sum(0), Kw * U32 * np.abs(d[l]).reshape(-1, 32).sum(0),
+                f"conv {l} bias gradient")
+        if l > 0:
+            D = 64 >> l
+            ref = onn.conv3d_backward_data(d[l], Wb[l], D) * (ins[l] > 0)
+            bound = (64 * 32 + 1) * U32 * onn.conv3d_backward_data(np.abs(d[l]), np.abs(Wb[l]), D)
+            _bf16_ok(d[l - 1], ref, bound, f"conv {l - 1} pre-activation gradient")
+    net.close()
