@@ -67,7 +67,16 @@ FP32_LANES_PER_SM = 128
 # kernel source they were taken on: DRAM bytes (read + write) per launch and
 # L2 -> L1 bytes per visited evaluation.  A workload without its own capture,
 # or whose kernel changed since, reports null.
-NCU_COUNTERS = {}
+NCU_COUNTERS = {
+    # profiles/measure_image224x208x176_n2048.md
+    "image224": {"measure_code_sha1": "4da90d17281f3040a9df29f4df6086daad5fa4ed",
+                 "dram_bytes_per_launch": 36267520, "l2_to_l1_bytes_per_eval": 139412340768 / 9388958565.74},
+    # profiles/measure_counters_mask64_combined256.md
+    "mask64": {"measure_code_sha1": "4da90d17281f3040a9df29f4df6086daad5fa4ed",
+               "dram_bytes_per_launch": 275968, "l2_to_l1_bytes_per_eval": 43838304 / 41168147.2},
+    "combined256": {"measure_code_sha1": "4da90d17281f3040a9df29f4df6086daad5fa4ed",
+                    "dram_bytes_per_launch": 140447588608, "l2_to_l1_bytes_per_eval": 2003333743264 / 152465706355.25},
+}
 
 
 # the measurement kernel's translation unit (its source and the headers it includes)
@@ -798,7 +807,7 @@ def conv_roofline(pk, torch, dev, stream, batch, reps=20):
     conv_flops = 2.0 * batch * (D // 2) ** 3 * 32 * 64 * 32
     peaks = measured_peaks()
     bf16_peak = peaks.get("bf16_tflops") or 1900.0
-    return {"bound": "tensor", "kernel": "k_umma_async<ConvFwdOp> (tcgen05, bf16 -> fp32)",
+    return {"bound": "tensor", "kernel": "k_conv_planes (tcgen05, bf16 -> fp32, input planes staged once by TMA)",
             "achieved": conv_flops / conv_s / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
             "frac": conv_flops / conv_s / 1e12 / bf16_peak, "traffic": None,
             "flops_per_launch": conv_flops, "avg_launch_ms": 1e3 * conv_s,

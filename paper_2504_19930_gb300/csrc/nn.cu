@@ -39,6 +39,10 @@ constexpr uint32_t kIdesc = umma::idesc_bf16_f32(kTileM, kTileN);
 
 __device__ unsigned int g_nn_error;   // set when a bounded wait gave up
 
+#ifndef PF_CONV_PLANES
+#define PF_CONV_PLANES 1   // 32-channel forward convolutions by the plane-staged kernel (conv.cu)
+#endif
+
 #ifndef PF_NN_ASYNC
 #define PF_NN_ASYNC 1   // forward / data-gradient / GEMM tiles fed by the cp.async pipeline
 #endif
@@ -995,8 +999,12 @@ cudaError_t nn_wait_selftest(cudaStream_t s) {
 }
 
 cudaError_t nn_error_flag(unsigned int *out, bool clear) {
-    cudaError_t e = cudaMemcpyFromSymbol(out, nn::g_nn_error, sizeof(unsigned int));
-    if (e != cudaSuccess || !clear) return e;
+    unsigned int conv = 0;
+    cudaError_t e = conv_planes_error_flag(&conv, clear);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, nn::g_nn_error, sizeof(unsigned int));
+    if (e != cudaSuccess) return e;
+    *out |= conv;
+    if (!clear) return e;
     const unsigned int z = 0;
     return cudaMemcpyToSymbol(nn::g_nn_error, &z, sizeof(z));
 }
@@ -1012,6 +1020,9 @@ cudaError_t nn_gemm(const uint16_t *A, const uint16_t *B, float *C, int M, int K
 
 cudaError_t nn_conv_fwd(const uint16_t *X, int batch, int D, int Cin, const uint16_t *W, const float *bias,
                         uint16_t *Y, cudaStream_t s) {
+#if PF_CONV_PLANES
+    if (conv_planes_applies(D, Cin)) return conv_planes_forward(X, batch, D, W, bias, Y, s);
+#endif
     nn::ConvFwdOp op{{batch, D, Cin}, X, W, bias, Y};
     const int Do = D / 2;
 #if PF_NN_ASYNC

@@ -59,4 +59,11 @@ struct NetPtrs {
     void *samples;                 // synthetic-pair parameters [B]
 };
 
+// The plane-staged forward convolution (conv.cu) for 32 input channels:
+// whether it applies to an input of edge D, the launch, and its error flag.
+bool conv_planes_applies(int D, int Cin);
+cudaError_t conv_planes_forward(const uint16_t *X, int batch, int D, const uint16_t *W, const float *bias,
+                                uint16_t *Y, cudaStream_t s);
+cudaError_t conv_planes_error_flag(unsigned int *out, bool clear);
+
 }  // namespace pfreg

@@ -72,7 +72,8 @@ def test_gemm_bf16(torch_, pk, M, K):
     assert np.all(err <= bound + 1e-30), f"worst {err.max():.3g}"
 
 
-@pytest.mark.parametrize("Bn,D,Cin", [(2, 10, 32), (2, 18, 2), (1, 2, 8), (4, 64, 2), (4, 32, 32)])
+@pytest.mark.parametrize("Bn,D,Cin", [(2, 10, 32), (2, 18, 2), (1, 2, 8), (4, 64, 2), (4, 32, 32), (1, 32, 32),
+                                      (2, 64, 32)])
 def test_conv_forward(torch_, pk, Bn, D, Cin):
     torch = torch_
     rng = np.random.default_rng(10 * D + Cin)
