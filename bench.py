@@ -46,7 +46,7 @@ WORKLOADS = {
     "conv32": dict(name="conv3d_b32_32x32x32x32_to_16x16x16x32_bf16", kind="conv"),
     "proposal": dict(name="proposal_speckle224x208x176_learned_n512_vs_plain_n2048_k50", kind="proposal",
                      n_particles=512, plain_particles=2048, n_iters=50, rot_limit_deg=30.0, trans_limit=25.0,
-                     seed=0, train_steps=1500, train_batch=32, lr=1e-3, std_inflate=1.5),
+                     seed=0, train_steps=3125, train_batch=32, lr=1e-3, std_inflate=1.5),
 }
 METRIC = "particle-voxel evals/s (dense N*iters*target voxels per registration) and ms per registration"
 UNIT = "particle-voxel evals/s"
@@ -106,7 +106,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="image224")
     ap.add_argument("--batch-regs", type=int, default=64)
-    ap.add_argument("--proposal-eval-pairs", type=int, default=32,
+    ap.add_argument("--proposal-eval-pairs", type=int, default=200,
                     help="held-out pairs of the learned-proposal comparison (seeds 5000 + 1000 rank + i)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -608,6 +608,17 @@ def run_ours(args, rank, world, local):
     dist.close()
 
 
+def _member_pair(spec):
+    """Pool worker: the synthetic pair of one batch member."""
+    kind, pseed, dims = spec
+    if kind == "mask_dice":
+        return pfsynth.ellipsoid_pair(pseed, src_dims=dims, tgt_dims=dims,
+                                      tgt_origin=(0.0, 0.0, float(int(0.2 * dims[2]))),
+                                      semi_axes=(0.31 * dims[0], 0.22 * dims[1], 0.22 * dims[2]),
+                                      max_trans=0.06 * min(dims))
+    return pfsynth.speckle_pair(pseed, src_dims=dims, with_masks=True)
+
+
 def batch_members(n_regs, seed, small=False):
     """The batched workload: registration r draws its grid (each axis 96..256),
     particle count {512, 1024, 4096, 8192}, iteration count 20..60 and mode
@@ -615,9 +626,10 @@ def batch_members(n_regs, seed, small=False):
     pair with its LV-cavity masks, which only the Dice trace reads), all from
     one seeded generator.  small: grids 40..80, particle counts {128, 256, 512,
     1024}, 8..16 iterations -- registrations too small to fill the GPU on
-    their own."""
+    their own.  The pairs are generated by spawned processes on the host
+    cores."""
     rng = np.random.default_rng(seed)
-    out = []
+    specs, out = [], []
     for r in range(n_regs):
         if small:
             dims = tuple(int(v) for v in rng.integers(40, 81, 3))
@@ -627,16 +639,16 @@ def batch_members(n_regs, seed, small=False):
             dims = tuple(int(v) for v in rng.integers(96, 257, 3))
             N = int(rng.choice([512, 1024, 4096, 8192]))
             K = int(rng.integers(20, 61))
-        if r % 2 == 0:
-            pair = pfsynth.cached(pfsynth.ellipsoid_pair, seed * 1000 + r, src_dims=dims, tgt_dims=dims,
-                                  tgt_origin=(0.0, 0.0, float(int(0.2 * dims[2]))),
-                                  semi_axes=(0.31 * dims[0], 0.22 * dims[1], 0.22 * dims[2]),
-                                  max_trans=0.06 * min(dims))
-            out.append(dict(mode="mask_dice", pair=pair, N=N, K=K, rot=np.deg2rad(15.0),
-                            trans=float(0.12 * min(dims))))
+        kind = "mask_dice" if r % 2 == 0 else "image_ncc"
+        specs.append((kind, seed * 1000 + r, dims))
+        if kind == "mask_dice":
+            out.append(dict(mode=kind, N=N, K=K, rot=np.deg2rad(15.0), trans=float(0.12 * min(dims))))
         else:
-            pair = pfsynth.cached(pfsynth.speckle_pair, seed * 1000 + r, src_dims=dims, with_masks=True)
-            out.append(dict(mode="image_ncc", pair=pair, N=N, K=K, rot=np.deg2rad(30.0), trans=25.0))
+            out.append(dict(mode=kind, N=N, K=K, rot=np.deg2rad(30.0), trans=25.0))
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, min(n_regs, os.cpu_count() or 1))) as pool:
+        for m, pair in zip(out, pool.map(_member_pair, specs)):
+            m["pair"] = pair
     return out
 
 
@@ -807,7 +819,7 @@ def conv_roofline(pk, torch, dev, stream, batch, reps=20):
     conv_flops = 2.0 * batch * (D // 2) ** 3 * 32 * 64 * 32
     peaks = measured_peaks()
     bf16_peak = peaks.get("bf16_tflops") or 1900.0
-    return {"bound": "tensor", "kernel": "k_conv_planes (tcgen05, bf16 -> fp32, input planes staged once by TMA)",
+    return {"bound": "tensor", "kernel": "k_conv_planes (tcgen05, bf16 -> fp32, input planes staged once in shared memory)",
             "achieved": conv_flops / conv_s / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
             "frac": conv_flops / conv_s / 1e12 / bf16_peak, "traffic": None,
             "flops_per_launch": conv_flops, "avg_launch_ms": 1e3 * conv_s,
@@ -825,12 +837,45 @@ def run_conv(args, rank, world, local):
     pk.build()
     pk.load()
     dev = torch.device("cuda", local)
-    r = conv_roofline(pk, torch, dev, torch.cuda.current_stream(), 32, reps=args.steps)
+    stream = torch.cuda.current_stream()
+    r = conv_roofline(pk, torch, dev, stream, 32, reps=args.steps)
+    grads = conv_grad_times(pk, torch, dev, stream, 32, reps=args.steps)
     if rank == 0:
         print(json.dumps({"metric": "bf16 TFLOP/s of the proposal network's 32^3 x 32 -> 16^3 x 32 convolution",
                           "value": r["achieved"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
                           "warmup": 3, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
-                          "config": {"workload": WORKLOADS["conv32"]["name"]}, "roofline": r}), flush=True)
+                          "config": {"workload": WORKLOADS["conv32"]["name"]}, "roofline": r,
+                          "gradients": grads}), flush=True)
+
+
+def conv_grad_times(pk, torch, dev, stream, batch, reps=20):
+    """The same layer's two gradients, each timed alone with CUDA events:
+    the data gradient (the 8 taps of each stride phase per input voxel) and
+    the weight gradient.  TFLOP/s counts the algorithmic products only (the
+    forward's 2 B Do^3 32 64 32 for each)."""
+    D, Do = 32, 16
+    dy = (0.1 * torch.randn((batch, Do, Do, Do, 32), device=dev)).to(torch.bfloat16)
+    wt = (0.05 * torch.randn((32, 64, 32), device=dev)).to(torch.bfloat16)
+    act = torch.randn((batch, D, D, D, 32), device=dev).relu().to(torch.bfloat16)
+    x = torch.randn((batch, D, D, D, 32), device=dev).abs().to(torch.bfloat16)
+    dx = torch.empty((batch, D, D, D, 32), dtype=torch.bfloat16, device=dev)
+    dw = torch.zeros((32, 64, 32), dtype=torch.float32, device=dev)
+    flops = 2.0 * batch * Do ** 3 * 32 * 64 * 32
+    out = {}
+    for name, fn in (("data", lambda: pk.nn_conv3d_backward_data(dy, wt, act, dx)),
+                     ("weights", lambda: pk.nn_conv3d_backward_weights(x, dy, dw))):
+        for _ in range(3):
+            fn()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(reps):
+            fn()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        assert pk.nn_status() == 0, "a tensor-core wait gave up"
+        sec = c0.elapsed_time(c1) / 1e3 / reps
+        out[name] = {"avg_launch_ms": 1e3 * sec, "tflops": flops / sec / 1e12}
+    return out
 
 
 def cpu_sample_size(args, w):
@@ -845,9 +890,8 @@ def cpu_sample_size(args, w):
 
 
 def _held_out_pair(seed):
-    """Pool worker: one held-out speckle pair with masks, into the disk cache."""
-    pfsynth.cached(pfsynth.speckle_pair, seed, with_masks=True)
-    return seed
+    """Pool worker: one held-out speckle pair with masks (returned, not cached)."""
+    return pfsynth.speckle_pair(seed, with_masks=True)
 
 
 def run_proposal(args, rank, world, local):
@@ -885,18 +929,17 @@ def run_proposal(args, rank, world, local):
 
     roofline = conv_roofline(pk, torch, dev, stream, w["train_batch"])
 
-    # --- held-out pairs (generated on the host cores by spawned processes first)
+    # --- held-out pairs, generated on the host cores by spawned processes
+    # while the GPU evaluates the previous ones
     n_eval = args.proposal_eval_pairs
     seeds = [5000 + 1000 * rank + i for i in range(n_eval)]
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(max(1, min(len(seeds), os.cpu_count() or 1))) as pool:
-        pool.map(_held_out_pair, seeds)
     rows = []
     units_learned, secs_learned = 0, 0.0
     launches0 = pk.pf_kernel_launches()
-    with ClockSampler(local) as clocks:
-        for seed in seeds:
-            pair = pfsynth.cached(pfsynth.speckle_pair, seed, with_masks=True)
+    with mp.get_context("spawn").Pool(max(1, min(len(seeds), os.cpu_count() or 1))) as pool, \
+            ClockSampler(local) as clocks:
+        for pair in pool.imap(_held_out_pair, seeds):
             vols = dict(src=torch.from_numpy(pair.src).to(dev), tgt=torch.from_numpy(pair.tgt).to(dev),
                         src_mask=torch.from_numpy(pair.src_mask).to(dev),
                         tgt_mask=torch.from_numpy(pair.tgt_mask).to(dev))

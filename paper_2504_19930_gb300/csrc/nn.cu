@@ -43,6 +43,10 @@ __device__ unsigned int g_nn_error;   // set when a bounded wait gave up
 #define PF_CONV_PLANES 1   // 32-channel forward convolutions by the plane-staged kernel (conv.cu)
 #endif
 
+#ifndef PF_DGRAD_PHASES
+#define PF_DGRAD_PHASES 1   // data gradient over the 8 taps of each stride phase (ConvDgradPhaseOp)
+#endif
+
 #ifndef PF_NN_ASYNC
 #define PF_NN_ASYNC 1   // forward / data-gradient / GEMM tiles fed by the cp.async pipeline
 #endif
@@ -364,6 +368,112 @@ struct ConvDgradOp {
             packed[i] = *reinterpret_cast<const uint32_t *>(&h);
         }
         uint4 *dst = reinterpret_cast<uint4 *>(dX + (size_t)row * 32);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+    }
+};
+
+// Data gradient by stride phases.  With stride 2, input voxel i = 2 j + p
+// (p its parity, per axis) receives only the taps k = (1 - p) + 2 t, t in
+// {0, 1}, from output o = j + p - t: 8 of the 64 taps, the same 8 for every
+// voxel of one parity class.  Rows are grouped by class (class c = pz 4 +
+// py 2 + px; within it (b, jz, jy, jx), padded to a whole number of tiles),
+// so a tile's K is 8 sub-taps x 32 co = 256 and its B operand is the class's
+// 8 weight taps: the dense form's arithmetic without its 7 zero taps in 8.
+struct ConvDgradPhaseOp {
+    ConvGeom g;             // the forward layer's geometry (input D, Cin = 32)
+    const uint16_t *dY;     // [B][Do^3][32]
+    const uint16_t *Wt;     // [32 ci][64][32 co]
+    const uint16_t *act;    // [B][D^3][32] or nullptr
+    uint16_t *dX;           // [B][D^3][32]
+    int R, Rp;              // rows per class (B Do^3) and that rounded up to whole tiles
+    __device__ int M() const { return 8 * Rp; }
+    __device__ int chunks() const { return 256 / kChunkK; }   // two sub-taps of 32 co per chunk
+    struct Row {
+        long long bbase;   // element offset of (b, 0, 0, 0) in dY
+        int z, y, x;       // j + p per axis (the output index of sub-tap t is this minus t)
+        bool live;
+    };
+    struct Vox {
+        int b, iz, iy, ix;
+        bool live;
+    };
+    __device__ Vox voxel(int r) const {
+        const int Do = g.Do();
+        const int cls = r / Rp, j = r - cls * Rp;
+        Vox v;
+        v.live = j < R;
+        const int jj = v.live ? j : 0;
+        const int jx = jj % Do, jy = (jj / Do) % Do, jz = (jj / (Do * Do)) % Do;
+        v.b = jj / (Do * Do * Do);
+        v.ix = 2 * jx + (cls & 1);
+        v.iy = 2 * jy + ((cls >> 1) & 1);
+        v.iz = 2 * jz + (cls >> 2);
+        return v;
+    }
+    __device__ Row row(int r) const {
+        const int Do = g.Do();
+        const Vox v = voxel(r);
+        Row w;
+        w.live = v.live;
+        w.bbase = (long long)v.b * Do * Do * Do * 32;
+        // j + p = (i + p) / 2 with i = 2 j + p
+        w.z = (v.iz + (v.iz & 1)) >> 1;
+        w.y = (v.iy + (v.iy & 1)) >> 1;
+        w.x = (v.ix + (v.ix & 1)) >> 1;
+        return w;
+    }
+    __device__ void issue_a(uint32_t tile, const Row &w, int c, int t) const {
+        const int Do = g.Do();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int sub = 2 * c + q;   // (tz, ty, tx) = bits 2, 1, 0
+            const int oz = w.z - (sub >> 2), oy = w.y - ((sub >> 1) & 1), ox = w.x - (sub & 1);
+            const bool ok = w.live && (unsigned)oz < (unsigned)Do && (unsigned)oy < (unsigned)Do &&
+                            (unsigned)ox < (unsigned)Do;
+            const long long e = ok ? w.bbase + (((long long)oz * Do + oy) * Do + ox) * 32 : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cp16(tile, t, 8 * (4 * q + j), dY + e + 8 * j, ok);
+        }
+    }
+    __device__ void issue_b(uint32_t tile, int c, int t) const {
+        // every row of this CTA's tile is of one class (Rp is whole tiles)
+        const int cls = (int)(((long long)blockIdx.x * kTileM) / Rp);
+        const int px = cls & 1, py = (cls >> 1) & 1, pz = cls >> 2;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const int q = t + 128 * i, n = q >> 3, j = q & 7;
+            const int sub = 2 * c + (j >> 2), co0 = 8 * (j & 3);
+            const int kz = 1 - pz + 2 * (sub >> 2), ky = 1 - py + 2 * ((sub >> 1) & 1), kx = 1 - px + 2 * (sub & 1);
+            const int tap = (kz * 4 + ky) * 4 + kx;
+            cp16(tile, n, 8 * j, Wt + (size_t)n * 2048 + tap * 32 + co0, true);
+        }
+    }
+    __device__ void epilogue(int row, const float *acc) const {
+        const Vox v = voxel(row);
+        if (row >= M() || !v.live) return;
+        const size_t vi = (((size_t)v.b * g.D + v.iz) * g.D + v.iy) * g.D + v.ix;
+        uint32_t mask[16];
+        if (act) {
+            const uint4 *a4 = reinterpret_cast<const uint4 *>(act + vi * 32);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint4 u = a4[i];
+                mask[4 * i] = u.x; mask[4 * i + 1] = u.y; mask[4 * i + 2] = u.z; mask[4 * i + 3] = u.w;
+            }
+        }
+        uint32_t packed[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            float a = acc[2 * i], b = acc[2 * i + 1];
+            if (act) {
+                a = (mask[i] & 0xFFFFu) ? a : 0.0f;
+                b = (mask[i] >> 16) ? b : 0.0f;
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            packed[i] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(dX + vi * 32);
 #pragma unroll
         for (int i = 0; i < 4; ++i) dst[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
     }
@@ -1034,6 +1144,16 @@ cudaError_t nn_conv_fwd(const uint16_t *X, int batch, int D, int Cin, const uint
 
 cudaError_t nn_conv_dgrad(const uint16_t *dY, int batch, int D, const uint16_t *Wt, const uint16_t *act,
                           uint16_t *dX, cudaStream_t s) {
+#if PF_NN_ASYNC && PF_DGRAD_PHASES
+    {
+        const int Do = D / 2;
+        const long long R = (long long)batch * Do * Do * Do;
+        const long long Rp = (R + nn::kTileM - 1) / nn::kTileM * nn::kTileM;
+        if (8 * Rp > 0x7fffffffLL) return cudaErrorInvalidValue;
+        nn::ConvDgradPhaseOp op{{batch, D, 32}, dY, Wt, act, dX, (int)R, (int)Rp};
+        return nn::launch_async(op, (int)(8 * Rp), s);
+    }
+#endif
     nn::ConvDgradOp op{{batch, D, 32}, dY, Wt, act, dX};
 #if PF_NN_ASYNC
     return nn::launch_async(op, batch * D * D * D, s);
