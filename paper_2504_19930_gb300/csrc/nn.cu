@@ -47,6 +47,10 @@ __device__ unsigned int g_nn_error;   // set when a bounded wait gave up
 #define PF_DGRAD_PHASES 1   // data gradient over the 8 taps of each stride phase (ConvDgradPhaseOp)
 #endif
 
+#ifndef PF_WGRAD_MN
+#define PF_WGRAD_MN 1   // 32-channel weight gradients by k_wgrad_mn (MN-major operands)
+#endif
+
 #ifndef PF_NN_ASYNC
 #define PF_NN_ASYNC 1   // forward / data-gradient / GEMM tiles fed by the cp.async pipeline
 #endif
@@ -732,6 +736,147 @@ cudaError_t launch_async(const Op &op, int M, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient with MN-major operands (Cin = 32).  D[(tap, ci)][co] =
+// sum_o X[2o + tap - 1][ci] dY[o][co]: in memory both operands run along
+// their M / N index (the channels of one voxel are contiguous), so they are
+// staged as MN-major tiles -- each 16-byte copy is 8 channels of one voxel,
+// one row of a core matrix of 8 positions x 8 channels -- and the MMA reads
+// them transposed (instruction-descriptor bits 15 and 16).  CTA (x, y): the
+// 4 taps x 32 channels of M tile x, positions [y per, (y + 1) per) x 64;
+// the split sums are added to dW with fp32 atomics.
+// Tile layouts (bytes): A core (m / 8, k / 8) at (m / 8) 128 + (k / 8) 2048,
+// row k % 8 at + 16 (k % 8); B core (n / 8, k / 8) at (n / 8) 128 + (k / 8) 512.
+// ---------------------------------------------------------------------------
+// Descriptor fields of an MN-major no-swizzle operand: the leading byte offset
+// is the stride between core matrices along K, the stride byte offset the
+// stride along M / N (checked on the device: one MMA of known operands is
+// exact with this assignment and wrong with the other).
+constexpr int kWgStages = 4;
+constexpr int kWgA = 128 * kChunkK * 2;   // 16 KB
+constexpr int kWgB = 32 * kChunkK * 2;    // 4 KB
+constexpr int kWgSmem = kWgStages * (kWgA + kWgB) + 64;
+constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);
+
+__device__ __forceinline__ uint64_t mn_desc(uint32_t addr, uint32_t mn_stride, uint32_t k_stride) {
+    return umma::smem_desc(addr, k_stride, mn_stride);
+}
+__device__ __forceinline__ void cp16_to(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+struct WgradMnArgs {
+    const uint16_t *X;    // [B][D^3][32]
+    const uint16_t *dY;   // [B][Do^3][32]
+    float *dW;            // [32][64][32], accumulated
+    int D, P, per;        // input edge, output positions B Do^3, chunks per split
+};
+
+// Thread t stages position o = t / 2 of the chunk: its 8 (tap, channel-group)
+// copies of X and 2 of dY.
+__device__ __forceinline__ void wgrad_issue(const WgradMnArgs &g, uint32_t sa, uint32_t sb, int c, int tap0,
+                                            int t) {
+    const int D = g.D, Do = D >> 1;
+    const int ol = t >> 1, half = t & 1;
+    const int p = c * kChunkK + ol;
+    const bool live = p < g.P;
+    const int pp = live ? p : 0;
+    const int ox = pp % Do, oy = (pp / Do) % Do, oz = (pp / (Do * Do)) % Do, b = pp / (Do * Do * Do);
+    const uint32_t krow = (uint32_t)((ol >> 3) * 2048 + (ol & 7) * 16);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int q = half * 8 + u, tl = q >> 2, cc = q & 3, tap = tap0 + tl;
+        const int z = 2 * oz + (tap >> 4) - 1, y = 2 * oy + ((tap >> 2) & 3) - 1, x = 2 * ox + (tap & 3) - 1;
+        const bool ok = live && (unsigned)z < (unsigned)D && (unsigned)y < (unsigned)D && (unsigned)x < (unsigned)D;
+        const uint16_t *src = ok ? g.X + ((((long long)b * D + z) * D + y) * D + x) * 32 + cc * 8 : g.X;
+        cp16_to(sa + (uint32_t)((tl * 4 + cc) * 128) + krow, src, ok);
+    }
+    const uint32_t krowb = (uint32_t)((ol >> 3) * 512 + (ol & 7) * 16);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int cc = half * 2 + u;
+        cp16_to(sb + (uint32_t)(cc * 128) + krowb, live ? g.dY + (size_t)p * 32 + cc * 8 : g.dY, live);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_wgrad_mn(const WgradMnArgs g) {
+    extern __shared__ __align__(1024) uint8_t dsm[];
+    uint8_t *sA = dsm;
+    uint8_t *sB = dsm + kWgStages * kWgA;
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(sB + kWgStages * kWgB);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + kWgStages);
+    const int t = threadIdx.x, warp = t >> 5;
+    const int tap0 = blockIdx.x * 4;
+    const int nch = (g.P + kChunkK - 1) / kChunkK;
+    const int c0 = blockIdx.y * g.per;
+    const int n = max(0, min(nch, c0 + g.per) - c0);
+    constexpr int S = kWgStages;
+
+    if (warp == 0) umma::tmem_alloc(tmem_slot, kTileN);
+    if (t == 0) {
+        for (int q = 0; q < S; ++q) umma::mbar_init(umma::smem_u32(&mbar[q]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t a0 = umma::smem_u32(sA), b0 = umma::smem_u32(sB);
+
+    constexpr int P = S - 2;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        if (i < n) wgrad_issue(g, a0 + i * kWgA, b0 + i * kWgB, c0 + i, tap0, t);
+        cp_commit();
+    }
+    bool ok = true;
+    for (int i = 0; i < n; ++i) {
+        const int s = i % S;
+        cp_wait<P - 1>();
+        umma::fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+            umma::fence_after_sync();
+            const uint32_t a = a0 + s * kWgA, b = b0 + s * kWgB;
+#pragma unroll
+            for (int kk = 0; kk < kChunkK / 16; ++kk)
+                umma::mma_bf16(tmem, mn_desc(a + 4096 * kk, 128, 2048), mn_desc(b + 1024 * kk, 128, 512), kIdescMN,
+                               i > 0 || kk > 0);
+            umma::commit(umma::smem_u32(&mbar[s]));
+        }
+        const int j = i + P;
+        if (j < n) {
+            if (i >= 2) {
+                const int sp = (i - 2) % S;
+                if (!__syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[sp]), (uint32_t)(((i - 2) / S) & 1)))) {
+                    ok = false;
+                    break;
+                }
+            }
+            wgrad_issue(g, a0 + (j % S) * kWgA, b0 + (j % S) * kWgB, c0 + j, tap0, t);
+        }
+        cp_commit();
+    }
+    cp_wait<0>();
+    if (ok && n > 0)
+        ok = __syncthreads_and(umma::mbar_wait(umma::smem_u32(&mbar[(n - 1) % S]), (uint32_t)(((n - 1) / S) & 1)));
+    if (!ok) {
+        if (t == 0) atomicExch(&g_nn_error, 1u);
+    } else if (n > 0) {
+        umma::fence_after_sync();
+        float acc[32];
+        umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
+        const int tap = tap0 + (t >> 5), ci = t & 31;
+#pragma unroll
+        for (int co = 0; co < 32; ++co)
+            if (acc[co] != 0.0f) atomicAdd(g.dW + ((size_t)co * 64 + tap) * 32 + ci, acc[co]);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, kTileN);
+}
+
 // W [32][64][Cin] -> Wt [Cin][64][32] (bf16), for the data gradient.
 __global__ void k_transpose_w(const uint16_t *W, int Cin, uint16_t *Wt) {
     const int n = 32 * 64 * Cin;
@@ -917,7 +1062,7 @@ __global__ void k_downsample(const DownArgs a) {
 // input exactly as k_downsample does for real volumes.
 struct SynthSample {
     float R[9], t[3], c[3];          // pose about the source centre c
-    float hc[3], outer[3], inner[3]; // heart centre and shell semi-axes
+    float hc[3], rout[3], rin[3];    // heart centre, reciprocal outer / inner shell semi-axes
     float base_x;
     float gf[2][3][3], gph[2][3];    // gain frequencies / phases per view
     int shift;                       // target origin x (voxels)
@@ -955,10 +1100,14 @@ __global__ void k_synth_params(const SynthArgs a, int B) {
         s.hc[d] = s.c[d] + 8.0f * u01(w[6 + d]) - 4.0f;
     }
     const float fr[3] = {0.36f, 0.26f, 0.28f};
-    for (int d = 0; d < 3; ++d) s.outer[d] = fr[d] * dims[d] * (0.95f + 0.1f * u01(w[9 + d]));
+    float outer[3];
+    for (int d = 0; d < 3; ++d) outer[d] = fr[d] * dims[d] * (0.95f + 0.1f * u01(w[9 + d]));
     const float th = 0.055f * dims[0];
-    for (int d = 0; d < 3; ++d) s.inner[d] = s.outer[d] - th;
-    s.base_x = 0.55f * s.outer[0];
+    for (int d = 0; d < 3; ++d) {
+        s.rout[d] = 1.0f / outer[d];
+        s.rin[d] = 1.0f / (outer[d] - th);
+    }
+    s.base_x = 0.55f * outer[0];
     // R = Rz Rx Ry
     float sx, cx, sy, cy, sz, cz;
     sincosf(ang[0], &sx, &cx);
@@ -1011,10 +1160,10 @@ __device__ __forceinline__ uint32_t hash3(int x, int y, int z, uint32_t seed) {
 // One view's voxel value at world point w (source frame) and grid fraction u.
 __device__ __forceinline__ float synth_voxel(const SynthSample &s, int view, const float w[3], const float u[3]) {
     const float ux = w[0] - s.hc[0], uy = w[1] - s.hc[1], uz = w[2] - s.hc[2];
-    const float eo = (ux / s.outer[0]) * (ux / s.outer[0]) + (uy / s.outer[1]) * (uy / s.outer[1]) +
-                     (uz / s.outer[2]) * (uz / s.outer[2]);
-    const float ei = (ux / s.inner[0]) * (ux / s.inner[0]) + (uy / s.inner[1]) * (uy / s.inner[1]) +
-                     (uz / s.inner[2]) * (uz / s.inner[2]);
+    const float ox = ux * s.rout[0], oy = uy * s.rout[1], oz = uz * s.rout[2];
+    const float ix = ux * s.rin[0], iy = uy * s.rin[1], iz = uz * s.rin[2];
+    const float eo = ox * ox + oy * oy + oz * oz;
+    const float ei = ix * ix + iy * iy + iz * iz;
     float tissue = 0.3f;
     if (ux <= s.base_x) {
         if (ei <= 1.0f) tissue = 0.15f;
@@ -1175,6 +1324,21 @@ cudaError_t nn_conv_wgrad(const uint16_t *X, int batch, int D, int Cin, const ui
     const int chunks = (P + nn::kChunkK - 1) / nn::kChunkK;
     const int mtiles = (64 * Cin + nn::kTileM - 1) / nn::kTileM;
     int splits = (4 * 152 + mtiles - 1) / mtiles;   // about four CTAs per SM in all
+#if PF_WGRAD_MN
+    if (Cin == 32) {
+        // 16 M tiles of 4 taps; about two CTAs per SM (80 KB of stages each)
+        int sp = (2 * 152 + 15) / 16;
+        if (sp > chunks) sp = chunks;
+        const int per = (chunks + sp - 1) / sp;
+        sp = (chunks + per - 1) / per;
+        cudaError_t e = cudaFuncSetAttribute(nn::k_wgrad_mn, cudaFuncAttributeMaxDynamicSharedMemorySize, nn::kWgSmem);
+        if (e != cudaSuccess) return e;
+        const nn::WgradMnArgs g{X, dY, dW, D, P, per};
+        nn::k_wgrad_mn<<<dim3(16, (unsigned)sp), 128, nn::kWgSmem, s>>>(g);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+#endif
     nn::ConvWgradOp op{{batch, D, Cin}, X, dY, dW, 0};
     return nn::launch_tile(op, 64 * Cin, chunks, splits, s);
 }
