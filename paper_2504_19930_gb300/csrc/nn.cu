@@ -1317,17 +1317,27 @@ cudaError_t nn_transpose_w(const uint16_t *W, int Cin, uint16_t *Wt, cudaStream_
     return cudaGetLastError();
 }
 
+// SMs of the current device (the K splits of the weight gradient are sized by it).
+static int current_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+        sms = 1;
+    return sms;
+}
+
 cudaError_t nn_conv_wgrad(const uint16_t *X, int batch, int D, int Cin, const uint16_t *dY, float *dW,
                           cudaStream_t s) {
     const int Do = D / 2;
     const int P = batch * Do * Do * Do;
     const int chunks = (P + nn::kChunkK - 1) / nn::kChunkK;
     const int mtiles = (64 * Cin + nn::kTileM - 1) / nn::kTileM;
-    int splits = (4 * 152 + mtiles - 1) / mtiles;   // about four CTAs per SM in all
+    const int sms = current_sms();
+    int splits = (4 * sms + mtiles - 1) / mtiles;   // about four CTAs per SM in all
 #if PF_WGRAD_MN
     if (Cin == 32) {
         // 16 M tiles of 4 taps; about two CTAs per SM (80 KB of stages each)
-        int sp = (2 * 152 + 15) / 16;
+        int sp = (2 * sms + 15) / 16;
         if (sp > chunks) sp = chunks;
         const int per = (chunks + sp - 1) / sp;
         sp = (chunks + per - 1) / per;
