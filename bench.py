@@ -115,6 +115,8 @@ def parse():
     ap.add_argument("--cpu-sample-iters", type=int, default=None,
                     help="oracle sample: iterations (default: 2, or all of the 64^3 mask workload's)")
     ap.add_argument("--cpu-all-cores-particles", type=int, default=512)
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the short 64^3 mask and convolution lines the default run attaches")
     args = ap.parse_args()
     if args.steps is None:   # the oracle arm's steps are bounded samples: 3 by default everywhere
         args.steps = WORKLOADS[args.workload].get("default_steps", 3) if args.impl == "ours" else 3
@@ -604,8 +606,39 @@ def run_ours(args, rank, world, local):
             "wall_s_timed": wall, "final_pose": [float(v) for v in pose],
             "true_pose": [float(v) for v in pair.true_pose],
         }
+        if world == 1 and args.workload == "image224" and not args.no_secondary:
+            line["secondary"] = run_secondary()
         print(json.dumps(line), flush=True)
     dist.close()
+
+
+def run_secondary():
+    """The default run's short companions, each its own bench.py process on
+    the same GPU after the main line's timed work: the 64^3 mask workload
+    (1500 timed registrations) and the proposal network's largest
+    convolution.  A summary of each line (or the reason it is missing)."""
+    out = {}
+    cmds = {"mask64": ["--workload", "mask64", "--no-cpu-baseline", "--e2e-steps", "2"],
+            "conv32": ["--workload", "conv32", "--steps", "20"]}
+    for name, extra in cmds.items():
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), *extra], capture_output=True, text=True,
+                               timeout=600)
+            lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            if r.returncode != 0 or not lines:
+                out[name] = {"missing": f"exit {r.returncode}: {r.stderr.strip().splitlines()[-1:]}"}
+                continue
+            d = json.loads(lines[-1])
+            rf = d.get("roofline") or {}
+            out[name] = {"workload": d["config"]["workload"], "metric": d["metric"], "value": d["value"],
+                         "unit": d["unit"], "steps": d["steps"], "ms_per_step": d.get("ms_per_step"),
+                         "roofline": {k: rf.get(k) for k in ("bound", "kernel", "achieved", "peak", "unit", "frac",
+                                                              "traffic")},
+                         "l2_frac": (rf.get("l2") or {}).get("frac"), "e2e": d.get("e2e"),
+                         "clocks": d.get("clocks"), "gradients": d.get("gradients")}
+        except Exception as e:   # a companion's failure never costs the main line
+            out[name] = {"missing": repr(e)}
+    return out
 
 
 def _member_pair(spec):
