@@ -50,3 +50,26 @@ def test_cpu_sample_size():
     given = types.SimpleNamespace(cpu_sample_particles=8, cpu_sample_iters=1)
     assert f(given, bench.WORKLOADS["image224"]) == (8, 1)
     assert f(types.SimpleNamespace(), bench.WORKLOADS["mask64"]) == (256, 10)
+
+
+def test_secondary_lines_summarised_and_failures_kept_out_of_the_main_line(monkeypatch):
+    import json
+    import subprocess
+    import types
+
+    good = {"metric": "m", "value": 2.5, "unit": "u", "steps": 1500, "ms_per_step": 1.8,
+            "config": {"workload": "mask64_dice_n256_k10"},
+            "roofline": {"bound": "alu", "frac": 0.12, "l2": {"frac": 0.03}},
+            "clocks": {"sm_mhz": 2070.0}, "e2e": None}
+
+    def fake_run(cmd, **kw):
+        if "mask64" in cmd:
+            return types.SimpleNamespace(returncode=0, stdout="noise\n" + json.dumps(good) + "\n", stderr="")
+        return types.SimpleNamespace(returncode=3, stdout="", stderr="boom\nlast line")
+
+    monkeypatch.setattr(subprocess, "run", fake_run)
+    out = bench.run_secondary()
+    assert out["mask64"]["value"] == 2.5 and out["mask64"]["roofline"]["frac"] == 0.12
+    assert out["mask64"]["l2_frac"] == 0.03 and out["mask64"]["clocks"]["sm_mhz"] == 2070.0
+    assert "exit 3" in out["conv32"]["missing"] and "last line" in out["conv32"]["missing"]
+    json.dumps(out)   # the summary is JSON-serialisable
