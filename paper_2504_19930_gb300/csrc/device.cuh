@@ -16,6 +16,11 @@ PF_HD double d_add(double a, double b) { return __dadd_rn(a, b); }
 PF_HD double d_sub(double a, double b) { return __dsub_rn(a, b); }
 PF_HD double d_div(double a, double b) { return __ddiv_rn(a, b); }
 PF_HD float d2f(double a) { return __double2float_rn(a); }
+// a * s and a / s with the exact shortcut for s = 1 (x * 1 = x / 1 = x in
+// IEEE arithmetic, so the result is the same bits; a division costs ~550
+// clocks of dependent latency here, and unit voxel spacing is the common case)
+PF_HD double d_mul_s(double a, double s) { return s == 1.0 ? a : __dmul_rn(a, s); }
+PF_HD double d_div_s(double a, double s) { return s == 1.0 ? a : __ddiv_rn(a, s); }
 PF_HD double u64_to_f64(unsigned long long v) { return __ull2double_rn(v); }
 
 // ---------------------------------------------------------------------------
@@ -103,7 +108,8 @@ struct Geometry {
 
 // Source-grid centre in world units, c_d = o_S,d + s_S,d (dims_S,d - 1)/2.
 PF_HD double grid_centre(const Geometry &g, int d) {
-    return d_add((double)g.so[d], d_mul((double)g.ss[d], d_div((double)(g.sd[d] - 1), 2.0)));
+    // (dims - 1) / 2 is an exact halving of a small integer, the same bits as the division
+    return d_add((double)g.so[d], d_mul_s(d_mul((double)(g.sd[d] - 1), 0.5), (double)g.ss[d]));
 }
 
 // Per-particle pose -> matrix on the device: sin/cos of the three angles
@@ -122,10 +128,10 @@ PF_HD void matrix_from_sincos(const float pose[6], double sa, double ca, double 
     mat3_mul(Rz, XY, R);
     for (int i = 0; i < 3; ++i) {
         const double si = (double)g.ss[i];
-        const double b = d_div(d_sub(d_add(grid_centre(g, i), (double)pose[3 + i]), (double)g.so[i]), si);
-        M[4 * i + 0] = d2f(d_div(d_mul(R[3 * i + 0], (double)g.ts[0]), si));
-        M[4 * i + 1] = d2f(d_div(d_mul(R[3 * i + 1], (double)g.ts[1]), si));
-        M[4 * i + 2] = d2f(d_div(d_mul(R[3 * i + 2], (double)g.ts[2]), si));
+        const double b = d_div_s(d_sub(d_add(grid_centre(g, i), (double)pose[3 + i]), (double)g.so[i]), si);
+        M[4 * i + 0] = d2f(d_div_s(d_mul_s(R[3 * i + 0], (double)g.ts[0]), si));
+        M[4 * i + 1] = d2f(d_div_s(d_mul_s(R[3 * i + 1], (double)g.ts[1]), si));
+        M[4 * i + 2] = d2f(d_div_s(d_mul_s(R[3 * i + 2], (double)g.ts[2]), si));
         M[4 * i + 3] = d2f(b);
     }
 }

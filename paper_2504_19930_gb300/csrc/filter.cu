@@ -350,10 +350,17 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bi = min(bi, __shfl_xor_sync(0xffffffffu, bi, o));
         if (lane == 0) sh_best_idx = bi;
-        if (lane < (P.estimator == 1 ? kRed : 7)) {
-            double t = 0.0;
-            for (int w = 0; w < kFinWarps; ++w) t = __dadd_rn(t, sh_d[w][lane]);
-            sh_est[lane] = t;
+        // the warps' partial sums, lane = warp, as trees (the estimate has no
+        // fixed summation order; fp64 adds are ~60 clocks of dependent latency)
+        const int nred = P.estimator == 1 ? kRed : 7;
+#pragma unroll
+        for (int d = 0; d < kRed; ++d) {
+            if (d < nred) {
+                double t = sh_d[lane][d];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t = __dadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
+                if (lane == 0) sh_est[d] = t;
+            }
         }
     }
     // 4. resampling: keep the measured cloud, gather the copies
@@ -379,11 +386,15 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
         for (int d = 0; d < 6; ++d) B.poses[(size_t)d * N + j] = B.poses_meas[(size_t)d * N + a];
     }
 
-    // 5. log and advance the iteration counter
+    // 5. log and advance the iteration counter (the six quotients on six lanes)
+    IterLog &L = B.log[k % P.log_capacity];
+    if (tid < 6) L.est[tid] = S > 0 ? __ddiv_rn(sh_est[tid], (double)S) : __ddiv_rn(sh_est[tid], (double)N);
+    if (tid == 6) {
+        const double Sd = (double)S, w2 = sh_est[6];
+        L.ess = w2 > 0.0 ? Sd * Sd / w2 : 0.0;
+    }
+    __syncwarp();
     if (tid == 0) {
-        IterLog &L = B.log[k % P.log_capacity];
-        for (int d = 0; d < 6; ++d)
-            L.est[d] = S > 0 ? __ddiv_rn(sh_est[d], (double)S) : __ddiv_rn(sh_est[d], (double)N);
         if (P.estimator == 1) {
             double A10[10], rot[3];
             const double norm = S > 0 ? (double)S : (double)N;
@@ -395,8 +406,6 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
         L.best_idx = sh_best_idx;
         L.evals = B.stats[1];
         L.est_dice = -1.0;
-        const double Sd = (double)S, w2 = sh_est[6];
-        L.ess = w2 > 0.0 ? Sd * Sd / w2 : 0.0;
         L.k = k;
         *B.k = k + 1;
     }
