@@ -24,7 +24,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpfreg.so")
 LIB_DEBUG = os.path.join(BUILD, "libpfreg_debug.so")
 SOURCES = ["api.cu", "measure.cu", "filter.cu", "warp.cu", "noalloc.cu", "nn.cu", "proposal.cu", "probe.cu",
-           "conv.cu"]
+           "conv.cu", "dgrad.cu"]
 DEBUG_SOURCES = ["api.cu", "measure.cu", "warp.cu"]   # the ones PF_DEBUG changes
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

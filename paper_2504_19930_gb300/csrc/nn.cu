@@ -43,6 +43,10 @@ __device__ unsigned int g_nn_error;   // set when a bounded wait gave up
 #define PF_CONV_PLANES 1   // 32-channel forward convolutions by the plane-staged kernel (conv.cu)
 #endif
 
+#ifndef PF_DGRAD_PLANES
+#define PF_DGRAD_PLANES 1   // 32-channel data gradients with D >= 32 by the plane-staged kernel (dgrad.cu)
+#endif
+
 #ifndef PF_DGRAD_PHASES
 #define PF_DGRAD_PHASES 1   // data gradient over the 8 taps of each stride phase (ConvDgradPhaseOp)
 #endif
@@ -1258,8 +1262,10 @@ cudaError_t nn_wait_selftest(cudaStream_t s) {
 }
 
 cudaError_t nn_error_flag(unsigned int *out, bool clear) {
-    unsigned int conv = 0;
+    unsigned int conv = 0, dg = 0;
     cudaError_t e = conv_planes_error_flag(&conv, clear);
+    if (e == cudaSuccess) e = dgrad_planes_error_flag(&dg, clear);
+    conv |= dg;
     if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, nn::g_nn_error, sizeof(unsigned int));
     if (e != cudaSuccess) return e;
     *out |= conv;
@@ -1293,6 +1299,9 @@ cudaError_t nn_conv_fwd(const uint16_t *X, int batch, int D, int Cin, const uint
 
 cudaError_t nn_conv_dgrad(const uint16_t *dY, int batch, int D, const uint16_t *Wt, const uint16_t *act,
                           uint16_t *dX, cudaStream_t s) {
+#if PF_DGRAD_PLANES
+    if (dgrad_planes_applies(D)) return dgrad_planes(dY, batch, D, Wt, act, dX, s);
+#endif
 #if PF_NN_ASYNC && PF_DGRAD_PHASES
     {
         const int Do = D / 2;

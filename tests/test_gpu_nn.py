@@ -89,7 +89,7 @@ def test_conv_forward(torch_, pk, Bn, D, Cin):
     _check_bf16(_host(torch, y), ref, bound, "conv forward")
 
 
-@pytest.mark.parametrize("Bn,D,masked", [(2, 10, True), (1, 8, False), (3, 16, True)])
+@pytest.mark.parametrize("Bn,D,masked", [(2, 10, True), (1, 8, False), (3, 16, True), (2, 32, True), (1, 64, False)])
 def test_conv_backward_data(torch_, pk, Bn, D, masked):
     torch = torch_
     rng = np.random.default_rng(100 + D)
