@@ -52,7 +52,6 @@ constexpr int kTileX = 8, kTileY = 16;         // output voxels per tile in x an
 #endif
 constexpr int kZC = PF_CONV_ZC;                 // output planes per CTA (1, 2, 4 or 8)
 constexpr int kSubX = kTileX + 1, kSubY = kTileY + 1;   // parity sub-plane extent (entries)
-constexpr int kChunkBytes = kSubY * kSubX * 16;         // 2448: one channel chunk of a sub-plane
 constexpr int kChunkPitch = 2576;                       // its slot (odd multiple of 16: conflict-free stores)
 constexpr int kPlaneBytes = 4 * 4 * kChunkPitch;        // 4 sub-planes x 4 chunks
 constexpr int kBufs = 2;                                // plane buffers
@@ -158,8 +157,8 @@ __device__ __forceinline__ void store_plane(uint8_t *buf, const uint4 (&v)[kPerT
     }
 }
 
-__device__ __forceinline__ Segment make_segment(const ConvPlaneArgs &p, long long t0, long long t1, int sb) {
-    const int Do = p.D >> 1, tiles_x = Do / kTileX, tiles_y = Do / kTileY;
+__device__ __forceinline__ Segment make_segment(int D, long long t0, long long t1, int sb) {
+    const int Do = D >> 1, tiles_x = Do / kTileX, tiles_y = Do / kTileY;
     Segment g;
     const long long pencil = t0 / Do;
     g.o0 = (int)(t0 - pencil * Do);
@@ -170,7 +169,7 @@ __device__ __forceinline__ Segment make_segment(const ConvPlaneArgs &p, long lon
     g.oy0 = ty * kTileY;
     g.sb = sb;
     g.zl = max(2 * g.o0 - 1, 0);
-    g.zh = min(2 * (g.o1 - 1) + 2, p.D - 1);
+    g.zh = min(2 * (g.o1 - 1) + 2, D - 1);
     return g;
 }
 
@@ -183,9 +182,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const long long t0 = p.tiles * blockIdx.x / gridDim.x, t1 = p.tiles * (blockIdx.x + 1) / gridDim.x;
     const long long cut = min(t1, (t0 / Do + 1) * Do);   // the end of t0's pencil
     Segment sg[2];
-    sg[0] = make_segment(p, t0, cut, 0);
+    sg[0] = make_segment(p.D, t0, cut, 0);
     const int nseg = cut < t1 ? 2 : 1;
-    sg[1] = nseg == 2 ? make_segment(p, cut, t1, (int)(cut - t0)) : sg[0];
+    sg[1] = nseg == 2 ? make_segment(p.D, cut, t1, (int)(cut - t0)) : sg[0];
     const int np0 = sg[0].zh - sg[0].zl + 1;
     const int nplanes = np0 + (nseg == 2 ? sg[1].zh - sg[1].zl + 1 : 0);
     // barriers: full[kBufs] (128 producer arrivals), empty[kBufs], all MMAs done
@@ -321,6 +320,192 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) umma::tmem_free(tmem, 32 * kZC);
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient of the same convolution, dW[co][tap][ci] += sum over the
+// output positions o of X[2 o + k - 1][ci] dY[o][co], on the same staged
+// input planes.  Contracted over positions, both operands are MN-major: in a
+// staged sub-plane the 16 bytes of an entry are 8 channels and consecutive
+// entries (8 consecutive output x) are 16 bytes apart -- a core matrix of 8
+// positions x 8 channels -- and the four parity sub-planes x four channel
+// chunks are 16 such groups at the uniform stride 2576: one A operand of
+// M = 128 rows (sub-plane, ci) = the four taps (ky, kx) with one in-plane
+// shift (ky >> 1, kx >> 1), K = 16 positions (two tile rows, stride 144).
+// The dY tiles of the CTA's output plane-tiles are staged once at the start
+// as B operands ([co chunk][oy 16][ox 8][8 co], 8 KB each, consecutive), so
+// an input plane's two output planes (taps kz = par and par + 2) are one
+// N = 64 operand [dY of qa - 1 ; dY of qa].  The accumulators -- 16 blocks
+// of 32 columns, one per (shift, kz), all of tensor memory -- sum over every
+// position the CTA covers and are added to dW with fp32 atomics at the end.
+// ---------------------------------------------------------------------------
+constexpr int kWgTile = 4 * kTileY * kTileX * 16;     // one dY tile: 4 chunks x 128 positions x 16 B (8 KB)
+constexpr int kWgSmemTiles = 0;
+constexpr int kWgSmemPlanes = kZC * kWgTile;           // 64 KB of dY tiles
+constexpr int kWgSmemBar = kWgSmemPlanes + kBufs * kPlaneBytes;
+constexpr int kWgSmemTotal = kWgSmemBar + 128;
+static_assert(kWgSmemTotal <= 232448, "fits the opt-in shared memory of one CTA");
+// instruction descriptors: bf16 -> fp32, both operands MN-major (bits 15, 16)
+constexpr uint32_t kIdescMN32 = kIdesc32 | (1u << 15) | (1u << 16);
+constexpr uint32_t kIdescMN64 = kIdesc64 | (1u << 15) | (1u << 16);
+
+__device__ unsigned int g_wgrad_error;   // a bounded wait of the weight-gradient kernel gave up
+
+struct WgradPlaneArgs {
+    const uint16_t *dY;   // [batch][Do][Do][Do][32] bf16
+    float *dW;            // [32 co][64 taps][32 ci] fp32, accumulated
+    int batch, D;
+    long long tiles;      // output plane-tiles (b, tile x, tile y, oz), in that order
+};
+
+// Accumulator block of (in-plane shift sh = 2 (ky >> 1) + (kx >> 1), kz):
+// the pair (kz = par + 2, kz = par) of one shift is adjacent, in that order,
+// so the N = 64 MMA [dY of qa - 1 ; dY of qa] writes both.
+__device__ __forceinline__ int wg_block(int sh, int kz) { return (sh * 2 + (kz & 1)) * 2 + 1 - (kz >> 1); }
+
+// The dY tile of output plane-tile (b, oz, ox0, oy0) into slot q: position
+// (oy, ox) of chunk c at q * 8 KB + c * 2048 + (oy * 8 + ox) * 16, by 16-byte
+// asynchronous copies (thread first, stride step).
+__device__ __forceinline__ void copy_dy_tile(uint32_t base, const uint16_t *__restrict__ dY, int Do, int b, int oz,
+                                             int ox0, int oy0, int q, int first, int step) {
+    for (int g = first; g < 4 * kTileY * kTileX; g += step) {   // g = (oy * 8 + ox) * 4 + c
+        const int c = g & 3, pos = g >> 2, ox = pos & 7, oy = pos >> 3;
+        const size_t vox = (((size_t)b * Do + oz) * Do + (oy0 + oy)) * Do + (ox0 + ox);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         base + (uint32_t)(q * kWgTile + c * 2048 + pos * 16)),
+                     "l"(reinterpret_cast<const uint4 *>(dY + vox * 32) + c)
+                     : "memory");
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wgrad_planes(const uint16_t *__restrict__ X, const WgradPlaneArgs p) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int D = p.D, Do = D >> 1;
+    const long long t0 = p.tiles * blockIdx.x / gridDim.x, t1 = p.tiles * (blockIdx.x + 1) / gridDim.x;
+    const long long cut = min(t1, (t0 / Do + 1) * Do);
+    Segment sg[2];
+    sg[0] = make_segment(D, t0, cut, 0);
+    const int nseg = cut < t1 ? 2 : 1;
+    sg[1] = nseg == 2 ? make_segment(D, cut, t1, (int)(cut - t0)) : sg[0];
+    const int np0 = sg[0].zh - sg[0].zl + 1;
+    const int nplanes = np0 + (nseg == 2 ? sg[1].zh - sg[1].zl + 1 : 0);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(sm + kWgSmemBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kWgSmemBar + 8 * (2 * kBufs + 1));
+    const uint32_t full0 = umma::smem_u32(&bars[0]), empty0 = umma::smem_u32(&bars[kBufs]);
+    const uint32_t done = umma::smem_u32(&bars[2 * kBufs]);
+    const uint32_t planes = umma::smem_u32(sm + kWgSmemPlanes), tiles = umma::smem_u32(sm + kWgSmemTiles);
+    auto seg_of = [&](int i) -> const Segment & { return i < np0 ? sg[0] : sg[1]; };
+    auto z_of = [&](int i) { return i < np0 ? sg[0].zl + i : sg[1].zl + (i - np0); };
+
+    if (warp == 0) umma::tmem_alloc(tmem_slot, 512);
+    if (t == 0) {
+        for (int i = 0; i < 2 * kBufs + 1; ++i)
+            umma::mbar_init(umma::smem_u32(&bars[i]), i < kBufs ? (uint32_t)kProducers : 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // the dY tiles of the CTA's plane-tiles, all in flight
+    for (int k = 0; k < nseg; ++k) {
+        const Segment &g = k ? sg[1] : sg[0];
+        for (int q = 0; q < g.o1 - g.o0; ++q)
+            copy_dy_tile(tiles, p.dY, Do, g.b, g.o0 + q, g.ox0, g.oy0, g.sb + q, t, kThreads);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    const int u = t - 64;
+    uint4 v[kPerThread];
+    if (warp >= 2 && nplanes > 0) {
+        const Segment &g = seg_of(0);
+        load_plane(v, X, D, g.b, z_of(0), g.ox0, g.oy0, u);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    umma::fence_async_smem();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    if (warp >= 2) {
+        for (int q = 0; q < 16; ++q) tmem_zero32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * q));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+
+    bool ok = true;
+    if (warp >= 2) {
+        for (int i = 0; i < nplanes; ++i) {
+            const int s = i % kBufs;
+            if (i >= kBufs && !umma::mbar_wait(empty0 + 8 * s, (uint32_t)(((i - kBufs) / kBufs) & 1))) {
+                ok = false;
+                break;
+            }
+            store_plane(sm + kWgSmemPlanes + s * kPlaneBytes, v, u);
+            umma::fence_async_smem();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full0 + 8 * s) : "memory");
+            if (i + 1 < nplanes) {
+                const Segment &g = seg_of(i + 1);
+                load_plane(v, X, D, g.b, z_of(i + 1), g.ox0, g.oy0, u);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MN-major descriptors: leading offset = the stride along K
+        // (positions: the next tile row), stride offset = the stride along
+        // M / N (the next 8 channels)
+        const uint64_t adesc0 = umma::smem_desc(planes, kSubX * 16, kChunkPitch);
+        const uint64_t bdesc0 = umma::smem_desc(tiles, kTileX * 16, 2048);
+        for (int i = 0; i < nplanes; ++i) {
+            const int s = i % kBufs;
+            if (!umma::mbar_wait(full0 + 8 * s, (uint32_t)((i / kBufs) & 1))) {
+                ok = false;
+                break;
+            }
+            umma::fence_after_sync();
+            const Segment &g = seg_of(i);
+            const int z = z_of(i), n = g.o1 - g.o0;
+            // plane z feeds output plane qa through kz = par and qa - 1 through
+            // kz = par + 2; dY tiles qa - 1 and qa are consecutive slots
+            const int par = (z + 1) & 1;
+            const int qa = ((z + 1 - par) >> 1) - g.o0, qb = qa - 1;
+            const bool va = qa >= 0 && qa < n, vb = qb >= 0 && qb < n;
+            const uint64_t ab = adesc0 + (uint64_t)((s * kPlaneBytes) >> 4);
+            const uint64_t bb = bdesc0 + (uint64_t)(((g.sb + (vb ? qb : qa)) * kWgTile) >> 4);
+            const uint32_t idesc = (va && vb) ? kIdescMN64 : kIdescMN32;
+            const int kz0 = vb ? par + 2 : par;   // the block of the first 32 columns
+#pragma unroll
+            for (int sh = 0; sh < 4; ++sh) {
+                const uint32_t dt = tmem + 32 * wg_block(sh, kz0);
+                const uint32_t aoff = (((sh >> 1) * kSubX + (sh & 1)) * 16) >> 4;
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)
+                    umma::mma_bf16(dt, ab + aoff + (uint32_t)((2 * ks * kSubX * 16) >> 4),
+                                   bb + (uint32_t)((2 * ks * kTileX * 16) >> 4), idesc, true);
+            }
+            umma::commit(empty0 + 8 * s);
+        }
+        if (ok) umma::commit(done);
+    }
+    bool waited = true;
+    if (warp >= 2 && ok) waited = umma::mbar_wait(done, 0u);
+    const bool all_ok = __syncthreads_and(ok && waited);
+    if (all_ok && warp >= 2) {
+        umma::fence_after_sync();
+        const int wq = warp & 3;   // this warp's tensor-memory lanes: rows (sub-plane wq, ci = lane)
+        for (int blk = 0; blk < 16; ++blk) {
+            float acc[32];
+            umma::tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(32 * blk), acc);
+            const int sh = blk >> 2, kz = ((blk >> 1) & 1) + 2 * (1 - (blk & 1));
+            const int ky = 2 * (sh >> 1) + (wq >> 1), kx = 2 * (sh & 1) + (wq & 1);
+            const int tap = (kz * 4 + ky) * 4 + kx;
+#pragma unroll
+            for (int co = 0; co < 32; ++co)
+                if (acc[co] != 0.0f) atomicAdd(p.dW + ((size_t)co * 64 + tap) * 32 + lane, acc[co]);
+        }
+    }
+    if (!all_ok && t == 0) atomicExch(&g_wgrad_error, 1u);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, 512);
+}
+
 }  // namespace convp
 }  // namespace pfreg
 
@@ -359,12 +544,41 @@ cudaError_t conv_planes_forward(const uint16_t *X, int batch, int D, const uint1
     return cudaGetLastError();
 }
 
-// The error flag of the plane-staged kernel (a bounded wait gave up).
+// dW[co][tap][ci] += sum_o X[2 o + k - 1][ci] dY[o][co] for 32 -> 32
+// channels (the weight-gradient kernel above); x [batch][D^3][32], dy
+// [batch][(D/2)^3][32] bf16, dw [32][64][32] fp32 (accumulated).
+cudaError_t conv_planes_wgrad(const uint16_t *X, int batch, int D, const uint16_t *dY, float *dW, cudaStream_t s) {
+    using namespace convp;
+    if (!conv_planes_applies(D, 32) || batch < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad_planes, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmemTotal);
+    if (e != cudaSuccess) return e;
+    const int Do = D / 2;
+    const long long tiles = (long long)batch * (Do / kTileX) * (Do / kTileY) * Do;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    long long grid = tiles < sms ? tiles : sms;
+    if ((tiles + grid - 1) / grid > kZC) grid = (tiles + kZC - 1) / kZC;
+    if (grid > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    const WgradPlaneArgs a{dY, dW, batch, D, tiles};
+    k_wgrad_planes<<<(unsigned)grid, kThreads, kWgSmemTotal, s>>>(X, a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// The error flags of the plane-staged kernels (a bounded wait gave up).
 cudaError_t conv_planes_error_flag(unsigned int *out, bool clear) {
-    cudaError_t e = cudaMemcpyFromSymbol(out, convp::g_conv_error, sizeof(unsigned int));
-    if (e != cudaSuccess || !clear) return e;
+    unsigned int f = 0, w = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&f, convp::g_conv_error, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&w, convp::g_wgrad_error, sizeof(unsigned int));
+    if (e != cudaSuccess) return e;
+    *out = f | w;
+    if (!clear) return e;
     const unsigned int z = 0;
-    return cudaMemcpyToSymbol(convp::g_conv_error, &z, sizeof(z));
+    e = cudaMemcpyToSymbol(convp::g_conv_error, &z, sizeof(z));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(convp::g_wgrad_error, &z, sizeof(z));
+    return e;
 }
 
 }  // namespace pfreg

@@ -51,6 +51,10 @@ __device__ unsigned int g_nn_error;   // set when a bounded wait gave up
 #define PF_DGRAD_PHASES 1   // data gradient over the 8 taps of each stride phase (ConvDgradPhaseOp)
 #endif
 
+#ifndef PF_WGRAD_PLANES
+#define PF_WGRAD_PLANES 1   // 32-channel weight gradients with D >= 32 by the plane-staged kernel (conv.cu)
+#endif
+
 #ifndef PF_WGRAD_MN
 #define PF_WGRAD_MN 1   // 32-channel weight gradients by k_wgrad_mn (MN-major operands)
 #endif
@@ -1343,6 +1347,9 @@ cudaError_t nn_conv_wgrad(const uint16_t *X, int batch, int D, int Cin, const ui
     const int mtiles = (64 * Cin + nn::kTileM - 1) / nn::kTileM;
     const int sms = current_sms();
     int splits = (4 * sms + mtiles - 1) / mtiles;   // about four CTAs per SM in all
+#if PF_WGRAD_PLANES
+    if (conv_planes_applies(D, Cin)) return conv_planes_wgrad(X, batch, D, dY, dW, s);
+#endif
 #if PF_WGRAD_MN
     if (Cin == 32) {
         // 16 M tiles of 4 taps; about two CTAs per SM (80 KB of stages each)

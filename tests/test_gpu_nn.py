@@ -110,7 +110,7 @@ def test_conv_backward_data(torch_, pk, Bn, D, masked):
     _check_bf16(_host(torch, dx), ref, bound, "conv backward data")
 
 
-@pytest.mark.parametrize("Bn,D,Cin", [(2, 10, 32), (2, 18, 2), (4, 32, 32)])
+@pytest.mark.parametrize("Bn,D,Cin", [(2, 10, 32), (2, 18, 2), (4, 32, 32), (2, 64, 32)])
 def test_conv_backward_weights(torch_, pk, Bn, D, Cin):
     torch = torch_
     rng = np.random.default_rng(200 + D + Cin)
