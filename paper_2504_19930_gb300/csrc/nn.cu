@@ -775,14 +775,24 @@ __device__ __forceinline__ void cp16_to(uint32_t dst, const void *src, bool vali
 }
 
 struct WgradMnArgs {
-    const uint16_t *X;    // [B][D^3][32]
+    const uint16_t *X;    // [B][D^3][CIN]
     const uint16_t *dY;   // [B][Do^3][32]
-    float *dW;            // [32][64][32], accumulated
+    float *dW;            // [32][64][CIN], accumulated
     int D, P, per;        // input edge, output positions B Do^3, chunks per split
 };
 
-// Thread t stages position o = t / 2 of the chunk: its 8 (tap, channel-group)
-// copies of X and 2 of dY.
+__device__ __forceinline__ void cp4_to(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+// Thread t stages position o = t / 2 of the chunk.  CIN = 32: its 8 (tap,
+// channel-group) 16-byte copies of X (M tile = 4 taps x 32 channels).
+// CIN = 2 (M tile = all 64 taps x 2 channels): its 8 (kz, ky) rows, each the
+// 4 voxels kx = 0..3 of one input row (16 contiguous bytes, but only 4-byte
+// aligned: four 4-byte copies, each zero-filled when its voxel is outside).
+// Both: 2 of the 4 channel groups of dY.
+template <int CIN>
 __device__ __forceinline__ void wgrad_issue(const WgradMnArgs &g, uint32_t sa, uint32_t sb, int c, int tap0,
                                             int t) {
     const int D = g.D, Do = D >> 1;
@@ -792,13 +802,29 @@ __device__ __forceinline__ void wgrad_issue(const WgradMnArgs &g, uint32_t sa, u
     const int pp = live ? p : 0;
     const int ox = pp % Do, oy = (pp / Do) % Do, oz = (pp / (Do * Do)) % Do, b = pp / (Do * Do * Do);
     const uint32_t krow = (uint32_t)((ol >> 3) * 2048 + (ol & 7) * 16);
+    if (CIN == 32) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const int q = half * 8 + u, tl = q >> 2, cc = q & 3, tap = tap0 + tl;
-        const int z = 2 * oz + (tap >> 4) - 1, y = 2 * oy + ((tap >> 2) & 3) - 1, x = 2 * ox + (tap & 3) - 1;
-        const bool ok = live && (unsigned)z < (unsigned)D && (unsigned)y < (unsigned)D && (unsigned)x < (unsigned)D;
-        const uint16_t *src = ok ? g.X + ((((long long)b * D + z) * D + y) * D + x) * 32 + cc * 8 : g.X;
-        cp16_to(sa + (uint32_t)((tl * 4 + cc) * 128) + krow, src, ok);
+        for (int u = 0; u < 8; ++u) {
+            const int q = half * 8 + u, tl = q >> 2, cc = q & 3, tap = tap0 + tl;
+            const int z = 2 * oz + (tap >> 4) - 1, y = 2 * oy + ((tap >> 2) & 3) - 1, x = 2 * ox + (tap & 3) - 1;
+            const bool ok = live && (unsigned)z < (unsigned)D && (unsigned)y < (unsigned)D && (unsigned)x < (unsigned)D;
+            const uint16_t *src = ok ? g.X + ((((long long)b * D + z) * D + y) * D + x) * 32 + cc * 8 : g.X;
+            cp16_to(sa + (uint32_t)((tl * 4 + cc) * 128) + krow, src, ok);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int grp = half * 8 + u, kz = grp >> 2, ky = grp & 3;   // M group = (kz, ky): taps 4 grp .. 4 grp + 3
+            const int z = 2 * oz + kz - 1, y = 2 * oy + ky - 1;
+            const bool row = live && (unsigned)z < (unsigned)D && (unsigned)y < (unsigned)D;
+            const long long rbase = (((long long)b * D + z) * D + y) * D;
+#pragma unroll
+            for (int kx = 0; kx < 4; ++kx) {
+                const int x = 2 * ox + kx - 1;
+                const bool ok = row && (unsigned)x < (unsigned)D;
+                cp4_to(sa + (uint32_t)(grp * 128 + kx * 4) + krow, ok ? g.X + (rbase + x) * 2 : g.X, ok);
+            }
+        }
     }
     const uint32_t krowb = (uint32_t)((ol >> 3) * 512 + (ol & 7) * 16);
 #pragma unroll
@@ -808,6 +834,7 @@ __device__ __forceinline__ void wgrad_issue(const WgradMnArgs &g, uint32_t sa, u
     }
 }
 
+template <int CIN>
 __global__ void __launch_bounds__(128) k_wgrad_mn(const WgradMnArgs g) {
     extern __shared__ __align__(1024) uint8_t dsm[];
     uint8_t *sA = dsm;
@@ -835,7 +862,7 @@ __global__ void __launch_bounds__(128) k_wgrad_mn(const WgradMnArgs g) {
     constexpr int P = S - 2;
 #pragma unroll
     for (int i = 0; i < P; ++i) {
-        if (i < n) wgrad_issue(g, a0 + i * kWgA, b0 + i * kWgB, c0 + i, tap0, t);
+        if (i < n) wgrad_issue<CIN>(g, a0 + i * kWgA, b0 + i * kWgB, c0 + i, tap0, t);
         cp_commit();
     }
     bool ok = true;
@@ -862,7 +889,7 @@ __global__ void __launch_bounds__(128) k_wgrad_mn(const WgradMnArgs g) {
                     break;
                 }
             }
-            wgrad_issue(g, a0 + (j % S) * kWgA, b0 + (j % S) * kWgB, c0 + j, tap0, t);
+            wgrad_issue<CIN>(g, a0 + (j % S) * kWgA, b0 + (j % S) * kWgB, c0 + j, tap0, t);
         }
         cp_commit();
     }
@@ -875,10 +902,11 @@ __global__ void __launch_bounds__(128) k_wgrad_mn(const WgradMnArgs g) {
         umma::fence_after_sync();
         float acc[32];
         umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
-        const int tap = tap0 + (t >> 5), ci = t & 31;
+        // M row t: (tap0 + t / 32, ci = t % 32) for CIN = 32, (tap = t / 2, ci = t % 2) for CIN = 2
+        const int tap = CIN == 32 ? tap0 + (t >> 5) : t >> 1, ci = CIN == 32 ? t & 31 : t & 1;
 #pragma unroll
         for (int co = 0; co < 32; ++co)
-            if (acc[co] != 0.0f) atomicAdd(g.dW + ((size_t)co * 64 + tap) * 32 + ci, acc[co]);
+            if (acc[co] != 0.0f) atomicAdd(g.dW + ((size_t)co * 64 + tap) * CIN + ci, acc[co]);
     }
     umma::fence_before_sync();
     __syncthreads();
@@ -1351,16 +1379,19 @@ cudaError_t nn_conv_wgrad(const uint16_t *X, int batch, int D, int Cin, const ui
     if (conv_planes_applies(D, Cin)) return conv_planes_wgrad(X, batch, D, dY, dW, s);
 #endif
 #if PF_WGRAD_MN
-    if (Cin == 32) {
-        // 16 M tiles of 4 taps; about two CTAs per SM (80 KB of stages each)
-        int sp = (2 * sms + 15) / 16;
+    if (Cin == 32 || Cin == 2) {
+        // 32 channels: 16 M tiles of 4 taps; 2 channels: one M tile of all
+        // 64 taps; K split for about two CTAs per SM (80 KB of stages each)
+        const int mt = Cin == 32 ? 16 : 1;
+        int sp = (2 * sms + mt - 1) / mt;
         if (sp > chunks) sp = chunks;
         const int per = (chunks + sp - 1) / sp;
         sp = (chunks + per - 1) / per;
-        cudaError_t e = cudaFuncSetAttribute(nn::k_wgrad_mn, cudaFuncAttributeMaxDynamicSharedMemorySize, nn::kWgSmem);
+        auto kern = Cin == 32 ? nn::k_wgrad_mn<32> : nn::k_wgrad_mn<2>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, nn::kWgSmem);
         if (e != cudaSuccess) return e;
         const nn::WgradMnArgs g{X, dY, dW, D, P, per};
-        nn::k_wgrad_mn<<<dim3(16, (unsigned)sp), 128, nn::kWgSmem, s>>>(g);
+        kern<<<dim3(mt, (unsigned)sp), 128, nn::kWgSmem, s>>>(g);
         count_launches(1);
         return cudaGetLastError();
     }
