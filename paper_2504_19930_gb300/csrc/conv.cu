@@ -506,6 +506,211 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) umma::tmem_free(tmem, 512);
 }
 
+// ---------------------------------------------------------------------------
+// Forward convolution of the 2-channel first layer.  With two channels the
+// four taps kx = 0..3 of one (kz, ky) read four consecutive input voxels,
+// 16 contiguous bytes = one 8-element K group.  For each input row y of the
+// tile's window an input plane is staged as 8 entries (one per output x of
+// the tile), entry ox = the 16 bytes of voxels 2 ox - 1 .. 2 ox + 2 (4-byte
+// loads: the run is only 4-byte aligned; voxels outside are zeros): [row
+// 34][ox 8][16 B], rows 128 bytes apart.  The A operand of output rows
+// (ox, oy) and tap row ky is then entry (2 oy + ky, ox): rows 16 bytes apart
+// (a core matrix of 8 ox), row groups (next oy) 256 bytes, K groups (next
+// ky) 128 bytes -- one MMA of K = 16 takes the ky pair (2 m, 2 m + 1).  An
+// input plane feeds two output planes (kz = par and par + 2): one N = 64
+// MMA against the weight pair, as in the 32-channel kernel.
+// ---------------------------------------------------------------------------
+constexpr int kC2Rows = 2 * kTileY + 2;                 // 34 input rows of the window
+constexpr int kC2Plane = kC2Rows * kTileX * 16;         // 4352 bytes
+constexpr int kC2Bufs = 4;
+constexpr int kC2Pieces = kC2Rows * kTileX * 4;         // 4-byte pieces of one staged plane
+constexpr int kC2PerThread = (kC2Pieces + kProducers - 1) / kProducers;   // 9
+constexpr int kC2Weights = 4 * 2048;                    // 4 kz slots of 32 co x 32 (ky, kx, ci)
+constexpr int kC2SmemWeights = 0;
+constexpr int kC2SmemPlanes = kC2Weights;
+constexpr int kC2SmemBar = kC2SmemPlanes + kC2Bufs * kC2Plane;
+constexpr int kC2SmemTotal = kC2SmemBar + 128;
+
+__device__ unsigned int g_c2_error;   // a bounded wait of the first-layer kernel gave up
+
+struct C2Args {
+    const uint16_t *W;   // [32 co][64 taps][2 ci] bf16
+    const float *bias;   // [32]
+    uint16_t *Y;         // [batch][Do][Do][Do][32] bf16
+    int batch, D;
+    long long tiles;     // output plane-tiles (b, tile x, tile y, oz), in that order
+};
+
+// kz slot: the pair (kz = par + 2, kz = par) at slots 2 par, 2 par + 1;
+// element (co, k = (ky 4 + kx) 2 + ci) at slot 2048 + (co / 8) 512 + (k / 8)
+// 128 + (co % 8) 16 + (k % 8) 2 (LBO 128, SBO 512).
+__device__ __forceinline__ int c2_slot(int kz) { return 2 * (kz & 1) + 1 - (kz >> 1); }
+__device__ __forceinline__ void c2_copy_weights(uint32_t wbase, const uint16_t *__restrict__ W, int first,
+                                                int step) {
+    for (int g = first; g < 32 * 4 * 4; g += step) {   // g = (co * 4 + kz) * 4 + kg
+        const int kg = g & 3, kz = (g >> 2) & 3, co = g >> 4;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         wbase + c2_slot(kz) * 2048 + (co >> 3) * 512 + kg * 128 + (co & 7) * 16),
+                     "l"(W + ((size_t)co * 64 + kz * 16) * 2 + kg * 8)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// One input plane z of the window by the 128 producers: piece g = u + 128 k
+// = (row, ox, kx) -> voxel (2 ox0 - 1 + 2 ox + kx, 2 oy0 - 1 + row), a
+// warp's 32 pieces being one row's 8 entries (coalesced, 72 bytes).
+__device__ __forceinline__ void c2_load_plane(uint32_t (&v)[kC2PerThread], const uint16_t *__restrict__ X, int D,
+                                              int b, int z, int ox0, int oy0, int u) {
+    const size_t plane = (((size_t)b * D + z) * D) * D;
+#pragma unroll
+    for (int k = 0; k < kC2PerThread; ++k) {
+        const int g = u + k * kProducers;
+        v[k] = 0u;
+        if (g < kC2Pieces) {
+            const int kx = g & 3, ox = (g >> 2) & 7, row = g >> 5;
+            const int x = 2 * (ox0 + ox) - 1 + kx, y = 2 * oy0 - 1 + row;
+            if ((unsigned)x < (unsigned)D && (unsigned)y < (unsigned)D)
+                v[k] = __ldg(reinterpret_cast<const uint32_t *>(X + (plane + (size_t)y * D + x) * 2));
+        }
+    }
+}
+__device__ __forceinline__ void c2_store_plane(uint8_t *buf, const uint32_t (&v)[kC2PerThread], int u) {
+#pragma unroll
+    for (int k = 0; k < kC2PerThread; ++k) {
+        const int g = u + k * kProducers;
+        if (g < kC2Pieces) *reinterpret_cast<uint32_t *>(buf + g * 4) = v[k];   // (row, ox, kx) -> row 128 + ox 16 + kx 4
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_conv_c2(const uint16_t *__restrict__ X, const C2Args p) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int D = p.D, Do = D >> 1;
+    const long long t0 = p.tiles * blockIdx.x / gridDim.x, t1 = p.tiles * (blockIdx.x + 1) / gridDim.x;
+    const long long cut = min(t1, (t0 / Do + 1) * Do);
+    Segment sg[2];
+    sg[0] = make_segment(D, t0, cut, 0);
+    const int nseg = cut < t1 ? 2 : 1;
+    sg[1] = nseg == 2 ? make_segment(D, cut, t1, (int)(cut - t0)) : sg[0];
+    const int np0 = sg[0].zh - sg[0].zl + 1;
+    const int nplanes = np0 + (nseg == 2 ? sg[1].zh - sg[1].zl + 1 : 0);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(sm + kC2SmemBar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kC2SmemBar + 8 * (2 * kC2Bufs + 1));
+    const uint32_t full0 = umma::smem_u32(&bars[0]), empty0 = umma::smem_u32(&bars[kC2Bufs]);
+    const uint32_t done = umma::smem_u32(&bars[2 * kC2Bufs]);
+    const uint32_t planes = umma::smem_u32(sm + kC2SmemPlanes), wbase = umma::smem_u32(sm + kC2SmemWeights);
+    auto seg_of = [&](int i) -> const Segment & { return i < np0 ? sg[0] : sg[1]; };
+    auto z_of = [&](int i) { return i < np0 ? sg[0].zl + i : sg[1].zl + (i - np0); };
+
+    if (warp == 0) umma::tmem_alloc(tmem_slot, 32 * kZC);
+    if (t == 0) {
+        for (int i = 0; i < 2 * kC2Bufs + 1; ++i)
+            umma::mbar_init(umma::smem_u32(&bars[i]), i < kC2Bufs ? (uint32_t)kProducers : 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    c2_copy_weights(wbase, p.W, t, kThreads);
+    const int u = t - 64;
+    uint32_t v[kC2PerThread];
+    if (warp >= 2 && nplanes > 0) {
+        const Segment &g = seg_of(0);
+        c2_load_plane(v, X, D, g.b, z_of(0), g.ox0, g.oy0, u);
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    umma::fence_async_smem();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    if (warp >= 2) {
+        for (int q = 0; q < kZC; ++q) tmem_zero32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * q));
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+
+    bool ok = true;
+    if (warp >= 2) {
+        for (int i = 0; i < nplanes; ++i) {
+            const int s = i % kC2Bufs;
+            if (i >= kC2Bufs && !umma::mbar_wait(empty0 + 8 * s, (uint32_t)(((i - kC2Bufs) / kC2Bufs) & 1))) {
+                ok = false;
+                break;
+            }
+            c2_store_plane(sm + kC2SmemPlanes + s * kC2Plane, v, u);
+            umma::fence_async_smem();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full0 + 8 * s) : "memory");
+            if (i + 1 < nplanes) {
+                const Segment &g = seg_of(i + 1);
+                c2_load_plane(v, X, D, g.b, z_of(i + 1), g.ox0, g.oy0, u);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // K-major descriptors: A rows (ox) 16 B apart, LBO 128 (next ky row),
+        // SBO 256 (next oy: two input rows); B as in the 32-channel kernel
+        const uint64_t adesc0 = umma::smem_desc(planes, kTileX * 16, 2 * kTileX * 16);
+        const uint64_t bdesc0 = umma::smem_desc(wbase, 128, 512);
+        for (int i = 0; i < nplanes; ++i) {
+            const int s = i % kC2Bufs;
+            if (!umma::mbar_wait(full0 + 8 * s, (uint32_t)((i / kC2Bufs) & 1))) {
+                ok = false;
+                break;
+            }
+            umma::fence_after_sync();
+            const Segment &g = seg_of(i);
+            const int z = z_of(i), n = g.o1 - g.o0;
+            const int par = (z + 1) & 1;
+            const int qa = ((z + 1 - par) >> 1) - g.o0, qb = qa - 1;
+            const bool va = qa >= 0 && qa < n, vb = qb >= 0 && qb < n;
+            const uint64_t ab = adesc0 + (uint64_t)((s * kC2Plane) >> 4);
+            const uint64_t bpair = bdesc0 + (uint64_t)((2 * par * 2048) >> 4);
+            const uint32_t dt = tmem + 32 * (g.sb + (vb ? qb : qa));
+            const uint32_t idesc = (va && vb) ? kIdesc64 : kIdesc32;
+            const uint32_t bsel = (va && vb) ? 0u : (va ? 2048u >> 4 : 0u);
+#pragma unroll
+            for (int m = 0; m < 2; ++m)   // ky pair (2 m, 2 m + 1): rows 2 m .. of the window, K groups 2 m ..
+                umma::mma_bf16(dt, ab + (uint32_t)((2 * m * kTileX * 16) >> 4), bpair + bsel + (uint32_t)((2 * m * 128) >> 4),
+                               idesc, true);
+            umma::commit(empty0 + 8 * s);
+        }
+        if (ok) umma::commit(done);
+    }
+    bool waited = true;
+    if (warp >= 2 && ok) waited = umma::mbar_wait(done, 0u);
+    const bool all_ok = __syncthreads_and(ok && waited);
+    if (all_ok && warp >= 2) {
+        umma::fence_after_sync();
+        const int wq = warp & 3;
+        const int r = 32 * wq + lane;
+        for (int k = 0; k < nseg; ++k) {
+            const Segment &g = k ? sg[1] : sg[0];
+            const int ox = g.ox0 + (r & 7), oy = g.oy0 + (r >> 3);
+            for (int q = 0; q < g.o1 - g.o0; ++q) {
+                float acc[32];
+                umma::tmem_ld32(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(32 * (g.sb + q)), acc);
+                uint32_t packed[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float a = fmaxf(acc[2 * i] + p.bias[2 * i], 0.0f);
+                    const float c = fmaxf(acc[2 * i + 1] + p.bias[2 * i + 1], 0.0f);
+                    const __nv_bfloat162 hv = __floats2bfloat162_rn(a, c);
+                    packed[i] = *reinterpret_cast<const uint32_t *>(&hv);
+                }
+                const size_t row = (((size_t)g.b * Do + (g.o0 + q)) * Do + oy) * Do + ox;
+                uint4 *dst = reinterpret_cast<uint4 *>(p.Y + row * 32);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    dst[i] = make_uint4(packed[4 * i], packed[4 * i + 1], packed[4 * i + 2], packed[4 * i + 3]);
+            }
+        }
+    }
+    if (!all_ok && t == 0) atomicExch(&g_c2_error, 1u);
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, 32 * kZC);
+}
+
 }  // namespace convp
 }  // namespace pfreg
 
@@ -567,17 +772,47 @@ cudaError_t conv_planes_wgrad(const uint16_t *X, int batch, int D, const uint16_
     return cudaGetLastError();
 }
 
+// The first layer's forward convolution (2 -> 32 channels; the kernel
+// above) applies to inputs whose output edge is a multiple of 16.
+bool conv_c2_applies(int D, int Cin) { return Cin == 2 && D >= 32 && D % 32 == 0 && D <= 512; }
+
+// y = relu(conv(x, w) + bias) for 2 -> 32 channels; x [batch][D^3][2],
+// w [32][64][2], y [batch][(D/2)^3][32], bf16.
+cudaError_t conv_c2_forward(const uint16_t *X, int batch, int D, const uint16_t *W, const float *bias, uint16_t *Y,
+                            cudaStream_t s) {
+    using namespace convp;
+    if (!conv_c2_applies(D, 2) || batch < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_conv_c2, cudaFuncAttributeMaxDynamicSharedMemorySize, kC2SmemTotal);
+    if (e != cudaSuccess) return e;
+    const int Do = D / 2;
+    const long long tiles = (long long)batch * (Do / kTileX) * (Do / kTileY) * Do;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    // two CTAs per SM (256 tensor-memory columns each), ranges of at most kZC plane-tiles
+    long long grid = tiles < 2LL * sms ? tiles : 2LL * sms;
+    if ((tiles + grid - 1) / grid > kZC) grid = (tiles + kZC - 1) / kZC;
+    if (grid > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    const C2Args a{W, bias, Y, batch, D, tiles};
+    k_conv_c2<<<(unsigned)grid, kThreads, kC2SmemTotal, s>>>(X, a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 // The error flags of the plane-staged kernels (a bounded wait gave up).
 cudaError_t conv_planes_error_flag(unsigned int *out, bool clear) {
-    unsigned int f = 0, w = 0;
+    unsigned int f = 0, w = 0, c2 = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&f, convp::g_conv_error, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&w, convp::g_wgrad_error, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&c2, convp::g_c2_error, sizeof(unsigned int));
     if (e != cudaSuccess) return e;
-    *out = f | w;
+    *out = f | w | c2;
     if (!clear) return e;
     const unsigned int z = 0;
     e = cudaMemcpyToSymbol(convp::g_conv_error, &z, sizeof(z));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(convp::g_wgrad_error, &z, sizeof(z));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(convp::g_c2_error, &z, sizeof(z));
     return e;
 }
 

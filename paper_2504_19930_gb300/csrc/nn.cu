@@ -1319,6 +1319,7 @@ cudaError_t nn_conv_fwd(const uint16_t *X, int batch, int D, int Cin, const uint
                         uint16_t *Y, cudaStream_t s) {
 #if PF_CONV_PLANES
     if (conv_planes_applies(D, Cin)) return conv_planes_forward(X, batch, D, W, bias, Y, s);
+    if (conv_c2_applies(D, Cin)) return conv_c2_forward(X, batch, D, W, bias, Y, s);
 #endif
     nn::ConvFwdOp op{{batch, D, Cin}, X, W, bias, Y};
     const int Do = D / 2;

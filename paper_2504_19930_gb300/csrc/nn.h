@@ -65,6 +65,9 @@ bool conv_planes_applies(int D, int Cin);
 cudaError_t conv_planes_forward(const uint16_t *X, int batch, int D, const uint16_t *W, const float *bias,
                                 uint16_t *Y, cudaStream_t s);
 cudaError_t conv_planes_error_flag(unsigned int *out, bool clear);
+bool conv_c2_applies(int D, int Cin);
+cudaError_t conv_c2_forward(const uint16_t *X, int batch, int D, const uint16_t *W, const float *bias, uint16_t *Y,
+                            cudaStream_t s);
 cudaError_t conv_planes_wgrad(const uint16_t *X, int batch, int D, const uint16_t *dY, float *dW, cudaStream_t s);
 // the plane-staged data gradient of the same convolution (dgrad.cu)
 bool dgrad_planes_applies(int D);

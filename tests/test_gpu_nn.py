@@ -73,7 +73,7 @@ def test_gemm_bf16(torch_, pk, M, K):
 
 
 @pytest.mark.parametrize("Bn,D,Cin", [(2, 10, 32), (2, 18, 2), (1, 2, 8), (4, 64, 2), (4, 32, 32), (1, 32, 32),
-                                      (2, 64, 32)])
+                                      (2, 64, 32), (1, 32, 2)])
 def test_conv_forward(torch_, pk, Bn, D, Cin):
     torch = torch_
     rng = np.random.default_rng(10 * D + Cin)
