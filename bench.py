@@ -68,14 +68,13 @@ FP32_LANES_PER_SM = 128
 # L2 -> L1 bytes per visited evaluation.  A workload without its own capture,
 # or whose kernel changed since, reports null.
 NCU_COUNTERS = {
-    # profiles/measure_image224x208x176_n2048.md
-    "image224": {"measure_code_sha1": "4da90d17281f3040a9df29f4df6086daad5fa4ed",
-                 "dram_bytes_per_launch": 36267520, "l2_to_l1_bytes_per_eval": 139412340768 / 9388958565.74},
-    # profiles/measure_counters_mask64_combined256.md
-    "mask64": {"measure_code_sha1": "4da90d17281f3040a9df29f4df6086daad5fa4ed",
-               "dram_bytes_per_launch": 275968, "l2_to_l1_bytes_per_eval": 43838304 / 41168147.2},
-    "combined256": {"measure_code_sha1": "4da90d17281f3040a9df29f4df6086daad5fa4ed",
-                    "dram_bytes_per_launch": 140447588608, "l2_to_l1_bytes_per_eval": 2003333743264 / 152465706355.25},
+    # profiles/measure_counters_image224_mask64_combined256.md
+    "image224": {"measure_code_sha1": "42c6fb5ada11cf158665be670855a77ffecc4fe2",
+                 "dram_bytes_per_launch": 36182784, "l2_to_l1_bytes_per_eval": 139406476736 / 9388958565.74},
+    "mask64": {"measure_code_sha1": "42c6fb5ada11cf158665be670855a77ffecc4fe2",
+               "dram_bytes_per_launch": 278528, "l2_to_l1_bytes_per_eval": 46382912 / 41168147.2},
+    "combined256": {"measure_code_sha1": "42c6fb5ada11cf158665be670855a77ffecc4fe2",
+                    "dram_bytes_per_launch": 140074539520, "l2_to_l1_bytes_per_eval": 2002563646368 / 152465706355.25},
 }
 
 
