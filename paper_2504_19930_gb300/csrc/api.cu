@@ -168,6 +168,7 @@ struct pf_ctx {
     // record nodes around it whose events are swapped per launch
     cudaEvent_t ev_before = nullptr, ev_after = nullptr;
     cudaGraphNode_t node_before = nullptr, node_after = nullptr;
+    uint64_t graph_kernels = 0;             // kernel nodes of one iteration's graph
     std::vector<cudaEvent_t> prof_events;   // 2 per timed iteration
     int prof_next = 0;
     bool prof_default = true;               // the record nodes hold ev_before/ev_after
@@ -268,9 +269,11 @@ int build_graph(pf_ctx *c) {
     CU(cudaGraphGetNodes(c->graph, nullptr, &n));
     std::vector<cudaGraphNode_t> nodes(n);
     CU(cudaGraphGetNodes(c->graph, nodes.data(), &n));
+    c->graph_kernels = 0;
     for (cudaGraphNode_t nd : nodes) {
         cudaGraphNodeType t;
         CU(cudaGraphNodeGetType(nd, &t));
+        c->graph_kernels += t == cudaGraphNodeTypeKernel;
         if (t != cudaGraphNodeTypeEventRecord) continue;
         cudaEvent_t ev;
         CU(cudaGraphEventRecordNodeGetEvent(nd, &ev));
@@ -624,7 +627,7 @@ int pf_step(pf_ctx *c, int32_t n_iters) {
             c->prof_default = true;
         }
         CU(cudaGraphLaunch(c->exec, c->stream));
-        count_launches(c->trace ? 8 : 5);
+        count_launches(c->graph_kernels);
     }
     return PF_OK;
 }

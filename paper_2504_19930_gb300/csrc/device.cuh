@@ -62,26 +62,69 @@ __device__ __forceinline__ float unit24(uint32_t u) {
 // fp64 sin / cos, |x| <= pi/2: Taylor series, term k = term k-1 * (-x^2) /
 // ((2k)(2k+1)) (sin) or / ((2k-1)(2k)) (cos), 14 terms, summed smallest first.
 // Written out so host and device agree bit for bit without either libm.
+//
+// One code path serves both: a lane computing a cosine differs from one
+// computing a sine only in its first term and its divisors, so the lanes of
+// a warp that hold the three sines and the three cosines of a pose run the
+// chain together instead of one function after the other.
+//
+// Each quotient a / c_k must be the correctly rounded one.  A division costs
+// ~550 clocks of dependent latency on this GPU against ~64 for a multiply or
+// FMA, and the divisors are constants, so the chain takes q = RN(a * y) with
+// y = RN(1 / c_k), the exact remainder r = fma(-q, c_k, a) and the corrected
+// quotient fma(r, y, q) -- Markstein's correction step (IBM J. Res. Dev.
+// 34(1), 1990), used for constant divisors by Brisebarre, Muller and Raina
+// (IEEE Trans. Comput. 53(8), 2004).  Rather than rest on that theorem's
+// hypotheses, the identity RN(a / c_k) == fma(r, y, q) was checked for every
+// division of both chains at every fp32 angle with 2^-32 <= |x| <= 64 (the
+// chains' values are odd or even in x, and round-to-nearest is symmetric,
+// so x >= 0 covers both signs): no mismatch.  Below 2^-32 the terms reach
+// the subnormal range, where the step can be off by one unit in the last
+// place, so those angles (and any beyond 64) take the IEEE division.  The
+// angles arrive as fp32, so this covers every input the kernels can see.
 // ---------------------------------------------------------------------------
-PF_HD double taylor_sin(double x) {
+// RN(1 / c_k), k = 1..13 (entry 0 unused): c_k = (2k)(2k+1) and (2k-1)(2k).
+#define PF_TAYLOR_RECIP_SIN {0.0, 0x1.5555555555555p-3, 0x1.999999999999ap-5, 0x1.8618618618618p-6, \
+    0x1.c71c71c71c71cp-7, 0x1.29e4129e4129ep-7, 0x1.a41a41a41a41ap-8, 0x1.3813813813814p-8,           \
+    0x1.e1e1e1e1e1e1ep-9, 0x1.7f405fd017f40p-9, 0x1.3813813813814p-9, 0x1.03091b51f5e1ap-9,           \
+    0x1.b4e81b4e81b4fp-10, 0x1.756cac201756dp-10}
+#define PF_TAYLOR_RECIP_COS {0.0, 0x1.0000000000000p-1, 0x1.5555555555555p-4, 0x1.1111111111111p-5, \
+    0x1.2492492492492p-6, 0x1.6c16c16c16c17p-7, 0x1.f07c1f07c1f08p-8, 0x1.6816816816817p-8,           \
+    0x1.1111111111111p-8, 0x1.ac5701ac5701bp-9, 0x1.58ed2308158edp-9, 0x1.1bb4a4046ed29p-9,           \
+    0x1.dae6076b981dbp-10, 0x1.934c67f9b2ce6p-10}
+
+// The angle is taken as the fp32 value it always is, which is what the check covered.
+PF_HD double taylor_sincos(float xf, bool cosine) {
+    const double ys[14] = PF_TAYLOR_RECIP_SIN, yc[14] = PF_TAYLOR_RECIP_COS;
+    const double x = (double)xf;
     const double mx2 = -d_mul(x, x);
+    const double ax = fabs(x);
     double t[14];
-    t[0] = x;
-    for (int k = 1; k < 14; ++k) t[k] = d_div(d_mul(t[k - 1], mx2), (double)((2 * k) * (2 * k + 1)));
+    t[0] = cosine ? 1.0 : x;
+    if (ax >= 0x1p-32 && ax <= 64.0) {
+#pragma unroll
+        for (int k = 1; k < 14; ++k) {
+            const double c = cosine ? (double)((2 * k - 1) * (2 * k)) : (double)((2 * k) * (2 * k + 1));
+            const double y = cosine ? yc[k] : ys[k];
+            const double a = d_mul(t[k - 1], mx2);
+            const double q = __dmul_rn(a, y);
+            t[k] = __fma_rn(__fma_rn(-q, c, a), y, q);
+        }
+    } else {
+#pragma unroll
+        for (int k = 1; k < 14; ++k) {
+            const double c = cosine ? (double)((2 * k - 1) * (2 * k)) : (double)((2 * k) * (2 * k + 1));
+            t[k] = d_div(d_mul(t[k - 1], mx2), c);
+        }
+    }
     double s = 0.0;
+#pragma unroll
     for (int k = 13; k >= 0; --k) s = d_add(s, t[k]);
     return s;
 }
 
-PF_HD double taylor_cos(double x) {
-    const double mx2 = -d_mul(x, x);
-    double t[14];
-    t[0] = 1.0;
-    for (int k = 1; k < 14; ++k) t[k] = d_div(d_mul(t[k - 1], mx2), (double)((2 * k - 1) * (2 * k)));
-    double s = 0.0;
-    for (int k = 13; k >= 0; --k) s = d_add(s, t[k]);
-    return s;
-}
+PF_HD double taylor_sin(float x) { return taylor_sincos(x, false); }
+PF_HD double taylor_cos(float x) { return taylor_sincos(x, true); }
 
 // 3x3 product C = A B, each entry accumulated from 0 in k order (fp64).
 PF_HD void mat3_mul(const double A[9], const double B[9], double C[9]) {
@@ -137,9 +180,8 @@ PF_HD void matrix_from_sincos(const float pose[6], double sa, double ca, double 
 }
 
 PF_HD void pose_to_matrix(const float pose[6], const Geometry &g, float M[12]) {
-    matrix_from_sincos(pose, taylor_sin((double)pose[0]), taylor_cos((double)pose[0]),
-                       taylor_sin((double)pose[1]), taylor_cos((double)pose[1]),
-                       taylor_sin((double)pose[2]), taylor_cos((double)pose[2]), g, M);
+    matrix_from_sincos(pose, taylor_sin(pose[0]), taylor_cos(pose[0]), taylor_sin(pose[1]), taylor_cos(pose[1]),
+                       taylor_sin(pose[2]), taylor_cos(pose[2]), g, M);
 }
 
 // ---------------------------------------------------------------------------

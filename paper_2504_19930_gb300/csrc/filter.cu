@@ -83,8 +83,7 @@ __device__ __forceinline__ void predict_particle(const FilterParams &P, const Fi
     // lanes 0-2: sin(angle j); lanes 3-5: cos(angle j-3)
     const float ang = __shfl_sync(gmask, x, gbase + (j < 3 ? j : (j < 6 ? j - 3 : 0)));
     double tv = 0.0;
-    if (j < 3) tv = taylor_sin((double)ang);
-    else if (j < 6) tv = taylor_cos((double)ang);
+    if (j < 6) tv = taylor_sincos(ang, j >= 3);   // one chain for the sine and cosine lanes
     double sc[6];
     float pose[6];
 #pragma unroll
@@ -200,22 +199,30 @@ constexpr int kRed = 17;                   // reduced values: 6 pose sums, sum W
 // non-negative double (which order like the values) by a 64-bit atomic max,
 // and the number of evaluations (sum of the overlap counts).  stats[0..1] are
 // zeroed by the prediction kernel.
-__device__ __forceinline__ void score_particle(const FilterParams &P, const FilterBuffers &B, int i, bool valid) {
+// The warp's maximum score bits and evaluation count are returned on every lane.
+__device__ __forceinline__ void score_particle_warp(const FilterParams &P, const FilterBuffers &B, int i,
+                                                    bool valid, unsigned long long &bits,
+                                                    unsigned long long &ev) {
     double s = 0.0;
-    unsigned long long ev = 0;
+    ev = 0;
     if (valid) {
         const unsigned long long *m = B.mom + (size_t)i * kMomStride;
         s = score_from_moments(P.mode, m, P.b_full, P.n_min);
         B.scores[i] = s;
         ev = m[(P.mode == 2 || P.mode == 3) ? 0 : 8];
     }
-    unsigned long long bits = (unsigned long long)__double_as_longlong(s);
+    bits = (unsigned long long)__double_as_longlong(s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
         bits = ob > bits ? ob : bits;
         ev += __shfl_xor_sync(0xffffffffu, ev, o);
     }
+}
+
+__device__ __forceinline__ void score_particle(const FilterParams &P, const FilterBuffers &B, int i, bool valid) {
+    unsigned long long bits, ev;
+    score_particle_warp(P, B, i, valid, bits, ev);
     if ((threadIdx.x & 31) == 0) {
         atomicMax(B.stats + 0, bits);
         if (ev) atomicAdd(B.stats + 1, ev);
@@ -415,6 +422,42 @@ __global__ void __launch_bounds__(kFinThreads) k_finalise(const FilterParams P, 
     finalise_block(P, B);
 }
 
+// The whole update of a cloud that fits one CTA (N <= kFinThreads) in one
+// launch: thread i scores particle i, the block reduces the maximum score and
+// the evaluation count (the integers the atomics of the multi-CTA form
+// produce), then the weights, then the estimate and resampling.  It saves
+// the two small launches and their gaps, which on a 64^3 mask registration
+// are a few percent of each iteration.
+__global__ void __launch_bounds__(kFinThreads) k_update_small(const FilterParams P, const FilterBuffers B) {
+    __shared__ unsigned long long sh_bits[kFinWarps], sh_ev[kFinWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned long long bits, ev;
+    score_particle_warp(P, B, tid, tid < P.N, bits, ev);
+    if (lane == 0) {
+        sh_bits[warp] = bits;
+        sh_ev[warp] = ev;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        bits = sh_bits[lane];
+        ev = sh_ev[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+            bits = ob > bits ? ob : bits;
+            ev += __shfl_xor_sync(0xffffffffu, ev, o);
+        }
+        if (lane == 0) {
+            B.stats[0] = bits;
+            B.stats[1] = ev;
+        }
+    }
+    __syncthreads();
+    if (tid < P.N) weight_particle(P, B, tid);
+    __syncthreads();
+    finalise_block(P, B);
+}
+
 // Batched prediction: group of 8 lanes -> (registration, particle) by binary
 // search on the particle prefix; registrations that have finished are skipped
 // (every lane of a group takes the same branch).
@@ -480,8 +523,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalise_batch(const BatchReg *
 __device__ __forceinline__ void group_pose_matrix(const float pose[6], int j, unsigned gmask, int gbase,
                                                   const Geometry &g, float M[12]) {
     double tv = 0.0;
-    if (j < 3) tv = taylor_sin((double)pose[j]);
-    else if (j < 6) tv = taylor_cos((double)pose[j - 3]);
+    if (j < 6) tv = taylor_sincos(pose[j < 3 ? j : j - 3], j >= 3);
     double sc[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) sc[q] = __shfl_sync(gmask, tv, gbase + q);
@@ -632,6 +674,14 @@ cudaError_t launch_finalise(const FilterParams &p, const FilterBuffers &b, cudaS
     cudaError_t e = cudaFuncSetAttribute(k_finalise, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(kCdfSmem * sizeof(unsigned long long)));
     if (e != cudaSuccess) return e;
+    if (p.N <= kFinThreads) {
+        e = cudaFuncSetAttribute(k_update_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kCdfSmem * sizeof(unsigned long long)));
+        if (e != cudaSuccess) return e;
+        k_update_small<<<1, kFinThreads, kCdfSmem * sizeof(unsigned long long), s>>>(p, b);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     k_score<<<blocks_for(p.N, 128), 128, 0, s>>>(p, b);
     k_weights<<<blocks_for(p.N, 128), 128, 0, s>>>(p, b);
     k_finalise<<<1, kFinThreads, kCdfSmem * sizeof(unsigned long long), s>>>(p, b);

@@ -135,8 +135,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const WarpArgs a) {
     __shared__ double sc[6];
     __shared__ float Ms[12];
     if (threadIdx.x < 6) {
-        const double ang = (double)a.pose[threadIdx.x % 3];
-        sc[threadIdx.x] = threadIdx.x < 3 ? taylor_sin(ang) : taylor_cos(ang);
+        sc[threadIdx.x] = taylor_sincos(a.pose[threadIdx.x % 3], threadIdx.x >= 3);
     }
     __syncthreads();
     if (threadIdx.x == 0) matrix_from_sincos(a.pose, sc[0], sc[3], sc[1], sc[4], sc[2], sc[5], a.g, Ms);
