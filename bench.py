@@ -69,10 +69,10 @@ FP32_LANES_PER_SM = 128
 # or whose kernel changed since, reports null.
 NCU_COUNTERS = {
     # profiles/measure_counters_image224_mask64_combined256.md
-    "image224": {"measure_code_sha1": "42c6fb5ada11cf158665be670855a77ffecc4fe2",
-                 "dram_bytes_per_launch": 36182784, "l2_to_l1_bytes_per_eval": 139406476736 / 9388958565.74},
-    "mask64": {"measure_code_sha1": "42c6fb5ada11cf158665be670855a77ffecc4fe2",
-               "dram_bytes_per_launch": 278528, "l2_to_l1_bytes_per_eval": 46382912 / 41168147.2},
+    "image224": {"measure_code_sha1": "1d26970369b009c4d4885828ca94135a828b8568",
+                 "dram_bytes_per_launch": 36136704, "l2_to_l1_bytes_per_eval": 139410378752 / 9388958565.74},
+    "mask64": {"measure_code_sha1": "1d26970369b009c4d4885828ca94135a828b8568",
+               "dram_bytes_per_launch": 278016, "l2_to_l1_bytes_per_eval": 43771840 / 41168147.2},
     "combined256": {"measure_code_sha1": "42c6fb5ada11cf158665be670855a77ffecc4fe2",
                     "dram_bytes_per_launch": 140074539520, "l2_to_l1_bytes_per_eval": 2002563646368 / 152465706355.25},
 }
