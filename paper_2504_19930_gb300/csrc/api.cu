@@ -179,19 +179,46 @@ struct pf_ctx {
     std::vector<void *> allocs;
 
     long long alloc_bytes = 0;
+    // One device block that alloc() carves the context's buffers from (one
+    // cudaMalloc instead of one per buffer: creation lies inside the time of
+    // every registration, and a 64^3 one takes under 2 ms).
+    char *arena = nullptr;
+    size_t arena_cap = 0, arena_used = 0;
 
-    template <class T>
-    cudaError_t alloc(T **p, size_t count) {
-        const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 1;
+    static size_t padded(size_t bytes) { return ((bytes > 0 ? bytes : 1) + 255) & ~(size_t)255; }
+
+    cudaError_t raw_alloc(void **q, size_t bytes) {
         const long long cap = g_alloc_limit.load();
         if (cap > 0 && alloc_bytes + (long long)bytes > cap) return cudaErrorMemoryAllocation;
-        void *q = nullptr;
-        cudaError_t e = dev_malloc(&q, bytes);
+        cudaError_t e = dev_malloc(q, bytes);
         if (e == cudaSuccess) {
-            allocs.push_back(q);
+            allocs.push_back(*q);
             alloc_bytes += (long long)bytes;
-            *p = static_cast<T *>(q);
         }
+        return e;
+    }
+    cudaError_t reserve(size_t bytes) {
+        void *q = nullptr;
+        cudaError_t e = raw_alloc(&q, bytes);
+        if (e == cudaSuccess) {
+            arena = static_cast<char *>(q);
+            arena_cap = bytes;
+            arena_used = 0;
+        }
+        return e;
+    }
+    // count elements of T, 256-byte aligned; from the block while it has room
+    template <class T>
+    cudaError_t alloc(T **p, size_t count) {
+        const size_t bytes = padded(count * sizeof(T));
+        if (arena && arena_cap - arena_used >= bytes) {
+            *p = reinterpret_cast<T *>(arena + arena_used);
+            arena_used += bytes;
+            return cudaSuccess;
+        }
+        void *q = nullptr;
+        cudaError_t e = raw_alloc(&q, bytes);
+        if (e == cudaSuccess) *p = static_cast<T *>(q);
         return e;
     }
     ~pf_ctx() {
@@ -504,24 +531,52 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
     P.estimator = cfg->estimator;
 
     FilterBuffers &B = c->B;
-    CK(c->alloc(&B.poses, 6 * (size_t)N));
-    CK(c->alloc(&B.poses_meas, 6 * (size_t)N));
-    CK(c->alloc(&B.mats, 12 * (size_t)N));
-    CK(c->alloc(&B.mom, (size_t)kMomStride * N));
-    CK(c->alloc(&B.scores, (size_t)N));
-    CK(c->alloc(&B.W, (size_t)N));
-    CK(c->alloc(&B.C, (size_t)N));
-    CK(c->alloc(&B.idx, (size_t)N));
-    CK(c->alloc(&B.k, 1));
-    CK(c->alloc(&B.log, (size_t)kLogCapacity));
-    if (P.estimator == PF_EST_QUATERNION) CK(c->alloc(&B.quat, 4 * (size_t)N));
-    CK(c->alloc(&c->d_u64, 4));
-    CK(c->alloc(&c->d_score, 1));
+    uint8_t *tmp = nullptr;   // staging of host masks
+    const bool host_masks = have_masks && (!src_mask->is_device || !tgt_mask->is_device);
+    // Every device buffer of the context, listed once: the list is walked to
+    // size the block, then again to carve the buffers from it.
+    auto buffers = [&](auto &&take) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        auto want = [&](auto **p, size_t n) {
+            if (e == cudaSuccess) e = take(p, n);
+        };
+        want(&B.poses, 6 * (size_t)N);
+        want(&B.poses_meas, 6 * (size_t)N);
+        want(&B.mats, 12 * (size_t)N);
+        want(&B.mom, (size_t)kMomStride * N);
+        want(&B.scores, (size_t)N);
+        want(&B.W, (size_t)N);
+        want(&B.C, (size_t)N);
+        want(&B.idx, (size_t)N);
+        want(&B.k, 1);
+        want(&B.log, (size_t)kLogCapacity);
+        if (P.estimator == PF_EST_QUATERNION) want(&B.quat, 4 * (size_t)N);
+        want(&c->d_u64, 4);
+        want(&c->d_score, 1);
+        if (img) {
+            want(&c->src_quad, ns);
+            want(&c->tgt_img, nt);
+        }
+        want(&B.stats, 2);
+        want(&B.trace_mat, 12);
+        want(&B.trace_mom, (size_t)kMomStride);
+        if (have_masks) {
+            want(&c->src_bits, (ns + 31) / 32);
+            want(&c->tgt_mask, nt);
+            if (host_masks) want(&tmp, ns > nt ? ns : nt);
+        }
+        return e;
+    };
+    size_t block = 0;
+    buffers([&](auto **p, size_t n) {
+        block += pf_ctx::padded(n * sizeof(**p));
+        return cudaSuccess;
+    });
+    CK(c->reserve(block));
+    CK(buffers([&](auto **p, size_t n) { return c->alloc(p, n); }));
 
     if (img) {
         uint8_t *raw = nullptr;
-        CK(c->alloc(&c->src_quad, ns));
-        CK(c->alloc(&c->tgt_img, nt));
         const uint8_t *sp = static_cast<const uint8_t *>(src->data);
         if (!src->is_device) {
             CK(dev_malloc_async(&raw, ns, c->stream));
@@ -532,16 +587,9 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
         if (raw) CK(cudaFreeAsync(raw, c->stream));
         CK(copy_in(c->tgt_img, tgt, nt, c->stream));
     }
-    CK(c->alloc(&B.stats, 2));
-    CK(c->alloc(&B.trace_mat, 12));
-    CK(c->alloc(&B.trace_mom, (size_t)kMomStride));
     if (have_masks) {
-        uint8_t *tmp = nullptr;
-        CK(c->alloc(&c->src_bits, (ns + 31) / 32));
-        CK(c->alloc(&c->tgt_mask, nt));
         const uint8_t *sm = static_cast<const uint8_t *>(src_mask->data);
         const uint8_t *tm = static_cast<const uint8_t *>(tgt_mask->data);
-        if (!src_mask->is_device || !tgt_mask->is_device) CK(c->alloc(&tmp, ns > nt ? ns : nt));
         if (!src_mask->is_device) {
             CK(copy_in(tmp, src_mask, ns, c->stream));
             sm = tmp;
@@ -555,10 +603,6 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
         CK(launch_binarise(tm, c->tgt_mask, (int64_t)nt, c->stream));
         CK(cudaMemsetAsync(c->d_u64, 0, sizeof(unsigned long long), c->stream));
         CK(launch_count_nonzero(c->tgt_mask, (int64_t)nt, c->d_u64, c->stream));
-        unsigned long long bfull = 0;
-        CK(cudaMemcpyAsync(&bfull, c->d_u64, sizeof bfull, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        P.b_full = bfull;
     }
 
     MeasureArgs &MA = c->MA;
@@ -580,8 +624,11 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt, c
 
     CK(cudaMemsetAsync(B.k, 0, sizeof(int32_t), c->stream));
     CK(cudaMemsetAsync(B.mom, 0, sizeof(unsigned long long) * kMomStride * (size_t)N, c->stream));
-    CK(launch_init_particles(P, B, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(launch_init_particles(P, B, c->stream));   // the initial cloud does not depend on b_full
+    unsigned long long bfull = 0;
+    if (have_masks) CK(cudaMemcpyAsync(&bfull, c->d_u64, sizeof bfull, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));   // one wait for all the set-up work
+    P.b_full = bfull;
     if (cfg->autotune) {
         rc = autotune_ctx(c);
         if (rc) return bail(rc);
