@@ -309,7 +309,11 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
     }
     const unsigned long long S = carry;
 
-    // 3. estimate and sum of squared weights, one block reduction of 7 values
+    // 3. estimate and sum of squared weights, one block reduction of 7 values.
+    // Only the warps that hold particles reduce: the others' sums are +0.0,
+    // which warp 0 substitutes, and the fp64 pipe (2 lanes per clock per SM)
+    // would spend ~16 clocks per warp instruction on their zeros.
+    const int nw = N < kFinThreads ? (N + 31) / 32 : kFinWarps;
     double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int i = tid; i < N; i += kFinThreads) {
         const double w = (double)B.W[i];
@@ -320,11 +324,13 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
         }
         acc[6] = __dadd_rn(acc[6], __dmul_rn(w, w));
     }
+    if (warp < nw) {
 #pragma unroll
-    for (int d = 0; d < 7; ++d) {
+        for (int d = 0; d < 7; ++d) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[d] = __dadd_rn(acc[d], __shfl_xor_sync(0xffffffffu, acc[d], o));
-        if (lane == 0) sh_d[warp][d] = acc[d];
+            for (int o = 16; o > 0; o >>= 1) acc[d] = __dadd_rn(acc[d], __shfl_xor_sync(0xffffffffu, acc[d], o));
+            if (lane == 0) sh_d[warp][d] = acc[d];
+        }
     }
     if (P.estimator == 1) {   // the 10 entries of sum W q q^T (upper triangle, row by row)
         double aq[10];
@@ -344,11 +350,13 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
                     aq[t] = __dadd_rn(aq[t], S > 0 ? __dmul_rn(w, qq) : qq);
                 }
         }
+        if (warp < nw) {
 #pragma unroll
-        for (int t = 0; t < 10; ++t) {
+            for (int t = 0; t < 10; ++t) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) aq[t] = __dadd_rn(aq[t], __shfl_xor_sync(0xffffffffu, aq[t], o));
-            if (lane == 0) sh_d[warp][7 + t] = aq[t];
+                for (int o = 16; o > 0; o >>= 1) aq[t] = __dadd_rn(aq[t], __shfl_xor_sync(0xffffffffu, aq[t], o));
+                if (lane == 0) sh_d[warp][7 + t] = aq[t];
+            }
         }
     }
     __syncthreads();
@@ -363,7 +371,7 @@ __device__ __forceinline__ void finalise_block(const FilterParams &P, const Filt
 #pragma unroll
         for (int d = 0; d < kRed; ++d) {
             if (d < nred) {
-                double t = sh_d[lane][d];
+                double t = lane < nw ? sh_d[lane][d] : 0.0;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) t = __dadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
                 if (lane == 0) sh_est[d] = t;
