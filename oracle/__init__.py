@@ -61,7 +61,10 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
+            # PF_ORACLE_LIB names another build of pf_oracle.c: the mutation
+            # tests load copies with a planted mistake to show that the pins
+            # catch it.
+            _lib = C.CDLL(os.environ.get("PF_ORACLE_LIB") or build())
             _declare(_lib)
     return _lib
 

@@ -393,6 +393,17 @@ def test_score_zero_cases(orc):
     assert orc.dice_from_counts(10, 0, 0, 0) == 0.0
 
 
+def test_min_overlap_boundary(orc):
+    # the reading: a score is 0 when the overlap n is BELOW n_min, so n = n_min
+    # still scores.  Samples (1, 2, 3, 4) against (1, 2, 3, 5): r^2 = 0.9657...
+    m = [4, 10, 30, 0, 34, 11, 39]
+    r = np.corrcoef([1, 2, 3, 4], [1, 2, 3, 5])[0, 1]
+    assert orc.ncc2_from_moments(m, n_min=4) == pytest.approx(r * r, rel=1e-12)
+    assert orc.ncc2_from_moments(m, n_min=5) == 0.0
+    assert orc.dice_from_counts(7, 3, 2, 5, n_min=7) == pytest.approx(2 * 2 / (3 + 5))
+    assert orc.dice_from_counts(7, 3, 2, 5, n_min=8) == 0.0
+
+
 # ------------------------------------------------------ weights, resampling
 
 def test_weights_definition(orc):
@@ -461,6 +472,52 @@ def test_init_and_perturb_statistics(orc):
     assert np.all(np.abs(xc) <= lim[:, None])
     s = orc.sigma(0.25, 0.8, 3, lim)
     np.testing.assert_allclose(s, 0.25 * lim * 0.8**3, rtol=1e-6)
+
+
+def test_random_draws_independent_across_dofs_iterations_and_particles(orc):
+    # Each (particle, iteration, DOF) draws its own counter-based numbers: the
+    # initial DOFs are uncorrelated with one another, the perturbation noise
+    # of one iteration with that of the next and across DOFs, and the
+    # resampling offsets of successive iterations are uniform on [0, 2^32).
+    from scipy import stats as st
+    N = 20000
+    bound = 5 / math.sqrt(N)
+    lim = np.array([0.5, 0.4, 0.3, 8, 6, 4], np.float32)
+    x = orc.init_particles(N, 11, lim)
+    c = np.corrcoef(x)
+    assert np.all(np.abs(c[np.triu_indices(6, 1)]) < bound)
+    z = np.zeros((6, N), np.float32)
+    sig = np.full(6, 0.01, np.float32)
+    big = np.full(6, 1e3, np.float32)
+    e1 = orc.perturb(z, 11, 1, sig, big)
+    e2 = orc.perturb(z, 11, 2, sig, big)
+    for d in range(6):
+        assert abs(np.corrcoef(e1[d], e2[d])[0, 1]) < bound
+    c = np.corrcoef(e1)
+    assert np.all(np.abs(c[np.triu_indices(6, 1)]) < bound)
+    u = np.array([orc.resample_offset(11, k) for k in range(4096)], np.float64)
+    assert len(np.unique(u)) >= 4090
+    assert st.kstest(u / 2.0**32, "uniform").pvalue > 1e-4
+
+
+def test_register_noise_scale_follows_the_schedule_and_the_proposal_spread(orc):
+    # One step of the filter from a given cloud: the perturbation of
+    # iteration 1 moves each resampled particle by sigma_1 * eps, eps of unit
+    # variance, with sigma_1 = sigma0_frac * L * decay by default and
+    # sig_base * decay when a proposal's spread is given.
+    N, decay = 4096, 0.8
+    src = pfsynth.random_mask(4, (9, 9, 9), 0.5)
+    lim_r, lim_t = 3.0, 100.0
+    rng = np.random.default_rng(3)
+    x0 = (rng.uniform(-1, 1, (6, N)) * np.array([0.05] * 3 + [1.0] * 3)[:, None]).astype(np.float32)
+    for sig_base, want in ((None, 0.25 * np.array([lim_r] * 3 + [lim_t] * 3) * decay),
+                           (np.array([0.01, 0.02, 0.03, 0.4, 0.5, 0.6], np.float32),
+                            np.array([0.01, 0.02, 0.03, 0.4, 0.5, 0.6]) * decay)):
+        r = orc.register("mask_dice", (9, 9, 9), np.zeros(3, np.float32), (9, 9, 9), np.zeros(3, np.float32),
+                         N, 2, lim_r, lim_t, seed=5, src_mask=src, tgt_mask=src, poses=x0.copy(),
+                         sigma_decay=decay, sig_base=sig_base)
+        moved = r["tr_poses"][1] - r["tr_poses"][0][:, r["tr_idx"][0]]
+        np.testing.assert_allclose(moved.std(1), want, rtol=0.05)
 
 
 # ----------------------------------------------------------------- warp
