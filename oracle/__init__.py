@@ -18,7 +18,10 @@ Parity status of each function (what pins it, see ``tests/test_oracle_pins.py``)
                     the fp64 two-pass NCC within the rounding bound
   ncc2_f64          scipy.stats.pearsonr squared on the same samples
   weights/resample  closed forms (uniform, one-hot, copy counts) and an
-                    O(N^2) brute-force definition
+                    O(N^2) brute-force definition; offsets uniform over
+                    iterations
+  init / perturb    bounds, mean and variance, independence across DOFs,
+                    particles and iterations; the scheduled step size
   register          recovers the generating pose of a synthetic pair;
                     reaches the exhaustive grid optimum on tiny masks
   warp              identity returns the input; 90-degree maps equal numpy
