@@ -18,6 +18,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "pf_oracle.c")
 PINS = [os.path.join(ROOT, "tests", f) for f in ("test_oracle_pins.py", "test_oracle_filter.py")]
+NN_SRC = os.path.join(ROOT, "oracle", "nn.py")
+NN_PINS = [os.path.join(ROOT, "tests", "test_oracle_nn.py")]
 
 # (name, where in the paper the correct form comes from, text, planted text)
 MUTANTS = [
@@ -136,6 +138,53 @@ MUTANTS = [
 ]
 
 
+# The proposal network's oracle (oracle/nn.py, numpy) and its pins.
+NN_MUTANTS = [
+    ("conv_taps_transposed", "convolution (4^3 taps, stride 2, padding 1)",
+     "patch = xp[:, kz:kz + 2 * Do:2, ky:ky + 2 * Do:2, kx:kx + 2 * Do:2, :]\n        out += patch",
+     "patch = xp[:, kz:kz + 2 * Do:2, kx:kx + 2 * Do:2, ky:ky + 2 * Do:2, :]\n        out += patch"),
+    ("conv_bias_dropped", "convolution", "        out += np.asarray(bias, np.float64)\n", "        out += 0.0\n"),
+    ("dgrad_tap_flipped", "data gradient (adjoint of the convolution)",
+     "+= dy @ w[:, t, :]", "+= dy @ w[:, 63 - t, :]"),
+    ("wgrad_operands", "weight gradient", "dw[:, t, :] = g.T @ patch", "dw[:, t, :] = g.T @ np.roll(patch, 1, axis=0)"),
+    ("nll_mean_gradient_sign", "loss (Gaussian NLL)",
+     "g[:, :6] = -(y - mu) * np.exp(-s) / out.shape[0]", "g[:, :6] = (y - mu) * np.exp(-s) / out.shape[0]"),
+    ("nll_variance_gradient_half", "loss (Gaussian NLL)",
+     "g[:, 6:12] = 0.5 * (1.0 - r2 * np.exp(-s)) / out.shape[0]", "g[:, 6:12] = (1.0 - r2 * np.exp(-s)) / out.shape[0]"),
+    ("adam_no_bias_correction", "Adam", "mh = m / (1.0 - beta1 ** t)", "mh = m"),
+    ("adam_second_moment", "Adam", "v = beta2 * v + (1.0 - beta2) * g * g", "v = beta2 * v + (1.0 - beta2) * np.abs(g)"),
+    ("fc_relu_mask_dropped", "network backward", "dh = (dout @ P[\"f2w\"]) * (h > 0)", "dh = dout @ P[\"f2w\"]"),
+    ("conv_relu_mask_dropped", "network backward",
+     "d = rnd(conv3d_backward_data(d, rnd(P[f\"cw{l}\"]), below.shape[1]) * (below > 0))",
+     "d = rnd(conv3d_backward_data(d, rnd(P[f\"cw{l}\"]), below.shape[1]))"),
+    ("bias_gradient_scaled", "network backward", "put(f\"cb{l}\", d.reshape(-1, 32).sum(0))",
+     "put(f\"cb{l}\", d.reshape(-1, 32).mean(0))"),
+    ("bf16_ties_away", "bf16 rounding (nearest, ties to even)",
+     "r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)",
+     "r = ((u + np.uint64(0x8000)) >> np.uint64(16)) << np.uint64(16)"),
+    ("box_average_scale", "network input (box average / 64)",
+     "return np.where(cnt > 0, tot / np.maximum(cnt, 1) / 64.0, 0.0)",
+     "return np.where(cnt > 0, tot / np.maximum(cnt, 1), 0.0)"),
+    ("box_average_edge", "network input (box average)",
+     "lo = np.ceil((box_o[d] + h[d] * np.arange(G) - origin[d]) / spacing[d]).astype(np.int64)",
+     "lo = np.floor((box_o[d] + h[d] * np.arange(G) - origin[d]) / spacing[d]).astype(np.int64)"),
+]
+
+# Runs the network pins with a mutant module standing in for oracle.nn.
+_NN_RUNNER = """
+import importlib.util, sys
+sys.path.insert(0, sys.argv[1])
+import oracle
+spec = importlib.util.spec_from_file_location("oracle.nn", sys.argv[2])
+mod = importlib.util.module_from_spec(spec)
+sys.modules["oracle.nn"] = mod
+oracle.nn = mod
+spec.loader.exec_module(mod)
+import pytest
+sys.exit(pytest.main(sys.argv[3:]))
+"""
+
+
 def _build(name, text, planted, outdir):
     src = open(SRC).read()
     assert src.count(text) == 1, f"{name}: the text to replace must occur exactly once"
@@ -156,19 +205,46 @@ def _run_pins(so):
     return r.returncode, failed
 
 
+def _write_nn(name, text, planted, outdir):
+    src = open(NN_SRC).read()
+    assert src.count(text) == 1, f"{name}: the text to replace must occur exactly once"
+    path = os.path.join(outdir, f"nn_{name}.py")
+    with open(path, "w") as f:
+        f.write(src.replace(text, planted))
+    return path
+
+
+def _run_nn_pins(path):
+    r = subprocess.run([sys.executable, "-c", _NN_RUNNER, ROOT, path, *NN_PINS, "-x", "-q", "-p", "no:cacheprovider"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=900)
+    failed = [ln.split(" ")[1] for ln in r.stdout.splitlines() if ln.startswith("FAILED ")]
+    return r.returncode, failed
+
+
 def test_mutant_table_is_well_formed():
-    names = [m[0] for m in MUTANTS]
-    assert len(names) == len(set(names))
-    src = open(SRC).read()
-    for name, _, text, planted in MUTANTS:
-        assert src.count(text) == 1, name
-        assert text != planted, name
+    for table, path in ((MUTANTS, SRC), (NN_MUTANTS, NN_SRC)):
+        names = [m[0] for m in table]
+        assert len(names) == len(set(names))
+        src = open(path).read()
+        for name, _, text, planted in table:
+            assert src.count(text) == 1, name
+            assert text != planted, name
 
 
 def test_every_planted_mistake_fails_a_pin(tmp_path):
     sos = [(m[0], _build(m[0], m[2], m[3], str(tmp_path))) for m in MUTANTS]
     with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, 16))) as ex:
         results = list(ex.map(lambda t: (t[0],) + _run_pins(t[1]), sos))
+    survivors = [name for name, rc, _ in results if rc == 0]
+    assert not survivors, f"planted mistakes no pin caught: {survivors}"
+    for name, rc, failed in results:
+        assert rc == 1, f"{name}: the pin run ended with {rc} (a crash, not a failing pin)"
+
+
+def test_every_planted_network_mistake_fails_a_pin(tmp_path):
+    paths = [(m[0], _write_nn(m[0], m[2], m[3], str(tmp_path))) for m in NN_MUTANTS]
+    with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, 16))) as ex:
+        results = list(ex.map(lambda t: (t[0],) + _run_nn_pins(t[1]), paths))
     survivors = [name for name, rc, _ in results if rc == 0]
     assert not survivors, f"planted mistakes no pin caught: {survivors}"
     for name, rc, failed in results:
