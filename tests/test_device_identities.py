@@ -1,12 +1,17 @@
-"""The device sin/cos chain's division shortcut, checked on the CPU.
+"""Arithmetic shortcuts of the device code, checked exhaustively on the CPU.
 
-The fp64 Taylor chain of the pose -> matrix step (Eq. 3) divides every term
-by a constant; the device takes each quotient from a stored reciprocal and
-one FMA correction (Markstein, 1990) for fp32 angles with
-2^-32 <= |x| <= 64, and from the IEEE division elsewhere.  These tests pin
-the stored reciprocals to their definition and walk every fp32 angle of that
-range through both chains, so the shortcut is the correctly rounded quotient
-on every input the kernels can receive.
+1. The fp64 Taylor chain of the pose -> matrix step (Eq. 3) divides every
+   term by a constant; the device takes each quotient from a stored
+   reciprocal and one FMA correction (Markstein, 1990) for fp32 angles with
+   2^-32 <= |x| <= 64, and from the IEEE division elsewhere.  The stored
+   reciprocals are pinned to their definition and every fp32 angle of that
+   range is walked through both chains, so the shortcut is the correctly
+   rounded quotient on every input the kernels can receive.
+2. The measurement kernel replaces conversions by fp32 adds: floors as the
+   bits of 2^23 + q rounded down, the 15-bit fixed-point sample as the bits
+   of s + 256, bytes as floats with the bits 2^23 + b.  Each is walked over
+   every fp32 input of its range against the plain operation the oracle
+   uses (floorf, lrintf(32768 s), (float)b).
 """
 import os
 import platform
@@ -18,6 +23,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "device.cuh")
 CHECK_C = os.path.join(ROOT, "tests", "taylor_division_check.c")
+IDENT_C = os.path.join(ROOT, "tests", "device_identities_check.c")
 
 
 def _literals(name):
@@ -50,9 +56,9 @@ def _flags():
     return flags
 
 
-def test_division_shortcut_is_exact_for_every_fp32_angle(tmp_path):
-    exe = str(tmp_path / "taylor_division_check")
-    subprocess.run(["gcc", *_flags(), "-o", exe, CHECK_C], check=True)
+def _run_parts(src, exe, extra=()):
+    """Compile a checker and run it split over the host's cores; (checked, mismatches)."""
+    subprocess.run(["gcc", *_flags(), *extra, "-o", exe, src, "-lm"], check=True)
     nparts = max(1, min(os.cpu_count() or 1, 32))
     procs = [subprocess.Popen([exe, str(p), str(nparts)], stdout=subprocess.PIPE, text=True)
              for p in range(nparts)]
@@ -63,6 +69,19 @@ def test_division_shortcut_is_exact_for_every_fp32_angle(tmp_path):
         m = re.match(r"checked (\d+) mismatches (\d+)", out)
         checked += int(m.group(1))
         bad += int(m.group(2))
+    return checked, bad
+
+
+def test_division_shortcut_is_exact_for_every_fp32_angle(tmp_path):
+    checked, bad = _run_parts(CHECK_C, str(tmp_path / "taylor_division_check"))
     n_angles = 0x42800000 - 0x2F800000 + 1          # fp32 bit patterns of 2^-32 .. 64
     assert checked == 26 * n_angles                 # 13 divisions in each of the two chains
+    assert bad == 0
+
+
+def test_conversion_shortcuts_are_exact_over_their_ranges(tmp_path):
+    checked, bad = _run_parts(IDENT_C, str(tmp_path / "device_identities_check"), ("-frounding-math",))
+    n_floor = 0x4B000000                            # fp32 bit patterns of [0, 2^23)
+    n_fixed = 0x437F0000 + 1                        # ... of [0, 255]
+    assert checked == n_floor + n_fixed + 256 * 256
     assert bad == 0
