@@ -265,6 +265,17 @@ def test_trajectory_bit_exact_small(pk, orc, mode):
         _assert_trajectory(reg, ref, K)
 
 
+@pytest.mark.parametrize("N", [1, 1024, 1025])
+def test_trajectory_at_the_update_kernel_boundary(pk, orc, N):
+    """Clouds of up to 1024 particles take the one-CTA update, larger ones
+    the three-kernel form; a single particle is the degenerate cloud."""
+    pair = pfsynth.ellipsoid_pair(12, src_dims=(26, 24, 22), tgt_dims=(25, 24, 18), tgt_origin=(0, 0, 4),
+                                  semi_axes=(9, 6, 5), asymmetric=True, max_rot_deg=8, max_trans=3)
+    ref = _oracle_run(orc, "mask_dice", pair, N, 3, 0.2, 3.0, seed=31)
+    with _reg(pk, "mask_dice", pair, N, 0.2, 3.0, 31) as reg:
+        _assert_trajectory(reg, ref, 3)
+
+
 def test_host_inputs_equal_device_inputs(pk, orc):
     pair = pfsynth.ellipsoid_pair(8, src_dims=(26, 24, 22), tgt_dims=(25, 24, 18), tgt_origin=(0, 0, 4),
                                   semi_axes=(9, 6, 5))
