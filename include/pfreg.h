@@ -140,8 +140,10 @@ int pf_register_init(pf_ctx **out, const pf_volume *src, const pf_volume *tgt,
 int pf_step(pf_ctx *ctx, int32_t n_iters);
 
 /* Synchronise the stream and return the estimate of the last iteration
- * (weighted mean pose) and, when score_out is not NULL, the score of that
- * pose (one extra measurement).  PF_ESTATE before the first pf_step. */
+ * (Fig. 1 "estimation": the weighted mean pose, or the quaternion average
+ * of pf_config.estimator) and, when score_out is not NULL, the score of that
+ * pose (one extra measurement).  Errors: PF_EINVAL (NULL ctx or pose_out),
+ * PF_ESTATE (before the first pf_step), PF_ECUDA. */
 int pf_estimate(pf_ctx *ctx, float pose_out[6], double *score_out);
 
 /* Seed the cloud from a proposal (the learned approach named as future work
@@ -156,7 +158,8 @@ int pf_estimate(pf_ctx *ctx, float pose_out[6], double *score_out);
  * PF_ESTATE (after the first iteration, or while profiling is armed), PF_ECUDA. */
 int pf_seed_gaussian(pf_ctx *ctx, const float mean[6], const float std[6]);
 
-/* Release the context and its device memory (NULL is accepted). */
+/* Release the context and its device memory (NULL is accepted; no
+ * counterpart in the paper).  Waits for the context's stream first. */
 int pf_register_destroy(pf_ctx *ctx);
 
 /* Warp every frame of a sequence by one pose (Abstract; Sec. 3.3: the
@@ -202,7 +205,8 @@ int pf_batch_create(pf_batch **out, pf_ctx *const *ctxs, int32_t n, const int32_
  * launches by timing the candidates on the members' initial clouds.
  * pf_batch_tile_shape reports it (work items per warp). */
 int pf_batch_tile_shape(pf_batch *b, int32_t *items_per_warp);
-/* Launch n_iters batch iterations (asynchronous on the contexts' stream). */
+/* Launch n_iters batch iterations, each the Fig. 1 cycle of every running
+ * member (asynchronous on the contexts' stream). */
 int pf_batch_step(pf_batch *b, int32_t n_iters);
 /* Launch as many batch iterations as the longest remaining registration needs. */
 int pf_batch_run(pf_batch *b);
@@ -239,7 +243,8 @@ int pf_moments_device(pf_ctx *ctx, uint64_t **moments, int64_t *n_words);
 
 /* ---- inspection, checkpoint and test exports (host buffers, synchronous) ---- */
 
-/* Number of iterations run so far (the next iteration's index k). */
+/* Number of iterations run so far (the next iteration's index k; Fig. 1
+ * iterations).  Synchronous. */
 int pf_get_iteration(pf_ctx *ctx, int32_t *k_out);
 
 /* Copy the state of the last iteration to host buffers (any may be NULL):
@@ -309,14 +314,18 @@ int pf_pose_matrix(const float pose[6], const int32_t src_dims[3], const float s
  * Process-wide.  Errors: PF_EINVAL (bytes < 0). */
 int pf_debug_alloc_limit(int64_t bytes);
 
-/* The measurement's tile shape: target rows per work item (one warp's rows)
- * and consecutive work items per warp (the autotuned parameter). */
+/* The measurement's tile shape (no counterpart in the paper): target rows per
+ * work item (one warp's rows) and consecutive work items per warp (the
+ * autotuned parameter). */
 int pf_tile_shape(pf_ctx *ctx, int32_t *rows_per_item, int32_t *items_per_warp);
 
-/* Philox4x32-10 of (ctr, key) computed on the device (tests of the generator). */
+/* Philox4x32-10 (Salmon et al., SC'11; the generator of every random draw of
+ * the Fig. 1 cycle) of (ctr, key) computed on the device, for tests of the
+ * generator against its published known answers. */
 int pf_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
-/* Timing of the measurement kernel (the hot loop) inside the iteration graph:
+/* Timing of the measurement kernel (the hot loop; no counterpart in the
+ * paper) inside the iteration graph:
  * pf_profile_begin arms CUDA events for the next `capacity` iterations run by
  * pf_step (0 disarms); pf_profile_end synchronises and returns the summed
  * device time of those measurement launches (ms) and how many were timed. */
