@@ -1,0 +1,36 @@
+/* Host stand-ins for the CUDA names that the device header
+ * paper_2504_19930_gb300/csrc/device.cuh uses, so that a test can compile
+ * its arithmetic for the CPU and compare it with the oracle on many more
+ * inputs than a GPU test samples.  Test infrastructure only: the package
+ * never builds or loads this.  Each intrinsic becomes the IEEE operation its
+ * name fixes (round to nearest; fma correctly rounded); build with
+ * -ffp-contract=off so that nothing else is fused. */
+#pragma once
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#define __device__
+#define __host__
+#define __forceinline__ inline
+
+inline double __dmul_rn(double a, double b) { return a * b; }
+inline double __dadd_rn(double a, double b) { return a + b; }
+inline double __dsub_rn(double a, double b) { return a - b; }
+inline double __ddiv_rn(double a, double b) { return a / b; }
+inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
+inline float __double2float_rn(double a) { return (float)a; }
+inline double __ull2double_rn(unsigned long long v) { return (double)v; }
+inline float __fmul_rn(float a, float b) { return a * b; }
+inline float __fadd_rn(float a, float b) { return a + b; }
+inline float __fsub_rn(float a, float b) { return a - b; }
+inline float __fmaf_rn(float a, float b, float c) { return std::fmaf(a, b, c); }
+inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
+inline float __uint_as_float(uint32_t u) {
+    float f;
+    std::memcpy(&f, &u, sizeof f);
+    return f;
+}
+using std::max;
+using std::min;
