@@ -1,7 +1,9 @@
-// The device header's pose arithmetic (fp64 sin/cos chain, pose -> matrix,
-// Philox) compiled for the host through tests/host_shim, exported with a C
-// ABI for tests/test_device_identities.py.  Test infrastructure only.
+// The device headers' scalar arithmetic (fp64 sin/cos chain, pose -> matrix,
+// Philox; scores and quantised weights from the integer moments) compiled for
+// the host through tests/host_shim, exported with a C ABI for
+// tests/test_device_identities.py.  Test infrastructure only.
 #include "../paper_2504_19930_gb300/csrc/device.cuh"
+#include "../paper_2504_19930_gb300/csrc/score.cuh"
 
 extern "C" {
 
@@ -27,4 +29,10 @@ void dm_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
     out[2] = r.z;
     out[3] = r.w;
 }
+
+double dm_score(int mode, const uint64_t mom[12], uint64_t b_full, uint64_t n_min) {
+    return pfreg::score_from_moments(mode, reinterpret_cast<const unsigned long long *>(mom), b_full, n_min);
+}
+
+uint64_t dm_weight(double s, double smax, int g) { return pfreg::quantised_weight(s, smax, g); }
 }

@@ -22,6 +22,7 @@ inline double __ddiv_rn(double a, double b) { return a / b; }
 inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
 inline float __double2float_rn(double a) { return (float)a; }
 inline double __ull2double_rn(unsigned long long v) { return (double)v; }
+inline unsigned long long __double2ull_rz(double a) { return (unsigned long long)a; }   // a >= 0 here
 inline float __fmul_rn(float a, float b) { return a * b; }
 inline float __fadd_rn(float a, float b) { return a + b; }
 inline float __fsub_rn(float a, float b) { return a - b; }

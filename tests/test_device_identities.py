@@ -12,11 +12,13 @@
    of s + 256, bytes as floats with the bits 2^23 + b.  Each is walked over
    every fp32 input of its range against the plain operation the oracle
    uses (floorf, lrintf(32768 s), (float)b).
-3. The device header's pose arithmetic (sin/cos chain, pose -> matrix with
-   spacings, Philox) compiled for the host through tests/host_shim (each
+3. The device headers' scalar arithmetic (sin/cos chain, pose -> matrix
+   with spacings, Philox, the four scores from the integer moments and the
+   quantised weights) compiled for the host through tests/host_shim (each
    intrinsic mapped to the IEEE operation it names) equals the oracle bit for
-   bit on 10^5 angles and 5000 random poses and grids, far more than the GPU
-   test samples.  (A stored reciprocal off by one unit in the last place is
+   bit on 10^5 angles, 5000 random poses and grids, 20000 random moment
+   vectors in every mode and 11 weight exponents, far more than the GPU
+   tests sample.  (A stored reciprocal off by one unit in the last place is
    mostly absorbed by the correction step, which is why the literals are
    pinned on their own.)
 """
@@ -118,6 +120,11 @@ def dm(tmp_path_factory):
     u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
     L.dm_pose_matrix.argtypes = [f32p, i32p, f32p, f32p, f32p, f32p, f32p]
     L.dm_philox.argtypes = [u32p, u32p, u32p]
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    L.dm_score.restype = C.c_double
+    L.dm_score.argtypes = [C.c_int, u64p, C.c_uint64, C.c_uint64]
+    L.dm_weight.restype = C.c_uint64
+    L.dm_weight.argtypes = [C.c_double, C.c_double, C.c_int]
     return L
 
 
@@ -155,3 +162,50 @@ def test_device_philox_equals_the_oracle(dm, orc):
         out = np.zeros(4, np.uint32)
         dm.dm_philox(ctr, key, out)
         assert np.array_equal(out, orc.philox(ctr, key))
+
+
+def _random_moments(rng):
+    """A moment vector [n S1 S2lo S2hi ST T1 T2 0 | n_nn A B C] with the
+    ranges a measurement can produce (15-bit fixed-point samples < 2^23,
+    uint8 targets), variances sometimes zero."""
+    n = int(rng.integers(0, 1 << 26))
+    s1 = int(rng.integers(0, n * ((1 << 23) - 1) + 1)) if n else 0
+    s2 = (s1 * s1 + n - 1) // n if n else 0
+    if rng.random() < 0.9 and n:
+        s2 += int(rng.integers(0, 1 << 62)) * int(rng.integers(1, 1 << 16))
+    st = int(rng.integers(0, n * ((1 << 23) - 1) * 255 + 1)) if n else 0
+    t1 = int(rng.integers(0, 255 * n + 1)) if n else 0
+    t2 = (t1 * t1 + n - 1) // n if n else 0
+    if rng.random() < 0.9 and n:
+        t2 += int(rng.integers(0, 65025 * n // 4 + 1))
+    nn = int(rng.integers(0, 1 << 26))
+    a, b = int(rng.integers(0, nn + 1)), int(rng.integers(0, nn + 1))
+    c = int(rng.integers(0, min(a, b) + 1))
+    mom = [n, s1, s2 & (2**64 - 1), s2 >> 64, st, t1, t2, 0, nn, a, b, c]
+    return np.array(mom, np.uint64), b + int(rng.integers(0, 1 << 20))
+
+
+def test_device_scores_equal_the_oracle(dm, orc):
+    rng = np.random.default_rng(24)
+    for i in range(20000):
+        mom, b_full = _random_moments(rng)
+        n_min = int(rng.choice([0, int(mom[0]), int(mom[0]) + 1, int(mom[8]), 1 << 20]))
+        for mode in range(4):
+            got = dm.dm_score(mode, mom, b_full, n_min)
+            want = orc.score(mode, mom, b_full, n_min)
+            assert got == want or (np.isnan(got) and np.isnan(want)), (i, mode, mom, got, want)
+
+
+def test_device_weights_equal_the_oracle(dm, orc):
+    rng = np.random.default_rng(25)
+    for g in range(11):
+        s = rng.uniform(0, 1, 2000)
+        s[:50] = 0.0
+        s[50:60] = s.max()
+        s[60:70] = rng.uniform(0, 1e-300, 10)
+        want = orc.weights(s, g)
+        smax = float(s.max())
+        got = np.array([dm.dm_weight(float(v), smax, g) for v in s], np.uint64)
+        assert np.array_equal(got, want), g
+    assert dm.dm_weight(0.5, 0.0, 5) == 0
+
