@@ -18,7 +18,13 @@
    intrinsic mapped to the IEEE operation it names) equals the oracle bit for
    bit on 10^5 angles, 5000 random poses and grids, 20000 random moment
    vectors in every mode and 11 weight exponents, far more than the GPU
-   tests sample.  (A stored reciprocal off by one unit in the last place is
+   tests sample.
+4. The measurement kernel's row set-up -- the conservative x-range of a
+   target row and its exact inside interval (the functions copied verbatim
+   out of measure.cu) -- equals, row by row, the voxels the oracle samples
+   inside the source, for 800 random poses and grids in both the
+   nearest-neighbour and trilinear bounds; six planted mistakes in a copy of
+   it are each caught.  (A stored reciprocal off by one unit in the last place is
    mostly absorbed by the correction step, which is why the literals are
    pinned on their own.)
 """
@@ -209,3 +215,105 @@ def test_device_weights_equal_the_oracle(dm, orc):
         assert np.array_equal(got, want), g
     assert dm.dm_weight(0.5, 0.0, 5) == 0
 
+
+
+# ---------------------------------------- the measurement's row set-up on the host
+
+MEASURE_CU = os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "measure.cu")
+RI_CPP = os.path.join(ROOT, "tests", "row_interval_host.cpp")
+RI_BEGIN = "// Coordinate q_d(x) of target voxel x of a row"
+RI_END = "// One work item = (particle p, 32 target rows)"
+
+
+@pytest.fixture(scope="module")
+def ri(tmp_path_factory):
+    """The kernel's row set-up (row_interval, and coord1 / axis_conds /
+    exact_interval copied verbatim from measure.cu) built for the CPU."""
+    import ctypes as C
+    d = tmp_path_factory.mktemp("ri")
+    src = open(MEASURE_CU).read()
+    assert src.count(RI_BEGIN) == 1 and src.count(RI_END) == 1
+    (d / "measure_row_interval.inc").write_text(src[src.index(RI_BEGIN):src.index(RI_END)])
+    so = str(d / "libri.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(d), RI_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    L.dm_row_intervals.argtypes = [f32p, f32p, i32p, i32p, C.c_int, i32p, i32p]
+    return L
+
+
+def test_row_intervals_equal_the_oracles_inside_sets(ri, orc):
+    # every target row's visited interval [xl, xr] is exactly the set of
+    # voxels the oracle samples inside the source (nearest-neighbour or
+    # trilinear bounds): the oracle warps a source of 255s, which marks them
+    rng = np.random.default_rng(26)
+    half_pi = np.float32(np.pi / 2)
+    for i in range(800):
+        sd = rng.integers(2, 40, 3).astype(np.int32)
+        td = rng.integers(2, 48, 3).astype(np.int32)
+        so = rng.uniform(-15, 15, 3).astype(np.float32)
+        to = rng.uniform(-15, 15, 3).astype(np.float32)
+        if i % 5 == 0:      # no rotation: r_10 = r_20 = 0, q_y and q_z constant along a row
+            ang = np.zeros(3)
+        elif i % 5 == 1:    # quarter turns
+            ang = rng.choice([-half_pi, 0.0, half_pi], 3)
+        else:
+            ang = rng.uniform(-1.57, 1.57, 3)
+        pose = np.concatenate([ang, rng.uniform(-20, 20, 3)]).astype(np.float32)
+        if i % 5 == 0 and i % 2 == 0:
+            # half-integer origins and translations without rotation put
+            # samples exactly on the bounds (q = D - 1, q + 0.5 = D)
+            so, to = np.round(so * 2) / 2, np.round(to * 2) / 2
+            pose[3:] = np.round(pose[3:] * 2) / 2
+        M, a = orc.pose_matrix(pose, sd, so, to)
+        ones = np.full((sd[2], sd[1], sd[0]), 255, np.uint8)
+        X = int(td[0])
+        for tri in (0, 1):
+            inside = orc.warp_matrix(ones, tuple(int(v) for v in td), M, a, tri).reshape(-1, X) == 255
+            xl = np.zeros(inside.shape[0], np.int32)
+            xr = np.zeros(inside.shape[0], np.int32)
+            ri.dm_row_intervals(M, a, sd, td, tri, xl, xr)
+            cnt = inside.sum(1)
+            first = np.argmax(inside, 1)
+            last = X - 1 - np.argmax(inside[:, ::-1], 1)
+            has = cnt > 0
+            assert np.all(cnt[has] == last[has] - first[has] + 1), (i, tri)     # one interval per row
+            assert np.array_equal(xl[has], first[has]) and np.array_equal(xr[has], last[has]), (i, tri)
+            assert np.all(xr[~has] < xl[~has]), (i, tri)
+
+
+# planted mistakes in a copy of the kernel's row set-up, each of which the
+# comparison above must catch (it is only as good as the rows it samples)
+RI_MUTANTS = [
+    ("trilinear upper bound strict", "upper = q <= D - 1.0f;", "upper = q < D - 1.0f;"),
+    ("nearest-neighbour upper bound inclusive", "upper = h < D;", "upper = h <= D;"),
+    ("two probes counted as four", "if (++cnt == 4) break;\n    }\n    if (cnt == 4 && l < xe)",
+     "if (++cnt == 2) break;\n    }\n    if (cnt == 4 && l < xe)"),
+    ("binary search too short", "for (int step = 2048; step > 0; step >>= 1)\n            if (pl + step",
+     "for (int step = 2; step > 0; step >>= 1)\n            if (pl + step"),
+    ("constant axes ignored", "xr = constant_ok ? r : xl - 1;", "xr = r;"),
+    ("wrong bound for a decreasing axis", "ok &= r0[d] > 0.0f ? up : (r0[d] < 0.0f ? lo : true);",
+     "ok &= r0[d] > 0.0f ? up : (r0[d] < 0.0f ? up : true);"),
+]
+
+
+def test_row_interval_comparison_catches_planted_mistakes(orc, tmp_path):
+    import ctypes as C
+    src = open(MEASURE_CU).read()
+    inc = src[src.index(RI_BEGIN):src.index(RI_END)]
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    for k, (name, text, planted) in enumerate(RI_MUTANTS):
+        assert inc.count(text) == 1, name
+        d = tmp_path / f"m{k}"
+        d.mkdir()
+        (d / "measure_row_interval.inc").write_text(inc.replace(text, planted))
+        so = str(d / "libri.so")
+        subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                        "-I" + str(d), RI_CPP, "-o", so], check=True)
+        L = C.CDLL(so)
+        L.dm_row_intervals.argtypes = [f32p, f32p, i32p, i32p, C.c_int, i32p, i32p]
+        with pytest.raises(AssertionError):
+            test_row_intervals_equal_the_oracles_inside_sets(L, orc)
