@@ -12,6 +12,7 @@
 #include <cstring>
 
 #define __device__
+#define __global__
 #define __host__
 #define __forceinline__ inline
 
@@ -34,5 +35,17 @@ inline float __uint_as_float(uint32_t u) {
     std::memcpy(&f, &u, sizeof f);
     return f;
 }
+inline int __float2int_rn(float x) { return (int)std::nearbyint(x); }   // round half to even
+inline uint32_t __float_as_uint(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof u);
+    return u;
+}
+template <class T>
+inline T __ldg(const T *p) { return *p; }
+// the types the host-side declarations of kernels.h name
+typedef int cudaError_t;
+typedef struct CUstream_st *cudaStream_t;
+enum { cudaSuccess = 0 };
 using std::max;
 using std::min;

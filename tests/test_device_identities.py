@@ -24,7 +24,12 @@
    out of measure.cu) -- equals, row by row, the voxels the oracle samples
    inside the source, for 800 random poses and grids in both the
    nearest-neighbour and trilinear bounds; six planted mistakes in a copy of
-   it are each caught.  (A stored reciprocal off by one unit in the last place is
+   it are each caught.
+5. The sequence warp's per-voxel code (sample_at / sample_frame copied
+   verbatim out of warp.cu), driven as the warp kernel drives it, equals the
+   oracle's warp voxel for voxel on 300 random images, poses and grids, both
+   interpolations, with and without voxel spacing.
+   (A stored reciprocal off by one unit in the last place is
    mostly absorbed by the correction step, which is why the literals are
    pinned on their own.)
 """
@@ -317,3 +322,49 @@ def test_row_interval_comparison_catches_planted_mistakes(orc, tmp_path):
         L.dm_row_intervals.argtypes = [f32p, f32p, i32p, i32p, C.c_int, i32p, i32p]
         with pytest.raises(AssertionError):
             test_row_intervals_equal_the_oracles_inside_sets(L, orc)
+
+
+# --------------------------------------------- the sequence warp's voxels on the host
+
+WARP_CU = os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "warp.cu")
+WH_CPP = os.path.join(ROOT, "tests", "warp_host.cpp")
+WH_BEGIN = "struct WarpArgs {"
+WH_END = "// One target row per warp at a time"
+
+
+def test_warp_voxels_equal_the_oracle(orc, tmp_path):
+    # the warp kernel's per-voxel code (sample_at / sample_frame copied
+    # verbatim out of warp.cu) driven as k_warp drives it, against the
+    # oracle's warp, both interpolations, with and without voxel spacing
+    import ctypes as C
+    import pfsynth
+    src = open(WARP_CU).read()
+    assert src.count(WH_BEGIN) == 1 and src.count(WH_END) == 1
+    (tmp_path / "warp_sample.inc").write_text(src[src.index(WH_BEGIN):src.index(WH_END)])
+    so_path = str(tmp_path / "libwh.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(tmp_path), WH_CPP, "-o", so_path], check=True)
+    L = C.CDLL(so_path)
+    u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    L.dm_warp.argtypes = [u8p, i32p, f32p, f32p, u8p, i32p, f32p, f32p, f32p, f32p, C.c_int]
+    rng = np.random.default_rng(27)
+    for i in range(300):
+        sd = rng.integers(2, 30, 3).astype(np.int32)
+        td = rng.integers(2, 30, 3).astype(np.int32)
+        img = pfsynth.random_image(int(rng.integers(0, 1 << 30)), tuple(int(v) for v in sd))
+        so = rng.uniform(-10, 10, 3).astype(np.float32)
+        to = rng.uniform(-10, 10, 3).astype(np.float32)
+        unit = i % 2 == 0
+        ss = np.ones(3, np.float32) if unit else rng.uniform(0.3, 2.5, 3).astype(np.float32)
+        ts = np.ones(3, np.float32) if unit else rng.uniform(0.3, 2.5, 3).astype(np.float32)
+        pose = np.concatenate([rng.uniform(-1.5, 1.5, 3), rng.uniform(-12, 12, 3)]).astype(np.float32)
+        if i % 10 == 0:
+            pose[:3] = 0.0
+        _, a = orc.pose_matrix(pose, sd, so, to, ss, ts)
+        for interp in (0, 1):
+            out = np.zeros((td[2], td[1], td[0]), np.uint8)
+            L.dm_warp(np.ascontiguousarray(img), sd, so, ss, out, td, to, ts, a, pose, interp)
+            want = orc.warp(img, so, tuple(int(v) for v in td), to, pose, interp, ss, ts)
+            assert np.array_equal(out, want), (i, interp, int((out != want).sum()))
