@@ -7,7 +7,9 @@
  * -ffp-contract=off so that nothing else is fused. */
 #pragma once
 #include <algorithm>
+#include <cfenv>
 #include <cmath>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 
@@ -43,6 +45,30 @@ inline uint32_t __float_as_uint(float f) {
 }
 template <class T>
 inline T __ldg(const T *p) { return *p; }
+// a + b rounded toward -infinity (build with -frounding-math)
+inline float __fadd_rd(float a, float b) {
+    std::fesetround(FE_DOWNWARD);
+    volatile float x = a, y = b;
+    volatile float r = x + y;
+    std::fesetround(FE_TONEAREST);
+    return r;
+}
+// byte n of the result = byte (selector nibble n & 7) of the 8 bytes y:x
+inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
+    const uint64_t v = ((uint64_t)y << 32) | x;
+    uint32_t r = 0;
+    for (int n = 0; n < 4; ++n) r |= (uint32_t)((v >> (8 * ((s >> (4 * n)) & 7u))) & 0xFFu) << (8 * n);
+    return r;
+}
+// warp shuffles have no host meaning: a host test that reached one would be wrong
+inline unsigned long long __shfl_xor_sync(unsigned, unsigned long long, int) { std::abort(); }
+// the vector types the device code names
+struct float2 {
+    float x, y;
+};
+struct float4 {
+    float x, y, z, w;
+};
 // the types the host-side declarations of kernels.h name
 typedef int cudaError_t;
 typedef struct CUstream_st *cudaStream_t;

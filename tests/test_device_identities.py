@@ -29,6 +29,12 @@
    verbatim out of warp.cu), driven as the warp kernel drives it, equals the
    oracle's warp voxel for voxel on 300 random images, poses and grids, both
    interpolations, with and without voxel spacing.
+6. The measurement kernel's per-voxel code (eval_pair with the helpers and
+   the row set-up, copied verbatim out of measure.cu, the packed fp32 pairs
+   in their scalar form), driven over each row's inside interval, gives the
+   oracle's moments and counts bit for bit in the image, mask and combined
+   forms, with the fp32 and the integer quad index; ten planted mistakes in
+   a copy of it are each caught.
    (A stored reciprocal off by one unit in the last place is
    mostly absorbed by the correction step, which is why the literals are
    pinned on their own.)
@@ -368,3 +374,114 @@ def test_warp_voxels_equal_the_oracle(orc, tmp_path):
             L.dm_warp(np.ascontiguousarray(img), sd, so, ss, out, td, to, ts, a, pose, interp)
             want = orc.warp(img, so, tuple(int(v) for v in td), to, pose, interp, ss, ts)
             assert np.array_equal(out, want), (i, interp, int((out != want).sum()))
+
+
+# ------------------------------------ the measurement's per-voxel code on the host
+
+MH_CPP = os.path.join(ROOT, "tests", "measure_host.cpp")
+MV_BEGIN = "constexpr int kWarps = 8;"
+
+
+def _build_measure_host(src_text, d):
+    import ctypes as C
+    assert src_text.count(MV_BEGIN) == 1 and src_text.count(RI_END) == 1
+    (d / "measure_voxel.inc").write_text(src_text[src_text.index(MV_BEGIN):src_text.index(RI_END)])
+    so = str(d / "libmh.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-frounding-math", "-fPIC", "-shared",
+                    "-I" + SHIM, "-I" + str(d), MH_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    u8p = C.c_void_p
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    L.dm_measure.argtypes = [C.c_int, C.c_int, C.c_int, u8p, u8p, i32p, u8p, u8p, i32p, f32p, C.c_int, f32p, u64p]
+    return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _measure_cases(orc, seed, count):
+    import pfsynth
+    rng = np.random.default_rng(seed)
+    for i in range(count):
+        sd = tuple(int(v) for v in rng.integers(2, 26, 3))
+        td = tuple(int(v) for v in rng.integers(2, 28, 3))
+        src = pfsynth.random_image(int(rng.integers(0, 1 << 30)), sd)
+        tgt = pfsynth.random_image(int(rng.integers(0, 1 << 30)), td)
+        smask = (rng.random((sd[2], sd[1], sd[0])) < 0.5).astype(np.uint8)
+        tmask = (rng.random((td[2], td[1], td[0])) < 0.5).astype(np.uint8)
+        so = rng.uniform(-8, 8, 3).astype(np.float32)
+        to = rng.uniform(-8, 8, 3).astype(np.float32)
+        P = 6
+        poses = np.concatenate([rng.uniform(-1.5, 1.5, (3, P)), rng.uniform(-10, 10, (3, P))]).astype(np.float32)
+        if i % 4 == 0:
+            poses[:3, :2] = 0.0
+            so, to = np.round(so * 2) / 2, np.round(to * 2) / 2
+            poses[3:, :2] = np.round(poses[3:, :2] * 4) / 4
+        mats, a = orc.pose_matrices(poses, sd, so, to)
+        yield sd, td, src, tgt, smask, tmask, np.ascontiguousarray(mats, np.float32), a
+
+
+def _check_measure(L, orc, seed=28, count=120):
+    for sd, td, src, tgt, smask, tmask, mats, a in _measure_cases(orc, seed, count):
+        P = mats.shape[0]
+        sdv, tdv = np.array(sd, np.int32), np.array(td, np.int32)
+        want_img = orc.measure_image(src, tgt, mats, a)
+        want_msk = orc.measure_mask(smask, tmask, mats, a)
+        for img, msk, int_index in ((1, 0, 0), (1, 0, 1), (0, 1, 0), (1, 1, 0), (1, 1, 1)):
+            got = np.zeros((P, 12), np.uint64)
+            L.dm_measure(img, msk, int_index, _ptr(src) if img else None, _ptr(smask) if msk else None, sdv,
+                         _ptr(tgt) if img else None, _ptr(tmask) if msk else None, tdv, mats, P, a, got)
+            if img:
+                assert np.array_equal(got[:, 0:7], want_img), (sd, td, img, msk, int_index)
+            if msk:
+                assert np.array_equal(got[:, 8:12], want_msk), (sd, td, img, msk, int_index)
+
+
+def test_measurement_voxels_equal_the_oracle(orc, tmp_path):
+    # eval_pair and the row set-up (copied verbatim out of measure.cu) with
+    # the scalar forms of the packed fp32 pairs: per-matrix moments and counts
+    # equal the oracle's in the image, mask and combined forms, on random
+    # volumes, grids and poses (with samples on the bounds), with both the
+    # fp32 quad index (sources up to 2^23 voxels) and the integer one
+    L = _build_measure_host(open(MEASURE_CU).read(), tmp_path)
+    _check_measure(L, orc)
+
+
+# planted mistakes in a copy of the kernel's per-voxel code, each of which the
+# comparison above must catch
+MV_MUTANTS = [
+    ("byte read from the wrong lane", "return __uint_as_float(__byte_perm(w, kTwo23Bits, 0x7540u | k));",
+     "return __uint_as_float(__byte_perm(w, kTwo23Bits, 0x7540u | (k ^ 1u)));"),
+    ("fixed point at 14 bits", "const f2 s = add2(lerp2(c0, c1, fz), splat(256.0f));",
+     "const f2 s = add2(lerp2(c0, c1, fz), splat(512.0f));"),
+    ("cross moment with the other voxel's target", "ia.ST += (unsigned long long)sq0 * t0;",
+     "ia.ST += (unsigned long long)sq0 * t1;"),
+    ("nearest neighbour without the half-voxel shift", "const f2 bxn = addrm2(add2(qx, splat(0.5f)), splat(kTwo23));",
+     "const f2 bxn = addrm2(qx, splat(kTwo23));"),
+    ("fp32 quad index with z for y", "const f2 w = fma2(splat(a.fdims[1]), flz, fma2(splat(a.fdims[0]), fly, bx));",
+     "const f2 w = fma2(splat(a.fdims[1]), flz, fma2(splat(a.fdims[0]), flz, bx));"),
+    ("y lerps with the z fraction", "const f2 c0 = lerp2(c00, c10, fy), c1 = lerp2(c01, c11, fy);",
+     "const f2 c0 = lerp2(c00, c10, fz), c1 = lerp2(c01, c11, fy);"),
+    ("x fraction from the y floor", "const f2 fx = sub2(qx, flx), fy = sub2(qy, fly), fz = sub2(qz, flz);",
+     "const f2 fx = sub2(qx, fly), fy = sub2(qy, fly), fz = sub2(qz, flz);"),
+    ("S2 sums the sample", "ia.S2 += (unsigned long long)sq0 * sq0;", "ia.S2 += (unsigned long long)sq0;"),
+    ("mask intersection as a union", "ma.C += sb & tb;", "ma.C += sb | tb;"),
+    ("integer quad index bias off by one row", "const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY);",
+     "const uint32_t bias = 0u - kTwo23Bits * (1u + (uint32_t)SX + SXY) + (uint32_t)SX;"),
+]
+
+
+def test_measurement_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(MEASURE_CU).read()
+    region = src[src.index(MV_BEGIN):src.index(RI_END)]
+    for k, (name, text, planted) in enumerate(MV_MUTANTS):
+        assert region.count(text) >= 1, name
+        d = tmp_path / f"m{k}"
+        d.mkdir()
+        L = _build_measure_host(src.replace(text, planted), d)
+        with pytest.raises(AssertionError):
+            _check_measure(L, orc, seed=29, count=12)
+
