@@ -1,4 +1,9 @@
-"""Arithmetic shortcuts of the device code, checked exhaustively on the CPU.
+"""The device code's arithmetic, checked on the CPU against the oracle.
+
+The sources are the product's own (headers included, kernel functions
+copied verbatim out of the .cu files), compiled for the host through
+tests/host_shim, which maps each CUDA intrinsic to the IEEE operation it
+names; the package never builds or loads any of this.
 
 1. The fp64 Taylor chain of the pose -> matrix step (Eq. 3) divides every
    term by a constant; the device takes each quotient from a stored
@@ -18,7 +23,9 @@
    intrinsic mapped to the IEEE operation it names) equals the oracle bit for
    bit on 10^5 angles, 5000 random poses and grids, 20000 random moment
    vectors in every mode and 11 weight exponents, far more than the GPU
-   tests sample.
+   tests sample.  (A stored reciprocal off by one unit in the last place is
+   mostly absorbed by the correction step, which is why the literals are
+   pinned on their own.)
 4. The measurement kernel's row set-up -- the conservative x-range of a
    target row and its exact inside interval (the functions copied verbatim
    out of measure.cu) -- equals, row by row, the voxels the oracle samples
@@ -35,9 +42,6 @@
    oracle's moments and counts bit for bit in the image, mask and combined
    forms, with the fp32 and the integer quad index; ten planted mistakes in
    a copy of it are each caught.
-   (A stored reciprocal off by one unit in the last place is
-   mostly absorbed by the correction step, which is why the literals are
-   pinned on their own.)
 """
 import os
 import platform
