@@ -69,6 +69,12 @@ struct float2 {
 struct float4 {
     float x, y, z, w;
 };
+// thread coordinates, for tests that run a kernel without shared memory,
+// barriers or shuffles as a host loop over its threads (the test sets them)
+struct dim3 {
+    unsigned x = 1, y = 1, z = 1;
+};
+extern dim3 threadIdx, blockIdx, blockDim, gridDim;
 // the types the host-side declarations of kernels.h name
 typedef int cudaError_t;
 typedef struct CUstream_st *cudaStream_t;

@@ -42,6 +42,10 @@ names; the package never builds or loads any of this.
    oracle's moments and counts bit for bit in the image, mask and combined
    forms, with the fp32 and the integer quad index; ten planted mistakes in
    a copy of it are each caught.
+7. Kernels with no shared memory, barrier or shuffle -- the initial clouds
+   (k_init, k_seed_gaussian) and the quad packing (k_pack_quads) -- run as a
+   host loop over their threads equal the oracle's initial clouds and the
+   quad layout written out in numpy.
 """
 import os
 import platform
@@ -489,3 +493,56 @@ def test_measurement_comparison_catches_planted_mistakes(orc, tmp_path):
         with pytest.raises(AssertionError):
             _check_measure(L, orc, seed=29, count=12)
 
+
+
+# ------------------------------- kernels without shared state, as host loops
+
+FILTER_CU = os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "filter.cu")
+KH_CPP = os.path.join(ROOT, "tests", "kernels_host.cpp")
+
+
+def test_initial_clouds_and_quad_packing_equal_their_definitions(orc, tmp_path):
+    # k_init and k_seed_gaussian (copied verbatim out of filter.cu) against
+    # the oracle's initial clouds, and k_pack_quads (out of measure.cu)
+    # against the quad layout written out in numpy, each kernel run as a loop
+    # over its threads
+    import ctypes as C
+    import pfsynth
+    f = open(FILTER_CU).read()
+    b0, e0 = "// Initial particles (Abstract", "// Prediction for k > 0"
+    assert f.count(b0) == 1 and f.count(e0) == 1
+    (tmp_path / "filter_init.inc").write_text(f[f.index(b0):f.index(e0)])
+    m = open(MEASURE_CU).read()
+    b1 = "__global__ void k_pack_quads("
+    assert m.count(b1) == 1
+    i = m.index(b1)
+    (tmp_path / "pack_quads.inc").write_text(m[i:m.index("}  // namespace", i)])
+    so = str(tmp_path / "libkh.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(tmp_path), KH_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+    L.dm_init.argtypes = [C.c_int, C.c_uint64, f32p, f32p]
+    L.dm_seed.argtypes = [C.c_int, C.c_uint64, f32p, f32p, f32p, f32p]
+    L.dm_pack_quads.argtypes = [u8p, i32p, u32p]
+    rng = np.random.default_rng(30)
+    for N, seed in ((1, 0), (257, 3), (4096, 2**40 + 7)):
+        lim = rng.uniform(0.1, 30, 6).astype(np.float32)
+        got = np.zeros((6, N), np.float32)
+        L.dm_init(N, seed, lim, got)
+        assert np.array_equal(got, orc.init_particles(N, seed, lim))
+        mean = rng.uniform(-5, 5, 6).astype(np.float32)
+        sdev = rng.uniform(0.01, 8, 6).astype(np.float32)
+        L.dm_seed(N, seed, lim, mean, sdev, got)
+        assert np.array_equal(got, orc.init_gaussian(N, seed, mean, sdev, lim))
+    for dims in ((2, 2, 2), (7, 5, 3), (33, 17, 9)):
+        S = pfsynth.random_image(int(rng.integers(0, 1 << 30)), dims)
+        Q = np.zeros(S.size, np.uint32)
+        L.dm_pack_quads(np.ascontiguousarray(S), np.array(dims, np.int32), Q)
+        P = np.zeros((dims[2], dims[1] + 1, dims[0] + 1), np.uint32)
+        P[:, :-1, :-1] = S
+        want = P[:, :-1, :-1] | P[:, :-1, 1:] << 8 | P[:, 1:, :-1] << 16 | P[:, 1:, 1:] << 24
+        assert np.array_equal(Q.reshape(S.shape), want), dims
