@@ -60,8 +60,6 @@ inline uint32_t __byte_perm(uint32_t x, uint32_t y, uint32_t s) {
     for (int n = 0; n < 4; ++n) r |= (uint32_t)((v >> (8 * ((s >> (4 * n)) & 7u))) & 0xFFu) << (8 * n);
     return r;
 }
-// warp shuffles have no host meaning: a host test that reached one would be wrong
-inline unsigned long long __shfl_xor_sync(unsigned, unsigned long long, int) { std::abort(); }
 // the vector types the device code names
 struct float2 {
     float x, y;
@@ -69,6 +67,14 @@ struct float2 {
 struct float4 {
     float x, y, z, w;
 };
+// Warp-level operations exist only under the lockstep emulation of
+// tests/host_shim/warp_emulation.h; elsewhere a test that reached one would
+// be wrong, so it aborts.
+#ifndef PF_HOST_WARP_EMULATION
+inline unsigned long long __shfl_xor_sync(unsigned, unsigned long long, int) { std::abort(); }
+#endif
+inline float4 make_float4(float x, float y, float z, float w) { return float4{x, y, z, w}; }
+inline float2 make_float2(float x, float y) { return float2{x, y}; }
 // thread coordinates, for tests that run a kernel without shared memory,
 // barriers or shuffles as a host loop over its threads (the test sets them)
 struct dim3 {

@@ -7,6 +7,7 @@
 // inside interval; the per-row sums are folded into whole moments.  Exported
 // with a C ABI for tests/test_device_identities.py.  Test infrastructure only.
 #include "../paper_2504_19930_gb300/csrc/kernels.h"
+#include "host_layouts.h"
 
 #define PF_DEBUG 0
 #define PF_USE_F32X2 0
@@ -17,9 +18,6 @@ namespace pfreg {
 namespace {
 using namespace pfreg;
 
-// The source layouts the kernel reads: quads Q[x,y,z] = S[x,y,z] |
-// S[x+1,y,z] << 8 | S[x,y+1,z] << 16 | S[x+1,y+1,z] << 24 (0 past the grid),
-// and mask bits (bit i & 31 of word i >> 5).
 template <bool IMG, bool MASK, bool FIDX>
 void measure_one(const MeasureArgs &a, const float *M, uint64_t mom[12]) {
     constexpr bool BOTH = IMG && MASK;
@@ -93,20 +91,12 @@ extern "C" void dm_measure(int img, int mask, int int_index, const uint8_t *S, c
                            const float *mats, int P, const float a_off[3], uint64_t *mom) {
     const int SX = sd[0], SY = sd[1], SZ = sd[2];
     const size_t ns = (size_t)SX * SY * SZ;
-    uint32_t *quad = new uint32_t[ns];
-    uint32_t *bits = new uint32_t[(ns + 31) / 32]();
-    for (size_t i = 0; i < ns; ++i) {
-        const int x = (int)(i % SX), y = (int)((i / SX) % SY);
-        const bool xn = x + 1 < SX, yn = y + 1 < SY;
-        const uint32_t b0 = S ? S[i] : 0u, b1 = S && xn ? S[i + 1] : 0u;
-        const uint32_t b2 = S && yn ? S[i + SX] : 0u, b3 = S && xn && yn ? S[i + SX + 1] : 0u;
-        quad[i] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-        if (Smask && Smask[i]) bits[i >> 5] |= 1u << (i & 31);
-    }
+    std::vector<uint32_t> quad, bits;
+    host_layouts(S, Smask, sd, quad, bits);
     pfreg::MeasureArgs a{};
-    a.src_quad = quad;
+    a.src_quad = quad.data();
     a.tgt_img = T;
-    a.src_bits = bits;
+    a.src_bits = bits.data();
     a.tgt_mask = Tmask;
     for (int d = 0; d < 3; ++d) {
         a.g.sd[d] = sd[d];
@@ -129,6 +119,4 @@ extern "C" void dm_measure(int img, int mask, int int_index, const uint8_t *S, c
         else
             measure_one<false, true, false>(a, M, m);
     }
-    delete[] quad;
-    delete[] bits;
 }

@@ -46,6 +46,14 @@ names; the package never builds or loads any of this.
    (k_init, k_seed_gaussian) and the quad packing (k_pack_quads) -- run as a
    host loop over their threads equal the oracle's initial clouds and the
    quad layout written out in numpy.
+8. The measurement kernel's whole warp routine (measure_item: the row
+   set-up, the sweep of 32 rows' intervals in 64-voxel passes with the
+   row-crossing passes, the per-voxel code, the warp reduction and the
+   atomics with S2's carry) and the warp's x-product table, copied verbatim
+   out of measure.cu, run under a lockstep emulation of one warp
+   (tests/host_shim/warp_emulation.h) and give the oracle's moments in every
+   form the kernel instantiates; six planted mistakes in the sweep are each
+   caught.
 """
 import os
 import platform
@@ -485,11 +493,9 @@ MV_MUTANTS = [
 def test_measurement_comparison_catches_planted_mistakes(orc, tmp_path):
     src = open(MEASURE_CU).read()
     region = src[src.index(MV_BEGIN):src.index(RI_END)]
-    for k, (name, text, planted) in enumerate(MV_MUTANTS):
+    for name, text, _ in MV_MUTANTS:
         assert region.count(text) >= 1, name
-        d = tmp_path / f"m{k}"
-        d.mkdir()
-        L = _build_measure_host(src.replace(text, planted), d)
+    for L in _build_all(_build_measure_host, src, MV_MUTANTS, tmp_path):
         with pytest.raises(AssertionError):
             _check_measure(L, orc, seed=29, count=12)
 
@@ -546,3 +552,140 @@ def test_initial_clouds_and_quad_packing_equal_their_definitions(orc, tmp_path):
         P[:, :-1, :-1] = S
         want = P[:, :-1, :-1] | P[:, :-1, 1:] << 8 | P[:, 1:, :-1] << 16 | P[:, 1:, 1:] << 24
         assert np.array_equal(Q.reshape(S.shape), want), dims
+
+
+# ------------------- the measurement's warp routine under a lockstep warp emulation
+
+MW_CPP = os.path.join(ROOT, "tests", "measure_warp_host.cpp")
+MI_END = "// Measurement kernel of one registration."
+MX_BEGIN, MX_END = "constexpr int kTabMaxX = 512;", "// CTAB (with XTAB):"
+
+
+def _build_measure_warp(src_text, d):
+    import ctypes as C
+    for m in (MV_BEGIN, MI_END, MX_BEGIN, MX_END):
+        assert src_text.count(m) == 1, m
+    (d / "measure_item.inc").write_text(src_text[src_text.index(MV_BEGIN):src_text.index(MI_END)])
+    (d / "measure_xtab.inc").write_text(src_text[src_text.index(MX_BEGIN):src_text.index(MX_END)])
+    so = str(d / "libmw.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-frounding-math", "-fPIC", "-shared",
+                    "-I" + SHIM, "-I" + str(d), MW_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    L.dm_measure_warp.argtypes = [C.c_int] * 4 + [C.c_void_p, C.c_void_p, i32p, C.c_void_p, C.c_void_p, i32p,
+                                                   f32p, C.c_int, f32p, u64p]
+    return L
+
+
+def _warp_cases(orc, seed, count):
+    import pfsynth
+    rng = np.random.default_rng(seed)
+    for i in range(count):
+        # long source rows (so the visit intervals run over several 64-voxel
+        # passes) on some cases, short ones (every pass crosses rows) on others
+        sd = (int(rng.integers(2, 200 if i % 2 else 40)), int(rng.integers(2, 30)), int(rng.integers(2, 20)))
+        td = (int(rng.integers(2, 200)), int(rng.integers(2, 24)), int(rng.integers(2, 12)))
+        src = pfsynth.random_image(int(rng.integers(0, 1 << 30)), sd)
+        tgt = pfsynth.random_image(int(rng.integers(0, 1 << 30)), td)
+        smask = (rng.random((sd[2], sd[1], sd[0])) < 0.5).astype(np.uint8)
+        tmask = (rng.random((td[2], td[1], td[0])) < 0.5).astype(np.uint8)
+        so = rng.uniform(-10, 10, 3).astype(np.float32)
+        to = rng.uniform(-10, 10, 3).astype(np.float32)
+        P = 3
+        rot = 1.5 if i % 3 else 0.15
+        poses = np.concatenate([rng.uniform(-rot, rot, (3, P)), rng.uniform(-12, 12, (3, P))]).astype(np.float32)
+        if i % 4 == 0:
+            poses[:3, 0] = 0.0
+            so, to = np.round(so * 2) / 2, np.round(to * 2) / 2
+            poses[3:, 0] = np.round(poses[3:, 0] * 2) / 2
+        mats, a = orc.pose_matrices(poses, sd, so, to)
+        yield sd, td, src, tgt, smask, tmask, np.ascontiguousarray(mats, np.float32), a
+
+
+WARP_CONFIGS = ((1, 0, 0, 0), (1, 0, 0, 1), (1, 0, 1, 1), (0, 1, 0, 0), (0, 1, 0, 1), (1, 1, 0, 1), (1, 1, 1, 0))
+
+
+def _bright_case(orc):
+    # a bright source under a large overlap: one particle's S2 passes 2^64,
+    # so the high word is reached through the atomic's carry
+    rng = np.random.default_rng(33)
+    sd, td = (80, 80, 70), (74, 74, 62)
+    src = (255 - rng.integers(0, 3, (sd[2], sd[1], sd[0]))).astype(np.uint8)
+    tgt = rng.integers(0, 256, (td[2], td[1], td[0])).astype(np.uint8)
+    pose = np.array([0.01, -0.01, 0.02, 0.3, -0.2, 0.1], np.float32)
+    mats, a = orc.pose_matrices(pose[:, None], sd, np.zeros(3, np.float32), np.full(3, 3.0, np.float32))
+    return sd, td, src, tgt, None, None, np.ascontiguousarray(mats, np.float32), a
+
+
+def _check_measure_warp(L, orc, seed=31, count=24):
+    import itertools
+    bright = _bright_case(orc)
+    assert orc.measure_image(bright[2], bright[3], bright[6], bright[7])[0, 3] > 0   # S2 high word used
+    for sd, td, src, tgt, smask, tmask, mats, a in itertools.chain(_warp_cases(orc, seed, count), [bright]):
+        P = mats.shape[0]
+        sdv, tdv = np.array(sd, np.int32), np.array(td, np.int32)
+        want_img = orc.measure_image(src, tgt, mats, a)
+        want_msk = orc.measure_mask(smask, tmask, mats, a) if smask is not None else None
+        for img, msk, int_index, xtab in WARP_CONFIGS:
+            if msk and smask is None:   # the bright case is an image case
+                continue
+            got = np.zeros((P, 12), np.uint64)
+            L.dm_measure_warp(img, msk, int_index, xtab, _ptr(src) if img else None, _ptr(smask) if msk else None,
+                              sdv, _ptr(tgt) if img else None, _ptr(tmask) if msk else None, tdv, mats, P, a, got)
+            cfg = (sd, td, img, msk, int_index, xtab)
+            if img:
+                assert np.array_equal(got[:, 0:7], want_img), cfg
+            if msk:
+                assert np.array_equal(got[:, 8:12], want_msk), cfg
+
+
+def test_measurement_warp_routine_equals_the_oracle(orc, tmp_path):
+    # measure_item -- row set-up, the sweep of 32 rows' intervals in passes of
+    # 64 voxels with the row-crossing passes, the per-voxel code and the warp
+    # reduction with its atomics -- and the warp's x-product table, copied
+    # verbatim out of measure.cu and run by a lockstep emulation of one warp:
+    # the moments equal the oracle's in every form the kernel instantiates
+    # (image, mask, combined; fp32 or integer quad index; with or without the
+    # table), on rows longer than two passes, single-voxel rows and empty ones
+    L = _build_measure_warp(open(MEASURE_CU).read(), tmp_path)
+    _check_measure_warp(L, orc)
+
+
+# planted mistakes in the sweep, each of which the comparison above must catch
+MW_MUTANTS = [
+    ("a full pass advances 63 voxels", "pos += 64;\n                xf = __fadd_rn(xf, 64.0f);\n                toff += 64u;",
+     "pos += 63;\n                xf = __fadd_rn(xf, 63.0f);\n                toff += 63u;"),
+    ("the next row's share of a crossing pass miscounted", "const int used1 = 64 - len0;",
+     "const int used1 = 63 - len0;"),
+    ("the crossing pass's second entry from the wrong row",
+     "const bool in0a = e0 < len0, in1a = e1 < len0;", "const bool in0a = e0 < len0, in1a = e1 <= len0;"),
+    ("the last row's remainder dropped", "if (len0 == 0 && !has1) break;", "if (!has1) break;"),
+    ("the S2 carry lost", "if (old + S2 < old) atomicAdd(dst + 3, 1ull);", "(void)old;"),
+    ("the x table built from the second row of the matrix",
+     "const float r0 = __ldg(Mp + 0), r1 = __ldg(Mp + 4), r2 = __ldg(Mp + 8);",
+     "const float r0 = __ldg(Mp + 1), r1 = __ldg(Mp + 4), r2 = __ldg(Mp + 8);"),
+]
+
+
+def _build_all(build, src, mutants, tmp_path):
+    """Build one library per planted mistake, in parallel (compiles dominate)."""
+    from concurrent.futures import ThreadPoolExecutor
+    dirs = []
+    for k, (name, text, planted) in enumerate(mutants):
+        assert src.count(text) >= 1, name
+        d = tmp_path / f"m{k}"
+        d.mkdir()
+        dirs.append((d, src.replace(text, planted)))
+    with ThreadPoolExecutor(max_workers=max(1, min(os.cpu_count() or 1, 8))) as ex:
+        return list(ex.map(lambda t: build(t[1], t[0]), dirs))
+
+
+def test_measurement_warp_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(MEASURE_CU).read()
+    for text in (m[1] for m in MW_MUTANTS):
+        assert src.count(text) == 1, text
+    for L in _build_all(_build_measure_warp, src, MW_MUTANTS, tmp_path):
+        with pytest.raises(AssertionError):
+            _check_measure_warp(L, orc, seed=32, count=10)
