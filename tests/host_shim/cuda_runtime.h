@@ -15,6 +15,7 @@
 
 #define __device__
 #define __global__
+#define __launch_bounds__(...)
 #define __host__
 #define __forceinline__ inline
 
@@ -23,6 +24,7 @@ inline double __dadd_rn(double a, double b) { return a + b; }
 inline double __dsub_rn(double a, double b) { return a - b; }
 inline double __ddiv_rn(double a, double b) { return a / b; }
 inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
+inline double __dsqrt_rn(double a) { return std::sqrt(a); }
 inline float __double2float_rn(double a) { return (float)a; }
 inline double __ull2double_rn(unsigned long long v) { return (double)v; }
 inline unsigned long long __double2ull_rz(double a) { return (unsigned long long)a; }   // a >= 0 here

@@ -54,6 +54,12 @@ names; the package never builds or loads any of this.
    (tests/host_shim/warp_emulation.h) and give the oracle's moments in every
    form the kernel instantiates; six planted mistakes in the sweep are each
    caught.
+9. The prediction kernel k_predict (perturbation, the shared sin/cos chain,
+   pose -> matrix, 8 lanes per particle exchanging by shuffles), copied
+   verbatim out of filter.cu and run warp by warp under the same emulation,
+   gives the oracle's perturbed cloud and matrices for random cloud sizes,
+   iterations, limits (clamping included), seeds and grids; four planted
+   mistakes in it are each caught.
 """
 import os
 import platform
@@ -689,3 +695,83 @@ def test_measurement_warp_comparison_catches_planted_mistakes(orc, tmp_path):
     for L in _build_all(_build_measure_warp, src, MW_MUTANTS, tmp_path):
         with pytest.raises(AssertionError):
             _check_measure_warp(L, orc, seed=32, count=10)
+
+
+# ------------------------------------- the prediction kernel under the warp emulation
+
+PH_CPP = os.path.join(ROOT, "tests", "predict_host.cpp")
+PH_BEGIN, PH_END = "// Prediction for k > 0", "// Weighted quaternion average"
+
+
+def _build_predict(src_text, d):
+    import ctypes as C
+    assert src_text.count(PH_BEGIN) == 1 and src_text.count(PH_END) == 1
+    (d / "predict.inc").write_text(src_text[src_text.index(PH_BEGIN):src_text.index(PH_END)])
+    so = str(d / "libph.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(d), PH_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    L.dm_predict.argtypes = [C.c_int, C.c_int, C.c_uint64, f32p, C.c_float, C.c_float, i32p, f32p, f32p, i32p,
+                             f32p, f32p, f32p, f32p, f32p]
+    return L
+
+
+def _check_predict(L, orc, seed=34, count=40):
+    rng = np.random.default_rng(seed)
+    for i in range(count):
+        N = 4 * int(rng.integers(1, 129))
+        k = int(rng.choice([0, 1, 2, int(rng.integers(3, 60))]))
+        lim = np.concatenate([rng.uniform(0.05, 1.5707963, 3), rng.uniform(0.5, 60, 3)]).astype(np.float32)
+        s0, decay = float(rng.uniform(0.05, 1.0)), float(rng.uniform(0.5, 1.0))
+        seed_i = int(rng.integers(0, 2**63))
+        sd = rng.integers(2, 300, 3).astype(np.int32)
+        td = rng.integers(2, 300, 3).astype(np.int32)
+        so = rng.uniform(-30, 30, 3).astype(np.float32)
+        to = rng.uniform(-30, 30, 3).astype(np.float32)
+        unit = i % 2 == 0
+        ss = np.ones(3, np.float32) if unit else rng.uniform(0.3, 2.5, 3).astype(np.float32)
+        ts = np.ones(3, np.float32) if unit else rng.uniform(0.3, 2.5, 3).astype(np.float32)
+        _, a = orc.pose_matrix(np.zeros(6, np.float32), sd, so, to, ss, ts)
+        x0 = orc.init_particles(N, seed_i, lim)
+        if i % 5 == 0:   # clouds at the limits, so the perturbation clamps
+            x0 = np.where(rng.random(x0.shape) < 0.5, lim[:, None], -lim[:, None]).astype(np.float32)
+        x = x0.copy()
+        mats = np.zeros((N, 12), np.float32)
+        L.dm_predict(N, k, seed_i, lim, s0, decay, sd, so, ss, td, to, ts, a, x, mats)
+        want = orc.perturb(x0, seed_i, k, orc.sigma(s0, decay, k, lim), lim) if k > 0 else x0
+        assert np.array_equal(x, want), (i, N, k)
+        wm, _ = orc.pose_matrices(want, sd, so, to, ss, ts)
+        assert np.array_equal(mats, wm), (i, N, k)
+
+
+def test_prediction_kernel_equals_the_oracle(orc, tmp_path):
+    # k_predict (perturbation, the shared sin/cos chain, pose -> matrix; 8
+    # lanes per particle exchanging by shuffles), copied verbatim out of
+    # filter.cu and run warp by warp under the lockstep emulation: the
+    # perturbed cloud and every matrix equal the oracle's for random cloud
+    # sizes, iterations, limits (clamping included), seeds and grids
+    _check_predict(_build_predict(open(FILTER_CU).read(), tmp_path), orc)
+
+
+PH_MUTANTS = [
+    ("noise scale decays one step too few", "for (int q = 0; q < k; ++q) pk = __dmul_rn(pk, (double)P.sigma_decay);",
+     "for (int q = 1; q < k; ++q) pk = __dmul_rn(pk, (double)P.sigma_decay);"),
+    ("no lower clamp", "        if (v < -P.lim[j]) v = -P.lim[j];\n        x = v;", "        x = v;"),
+    ("cosine lanes take the wrong angle",
+     "const float ang = __shfl_sync(gmask, x, gbase + (j < 3 ? j : (j < 6 ? j - 3 : 0)));",
+     "const float ang = __shfl_sync(gmask, x, gbase + (j < 3 ? j : (j < 6 ? 5 - j : 0)));"),
+    ("sin and cos of one angle swapped",
+     "matrix_from_sincos(pose, sc[0], sc[3], sc[1], sc[4], sc[2], sc[5], P.g, M);",
+     "matrix_from_sincos(pose, sc[3], sc[0], sc[1], sc[4], sc[2], sc[5], P.g, M);"),
+]
+
+
+def test_prediction_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(FILTER_CU).read()
+    for name, text, _ in PH_MUTANTS:
+        assert src.count(text) == 1, name
+    for L in _build_all(_build_predict, src, PH_MUTANTS, tmp_path):
+        with pytest.raises(AssertionError):
+            _check_predict(L, orc, seed=35, count=10)
