@@ -16,6 +16,9 @@
 #define __device__
 #define __global__
 #define __launch_bounds__(...)
+#define __noinline__ __attribute__((noinline))
+// block-shared variables: one static instance, seen by every emulated thread
+#define __shared__ static
 #define __host__
 #define __forceinline__ inline
 
@@ -25,6 +28,16 @@ inline double __dsub_rn(double a, double b) { return a - b; }
 inline double __ddiv_rn(double a, double b) { return a / b; }
 inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
 inline double __dsqrt_rn(double a) { return std::sqrt(a); }
+inline long long __double_as_longlong(double a) {
+    long long r;
+    std::memcpy(&r, &a, sizeof r);
+    return r;
+}
+inline double __longlong_as_double(long long a) {
+    double r;
+    std::memcpy(&r, &a, sizeof r);
+    return r;
+}
 inline float __double2float_rn(double a) { return (float)a; }
 inline double __ull2double_rn(unsigned long long v) { return (double)v; }
 inline unsigned long long __double2ull_rz(double a) { return (unsigned long long)a; }   // a >= 0 here

@@ -10,7 +10,7 @@
 
 dim3 threadIdx, blockIdx, blockDim, gridDim;
 // under the emulation every lane sees its own thread index
-#define threadIdx (dim3{(unsigned)host_warp::lane, 1u, 1u})
+#define threadIdx (dim3{(unsigned)host_warp::tid, 1u, 1u})
 
 namespace pfreg {
 #include "predict.inc"

@@ -60,6 +60,12 @@ names; the package never builds or loads any of this.
    gives the oracle's perturbed cloud and matrices for random cloud sizes,
    iterations, limits (clamping included), seeds and grids; four planted
    mistakes in it are each caught.
+10. The update step -- k_update_small (one block of 1024 threads) and the
+   three-kernel form k_score / k_weights / k_finalise -- copied verbatim out
+   of filter.cu and run under the block emulation (barriers, shared memory,
+   warp scans), gives the oracle's scores, weights, scan, resampled indices
+   and cloud bit for bit and its estimate and ESS within their summation
+   rounding, for 1 to 13000 particles; six planted mistakes are each caught.
 """
 import os
 import platform
@@ -775,3 +781,111 @@ def test_prediction_comparison_catches_planted_mistakes(orc, tmp_path):
     for L in _build_all(_build_predict, src, PH_MUTANTS, tmp_path):
         with pytest.raises(AssertionError):
             _check_predict(L, orc, seed=35, count=10)
+
+
+# ------------------------------ the update step under the block emulation
+
+UH_CPP = os.path.join(ROOT, "tests", "update_host.cpp")
+UH_BEGIN, UH_END = "// Weighted quaternion average", "// Batched prediction"
+UH_EXTERN = "extern __shared__ unsigned long long sh_cdf[];"
+
+
+def _build_update(src_text, d):
+    import ctypes as C
+    assert src_text.count(UH_BEGIN) == 1 and src_text.count(UH_END) == 1
+    region = src_text[src_text.index(UH_BEGIN):src_text.index(UH_END)]
+    assert region.count(UH_EXTERN) == 1
+    # the dynamic shared array becomes the array the harness declares
+    (d / "update.inc").write_text(region.replace(UH_EXTERN, "extern unsigned long long sh_cdf[];"))
+    so = str(d / "libuh.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(d), UH_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    P = lambda t: np.ctypeslib.ndpointer(t, flags="C_CONTIGUOUS")   # noqa: E731
+    L.dm_update.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int, C.c_int,
+                            P(np.uint64), P(np.float32), P(np.float32), P(np.float64), P(np.uint64), P(np.uint64),
+                            P(np.int32), P(np.float64), P(np.float64), P(np.int32), P(np.uint64)]
+    return L
+
+
+def _check_update(L, orc, seed=36, sizes=(1, 31, 33, 256, 1024, 1025, 4096, 13000)):
+    rng = np.random.default_rng(seed)
+    for case, N in enumerate(sizes):
+        for three in ((0, 1) if N <= 1024 else (0,)):
+            mode, g = int(rng.integers(0, 4)), int(rng.integers(0, 8))
+            seed_i, k = int(rng.integers(0, 2**63)), int(rng.integers(0, 40))
+            moms, b_full = zip(*[_random_moments(rng) for _ in range(N)])
+            mom = np.ascontiguousarray(np.stack(moms))
+            b_full = max(b_full)
+            n_min = int(rng.choice([0, 1 << 24]))
+            if case == 2:                      # every score 0: the cloud is kept, the estimate is the plain mean
+                n_min = 1 << 40
+            x0 = rng.uniform(-1, 1, (6, N)).astype(np.float32)
+            poses, pm = x0.copy(), np.zeros_like(x0)
+            sc, W, Cc = np.zeros(N), np.zeros(N, np.uint64), np.zeros(N, np.uint64)
+            idx, log6, scal = np.zeros(N, np.int32), np.zeros(6), np.zeros(2)
+            ints, ev = np.zeros(2, np.int32), np.zeros(1, np.uint64)
+            L.dm_update(mode, N, g, b_full, n_min, seed_i, k, three, mom, poses, pm, sc, W, Cc, idx, log6, scal,
+                        ints, ev)
+            want_s = np.array([orc.score(mode, m, b_full, n_min) for m in mom])
+            want_W = orc.weights(want_s, g)
+            want_idx = orc.resample(want_W, orc.resample_offset(seed_i, k))
+            cfg = (N, three, mode, g)
+            assert np.array_equal(sc, want_s), cfg
+            assert np.array_equal(W, want_W) and np.array_equal(Cc, np.cumsum(want_W, dtype=np.uint64)), cfg
+            assert np.array_equal(idx, want_idx), cfg
+            assert np.array_equal(pm, x0) and np.array_equal(poses, x0[:, want_idx]), cfg
+            # the estimate's sums run in another order: equal within their rounding
+            np.testing.assert_allclose(log6, orc.estimate(x0, want_W), rtol=1e-12, atol=1e-12, err_msg=str(cfg))
+            assert scal[0] == want_s.max() and ints[0] == int(np.argmax(want_s)), cfg
+            S = float(want_W.sum())
+            want_ess = S * S / float(np.sum(want_W.astype(np.float64) ** 2)) if S > 0 else 0.0
+            assert abs(scal[1] - want_ess) <= 1e-12 * max(1.0, want_ess), cfg
+            col = 0 if mode in (2, 3) else 8
+            assert int(ev[0]) == int(mom[:, col].sum(dtype=np.uint64)) and ints[1] == k + 1, cfg
+    # one particle with a positive score after particles of weight 0, and an
+    # offset so small that the first pointer is T_0 = 0 = C_0: only the strict
+    # C_i > T_j of the resampling search skips the weightless particles
+    N, seed_i = 300, 10488
+    assert orc.resample_offset(seed_i, 0) < N * 256
+    mom = np.zeros((N, 12), np.uint64)
+    mom[5, 8:12] = (10, 5, 4, 3)
+    poses, pm = rng.uniform(-1, 1, (6, N)).astype(np.float32), np.zeros((6, N), np.float32)
+    idx = np.zeros(N, np.int32)
+    L.dm_update(0, N, 5, 10, 0, seed_i, 0, 0, mom, poses, pm, np.zeros(N), np.zeros(N, np.uint64),
+                np.zeros(N, np.uint64), idx, np.zeros(6), np.zeros(2), np.zeros(2, np.int32), np.zeros(1, np.uint64))
+    assert np.all(idx == 5), idx[:4]
+
+
+def test_update_step_equals_the_oracle(orc, tmp_path):
+    # k_update_small and k_score / k_weights / k_finalise, copied verbatim out
+    # of filter.cu and run under the block emulation: scores, integer weights,
+    # their scan, the resampled indices and cloud bit for bit, the estimate and
+    # ESS within their summation rounding, the best score and its first index,
+    # the evaluation count, for clouds of 1 to 13000 particles (past the
+    # 12288-entry shared-memory CDF), every mode, all-zero scores included
+    _check_update(_build_update(open(FILTER_CU).read(), tmp_path), orc)
+
+
+UH_MUTANTS = [
+    ("the warp scan adds a lane too few", "if (lane >= o) v += t;", "if (lane > o) v += t;"),
+    ("the systematic pointers divided by N + 1",
+     "const unsigned long long T = (unsigned long long)(num >> 32) / (unsigned long long)N;",
+     "const unsigned long long T = (unsigned long long)(num >> 32) / (unsigned long long)(N + 1);"),
+    ("the search takes C_i >= T_j", "if (cdf[mid] > T) hi = mid; else lo = mid + 1;",
+     "if (cdf[mid] >= T) hi = mid; else lo = mid + 1;"),
+    ("the last index attaining the maximum",
+     "for (int o = 16; o > 0; o >>= 1) bidx = min(bidx, __shfl_xor_sync(0xffffffffu, bidx, o));",
+     "for (int o = 16; o > 0; o >>= 1) bidx = max(bidx == INT_MAX ? -1 : bidx, __shfl_xor_sync(0xffffffffu, bidx == INT_MAX ? -1 : bidx, o));"),
+    ("ESS without the square", "L.ess = w2 > 0.0 ? Sd * Sd / w2 : 0.0;", "L.ess = w2 > 0.0 ? Sd / w2 : 0.0;"),
+    ("the evaluation count of one warp only", "B.stats[1] = ev;", "B.stats[1] = sh_ev[0];"),
+]
+
+
+def test_update_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(FILTER_CU).read()
+    for name, text, _ in UH_MUTANTS:
+        assert src.count(text) == 1, name
+    for L in _build_all(_build_update, src, UH_MUTANTS, tmp_path):
+        with pytest.raises(AssertionError):
+            _check_update(L, orc, seed=37, sizes=(7, 300, 1025, 2000))
