@@ -66,6 +66,11 @@ names; the package never builds or loads any of this.
    warp scans), gives the oracle's scores, weights, scan, resampled indices
    and cloud bit for bit and its estimate and ESS within their summation
    rounding, for 1 to 13000 particles; six planted mistakes are each caught.
+11. The measurement kernel k_measure itself, block by block under the
+   emulation -- per-warp and per-block (CTAB) x-product tables, mask bits in
+   shared memory or from the global array, both quad indexes, 1 to 8 items
+   per warp, blocks whose items span two particles -- gives the oracle's
+   moments in every combination its launch selects.
 """
 import os
 import platform
@@ -889,3 +894,72 @@ def test_update_comparison_catches_planted_mistakes(orc, tmp_path):
     for L in _build_all(_build_update, src, UH_MUTANTS, tmp_path):
         with pytest.raises(AssertionError):
             _check_update(L, orc, seed=37, sizes=(7, 300, 1025, 2000))
+
+
+# ------------------------------------ the measurement kernel under the block emulation
+
+KC_CPP = os.path.join(ROOT, "tests", "measure_cta_host.cpp")
+KC_END = "// Measurement of many registrations in one launch"
+KC_EXTERN = "extern __shared__ float4 smem_dyn[];"
+
+
+def test_measurement_kernel_equals_the_oracle(orc, tmp_path):
+    # k_measure itself (copied verbatim out of measure.cu), block by block
+    # under the emulation: per-warp and per-block (CTAB) x-product tables,
+    # mask bits in shared memory or read from the global array, the fp32 or
+    # integer quad index, 1 to 8 items per warp, blocks whose items span two
+    # particles; the moments equal the oracle's in every combination the
+    # launch selects
+    import ctypes as C
+    import pfsynth
+    src = open(MEASURE_CU).read()
+    assert src.count(MV_BEGIN) == 1 and src.count(KC_END) == 1
+    region = src[src.index(MV_BEGIN):src.index(KC_END)]
+    assert region.count(KC_EXTERN) == 1
+    (tmp_path / "k_measure.inc").write_text(region.replace(KC_EXTERN, "extern float4 smem_dyn[];"))
+    so = str(tmp_path / "libkc.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-frounding-math", "-fPIC", "-shared",
+                    "-I" + SHIM, "-I" + str(tmp_path), KC_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    L.dm_k_measure.argtypes = [C.c_int] * 7 + [C.c_void_p, C.c_void_p, i32p, C.c_void_p, C.c_void_p, i32p, f32p,
+                                                C.c_int, f32p, u64p]
+    rng = np.random.default_rng(38)
+    runs = ctab_runs = 0
+    for i in range(4):
+        sd = (int(rng.integers(8, 60)), int(rng.integers(8, 40)), int(rng.integers(8, 30)))
+        td = (int(rng.integers(8, 70)), int(rng.integers(16, 32)), int(rng.integers(16, 28)))
+        src_v = pfsynth.random_image(int(rng.integers(0, 1 << 30)), sd)
+        tgt_v = pfsynth.random_image(int(rng.integers(0, 1 << 30)), td)
+        smask = (rng.random((sd[2], sd[1], sd[0])) < 0.5).astype(np.uint8)
+        tmask = (rng.random((td[2], td[1], td[0])) < 0.5).astype(np.uint8)
+        P = int(rng.integers(2, 6))
+        poses = np.concatenate([rng.uniform(-1.2, 1.2, (3, P)), rng.uniform(-8, 8, (3, P))]).astype(np.float32)
+        mats, a = orc.pose_matrices(poses, sd, rng.uniform(-4, 4, 3).astype(np.float32),
+                                    rng.uniform(-4, 4, 3).astype(np.float32))
+        mats = np.ascontiguousarray(mats, np.float32)
+        want_img = orc.measure_image(src_v, tgt_v, mats, a)
+        want_msk = orc.measure_mask(smask, tmask, mats, a)
+        sdv, tdv = np.array(sd, np.int32), np.array(td, np.int32)
+        for img, msk in ((1, 0), (0, 1), (1, 1)):
+            for smem in ((0, 1) if msk else (0,)):
+                for int_index in ((0, 1) if img else (0,)):
+                    for xtab, ctab in ((0, 0), (1, 0), (1, 1)):
+                        ipw = int(rng.choice([1, 1, 2] if ctab else [1, 2, 4, 8]))
+                        got = np.zeros((P, 12), np.uint64)
+                        rc = L.dm_k_measure(img, msk, smem, int_index, xtab, ctab, ipw,
+                                            _ptr(src_v) if img else None, _ptr(smask) if msk else None, sdv,
+                                            _ptr(tgt_v) if img else None, _ptr(tmask) if msk else None, tdv,
+                                            mats, P, a, got)
+                        if rc != 0:        # a shape the launch does not use (CTAB without enough rows)
+                            continue
+                        runs += 1
+                        ctab_runs += ctab
+                        cfg = (sd, td, P, img, msk, smem, int_index, xtab, ctab, ipw)
+                        if img:
+                            assert np.array_equal(got[:, 0:7], want_img), cfg
+                        if msk:
+                            assert np.array_equal(got[:, 8:12], want_msk), cfg
+    assert runs >= 60 and ctab_runs >= 8, (runs, ctab_runs)
