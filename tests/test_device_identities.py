@@ -71,6 +71,10 @@ names; the package never builds or loads any of this.
    shared memory or from the global array, both quad indexes, 1 to 8 items
    per warp, blocks whose items span two particles -- gives the oracle's
    moments in every combination its launch selects.
+12. The sequence-warp kernel k_warp itself, block by block under the
+   emulation (matrix built in shared memory, grid-stride rows, four frames
+   at a time and the remainder, both index widths), equals the oracle's warp
+   of every frame.
 """
 import os
 import platform
@@ -963,3 +967,44 @@ def test_measurement_kernel_equals_the_oracle(orc, tmp_path):
                         if msk:
                             assert np.array_equal(got[:, 8:12], want_msk), cfg
     assert runs >= 60 and ctab_runs >= 8, (runs, ctab_runs)
+
+
+def test_warp_kernel_equals_the_oracle(orc, tmp_path):
+    # k_warp itself (copied verbatim out of warp.cu) block by block under the
+    # emulation: the matrix built in shared memory from six lanes' sin/cos,
+    # rows walked by a grid-stride loop, frames sampled four at a time with a
+    # remainder; both index widths and interpolations
+    import ctypes as C
+    import pfsynth
+    w = open(WARP_CU).read()
+    b0 = "constexpr int kWarpThreads = 256;"
+    assert w.count(b0) == 1
+    i = w.index(b0)
+    (tmp_path / "k_warp.inc").write_text(w[i:w.index("}  // namespace", i)])
+    so = str(tmp_path / "libwk.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(tmp_path), os.path.join(ROOT, "tests", "warp_kernel_host.cpp"), "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+    L.dm_k_warp.argtypes = [u8p, C.c_int, i32p, f32p, f32p, u8p, i32p, f32p, f32p, f32p, f32p, C.c_int, C.c_int,
+                            C.c_int]
+    rng = np.random.default_rng(39)
+    for i, (n_frames, blocks) in enumerate(((1, 1), (5, 2), (9, 3), (4, 1))):
+        sd = tuple(int(v) for v in rng.integers(3, 24, 3))
+        td = tuple(int(v) for v in rng.integers(3, 24, 3))
+        frames = np.stack([pfsynth.random_image(int(rng.integers(0, 1 << 30)), sd) for _ in range(n_frames)])
+        so, to = rng.uniform(-5, 5, 3).astype(np.float32), rng.uniform(-5, 5, 3).astype(np.float32)
+        ss = np.ones(3, np.float32) if i % 2 == 0 else rng.uniform(0.5, 2.0, 3).astype(np.float32)
+        ts = np.ones(3, np.float32) if i % 2 == 0 else rng.uniform(0.5, 2.0, 3).astype(np.float32)
+        pose = np.concatenate([rng.uniform(-1.2, 1.2, 3), rng.uniform(-6, 6, 3)]).astype(np.float32)
+        _, a = orc.pose_matrix(pose, sd, so, to, ss, ts)
+        for interp in (0, 1):
+            for wide in (0, 1):
+                out = np.zeros((n_frames, td[2], td[1], td[0]), np.uint8)
+                L.dm_k_warp(np.ascontiguousarray(frames), n_frames, np.array(sd, np.int32), so, ss, out,
+                            np.array(td, np.int32), to, ts, a, pose, interp, wide, blocks)
+                for f in range(n_frames):
+                    want = orc.warp(frames[f], so, td, to, pose, interp, ss, ts)
+                    assert np.array_equal(out[f], want), (i, f, interp, wide)
