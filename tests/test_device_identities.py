@@ -75,6 +75,11 @@ names; the package never builds or loads any of this.
    emulation (matrix built in shared memory, grid-stride rows, four frames
    at a time and the remainder, both index widths), equals the oracle's warp
    of every frame.
+13. One batch iteration -- k_predict_batch, k_measure_batch over the image,
+   mask and combined lists, k_score_batch, k_weights_batch, k_finalise_batch
+   -- under the emulation gives every member of a mixed batch the oracle's
+   single-registration steps (cloud, matrices, moments, scores, weights,
+   indices, resampled cloud), with and without the per-warp tables.
 """
 import os
 import platform
@@ -1008,3 +1013,110 @@ def test_warp_kernel_equals_the_oracle(orc, tmp_path):
                 for f in range(n_frames):
                     want = orc.warp(frames[f], so, td, to, pose, interp, ss, ts)
                     assert np.array_equal(out[f], want), (i, f, interp, wide)
+
+
+# --------------------------------- one batch iteration under the block emulation
+
+BH_CPP = os.path.join(ROOT, "tests", "batch_host.cpp")
+BF_END = "// Matrix of one pose by a group of 8 lanes"
+BM_END = "template <bool IMG, bool MASK, bool SMEM, bool FIDX, bool XTAB, bool CTAB>\ncudaError_t launch_variant"
+
+
+def _batch_member_type():
+    import ctypes as C
+    f3, i3 = C.c_float * 3, C.c_int32 * 3
+    P = C.c_void_p
+
+    class DmMember(C.Structure):
+        _fields_ = [("mode", C.c_int32), ("N", C.c_int32), ("k", C.c_int32), ("gamma_log2", C.c_int32),
+                    ("seed", C.c_uint64), ("b_full", C.c_uint64), ("n_min", C.c_uint64),
+                    ("lim", C.c_float * 6), ("sigma0_frac", C.c_float), ("sigma_decay", C.c_float),
+                    ("sd", i3), ("td", i3), ("so", f3), ("ss", f3), ("to", f3), ("ts", f3), ("a", f3),
+                    ("src", P), ("src_mask", P), ("tgt", P), ("tgt_mask", P), ("poses", P), ("poses_meas", P),
+                    ("mats", P), ("mom", P), ("W", P), ("C", P), ("scores", P), ("est", P), ("idx", P)]
+    return DmMember
+
+
+def test_batch_iteration_equals_the_oracle(orc, tmp_path):
+    # the batch kernels (copied verbatim out of filter.cu and measure.cu), one
+    # iteration of a batch of every mode and mixed sizes under the emulation:
+    # each member's perturbed cloud, matrices, moments, scores, weights,
+    # resampled indices and cloud equal the oracle's single-registration
+    # steps, its estimate within summation rounding
+    import ctypes as C
+    import pfsynth
+    f, m = open(FILTER_CU).read(), open(MEASURE_CU).read()
+    fr = f[f.index(PH_BEGIN):f.index(BF_END)]
+    mr = m[m.index(MV_BEGIN):m.index(BM_END)]
+    assert fr.count(UH_EXTERN) == 1 and mr.count(KC_EXTERN) == 2
+    (tmp_path / "batch_filter.inc").write_text(fr.replace(UH_EXTERN, "extern unsigned long long sh_cdf[];"))
+    (tmp_path / "batch_measure.inc").write_text(mr.replace(KC_EXTERN, "extern float4 smem_dyn[];"))
+    so_path = str(tmp_path / "libbh.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-frounding-math", "-fPIC", "-shared",
+                    "-I" + SHIM, "-I" + str(tmp_path), BH_CPP, "-o", so_path], check=True)
+    L = C.CDLL(so_path)
+    DmMember = _batch_member_type()
+    L.dm_batch_step.argtypes = [C.POINTER(DmMember), C.c_int, C.c_int, C.c_int]
+    rng = np.random.default_rng(40)
+    for ipw, use_tab in ((1, 1), (4, 0), (2, 1)):
+        n = 6
+        members = (DmMember * n)()
+        keep, want = [], []
+        for r in range(n):
+            mode = (r + ipw) % 4
+            sd = tuple(int(v) for v in rng.integers(6, 26, 3))
+            td = tuple(int(v) for v in rng.integers(6, 22, 3))
+            N = 4 * int(rng.integers(1, 11))
+            k = int(rng.integers(1, 8))
+            src = pfsynth.random_image(int(rng.integers(0, 1 << 30)), sd)
+            tgt = pfsynth.random_image(int(rng.integers(0, 1 << 30)), td)
+            smask = (rng.random((sd[2], sd[1], sd[0])) < 0.5).astype(np.uint8)
+            tmask = (rng.random((td[2], td[1], td[0])) < 0.5).astype(np.uint8)
+            so, to = rng.uniform(-4, 4, 3).astype(np.float32), rng.uniform(-4, 4, 3).astype(np.float32)
+            ss = ts = np.ones(3, np.float32)
+            lim = np.array([0.6, 0.5, 0.4, 6, 5, 4], np.float32)
+            seed_i, g = int(rng.integers(0, 2**63)), 5
+            img, msk = mode in (2, 3), mode != 2
+            b_full = int(np.count_nonzero(tmask)) if msk else 0
+            n_min = int(0.01 * np.prod(td))
+            _, a = orc.pose_matrix(np.zeros(6, np.float32), sd, so, to, ss, ts)
+            x0 = orc.init_particles(N, seed_i, lim)
+            bufs = dict(poses=x0.copy(), poses_meas=np.zeros((6, N), np.float32), mats=np.zeros((N, 12), np.float32),
+                        mom=np.zeros((N, 12), np.uint64), W=np.zeros(N, np.uint64), C=np.zeros(N, np.uint64),
+                        scores=np.zeros(N), est=np.zeros(6), idx=np.zeros(N, np.int32))
+            vols = dict(src=src if img else None, src_mask=smask if msk else None, tgt=tgt if img else None,
+                        tgt_mask=tmask if msk else None)
+            keep.append((bufs, vols))
+            M = members[r]
+            M.mode, M.N, M.k, M.gamma_log2 = mode, N, k, g
+            M.seed, M.b_full, M.n_min = seed_i, b_full, n_min
+            M.lim[:] = lim.tolist()
+            M.sigma0_frac, M.sigma_decay = 0.25, 0.8
+            M.sd[:], M.td[:] = sd, td
+            M.so[:], M.ss[:], M.to[:], M.ts[:], M.a[:] = so.tolist(), ss.tolist(), to.tolist(), ts.tolist(), a.tolist()
+            for name, v in vols.items():
+                setattr(M, name, None if v is None else v.ctypes.data)
+            for name, v in bufs.items():
+                setattr(M, name, v.ctypes.data)
+            # the oracle's steps of this member alone
+            x1 = orc.perturb(x0, seed_i, k, orc.sigma(0.25, 0.8, k, lim), lim)
+            mats, _ = orc.pose_matrices(x1, sd, so, to, ss, ts)
+            mom = np.zeros((N, 12), np.uint64)
+            if img:
+                mom[:, 0:7] = orc.measure_image(src, tgt, mats, a)
+            if msk:
+                mom[:, 8:12] = orc.measure_mask(smask, tmask, mats, a)
+            s = np.array([orc.score(mode, mom[i], b_full, n_min) for i in range(N)])
+            W = orc.weights(s, g)
+            idx = orc.resample(W, orc.resample_offset(seed_i, k))
+            want.append(dict(x1=x1, mats=mats, mom=mom, s=s, W=W, idx=idx, est=orc.estimate(x1, W)))
+        L.dm_batch_step(members, n, ipw, use_tab)
+        for r, ((bufs, _), w) in enumerate(zip(keep, want)):
+            cfg = (ipw, use_tab, r, int(members[r].mode), int(members[r].N))
+            assert np.array_equal(bufs["poses_meas"], w["x1"]), cfg
+            assert np.array_equal(bufs["mats"], w["mats"]), cfg
+            assert np.array_equal(bufs["mom"], w["mom"]), cfg
+            assert np.array_equal(bufs["scores"], w["s"]) and np.array_equal(bufs["W"], w["W"]), cfg
+            assert np.array_equal(bufs["idx"], w["idx"]), cfg
+            assert np.array_equal(bufs["poses"], w["x1"][:, w["idx"]]), cfg
+            np.testing.assert_allclose(bufs["est"], w["est"], rtol=1e-12, atol=1e-12, err_msg=str(cfg))
