@@ -135,6 +135,9 @@ MUTANTS = [
      "for (int d = 0; d < 6; ++d) sig[d] = sig[d];"),
     ("seed_mean_ignored", "Sec. 6 seeding",
      "float v = mean[d] + std[d] * e;", "float v = std[d] * e;"),
+    ("seed_lower_clamp_missing", "Sec. 6 seeding (clamp to the limits)",
+     "            float v = mean[d] + std[d] * e;\n            if (v > lim[d]) v = lim[d];\n            if (v < -lim[d]) v = -lim[d];",
+     "            float v = mean[d] + std[d] * e;\n            if (v > lim[d]) v = lim[d];"),
 ]
 
 

@@ -705,3 +705,6 @@ def test_init_gaussian_statistics(orc):
     far = mean.copy()
     far[3] = 40.0
     assert np.all(orc.init_gaussian(100, 7, far, std, lim)[3] == 20.0)
+    far[3], far[4] = -40.0, -25.0
+    x = orc.init_gaussian(100, 7, far, std, lim)
+    assert np.all(x[3] == -20.0) and np.all(x[4] == -20.0)
