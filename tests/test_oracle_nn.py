@@ -162,3 +162,27 @@ def test_box_average_against_loops():
                                 vals.append(vol[z, y, x])
                 want = np.mean(vals) / 64.0 if vals else 0.0
                 assert abs(got[gz, gy, gx] - want) < 1e-12
+
+
+def test_abs_bound_is_the_loop_over_absolute_values():
+    # the per-output sum of |x| |w| the GPU tests scale their error bounds by
+    rng = np.random.default_rng(11)
+    x = _rand(rng, 1, 4, 4, 4, 3)
+    w = _rand(rng, 2, 64, 3)
+    want = onn.conv3d_loop(np.abs(x), np.abs(w), np.zeros(2))
+    assert np.allclose(onn.conv3d_abs_bound(x, w), want, rtol=1e-12, atol=1e-12)
+
+
+def test_network_rounding_is_bf16_at_the_stated_points():
+    # net_forward's default rounding: the conv weights and every conv output
+    # (after ReLU) are bf16 values; with the identity it is the exact network
+    rng = np.random.default_rng(12)
+    _, total = onn.layout()
+    theta = rng.standard_normal(total) * 0.05
+    x = onn.bf16_round(rng.uniform(0, 4, (1, 64, 64, 64, 2)).astype(np.float32)).astype(np.float64)
+    out, h, acts = onn.net_forward(theta, x)
+    for a in acts:
+        assert np.array_equal(a, onn.bf16_round(a.astype(np.float32)).astype(np.float64))
+    out_exact, _, _ = onn.net_forward(theta, x, rnd=lambda v: v)
+    assert not np.array_equal(out, out_exact)
+    assert np.allclose(out, out_exact, rtol=0.05, atol=0.05 * np.abs(out_exact).max())
