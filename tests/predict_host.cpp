@@ -17,16 +17,18 @@ namespace pfreg {
 }
 
 // N a multiple of 4 (whole warps of 4 particles x 8 lanes); poses [6][N] in
-// and out (perturbed for k > 0), mats [N][12] out.
+// and out (perturbed for k > 0), mats [N][12] out; with estimator = 1 also
+// each pose's quaternion, quat [4][N].
 extern "C" void dm_predict(int N, int k, uint64_t seed, const float lim[6], float sigma0_frac, float decay,
                            const int32_t sd[3], const float so[3], const float ss[3], const int32_t td[3],
-                           const float to[3], const float ts[3], const float a_off[3], float *poses, float *mats) {
+                           const float to[3], const float ts[3], const float a_off[3], float *poses, float *mats,
+                           int estimator, double *quat) {
     pfreg::FilterParams P{};
     P.N = N;
     P.seed = seed;
     P.sigma0_frac = sigma0_frac;
     P.sigma_decay = decay;
-    P.estimator = 0;
+    P.estimator = estimator;
     for (int d = 0; d < 6; ++d) {
         P.lim[d] = lim[d];
         P.sig0[d] = (double)sigma0_frac * (double)lim[d];
@@ -48,6 +50,7 @@ extern "C" void dm_predict(int N, int k, uint64_t seed, const float lim[6], floa
     B.mom = mom.data();
     B.stats = stats.data();
     B.k = &kk;
+    B.quat = quat;
     blockDim.x = 32;
     gridDim.x = (unsigned)(N * 8 / 32);
     for (unsigned b = 0; b < gridDim.x; ++b) {

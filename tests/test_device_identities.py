@@ -57,15 +57,17 @@ names; the package never builds or loads any of this.
 9. The prediction kernel k_predict (perturbation, the shared sin/cos chain,
    pose -> matrix, 8 lanes per particle exchanging by shuffles), copied
    verbatim out of filter.cu and run warp by warp under the same emulation,
-   gives the oracle's perturbed cloud and matrices for random cloud sizes,
-   iterations, limits (clamping included), seeds and grids; four planted
-   mistakes in it are each caught.
+   gives the oracle's perturbed cloud and matrices (and, for the quaternion
+   estimator, each pose's quaternion) for random cloud sizes, iterations,
+   limits (clamping included), seeds and grids; four planted mistakes in it
+   are each caught.
 10. The update step -- k_update_small (one block of 1024 threads) and the
    three-kernel form k_score / k_weights / k_finalise -- copied verbatim out
    of filter.cu and run under the block emulation (barriers, shared memory,
    warp scans), gives the oracle's scores, weights, scan, resampled indices
    and cloud bit for bit and its estimate and ESS within their summation
-   rounding, for 1 to 13000 particles; six planted mistakes are each caught.
+   rounding (the quaternion average's rotation within 1e-9), for 1 to 13000
+   particles; six planted mistakes are each caught.
 11. The measurement kernel k_measure itself, block by block under the
    emulation -- per-warp and per-block (CTAB) x-product tables, mask bits in
    shared memory or from the global array, both quad indexes, 1 to 8 items
@@ -645,11 +647,27 @@ def _bright_case(orc):
     return sd, td, src, tgt, None, None, np.ascontiguousarray(mats, np.float32), a
 
 
+def _edge_case(orc):
+    # rows 64 voxels long for nearest-neighbour sampling whose trilinear
+    # interval ends one voxel earlier, on the source's top y plane (so the y
+    # corner is clamped): a combined full pass in which the image interval
+    # ends and the clamp is needed
+    rng = np.random.default_rng(41)
+    sd, td = (64, 6, 5), (70, 6, 5)
+    src = rng.integers(0, 256, (sd[2], sd[1], sd[0])).astype(np.uint8)
+    tgt = rng.integers(0, 256, (td[2], td[1], td[0])).astype(np.uint8)
+    smask = (rng.random(src.shape) < 0.5).astype(np.uint8)
+    tmask = (rng.random(tgt.shape) < 0.5).astype(np.uint8)
+    pose = np.array([0, 0, 0, 0.25, 0, 0], np.float32)
+    mats, a = orc.pose_matrices(pose[:, None], sd, np.zeros(3, np.float32), np.zeros(3, np.float32))
+    return sd, td, src, tgt, smask, tmask, np.ascontiguousarray(mats, np.float32), a
+
+
 def _check_measure_warp(L, orc, seed=31, count=24):
     import itertools
     bright = _bright_case(orc)
     assert orc.measure_image(bright[2], bright[3], bright[6], bright[7])[0, 3] > 0   # S2 high word used
-    for sd, td, src, tgt, smask, tmask, mats, a in itertools.chain(_warp_cases(orc, seed, count), [bright]):
+    for sd, td, src, tgt, smask, tmask, mats, a in itertools.chain(_warp_cases(orc, seed, count), [_edge_case(orc), bright]):
         P = mats.shape[0]
         sdv, tdv = np.array(sd, np.int32), np.array(td, np.int32)
         want_img = orc.measure_image(src, tgt, mats, a)
@@ -734,7 +752,7 @@ def _build_predict(src_text, d):
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     L.dm_predict.argtypes = [C.c_int, C.c_int, C.c_uint64, f32p, C.c_float, C.c_float, i32p, f32p, f32p, i32p,
-                             f32p, f32p, f32p, f32p, f32p]
+                             f32p, f32p, f32p, f32p, f32p, C.c_int, C.c_void_p]
     return L
 
 
@@ -759,11 +777,21 @@ def _check_predict(L, orc, seed=34, count=40):
             x0 = np.where(rng.random(x0.shape) < 0.5, lim[:, None], -lim[:, None]).astype(np.float32)
         x = x0.copy()
         mats = np.zeros((N, 12), np.float32)
-        L.dm_predict(N, k, seed_i, lim, s0, decay, sd, so, ss, td, to, ts, a, x, mats)
+        est_q = i % 3 == 1                 # the quaternion estimator's per-pose quaternions too
+        quat = np.zeros((4, N))
+        L.dm_predict(N, k, seed_i, lim, s0, decay, sd, so, ss, td, to, ts, a, x, mats, int(est_q),
+                     quat.ctypes.data if est_q else None)
         want = orc.perturb(x0, seed_i, k, orc.sigma(s0, decay, k, lim), lim) if k > 0 else x0
         assert np.array_equal(x, want), (i, N, k)
         wm, _ = orc.pose_matrices(want, sd, so, to, ss, ts)
         assert np.array_equal(mats, wm), (i, N, k)
+        if est_q:
+            # q and -q are one rotation; fp64 half-angle formulas against the
+            # oracle's sin/cos of the half angles
+            for j in range(N):
+                q = orc.quaternion(want[:, j])
+                sgn = 1.0 if np.dot(q, quat[:, j]) >= 0 else -1.0
+                np.testing.assert_allclose(quat[:, j], sgn * q, rtol=0, atol=1e-12, err_msg=str((i, j)))
 
 
 def test_prediction_kernel_equals_the_oracle(orc, tmp_path):
@@ -818,7 +846,8 @@ def _build_update(src_text, d):
     P = lambda t: np.ctypeslib.ndpointer(t, flags="C_CONTIGUOUS")   # noqa: E731
     L.dm_update.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, C.c_int, C.c_int,
                             P(np.uint64), P(np.float32), P(np.float32), P(np.float64), P(np.uint64), P(np.uint64),
-                            P(np.int32), P(np.float64), P(np.float64), P(np.int32), P(np.uint64)]
+                            P(np.int32), P(np.float64), P(np.float64), P(np.int32), P(np.uint64), C.c_int,
+                            C.c_void_p]
     return L
 
 
@@ -839,8 +868,10 @@ def _check_update(L, orc, seed=36, sizes=(1, 31, 33, 256, 1024, 1025, 4096, 1300
             sc, W, Cc = np.zeros(N), np.zeros(N, np.uint64), np.zeros(N, np.uint64)
             idx, log6, scal = np.zeros(N, np.int32), np.zeros(6), np.zeros(2)
             ints, ev = np.zeros(2, np.int32), np.zeros(1, np.uint64)
+            est_q = (case + three) % 2 == 1    # the quaternion estimator on every other case
+            quat = np.ascontiguousarray(np.stack([orc.quaternion(x0[:, j]) for j in range(N)], 1)) if est_q else None
             L.dm_update(mode, N, g, b_full, n_min, seed_i, k, three, mom, poses, pm, sc, W, Cc, idx, log6, scal,
-                        ints, ev)
+                        ints, ev, int(est_q), quat.ctypes.data if est_q else None)
             want_s = np.array([orc.score(mode, m, b_full, n_min) for m in mom])
             want_W = orc.weights(want_s, g)
             want_idx = orc.resample(want_W, orc.resample_offset(seed_i, k))
@@ -850,7 +881,13 @@ def _check_update(L, orc, seed=36, sizes=(1, 31, 33, 256, 1024, 1025, 4096, 1300
             assert np.array_equal(idx, want_idx), cfg
             assert np.array_equal(pm, x0) and np.array_equal(poses, x0[:, want_idx]), cfg
             # the estimate's sums run in another order: equal within their rounding
-            np.testing.assert_allclose(log6, orc.estimate(x0, want_W), rtol=1e-12, atol=1e-12, err_msg=str(cfg))
+            want_est = orc.estimate(x0, want_W)
+            np.testing.assert_allclose(log6[3:], want_est[3:], rtol=1e-12, atol=1e-12, err_msg=str(cfg))
+            if est_q:   # the rotation from the weighted quaternion average (eigenvector, then angles)
+                np.testing.assert_allclose(log6[:3], orc.estimate_quaternion(x0, want_W)[:3], rtol=0, atol=1e-9,
+                                           err_msg=str(cfg))
+            else:
+                np.testing.assert_allclose(log6[:3], want_est[:3], rtol=1e-12, atol=1e-12, err_msg=str(cfg))
             assert scal[0] == want_s.max() and ints[0] == int(np.argmax(want_s)), cfg
             S = float(want_W.sum())
             want_ess = S * S / float(np.sum(want_W.astype(np.float64) ** 2)) if S > 0 else 0.0
@@ -867,7 +904,8 @@ def _check_update(L, orc, seed=36, sizes=(1, 31, 33, 256, 1024, 1025, 4096, 1300
     poses, pm = rng.uniform(-1, 1, (6, N)).astype(np.float32), np.zeros((6, N), np.float32)
     idx = np.zeros(N, np.int32)
     L.dm_update(0, N, 5, 10, 0, seed_i, 0, 0, mom, poses, pm, np.zeros(N), np.zeros(N, np.uint64),
-                np.zeros(N, np.uint64), idx, np.zeros(6), np.zeros(2), np.zeros(2, np.int32), np.zeros(1, np.uint64))
+                np.zeros(N, np.uint64), idx, np.zeros(6), np.zeros(2), np.zeros(2, np.int32), np.zeros(1, np.uint64),
+                0, None)
     assert np.all(idx == 5), idx[:4]
 
 

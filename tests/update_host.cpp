@@ -42,7 +42,7 @@ extern "C" {
 void dm_update(int mode, int N, int gamma_log2, uint64_t b_full, uint64_t n_min, uint64_t seed, int k,
                int three_kernels, const uint64_t *mom, float *poses, float *poses_meas, double *scores,
                uint64_t *W, uint64_t *C, int32_t *idx, double log6[6], double scal[2], int32_t ints[2],
-               uint64_t *evals) {
+               uint64_t *evals, int estimator, const double *quat) {
     pfreg::FilterParams P{};
     P.mode = mode;
     P.N = N;
@@ -51,7 +51,7 @@ void dm_update(int mode, int N, int gamma_log2, uint64_t b_full, uint64_t n_min,
     P.n_min = n_min;
     P.seed = seed;
     P.log_capacity = 16;
-    P.estimator = 0;
+    P.estimator = estimator;   // 1: the rotation from the quaternions quat [4][N]
     std::vector<unsigned long long> momv(mom, mom + 12 * (size_t)N), stats(2, 0ull);
     std::vector<pfreg::IterLog> log(16);
     int32_t kk = k;
@@ -66,6 +66,7 @@ void dm_update(int mode, int N, int gamma_log2, uint64_t b_full, uint64_t n_min,
     B.k = &kk;
     B.log = log.data();
     B.stats = stats.data();
+    B.quat = const_cast<double *>(quat);
     if (N <= pfreg::kFinThreads && !three_kernels) {
         launch(1, pfreg::kFinThreads, [&] { pfreg::k_update_small(P, B); });
     } else {
