@@ -82,6 +82,10 @@ names; the package never builds or loads any of this.
    -- under the emulation gives every member of a mixed batch the oracle's
    single-registration steps (cloud, matrices, moments, scores, weights,
    indices, resampled cloud), with and without the per-warp tables.
+14. Whole trajectories: k_predict, k_measure and the update kernels run
+   iteration after iteration from the initial cloud, as the iteration graph
+   runs them, and every iteration equals the oracle registration's trace in
+   all four modes, on both sides of the one-block update.
 """
 import os
 import platform
@@ -1158,3 +1162,74 @@ def test_batch_iteration_equals_the_oracle(orc, tmp_path):
             assert np.array_equal(bufs["idx"], w["idx"]), cfg
             assert np.array_equal(bufs["poses"], w["x1"][:, w["idx"]]), cfg
             np.testing.assert_allclose(bufs["est"], w["est"], rtol=1e-12, atol=1e-12, err_msg=str(cfg))
+
+
+# -------------------------- whole trajectories of the kernels under the emulation
+
+TH_CPP = os.path.join(ROOT, "tests", "trajectory_host.cpp")
+
+
+def test_kernel_trajectories_equal_the_oracle(orc, tmp_path):
+    # k_predict, k_measure and the update kernels (copied verbatim out of
+    # filter.cu and measure.cu) run iteration after iteration from the
+    # initial cloud, as the iteration graph does: every iteration's measured
+    # cloud, moments, scores, weights and indices equal the oracle
+    # registration's trace, its estimate within summation rounding, in all
+    # four modes and on both sides of the one-block update (the larger cloud
+    # for one iteration on a small grid: the emulation is slow)
+    import ctypes as C
+    import pfsynth
+    f, m = open(FILTER_CU).read(), open(MEASURE_CU).read()
+    fr = f[f.index(PH_BEGIN):f.index(BF_END)]
+    mr = m[m.index(MV_BEGIN):m.index(BM_END)]
+    (tmp_path / "batch_filter.inc").write_text(fr.replace(UH_EXTERN, "extern unsigned long long sh_cdf[];"))
+    (tmp_path / "batch_measure.inc").write_text(mr.replace(KC_EXTERN, "extern float4 smem_dyn[];"))
+    so_path = str(tmp_path / "libth.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-frounding-math", "-fPIC", "-shared",
+                    "-I" + SHIM, "-I" + str(tmp_path), TH_CPP, "-o", so_path], check=True)
+    L = C.CDLL(so_path)
+    P = C.c_void_p
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    L.dm_trajectory.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, f32p, C.c_float, C.c_float, C.c_int,
+                                C.c_float, P, P, i32p, f32p, P, P, i32p, f32p, f32p, C.c_int, f32p,
+                                P, P, P, P, P, P]
+    cases = [("mask_dice", 64, 3, 2), ("mask_ncc", 60, 3, 1), ("image_ncc", 48, 3, 4), ("combined", 40, 3, 8),
+             ("mask_dice", 1028, 1, 32)]
+    for i, (mode, N, K, ipw) in enumerate(cases):
+        if mode in ("mask_dice", "mask_ncc"):
+            small = N > 1024             # the three-kernel update: a small grid keeps the emulation quick
+            pair = pfsynth.ellipsoid_pair(20 + i, src_dims=(12, 11, 10) if small else (18, 16, 14),
+                                          tgt_dims=(12, 10, 6) if small else (17, 14, 11),
+                                          tgt_origin=(0, 0, 2), semi_axes=(4, 3, 3) if small else (6, 5, 4),
+                                          asymmetric=True, max_rot_deg=8, max_trans=3)
+        else:
+            pair = pfsynth.speckle_pair(20 + i, src_dims=(20, 18, 16), tgt_dims=(19, 17, 14), overlap=(0.55, 0.7),
+                                        max_rot_deg=8, max_trans=3, with_masks=(mode == "combined"))
+        lr, lt, seed = 0.2, 3.0, 40 + i
+        ref = orc.register(mode, pair.src_dims, pair.src_origin, pair.tgt_dims, pair.tgt_origin, N, K, lr, lt,
+                           seed=seed, src=pair.src if mode in ("image_ncc", "combined") else None,
+                           tgt=pair.tgt if mode in ("image_ncc", "combined") else None,
+                           src_mask=pair.src_mask if mode != "image_ncc" else None,
+                           tgt_mask=pair.tgt_mask if mode != "image_ncc" else None)
+        lim = np.array([lr] * 3 + [lt] * 3, np.float32)
+        sd, td = np.array(pair.src_dims, np.int32), np.array(pair.tgt_dims, np.int32)
+        so = np.asarray(pair.src_origin, np.float32)
+        to = np.asarray(pair.tgt_origin, np.float32)
+        _, a = orc.pose_matrix(np.zeros(6, np.float32), sd, so, to)
+        poses = orc.init_particles(N, seed, lim)
+        tr = dict(p=np.zeros((K, 6, N), np.float32), m=np.zeros((K, N, 12), np.uint64), s=np.zeros((K, N)),
+                  W=np.zeros((K, N), np.uint64), i=np.zeros((K, N), np.int32), e=np.zeros((K, 6)))
+        img, msk = mode in ("image_ncc", "combined"), mode != "image_ncc"
+        vol = lambda v, use: (np.ascontiguousarray(v).ctypes.data if use else None)   # noqa: E731
+        L.dm_trajectory(orc.MODES[mode], N, K, seed, lim, 0.25, 0.8, 5, 0.01, vol(pair.src, img),
+                        vol(pair.src_mask, msk), sd, so, vol(pair.tgt, img), vol(pair.tgt_mask, msk), td, to, a,
+                        ipw, poses, *(tr[k].ctypes.data for k in ("p", "m", "s", "W", "i", "e")))
+        for kk in range(K):
+            cfg = (mode, N, kk)
+            assert np.array_equal(tr["p"][kk], ref["tr_poses"][kk]), cfg
+            assert np.array_equal(tr["m"][kk], ref["tr_mom"][kk]), cfg
+            assert np.array_equal(tr["s"][kk], ref["tr_score"][kk]), cfg
+            assert np.array_equal(tr["W"][kk], ref["tr_W"][kk]), cfg
+            assert np.array_equal(tr["i"][kk], ref["tr_idx"][kk]), cfg
+            np.testing.assert_allclose(tr["e"][kk], ref["tr_est"][kk], rtol=1e-12, atol=1e-12, err_msg=str(cfg))
