@@ -10,8 +10,9 @@
  *   __syncthreads: each thread hands control to the next thread of the block
  *     (warp-major), so when it resumes every thread has arrived.
  * Shared memory is the block's static storage (__shared__ is `static`), which
- * all contexts see.  Valid for code whose warp operations are uniform within
- * a warp (full mask) and whose barriers are uniform within the block, as the
+ * all contexts see.  Valid for code whose warp operations are uniform over
+ * the warp's live lanes and whose barriers are uniform over the block's live
+ * threads (a thread that has returned takes part in neither), as the
  * filter's kernels are.  host_warp::run(n, body) runs body(tid) on n threads
  * (a multiple of 32).  Include this before anything that includes
  * tests/host_shim/cuda_runtime.h.  Test infrastructure only. */
@@ -41,9 +42,18 @@ inline void switch_to(int next) {
     swapcontext(&ctx[cur], &ctx[next]);
     tid = cur;
 }
-// hand control to the next lane of this warp / the next thread of the block
-inline void pass_warp() { switch_to((tid & ~31) | ((tid + 1) & 31)); }
-inline void pass_block() { switch_to((tid + 1) % nthreads); }
+// hand control to the next live lane of this warp / the next live thread of
+// the block (threads that have returned take no part, as on the device)
+inline void pass_warp() {
+    int next = (tid & ~31) | ((tid + 1) & 31);
+    while (done[next]) next = (next & ~31) | ((next + 1) & 31);
+    if (next != tid) switch_to(next);
+}
+inline void pass_block() {
+    int next = (tid + 1) % nthreads;
+    while (done[next]) next = (next + 1) % nthreads;
+    if (next != tid) switch_to(next);
+}
 
 inline void thread_main(int t) {
     body(t);

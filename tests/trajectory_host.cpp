@@ -39,7 +39,7 @@ void launch(unsigned blocks, unsigned threads, K &&kernel) {
 }
 }  // namespace
 
-// K iterations from the initial cloud poses [6][N] (N a multiple of 4).
+// K iterations from the initial cloud poses [6][N].
 // Per iteration kk the traces receive the measured cloud tr_poses [K][6][N],
 // moments tr_mom [K][N][12], scores tr_s [K][N], weights tr_W [K][N],
 // indices tr_idx [K][N] and the estimate tr_est [K][6].  Volumes the mode
@@ -117,7 +117,7 @@ extern "C" void dm_trajectory(int mode, int N, int K, uint64_t seed, const float
     const unsigned mgrid = (unsigned)((items + kWarps * ipw_of(ipw) - 1) / (kWarps * ipw_of(ipw)));
     const bool fidx = (size_t)sd[0] * sd[1] * sd[2] <= ((size_t)1 << 23);
     for (int kk = 0; kk < K; ++kk) {
-        launch((unsigned)(N * kGroup / 32), 32, [&] { k_predict(P, B); });
+        launch((unsigned)((N * kGroup + 31) / 32), 32, [&] { k_predict(P, B); });
         launch(mgrid, kThreads, [&] {   // per-warp tables, mask bits from the global array
             if (img && mask)
                 fidx ? k_measure<true, true, false, true, true, false>(A) : k_measure<true, true, false, false, true, false>(A);
