@@ -13,7 +13,9 @@
 #include "../paper_2504_19930_gb300/csrc/kernels.h"
 #include "host_layouts.h"
 
-#define PF_DEBUG 0
+#ifndef PF_DEBUG
+#define PF_DEBUG 0   // -DPF_DEBUG=1: the debug build's gather bounds checks
+#endif
 #define PF_USE_F32X2 0
 namespace pfreg {
 #include "measure_item.inc"
@@ -93,4 +95,14 @@ extern "C" void dm_measure_warp(int img, int mask, int int_index, int xtab, cons
         fidx ? run_tab<true, false, true>(a, xt) : run_tab<true, false, false>(a, xt);
     else
         run_tab<false, true, false>(a, xt);
+}
+
+// Out-of-bounds gather indices the debug build's checks recorded (0 in the
+// release build, which has no checks).
+extern "C" unsigned long long dm_debug_hits() {
+#if PF_DEBUG
+    return pfreg::g_dbg_hits;
+#else
+    return 0;
+#endif
 }

@@ -86,6 +86,9 @@ names; the package never builds or loads any of this.
    iteration after iteration from the initial cloud, as the iteration graph
    runs them, and every iteration equals the oracle registration's trace in
    all four modes, on both sides of the one-block update.
+15. The debug build's bounds checks (every gather index against its buffer
+   before the load) over the measurement's and the warp kernel's runs: no
+   index outside.
 """
 import os
 import platform
@@ -427,7 +430,7 @@ def test_warp_voxels_equal_the_oracle(orc, tmp_path):
 # ------------------------------------ the measurement's per-voxel code on the host
 
 MH_CPP = os.path.join(ROOT, "tests", "measure_host.cpp")
-MV_BEGIN = "constexpr int kWarps = 8;"
+MV_BEGIN = "#if PF_DEBUG\n__device__ unsigned long long g_dbg_hits;"
 
 
 def _build_measure_host(src_text, d):
@@ -593,7 +596,7 @@ MI_END = "// Measurement kernel of one registration."
 MX_BEGIN, MX_END = "constexpr int kTabMaxX = 512;", "// CTAB (with XTAB):"
 
 
-def _build_measure_warp(src_text, d):
+def _build_measure_warp(src_text, d, debug=False):
     import ctypes as C
     for m in (MV_BEGIN, MI_END, MX_BEGIN, MX_END):
         assert src_text.count(m) == 1, m
@@ -601,8 +604,10 @@ def _build_measure_warp(src_text, d):
     (d / "measure_xtab.inc").write_text(src_text[src_text.index(MX_BEGIN):src_text.index(MX_END)])
     so = str(d / "libmw.so")
     subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-frounding-math", "-fPIC", "-shared",
-                    "-I" + SHIM, "-I" + str(d), MW_CPP, "-o", so], check=True)
+                    "-I" + SHIM, "-I" + str(d), *(["-DPF_DEBUG=1"] if debug else []), MW_CPP, "-o", so],
+                   check=True)
     L = C.CDLL(so)
+    L.dm_debug_hits.restype = C.c_ulonglong
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
@@ -687,6 +692,15 @@ def _check_measure_warp(L, orc, seed=31, count=24):
                 assert np.array_equal(got[:, 0:7], want_img), cfg
             if msk:
                 assert np.array_equal(got[:, 8:12], want_msk), cfg
+
+
+def test_measurement_gathers_stay_in_bounds(orc, tmp_path):
+    # the debug build's checks (every source, mask-bit and target index
+    # against its buffer before the load) over every case of the warp-routine
+    # comparison: no index outside, and the moments unchanged
+    L = _build_measure_warp(open(MEASURE_CU).read(), tmp_path, debug=True)
+    _check_measure_warp(L, orc)
+    assert L.dm_debug_hits() == 0
 
 
 def test_measurement_warp_routine_equals_the_oracle(orc, tmp_path):
@@ -1021,6 +1035,16 @@ def test_warp_kernel_equals_the_oracle(orc, tmp_path):
     # emulation: the matrix built in shared memory from six lanes' sin/cos,
     # rows walked by a grid-stride loop, frames sampled four at a time with a
     # remainder; both index widths and interpolations
+    _check_warp_kernel(orc, tmp_path, debug=False)
+
+
+def test_warp_kernel_gathers_stay_in_bounds(orc, tmp_path):
+    # the same runs in the debug build: no gather index outside its frame
+    L = _check_warp_kernel(orc, tmp_path, debug=True)
+    assert L.dm_debug_hits() == 0
+
+
+def _check_warp_kernel(orc, tmp_path, debug):
     import ctypes as C
     import pfsynth
     w = open(WARP_CU).read()
@@ -1030,8 +1054,10 @@ def test_warp_kernel_equals_the_oracle(orc, tmp_path):
     (tmp_path / "k_warp.inc").write_text(w[i:w.index("}  // namespace", i)])
     so = str(tmp_path / "libwk.so")
     subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
-                    "-I" + str(tmp_path), os.path.join(ROOT, "tests", "warp_kernel_host.cpp"), "-o", so], check=True)
+                    "-I" + str(tmp_path), *(["-DPF_DEBUG=1"] if debug else []),
+                    os.path.join(ROOT, "tests", "warp_kernel_host.cpp"), "-o", so], check=True)
     L = C.CDLL(so)
+    L.dm_debug_hits.restype = C.c_ulonglong
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
@@ -1055,6 +1081,7 @@ def test_warp_kernel_equals_the_oracle(orc, tmp_path):
                 for f in range(n_frames):
                     want = orc.warp(frames[f], so, td, to, pose, interp, ss, ts)
                     assert np.array_equal(out[f], want), (i, f, interp, wide)
+    return L
 
 
 # --------------------------------- one batch iteration under the block emulation

@@ -13,7 +13,9 @@
 dim3 threadIdx, blockIdx, blockDim, gridDim;
 #define threadIdx (dim3{(unsigned)host_warp::tid, 1u, 1u})
 
-#define PF_DEBUG 0
+#ifndef PF_DEBUG
+#define PF_DEBUG 0   // -DPF_DEBUG=1: the debug build's gather bounds checks
+#endif
 namespace pfreg {
 #include "k_warp.inc"
 }
@@ -53,4 +55,13 @@ extern "C" void dm_k_warp(const uint8_t *frames, int n_frames, const int32_t sd[
                 k_warp<false>(a);
         });
     }
+}
+
+// Out-of-bounds gather indices the debug build's checks recorded.
+extern "C" unsigned long long dm_debug_hits() {
+#if PF_DEBUG
+    return pfreg::g_wdbg_hits;
+#else
+    return 0;
+#endif
 }
