@@ -13,6 +13,14 @@
 #include <cstdint>
 #include <cstring>
 
+// -DPF_HOST_COUNT_FP32: count the fp32 lane operations executed (each
+// __fadd_rn / __fsub_rn / __fmul_rn / __fmaf_rn / __fadd_rd is one)
+#ifdef PF_HOST_COUNT_FP32
+inline unsigned long long g_host_fp32_ops = 0;
+#define PF_COUNT_FP32 (++g_host_fp32_ops)
+#else
+#define PF_COUNT_FP32 ((void)0)
+#endif
 #define __device__
 #define __global__
 #define __launch_bounds__(...)
@@ -41,10 +49,10 @@ inline double __longlong_as_double(long long a) {
 inline float __double2float_rn(double a) { return (float)a; }
 inline double __ull2double_rn(unsigned long long v) { return (double)v; }
 inline unsigned long long __double2ull_rz(double a) { return (unsigned long long)a; }   // a >= 0 here
-inline float __fmul_rn(float a, float b) { return a * b; }
-inline float __fadd_rn(float a, float b) { return a + b; }
-inline float __fsub_rn(float a, float b) { return a - b; }
-inline float __fmaf_rn(float a, float b, float c) { return std::fmaf(a, b, c); }
+inline float __fmul_rn(float a, float b) { return PF_COUNT_FP32, a * b; }
+inline float __fadd_rn(float a, float b) { return PF_COUNT_FP32, a + b; }
+inline float __fsub_rn(float a, float b) { return PF_COUNT_FP32, a - b; }
+inline float __fmaf_rn(float a, float b, float c) { return PF_COUNT_FP32, std::fmaf(a, b, c); }
 inline float __int2float_rn(int x) { return (float)x; }
 inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
 inline float __uint_as_float(uint32_t u) {
@@ -62,6 +70,7 @@ template <class T>
 inline T __ldg(const T *p) { return *p; }
 // a + b rounded toward -infinity (build with -frounding-math)
 inline float __fadd_rd(float a, float b) {
+    PF_COUNT_FP32;
     std::fesetround(FE_DOWNWARD);
     volatile float x = a, y = b;
     volatile float r = x + y;

@@ -106,3 +106,18 @@ extern "C" unsigned long long dm_debug_hits() {
     return 0;
 #endif
 }
+
+// fp32 lane operations executed so far (with -DPF_HOST_COUNT_FP32), reset by
+// dm_fp32_ops_reset.
+extern "C" unsigned long long dm_fp32_ops() {
+#ifdef PF_HOST_COUNT_FP32
+    return g_host_fp32_ops;
+#else
+    return 0;
+#endif
+}
+extern "C" void dm_fp32_ops_reset() {
+#ifdef PF_HOST_COUNT_FP32
+    g_host_fp32_ops = 0;
+#endif
+}

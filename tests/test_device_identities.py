@@ -596,7 +596,7 @@ MI_END = "// Measurement kernel of one registration."
 MX_BEGIN, MX_END = "constexpr int kTabMaxX = 512;", "// CTAB (with XTAB):"
 
 
-def _build_measure_warp(src_text, d, debug=False):
+def _build_measure_warp(src_text, d, debug=False, extra=()):
     import ctypes as C
     for m in (MV_BEGIN, MI_END, MX_BEGIN, MX_END):
         assert src_text.count(m) == 1, m
@@ -604,10 +604,11 @@ def _build_measure_warp(src_text, d, debug=False):
     (d / "measure_xtab.inc").write_text(src_text[src_text.index(MX_BEGIN):src_text.index(MX_END)])
     so = str(d / "libmw.so")
     subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-frounding-math", "-fPIC", "-shared",
-                    "-I" + SHIM, "-I" + str(d), *(["-DPF_DEBUG=1"] if debug else []), MW_CPP, "-o", so],
+                    "-I" + SHIM, "-I" + str(d), *(["-DPF_DEBUG=1"] if debug else []), *extra, MW_CPP, "-o", so],
                    check=True)
     L = C.CDLL(so)
     L.dm_debug_hits.restype = C.c_ulonglong
+    L.dm_fp32_ops.restype = C.c_ulonglong
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
@@ -1261,3 +1262,35 @@ def test_kernel_trajectories_equal_the_oracle(orc, tmp_path):
             assert np.array_equal(tr["W"][kk], ref["tr_W"][kk]), cfg
             assert np.array_equal(tr["i"][kk], ref["tr_idx"][kk]), cfg
             np.testing.assert_allclose(tr["e"][kk], ref["tr_est"][kk], rtol=1e-12, atol=1e-12, err_msg=str(cfg))
+
+
+def test_measurement_fp32_work_per_evaluation(orc, tmp_path):
+    # the fp32 lane operations the measurement code executes per visited
+    # evaluation (row set-up included), counted on its host build, against
+    # the 27 / 12 / 33 of the arithmetic definition the roofline uses: the
+    # image code's floors by rounding, unbiasing subtracts and fp32 quad
+    # index cost about ten more; the mask code's table and rounding floors
+    # bring it to the definition's count
+    import pfsynth
+    L = _build_measure_warp(open(MEASURE_CU).read(), tmp_path, extra=("-DPF_HOST_COUNT_FP32",))
+    rng = np.random.default_rng(42)
+    sd = td = (112, 40, 30)
+    src, tgt = pfsynth.random_image(1, sd), pfsynth.random_image(2, td)
+    smask = (rng.random(src.shape) < 0.5).astype(np.uint8)
+    tmask = (rng.random(tgt.shape) < 0.5).astype(np.uint8)
+    poses = np.array([[0.1, -0.05], [0.05, 0.1], [-0.1, 0.02], [2, -3], [1, 2], [-2, 1]], np.float32)
+    mats, a = orc.pose_matrices(poses, sd, np.zeros(3, np.float32), np.array([4, 0, 0], np.float32))
+    mats = np.ascontiguousarray(mats, np.float32)
+    per_eval = {}
+    for name, img, msk in (("image", 1, 0), ("mask", 0, 1), ("combined", 1, 1)):
+        L.dm_fp32_ops_reset()
+        got = np.zeros((2, 12), np.uint64)
+        L.dm_measure_warp(img, msk, 0, 1, _ptr(src) if img else None, _ptr(smask) if msk else None,
+                          np.array(sd, np.int32), _ptr(tgt) if img else None, _ptr(tmask) if msk else None,
+                          np.array(td, np.int32), mats, 2, a, got)
+        evals = int(got[:, 0].sum() if img else got[:, 8].sum())
+        per_eval[name] = L.dm_fp32_ops() / evals
+    assert 35 < per_eval["image"] < 40, per_eval
+    assert 11 < per_eval["mask"] < 13.5, per_eval
+    assert 42 < per_eval["combined"] < 48, per_eval
+
