@@ -45,7 +45,10 @@ names; the package never builds or loads any of this.
 7. Kernels with no shared memory, barrier or shuffle -- the initial clouds
    (k_init, k_seed_gaussian) and the quad packing (k_pack_quads) -- run as a
    host loop over their threads equal the oracle's initial clouds and the
-   quad layout written out in numpy.
+   quad layout written out in numpy.  The set-up kernels (mask bits, the
+   binarised mask, the voxel count), the pose -> matrix and single-score
+   exports and the estimate's traced Dice, under the block emulation, equal
+   their numpy definitions and the oracle.
 8. The measurement kernel's whole warp routine (measure_item: the row
    set-up, the sweep of 32 rows' intervals in 64-voxel passes with the
    row-crossing passes, the per-voxel code, the warp reduction and the
@@ -587,6 +590,85 @@ def test_initial_clouds_and_quad_packing_equal_their_definitions(orc, tmp_path):
         P[:, :-1, :-1] = S
         want = P[:, :-1, :-1] | P[:, :-1, 1:] << 8 | P[:, 1:, :-1] << 16 | P[:, 1:, 1:] << 24
         assert np.array_equal(Q.reshape(S.shape), want), dims
+
+
+SK_CPP = os.path.join(ROOT, "tests", "small_kernels_host.cpp")
+SK_BEGIN, SK_END = "// Matrix of one pose by a group of 8 lanes", "__global__ void k_philox("
+
+
+def test_set_up_export_and_trace_kernels_equal_their_definitions(orc, tmp_path):
+    # The registration's remaining kernels (copied verbatim out of filter.cu,
+    # run under the block emulation): the set-up kernels against their plain
+    # definitions in numpy, the pose -> matrix and single-score exports and
+    # the estimate's traced Dice against the oracle
+    import ctypes as C
+    f = open(FILTER_CU).read()
+    assert f.count(SK_BEGIN) == 1 and f.count(SK_END) == 1
+    (tmp_path / "small_kernels.inc").write_text(f[f.index(SK_BEGIN):f.index(SK_END)])
+    so = str(tmp_path / "libsk.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(tmp_path), SK_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+    u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+    u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+    L.dm_pack_bits.argtypes = [u8p, C.c_int64, u32p]
+    L.dm_binarise.argtypes = [u8p, u8p, C.c_int64]
+    L.dm_count_nonzero.restype = C.c_ulonglong
+    L.dm_count_nonzero.argtypes = [u8p, C.c_int64]
+    L.dm_pose_matrix_kernel.argtypes = [f32p, i32p, f32p, f32p, f32p, f32p]
+    L.dm_score_one.restype = C.c_double
+    L.dm_score_one.argtypes = [C.c_int, u64p, C.c_uint64, C.c_uint64]
+    L.dm_trace.argtypes = [f64p, i32p, f32p, f32p, f32p, C.c_uint64, f32p, u64p, f64p]
+    rng = np.random.default_rng(40)
+    # grid-stride loops over 3 x 64 threads and the last word's tail
+    for n in (0, 1, 31, 32, 33, 191, 192, 193, 4097, 20000):
+        v = (rng.integers(0, 256, n) * (rng.random(n) < 0.4)).astype(np.uint8)
+        v = np.ascontiguousarray(v) if n else np.zeros(1, np.uint8)
+        out = np.full(max(n, 1), 7, np.uint8)
+        L.dm_binarise(v, out, n)
+        assert np.array_equal(out[:n], (v[:n] != 0).astype(np.uint8)) and (n or out[0] == 7), n
+        assert L.dm_count_nonzero(v, n) == int(np.count_nonzero(v[:n])), n
+        words = (n + 31) // 32
+        bits = np.full(max(words, 1), 0xDEADBEEF, np.uint32)
+        L.dm_pack_bits(v, n, bits)
+        padded = np.zeros(words * 32, bool)
+        padded[:n] = v[:n] != 0
+        want = (padded.reshape(-1, 32).astype(np.uint64) << np.arange(32, dtype=np.uint64)).sum(1)
+        assert np.array_equal(bits[:words], want.astype(np.uint32)), n
+    for i in range(300):
+        pose = np.concatenate([rng.uniform(-1.57, 1.57, 3), rng.uniform(-60, 60, 3)]).astype(np.float32)
+        sd = rng.integers(2, 400, 3).astype(np.int32)
+        so, to = rng.uniform(-50, 50, 3).astype(np.float32), rng.uniform(-50, 50, 3).astype(np.float32)
+        M = np.zeros(12, np.float32)
+        L.dm_pose_matrix_kernel(pose, sd, so, to, np.zeros(3, np.float32), M)
+        assert np.array_equal(M, orc.pose_matrix(pose, sd, so, to)[0]), i
+    for i in range(2000):
+        mom, b_full = _random_moments(rng)
+        n_min = int(rng.choice([0, int(mom[0]), int(mom[8]) + 1]))
+        for mode in range(4):
+            got, want = L.dm_score_one(mode, mom, b_full, n_min), orc.score(mode, mom, b_full, n_min)
+            assert got == want or (np.isnan(got) and np.isnan(want)), (i, mode)
+    # the trace: the estimate rounded to fp32, its matrix, the whole-grid
+    # counts of that matrix and their Dice with no overlap threshold
+    for i in range(40):
+        sd = rng.integers(4, 24, 3).astype(np.int32)
+        td = rng.integers(4, 24, 3).astype(np.int32)
+        so, to = rng.uniform(-5, 5, 3).astype(np.float32), rng.uniform(-5, 5, 3).astype(np.float32)
+        est = np.concatenate([rng.uniform(-0.6, 0.6, 3), rng.uniform(-6, 6, 3)])
+        smask = (rng.random(sd[::-1]) < 0.5).astype(np.uint8)
+        tmask = (rng.random(td[::-1]) < 0.5).astype(np.uint8) * (i % 7 != 0)
+        want_M, a = orc.pose_matrix(est.astype(np.float32), sd, so, to)
+        counts = np.ascontiguousarray(orc.measure_mask(smask, tmask, want_M, a)[0])
+        b_full = int(np.count_nonzero(tmask))
+        M, dice = np.zeros(12, np.float32), np.zeros(1)
+        L.dm_trace(est, sd, so, to, a, b_full, M, counts, dice)
+        assert np.array_equal(M, want_M), i
+        assert dice[0] == orc.dice_from_counts(counts[0], counts[1], counts[3], b_full, 0), i
+        assert dice[0] == orc.score("mask_dice", np.r_[np.zeros(8, np.uint64), counts], b_full, 0), i
 
 
 # ------------------- the measurement's warp routine under a lockstep warp emulation
