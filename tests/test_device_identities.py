@@ -92,6 +92,12 @@ names; the package never builds or loads any of this.
 15. The debug build's bounds checks (every gather index against its buffer
    before the load) over the measurement's and the warp kernel's runs: no
    index outside.
+16. The proposal network's CUDA-core kernels (weight transpose, fully
+   connected layers and their gradients, bias gradient, Gaussian loss, Adam,
+   bf16 copies, uniform initialisation, the input's box average), under the
+   block emulation, equal the oracle's fp64 definitions within the fp32
+   accumulation bound (bit for bit where the result is a copy or a rounding);
+   six planted mistakes are each caught.
 """
 import os
 import platform
@@ -669,6 +675,195 @@ def test_set_up_export_and_trace_kernels_equal_their_definitions(orc, tmp_path):
         assert np.array_equal(M, want_M), i
         assert dice[0] == orc.dice_from_counts(counts[0], counts[1], counts[3], b_full, 0), i
         assert dice[0] == orc.score("mask_dice", np.r_[np.zeros(8, np.uint64), counts], b_full, 0), i
+
+
+NN_CU = os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "nn.cu")
+NS_CPP = os.path.join(ROOT, "tests", "nn_small_host.cpp")
+NS_BEGIN, NS_END = "// W [32][64][Cin] -> Wt", "// Synthetic training pairs:"
+U32 = 2.0 ** -24   # unit roundoff of fp32
+
+
+def _build_nn_small(src_text, d):
+    import ctypes as C
+    assert src_text.count(NS_BEGIN) == 1 and src_text.count(NS_END) == 1
+    (d / "nn_small.inc").write_text(src_text[src_text.index(NS_BEGIN):src_text.index(NS_END)])
+    so = str(d / "libnns.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(d), NS_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+    u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    vp = C.c_void_p
+    L.dm_transpose_w.argtypes = [u16p, C.c_int, u16p]
+    L.dm_fc_forward.argtypes = [C.c_int, vp, vp, C.c_int, C.c_int, f32p, f32p, C.c_int, f32p, C.c_int]
+    L.dm_fc_backward_input.argtypes = [C.c_int, f32p, C.c_int, C.c_int, f32p, C.c_int, vp, vp, vp, vp]
+    L.dm_fc_backward_weight.argtypes = [C.c_int, f32p, C.c_int, C.c_int, vp, vp, C.c_int, f32p, f32p]
+    L.dm_bias_grad.argtypes = [u16p, C.c_longlong, C.c_int, f32p]
+    L.dm_nll.argtypes = [f32p, f32p, C.c_int, f32p, f32p, C.c_int]
+    L.dm_adam.argtypes = [f32p, f32p, f32p, f32p, C.c_longlong, C.c_float, C.c_int]
+    L.dm_to_bf16.argtypes = [f32p, C.c_longlong, u16p]
+    L.dm_init_uniform.argtypes = [f32p, C.c_longlong, C.c_float, C.c_uint64, C.c_uint32]
+    L.dm_downsample.argtypes = [u8p, i32p, f32p, f32p, f32p, f32p, C.c_int, C.c_int, u16p]
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _check_nn_small(L, orc, seed=41):
+    """Each CUDA-core kernel of the proposal network against the oracle's
+    fp64 definition (oracle/nn.py), within the fp32 accumulation bound
+    (terms - 1) u sum|terms| plus, for bf16 results, the final rounding."""
+    import oracle.nn as onn
+    rng = np.random.default_rng(seed)
+    bf = lambda a: onn.bf16_bits(onn.bf16_round(np.asarray(a, np.float32)))   # noqa: E731
+    unbf = lambda b: onn.from_bf16_bits(b).astype(np.float64)                  # noqa: E731
+
+    def close_bf16(got_bits, ref, bound, what):
+        err = np.abs(unbf(got_bits) - ref)
+        tol = 2.0 ** -8 * (np.abs(ref) + bound) + bound + 1e-30
+        assert np.all(err <= tol), (what, float(err.max()))
+
+    # weight transpose [32][64][Cin] -> [Cin][64][32], bit for bit
+    for cin in (2, 32):
+        W = rng.integers(0, 1 << 16, 32 * 64 * cin).astype(np.uint16)
+        Wt = np.zeros_like(W)
+        L.dm_transpose_w(W, cin, Wt)
+        assert np.array_equal(Wt.reshape(cin, 64, 32), W.reshape(32, 64, cin).transpose(2, 1, 0)), cin
+    # fully connected layers as the network uses them: fc1 on the bf16
+    # flattened features (K = 2048, ReLU), fc2 on the fp32 hidden layer
+    for in_bf16, B, K, N, relu in ((1, 3, onn.FLAT, onn.HIDDEN, 1), (0, 3, onn.HIDDEN, onn.NOUT, 0),
+                                   (0, 2, 45, 7, 1)):
+        x = rng.normal(0, 1, (B, K)).astype(np.float32)
+        x16 = bf(x)
+        xv = unbf(x16) if in_bf16 else x.astype(np.float64)
+        W = rng.normal(0, 0.05, (N, K)).astype(np.float32)
+        b = rng.normal(0, 0.1, N).astype(np.float32)
+        out = np.zeros((B, N), np.float32)
+        L.dm_fc_forward(in_bf16, _p(x), _p(x16), B, K, W, b, N, out, relu)
+        pre = xv @ W.T.astype(np.float64) + b
+        ref = onn.relu(pre) if relu else pre
+        bound = (K + 1) * U32 * (np.abs(xv) @ np.abs(W.T).astype(np.float64) + np.abs(b))
+        assert np.all(np.abs(out - ref) <= bound + 1e-30), ("fc forward", K)
+        # data gradient through the ReLU of the layer's input activation
+        dout = rng.normal(0, 1, (B, N)).astype(np.float32)
+        act = rng.normal(0, 1, (B, K)).astype(np.float32)
+        act[0, :5] = 0.0
+        refd = (dout.astype(np.float64) @ W.astype(np.float64)) * (act > 0)
+        boundd = N * U32 * (np.abs(dout).astype(np.float64) @ np.abs(W).astype(np.float64)) * (act > 0)
+        if in_bf16:
+            din = np.zeros((B, K), np.uint16)
+            L.dm_fc_backward_input(1, dout, B, N, W, K, None, _p(bf(act)), None, _p(din))
+            refd = (dout.astype(np.float64) @ W.astype(np.float64)) * (unbf(bf(act)) > 0)
+            close_bf16(din, refd, boundd, "fc backward input bf16")
+        else:
+            din = np.zeros((B, K), np.float32)
+            L.dm_fc_backward_input(0, dout, B, N, W, K, _p(act), None, _p(din), None)
+            assert np.all(np.abs(din - refd) <= boundd + 1e-30), "fc backward input"
+        # weight and bias gradients accumulate into what is there
+        dW0 = rng.normal(0, 1, (N, K)).astype(np.float32)
+        db0 = rng.normal(0, 1, N).astype(np.float32)
+        dW, db = dW0.copy(), db0.copy()
+        L.dm_fc_backward_weight(in_bf16, dout, B, N, _p(x), _p(x16), K, dW, db)
+        refw = dW0 + dout.T.astype(np.float64) @ xv
+        boundw = (B + 1) * U32 * (np.abs(dout.T).astype(np.float64) @ np.abs(xv) + np.abs(dW0))
+        assert np.all(np.abs(dW - refw) <= boundw + 1e-30), "fc backward weight"
+        refb = db0 + dout.astype(np.float64).sum(0)
+        boundb = (B + 1) * U32 * (np.abs(dout).astype(np.float64).sum(0) + np.abs(db0))
+        assert np.all(np.abs(db - refb) <= boundb + 1e-30), "fc bias"
+    # conv bias gradient: 32 channel sums over bf16 rows (grid-stride rows)
+    for rows, blocks in ((1, 1), (37, 2), (5000, 3)):
+        dY = bf(rng.normal(0, 1, (rows, 32)))
+        db0 = rng.normal(0, 1, 32).astype(np.float32)
+        db = db0.copy()
+        L.dm_bias_grad(dY, rows, blocks, db)
+        ref = db0 + unbf(dY).sum(0)
+        bound = (rows + 10) * U32 * (np.abs(unbf(dY)).sum(0) + np.abs(db0))
+        assert np.all(np.abs(db - ref) <= bound), ("bias grad", rows)
+    # Gaussian negative log-likelihood and its gradient; the loss goes into
+    # the log entry of the step
+    for B in (1, 5, 32):
+        out = np.concatenate([rng.normal(0, 1, (B, 6)), rng.normal(0, 1.5, (B, 6))], 1).astype(np.float32)
+        y = rng.uniform(-1, 1, (B, 6)).astype(np.float32)
+        dout = np.zeros((B, 12), np.float32)
+        loss_log = np.full(4, 0.25, np.float32)
+        L.dm_nll(out, y, B, dout, loss_log, 2)
+        want, g = onn.gaussian_nll(out, y)
+        o64 = out.astype(np.float64)
+        terms = 0.5 * ((y - o64[:, :6]) ** 2 * np.exp(-o64[:, 6:]) + np.abs(o64[:, 6:])) / B
+        assert abs(loss_log[2] - 0.25 - want) <= (6 * B + 40) * U32 * (terms.sum() + 0.25), B
+        assert loss_log[[0, 1, 3]].tolist() == [0.25] * 3
+        assert np.all(np.abs(dout - g) <= 16 * U32 * (np.abs(g) + 0.5 / B * (1 + terms.max() * B))), B
+    # Adam with the step count t = step + 1, then the step counter's increment
+    for step in (0, 7):
+        n = 1000
+        th, m, v = (rng.normal(0, 1, n).astype(np.float32) for _ in range(3))
+        v = np.abs(v)
+        gr = rng.normal(0, 1, n).astype(np.float32)
+        th1, m1, v1 = th.copy(), m.copy(), v.copy()
+        L.dm_adam(th1, m1, v1, gr, n, 1e-3, step)
+        tw, mw, vw = onn.adam(th.astype(np.float64), m.astype(np.float64), v.astype(np.float64),
+                              gr.astype(np.float64), step + 1, np.float64(np.float32(1e-3)))
+        assert np.all(np.abs(m1 - mw) <= 8 * U32 * (np.abs(m) + np.abs(gr)))
+        assert np.all(np.abs(v1 - vw) <= 8 * U32 * (v + gr * gr))
+        assert np.all(np.abs(th1 - tw) <= 4 * U32 * np.abs(th) + 1e-3 * 1e-4)
+    # bf16 copies, bit for bit
+    a = np.concatenate([rng.normal(0, 1, 3000), [0.0, -0.0, 1.0 + 2.0**-8, 1.0 + 3 * 2.0**-8, 3e-39]]).astype(np.float32)
+    b16 = np.zeros(a.size, np.uint16)
+    L.dm_to_bf16(a, a.size, b16)
+    assert np.array_equal(b16, bf(a))
+    # uniform initialisation: U(-a, a) from the top 24 bits of Philox(seed)
+    # with the counter (i, tensor, 0x6E6E0000, 0), in fp32
+    p = np.zeros(300, np.float32)
+    L.dm_init_uniform(p, p.size, 0.125, 2**33 + 5, 3)
+    key = np.array([5, 2], np.uint32)
+    for i in (0, 1, 150, 299):
+        r = orc.philox(np.array([i, 3, 0x6E6E0000, 0], np.uint32), key)
+        u = np.float32(r[0] >> 8) * np.float32(2.0**-24)
+        assert p[i] == np.float32(0.125) * (np.float32(2.0) * u - np.float32(1.0)), i
+    assert np.all(np.abs(p) < 0.125) and len(np.unique(p)) == p.size
+    # the network input: box average of each cell / 64, rounded to bf16, in
+    # channel c of [G^3][2]
+    for dims, orig, sp, box, G in (((9, 7, 5), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), 4),
+                                   ((13, 11, 9), (1.5, -2.0, 0.25), (0.8, 1.1, 1.3), (-1.0, -3.0, 0.0), 6),
+                                   ((30, 20, 10), (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (-8.0, 4.0, -2.0), 8)):
+        vol = rng.integers(0, 256, dims[::-1]).astype(np.uint8)
+        h = np.array(dims, np.float32) * np.array(sp, np.float32) / np.float32(G)
+        for c in (0, 1):
+            x = np.full(G**3 * 2, 0x7777, np.uint16)
+            L.dm_downsample(vol, np.array(dims, np.int32), np.array(orig, np.float32), np.array(sp, np.float32),
+                            np.array(box, np.float32), h, G, c, x)
+            want = onn.box_average(vol, np.array(orig), np.array(sp), np.array(box), h.astype(np.float64), G)
+            got = unbf(x.reshape(-1, 2)[:, c]).reshape(G, G, G)
+            assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 4 * U32 * np.abs(want)), dims
+            assert np.all(x.reshape(-1, 2)[:, 1 - c] == 0x7777)
+
+
+def test_network_cuda_core_kernels_equal_the_oracle(orc, tmp_path):
+    _check_nn_small(_build_nn_small(open(NN_CU).read(), tmp_path), orc)
+
+
+NS_MUTANTS = [
+    ("bias of the batch row", "acc += bias[n];", "acc += bias[b];"),
+    ("ReLU mask keeps zeros", "if (!(to_f(act[i]) > 0.0f)) acc = 0.0f;", "if (!(to_f(act[i]) >= 0.0f)) acc = 0.0f;"),
+    ("bias gradient overwritten", "if (k == 0) db[n] += accb;", "if (k == 0) db[n] = accb;"),
+    ("log-variance gradient sign", "0.5f * (1.0f - r * r * e) / (float)B;", "0.5f * (1.0f + r * r * e) / (float)B;"),
+    ("second moment with beta1", "vi = b2 * v[i] + (1.0f - b2) * gi * gi;",
+     "vi = b2 * v[i] + (1.0f - b1) * gi * gi;"),
+    ("cell end rounded down", "hi[d] = min(a.dims[d], (int)ceilf(", "hi[d] = min(a.dims[d], (int)floorf("),
+]
+
+
+def test_network_kernel_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(NN_CU).read()
+    for text in (m[1] for m in NS_MUTANTS):
+        assert src.count(text) == 1, text
+    for L in _build_all(_build_nn_small, src, NS_MUTANTS, tmp_path):
+        with pytest.raises(AssertionError):
+            _check_nn_small(L, orc)
 
 
 # ------------------- the measurement's warp routine under a lockstep warp emulation
