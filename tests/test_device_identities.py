@@ -88,7 +88,8 @@ names; the package never builds or loads any of this.
 14. Whole trajectories: k_predict, k_measure and the update kernels run
    iteration after iteration from the initial cloud, as the iteration graph
    runs them, and every iteration equals the oracle registration's trace in
-   all four modes, on both sides of the one-block update.
+   all four modes, on both sides of the one-block update, with unit and
+   anisotropic voxel spacings.
 15. The debug build's bounds checks (every gather index against its buffer
    before the load) over the measurement's and the warp kernel's runs: no
    index outside.
@@ -1481,8 +1482,9 @@ def test_kernel_trajectories_equal_the_oracle(orc, tmp_path):
     # cloud, moments, scores, weights and indices equal the oracle
     # registration's trace, its estimate within summation rounding, in all
     # four modes, on both sides of the one-block update (the larger cloud
-    # for one iteration on a small grid: the emulation is slow) and for
-    # clouds that fill no whole warp (1 and 5 particles)
+    # for one iteration on a small grid: the emulation is slow), for
+    # clouds that fill no whole warp (1 and 5 particles) and with
+    # anisotropic voxel spacings in both volumes
     import ctypes as C
     import pfsynth
     f, m = open(FILTER_CU).read(), open(MEASURE_CU).read()
@@ -1498,11 +1500,14 @@ def test_kernel_trajectories_equal_the_oracle(orc, tmp_path):
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
     L.dm_trajectory.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, f32p, C.c_float, C.c_float, C.c_int,
-                                C.c_float, P, P, i32p, f32p, P, P, i32p, f32p, f32p, C.c_int, f32p,
+                                C.c_float, P, P, i32p, f32p, P, P, i32p, f32p, f32p, P, P, C.c_int, f32p,
                                 P, P, P, P, P, P]
-    cases = [("mask_dice", 64, 3, 2), ("mask_ncc", 61, 3, 1), ("image_ncc", 48, 3, 4), ("combined", 40, 3, 8),
-             ("mask_dice", 1, 3, 1), ("image_ncc", 5, 2, 2), ("mask_dice", 1025, 1, 32)]
-    for i, (mode, N, K, ipw) in enumerate(cases):
+    aniso = ((0.8, 1.1, 1.3), (1.2, 0.9, 0.7))   # source / target voxel spacings
+    cases = [("mask_dice", 64, 3, 2, None), ("mask_ncc", 61, 3, 1, None), ("image_ncc", 48, 3, 4, None),
+             ("combined", 40, 3, 8, None), ("mask_dice", 1, 3, 1, None), ("image_ncc", 5, 2, 2, None),
+             ("mask_dice", 1025, 1, 32, None), ("image_ncc", 33, 2, 2, aniso), ("combined", 20, 2, 1, aniso)]
+    for i, (mode, N, K, ipw, spacing) in enumerate(cases):
+        ss, ts = (None, None) if spacing is None else (np.array(v, np.float32) for v in spacing)
         if mode in ("mask_dice", "mask_ncc"):
             small = N > 1024             # the three-kernel update: a small grid keeps the emulation quick
             pair = pfsynth.ellipsoid_pair(20 + i, src_dims=(12, 11, 10) if small else (18, 16, 14),
@@ -1517,12 +1522,13 @@ def test_kernel_trajectories_equal_the_oracle(orc, tmp_path):
                            seed=seed, src=pair.src if mode in ("image_ncc", "combined") else None,
                            tgt=pair.tgt if mode in ("image_ncc", "combined") else None,
                            src_mask=pair.src_mask if mode != "image_ncc" else None,
-                           tgt_mask=pair.tgt_mask if mode != "image_ncc" else None)
+                           tgt_mask=pair.tgt_mask if mode != "image_ncc" else None,
+                           src_spacing=ss, tgt_spacing=ts)
         lim = np.array([lr] * 3 + [lt] * 3, np.float32)
         sd, td = np.array(pair.src_dims, np.int32), np.array(pair.tgt_dims, np.int32)
         so = np.asarray(pair.src_origin, np.float32)
         to = np.asarray(pair.tgt_origin, np.float32)
-        _, a = orc.pose_matrix(np.zeros(6, np.float32), sd, so, to)
+        _, a = orc.pose_matrix(np.zeros(6, np.float32), sd, so, to, ss, ts)
         poses = orc.init_particles(N, seed, lim)
         tr = dict(p=np.zeros((K, 6, N), np.float32), m=np.zeros((K, N, 12), np.uint64), s=np.zeros((K, N)),
                   W=np.zeros((K, N), np.uint64), i=np.zeros((K, N), np.int32), e=np.zeros((K, 6)))
@@ -1530,9 +1536,9 @@ def test_kernel_trajectories_equal_the_oracle(orc, tmp_path):
         vol = lambda v, use: (np.ascontiguousarray(v).ctypes.data if use else None)   # noqa: E731
         L.dm_trajectory(orc.MODES[mode], N, K, seed, lim, 0.25, 0.8, 5, 0.01, vol(pair.src, img),
                         vol(pair.src_mask, msk), sd, so, vol(pair.tgt, img), vol(pair.tgt_mask, msk), td, to, a,
-                        ipw, poses, *(tr[k].ctypes.data for k in ("p", "m", "s", "W", "i", "e")))
+                        _p(ss), _p(ts), ipw, poses, *(tr[k].ctypes.data for k in ("p", "m", "s", "W", "i", "e")))
         for kk in range(K):
-            cfg = (mode, N, kk)
+            cfg = (mode, N, kk, spacing)
             assert np.array_equal(tr["p"][kk], ref["tr_poses"][kk]), cfg
             assert np.array_equal(tr["m"][kk], ref["tr_mom"][kk]), cfg
             assert np.array_equal(tr["s"][kk], ref["tr_score"][kk]), cfg

@@ -43,12 +43,13 @@ void launch(unsigned blocks, unsigned threads, K &&kernel) {
 // Per iteration kk the traces receive the measured cloud tr_poses [K][6][N],
 // moments tr_mom [K][N][12], scores tr_s [K][N], weights tr_W [K][N],
 // indices tr_idx [K][N] and the estimate tr_est [K][6].  Volumes the mode
-// does not use are NULL.  ipw: work items per warp of the measurement.
+// does not use are NULL, and so are unit voxel spacings ss / ts.  ipw: work
+// items per warp of the measurement.
 extern "C" void dm_trajectory(int mode, int N, int K, uint64_t seed, const float lim[6], float sigma0_frac,
                               float decay, int gamma_log2, float min_overlap_frac, const uint8_t *src,
                               const uint8_t *src_mask, const int32_t sd[3], const float so[3], const uint8_t *tgt,
                               const uint8_t *tgt_mask, const int32_t td[3], const float to[3], const float a_off[3],
-                              int ipw, float *poses, float *tr_poses, uint64_t *tr_mom, double *tr_s,
+                              const float *ss, const float *ts, int ipw, float *poses, float *tr_poses, uint64_t *tr_mom, double *tr_s,
                               uint64_t *tr_W, int32_t *tr_idx, double *tr_est) {
     const bool img = mode == 2 || mode == 3, mask = mode != 2;
     std::vector<uint32_t> quad, bits;
@@ -76,8 +77,8 @@ extern "C" void dm_trajectory(int mode, int N, int K, uint64_t seed, const float
         P.g.td[d] = td[d];
         P.g.so[d] = so[d];
         P.g.to[d] = to[d];
-        P.g.ss[d] = 1.0f;
-        P.g.ts[d] = 1.0f;
+        P.g.ss[d] = ss ? ss[d] : 1.0f;
+        P.g.ts[d] = ts ? ts[d] : 1.0f;
         P.g.a[d] = a_off[d];
     }
     std::vector<float> pm(6 * (size_t)N), mats(12 * (size_t)N);
