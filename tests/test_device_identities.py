@@ -1421,7 +1421,10 @@ def test_batch_iteration_equals_the_oracle(orc, tmp_path):
             smask = (rng.random((sd[2], sd[1], sd[0])) < 0.5).astype(np.uint8)
             tmask = (rng.random((td[2], td[1], td[0])) < 0.5).astype(np.uint8)
             so, to = rng.uniform(-4, 4, 3).astype(np.float32), rng.uniform(-4, 4, 3).astype(np.float32)
-            ss = ts = np.ones(3, np.float32)
+            if r % 2:   # anisotropic voxels in odd members
+                ss, ts = (rng.uniform(0.7, 1.4, 3).astype(np.float32) for _ in range(2))
+            else:
+                ss = ts = np.ones(3, np.float32)
             lim = np.array([0.6, 0.5, 0.4, 6, 5, 4], np.float32)
             seed_i, g = int(rng.integers(0, 2**63)), 5
             img, msk = mode in (2, 3), mode != 2
