@@ -99,6 +99,11 @@ names; the package never builds or loads any of this.
    block emulation, equal the oracle's fp64 definitions within the fp32
    accumulation bound (bit for bit where the result is a copy or a rounding);
    six planted mistakes are each caught.
+17. The learned proposal's training labels (k_synth_params, run on the
+   host) are poses in the filter's convention: each synthetic pair's map
+   from target voxel to source point equals the oracle's pose -> matrix of
+   its label; four planted mistakes (rotation order, axis, centre, sign)
+   are each caught.
 """
 import os
 import platform
@@ -865,6 +870,84 @@ def test_network_kernel_comparison_catches_planted_mistakes(orc, tmp_path):
     for L in _build_all(_build_nn_small, src, NS_MUTANTS, tmp_path):
         with pytest.raises(AssertionError):
             _check_nn_small(L, orc)
+
+
+SY_CPP = os.path.join(ROOT, "tests", "nn_synth_host.cpp")
+SY_BEGIN, SY_END = "// Synthetic training pairs:", "__device__ __forceinline__ uint32_t hash3"
+
+
+def _build_synth(src_text, d):
+    import ctypes as C
+    assert src_text.count(SY_BEGIN) == 1 and src_text.count(SY_END) == 1
+    (d / "nn_synth.inc").write_text(src_text[src_text.index(SY_BEGIN):src_text.index(SY_END)])
+    so = str(d / "libsyn.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
+                    "-I" + str(d), SY_CPP, "-o", so], check=True)
+    L = C.CDLL(so)
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    L.dm_synth_params.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_int, C.c_int,
+                                  f32p, f32p, f32p, i32p, f32p]
+    return L
+
+
+def _synth(L, dims, rl, tl, seed, step, B):
+    R, t, c = np.zeros((B, 3, 3), np.float32), np.zeros((B, 3), np.float32), np.zeros((B, 3), np.float32)
+    shift, y = np.zeros(B, np.int32), np.zeros((B, 6), np.float32)
+    L.dm_synth_params(*dims, rl, tl, seed, step, B, R, t, c, shift, y)
+    return R, t, c, shift, y
+
+
+def _check_synth(L, orc):
+    """The learned proposal's training labels are poses in the filter's
+    convention: for each synthetic pair, the map from a target voxel to the
+    source point its tissue comes from equals the pose -> matrix step (Eq. 3)
+    applied to the label pose, with the source at the origin and the target
+    grid slid along x by the pair's shift."""
+    rng = np.random.default_rng(42)
+    for dims, seed, step in (((224, 208, 176), 7, 3), ((64, 48, 40), 2**40 + 1, 0), ((96, 96, 96), 5, 1000)):
+        rl, tl = np.float32(np.deg2rad(30.0)), np.float32(25.0)
+        B = 32
+        R, t, c, shift, y = _synth(L, dims, rl, tl, seed, step, B)
+        assert np.all(np.abs(y) <= 1.0) and np.std(y) > 0.3
+        assert np.array_equal(c, np.tile((np.array(dims, np.float32) - 1) / 2, (B, 1)))
+        assert np.all(shift >= int(0.40 * dims[0])) and np.all(shift <= int(np.ceil(0.65 * dims[0])))
+        R2 = _synth(L, dims, rl, tl, seed, step, B)[0]
+        assert np.array_equal(R, R2)                                   # seeded
+        assert not np.array_equal(R, _synth(L, dims, rl, tl, seed, step + 1, B)[0])
+        for b in range(B):
+            pose = np.concatenate([y[b, :3] * rl, y[b, 3:] * tl]).astype(np.float32)
+            assert np.allclose(pose[3:], t[b], rtol=1e-6, atol=1e-5), b
+            M, a = orc.pose_matrix(pose, np.array(dims, np.int32), np.zeros(3, np.float32),
+                                   np.array([shift[b], 0, 0], np.float32))
+            M = M.reshape(3, 4).astype(np.float64)
+            p = rng.uniform(0, np.array(dims) - 1, (16, 3))
+            q_filter = (p - a) @ M[:, :3].T + M[:, 3]
+            q_pair = (p + [shift[b], 0, 0] - c[b]) @ R[b].astype(np.float64).T + c[b] + t[b]
+            assert np.abs(q_filter - q_pair).max() < 1e-4, (dims, b)
+
+
+def test_training_labels_follow_the_filters_pose_convention(orc, tmp_path):
+    _check_synth(_build_synth(open(NN_CU).read(), tmp_path), orc)
+
+
+SY_MUTANTS = [
+    ("rotation order Rz Ry Rx", "const float Ry[9] = {cy, 0, sy, 0, 1, 0, -sy, 0, cy};",
+     "const float Ry[9] = {1, 0, 0, 0, cx, -sx, 0, sx, cx};"),
+    ("angle of the wrong axis", "sincosf(ang[0], &sx, &cx);", "sincosf(ang[2], &sx, &cx);"),
+    ("centre at dims / 2", "s.c[d] = 0.5f * (dims[d] - 1.0f);", "s.c[d] = 0.5f * dims[d];"),
+    ("label of the translation negated", "a.y[b * 6 + 3 + d] = tr[d] / a.trans_lim;",
+     "a.y[b * 6 + 3 + d] = -tr[d] / a.trans_lim;"),
+]
+
+
+def test_training_label_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(NN_CU).read()
+    for text in (m[1] for m in SY_MUTANTS):
+        assert src.count(text) == 1, text
+    for L in _build_all(_build_synth, src, SY_MUTANTS, tmp_path):
+        with pytest.raises(AssertionError):
+            _check_synth(L, orc)
 
 
 # ------------------- the measurement's warp routine under a lockstep warp emulation
