@@ -48,7 +48,8 @@ names; the package never builds or loads any of this.
    quad layout written out in numpy.  The set-up kernels (mask bits, the
    binarised mask, the voxel count), the pose -> matrix and single-score
    exports and the estimate's traced Dice, under the block emulation, equal
-   their numpy definitions and the oracle.
+   their numpy definitions and the oracle; five planted mistakes are each
+   caught.
 8. The measurement kernel's whole warp routine (measure_item: the row
    set-up, the sweep of 32 rows' intervals in 64-voxel passes with the
    row-crossing passes, the per-voxel code, the warp reduction and the
@@ -608,18 +609,13 @@ SK_CPP = os.path.join(ROOT, "tests", "small_kernels_host.cpp")
 SK_BEGIN, SK_END = "// Matrix of one pose by a group of 8 lanes", "__global__ void k_philox("
 
 
-def test_set_up_export_and_trace_kernels_equal_their_definitions(orc, tmp_path):
-    # The registration's remaining kernels (copied verbatim out of filter.cu,
-    # run under the block emulation): the set-up kernels against their plain
-    # definitions in numpy, the pose -> matrix and single-score exports and
-    # the estimate's traced Dice against the oracle
+def _build_small(src_text, d):
     import ctypes as C
-    f = open(FILTER_CU).read()
-    assert f.count(SK_BEGIN) == 1 and f.count(SK_END) == 1
-    (tmp_path / "small_kernels.inc").write_text(f[f.index(SK_BEGIN):f.index(SK_END)])
-    so = str(tmp_path / "libsk.so")
+    assert src_text.count(SK_BEGIN) == 1 and src_text.count(SK_END) == 1
+    (d / "small_kernels.inc").write_text(src_text[src_text.index(SK_BEGIN):src_text.index(SK_END)])
+    so = str(d / "libsk.so")
     subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
-                    "-I" + str(tmp_path), SK_CPP, "-o", so], check=True)
+                    "-I" + str(d), SK_CPP, "-o", so], check=True)
     L = C.CDLL(so)
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
@@ -635,6 +631,13 @@ def test_set_up_export_and_trace_kernels_equal_their_definitions(orc, tmp_path):
     L.dm_score_one.restype = C.c_double
     L.dm_score_one.argtypes = [C.c_int, u64p, C.c_uint64, C.c_uint64]
     L.dm_trace.argtypes = [f64p, i32p, f32p, f32p, f32p, C.c_uint64, f32p, u64p, f64p]
+    return L
+
+
+def _check_small(L, orc):
+    """The registration's remaining kernels: the set-up kernels against their
+    plain definitions in numpy, the pose -> matrix and single-score exports
+    and the estimate's traced Dice (Eq. 4) against the oracle."""
     rng = np.random.default_rng(40)
     # grid-stride loops over 3 x 64 threads and the last word's tail
     for n in (0, 1, 31, 32, 33, 191, 192, 193, 4097, 20000):
@@ -681,6 +684,30 @@ def test_set_up_export_and_trace_kernels_equal_their_definitions(orc, tmp_path):
         assert np.array_equal(M, want_M), i
         assert dice[0] == orc.dice_from_counts(counts[0], counts[1], counts[3], b_full, 0), i
         assert dice[0] == orc.score("mask_dice", np.r_[np.zeros(8, np.uint64), counts], b_full, 0), i
+
+
+def test_set_up_export_and_trace_kernels_equal_their_definitions(orc, tmp_path):
+    _check_small(_build_small(open(FILTER_CU).read(), tmp_path), orc)
+
+
+SK_MUTANTS = [
+    ("mask bits paired", "if (i < nvox && mask[i] != 0) v |= 1u << b;", "if (i < nvox && mask[i] != 0) v |= 1u << (b ^ 1);"),
+    ("count above one", "c += v[i] != 0;\n#pragma", "c += v[i] > 1;\n#pragma"),
+    ("trace of the current iteration", "const int k = *B.k - 1;\n    const unsigned", "const int k = *B.k;\n    const unsigned"),
+    ("Dice of B instead of A", "dice_from_counts(m[0], m[1], m[3], P.b_full, 0ull)",
+     "dice_from_counts(m[0], m[2], m[3], P.b_full, 0ull)"),
+    ("estimate perturbed before rounding", "for (int d = 0; d < 6; ++d) pose[d] = __double2float_rn(L.est[d]);",
+     "for (int d = 0; d < 6; ++d) pose[d] = __double2float_rn(L.est[d] * 1.0000001);"),
+]
+
+
+def test_small_kernel_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(FILTER_CU).read()
+    for text in (m[1] for m in SK_MUTANTS):
+        assert src.count(text) == 1, text
+    for L in _build_all(_build_small, src, SK_MUTANTS, tmp_path):
+        with pytest.raises(AssertionError):
+            _check_small(L, orc)
 
 
 NN_CU = os.path.join(ROOT, "paper_2504_19930_gb300", "csrc", "nn.cu")
