@@ -7,28 +7,8 @@
 // tests/test_device_identities.py.  Test infrastructure only.
 #include "host_shim/warp_emulation.h"
 
-#include <algorithm>
-#include <cmath>
-
 #include "../paper_2504_19930_gb300/csrc/kernels.h"
-
-// bf16 as the device stores it: the upper half of the fp32 pattern rounded to
-// nearest, ties to even (no non-finite values reach these kernels)
-struct __nv_bfloat16 {
-    uint16_t x;
-};
-inline __nv_bfloat16 __float2bfloat16_rn(float v) {
-    const uint32_t u = __float_as_uint(v);
-    return __nv_bfloat16{(uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16)};
-}
-inline float __expf(float x) { return std::exp(x); }   // the exponential it names
-inline float atomicAdd(float *p, float v) {            // one host thread runs every context
-    const float old = *p;
-    *p = old + v;
-    return old;
-}
-using std::max;
-using std::min;
+#include "host_shim/nn_device.h"
 
 dim3 threadIdx, blockIdx, blockDim, gridDim;
 #define threadIdx (dim3{(unsigned)host_warp::tid, 1u, 1u})

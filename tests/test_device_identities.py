@@ -104,7 +104,9 @@ names; the package never builds or loads any of this.
    host) are poses in the filter's convention: each synthetic pair's map
    from target voxel to source point equals the oracle's pose -> matrix of
    its label; four planted mistakes (rotation order, axis, centre, sign)
-   are each caught.
+   are each caught.  The pairs' network input (k_synth_views) is their
+   full-resolution views box-averaged as the oracle box-averages a real
+   volume; three planted mistakes are each caught.
 """
 import os
 import platform
@@ -900,12 +902,14 @@ def test_network_kernel_comparison_catches_planted_mistakes(orc, tmp_path):
 
 
 SY_CPP = os.path.join(ROOT, "tests", "nn_synth_host.cpp")
-SY_BEGIN, SY_END = "// Synthetic training pairs:", "__device__ __forceinline__ uint32_t hash3"
+SY_BEGIN, SY_END = "// Synthetic training pairs:", "}  // namespace nn\n\nnamespace nn {\n// Failure-detection"
 
 
 def _build_synth(src_text, d):
     import ctypes as C
     assert src_text.count(SY_BEGIN) == 1 and src_text.count(SY_END) == 1
+    assert src_text.count(NS_BEGIN) == 1
+    (d / "nn_small.inc").write_text(src_text[src_text.index(NS_BEGIN):src_text.index(SY_BEGIN)])
     (d / "nn_synth.inc").write_text(src_text[src_text.index(SY_BEGIN):src_text.index(SY_END)])
     so = str(d / "libsyn.so")
     subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-I" + SHIM,
@@ -913,8 +917,13 @@ def _build_synth(src_text, d):
     L = C.CDLL(so)
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
     L.dm_synth_params.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_int, C.c_int,
                                   f32p, f32p, f32p, i32p, f32p]
+    L.dm_synth_views.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_int,
+                                 C.c_int, f32p, u16p]
+    L.dm_synth_full.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_int, C.c_int,
+                                C.c_int, f32p, f32p]
     return L
 
 
@@ -954,8 +963,39 @@ def _check_synth(L, orc):
             assert np.abs(q_filter - q_pair).max() < 1e-4, (dims, b)
 
 
+def _check_synth_views(L, orc):
+    """The network input of each synthetic pair is its two full-resolution
+    views (the kernels' own per-voxel function) box-averaged as the oracle
+    box-averages a real volume: the source view over the box at the
+    origin, the target view, slid along x by the pair's shift, over the same
+    box (cells it does not reach stay 0), each / 64 in bf16."""
+    import oracle.nn as onn
+    rl, tl = np.float32(np.deg2rad(30.0)), np.float32(25.0)
+    for dims, G, seed, step, B in (((40, 36, 30), 16, 3, 2, 3), ((48, 40, 32), 8, 11, 0, 2)):
+        X, Y, Z = dims
+        y = np.zeros((B, 6), np.float32)
+        x = np.full((B, G**3, 2), 0x7777, np.uint16)
+        L.dm_synth_views(X, Y, Z, G, rl, tl, seed, step, B, y, x)
+        _, _, _, shift, y2 = _synth(L, dims, rl, tl, seed, step, B)
+        assert np.array_equal(y, y2)
+        h = np.array(dims, np.float64) / G
+        for b in range(B):
+            S, T = np.zeros((Z, Y, X), np.float32), np.zeros((Z, Y, X), np.float32)
+            L.dm_synth_full(X, Y, Z, rl, tl, seed, step, B, b, S, T)
+            assert S.min() >= 0 and S.max() <= 255 and np.array_equal(S, np.rint(S)) and S.std() > 5
+            for ch, (vol, org) in enumerate(((S, (0.0, 0.0, 0.0)), (T, (float(shift[b]), 0.0, 0.0)))):
+                want = onn.box_average(vol, np.array(org), np.ones(3), np.zeros(3), h, G)
+                got = onn.from_bf16_bits(x[b, :, ch]).astype(np.float64).reshape(G, G, G)
+                assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 1e-7), (dims, b, ch)
+            assert np.all(x[b, :, 1].reshape(G, G, G)[:, :, : int(shift[b] // h[0])] == 0)
+
+
 def test_training_labels_follow_the_filters_pose_convention(orc, tmp_path):
     _check_synth(_build_synth(open(NN_CU).read(), tmp_path), orc)
+
+
+def test_training_inputs_are_the_box_averaged_views(orc, tmp_path):
+    _check_synth_views(_build_synth(open(NN_CU).read(), tmp_path), orc)
 
 
 SY_MUTANTS = [
@@ -975,6 +1015,24 @@ def test_training_label_comparison_catches_planted_mistakes(orc, tmp_path):
     for L in _build_all(_build_synth, src, SY_MUTANTS, tmp_path):
         with pytest.raises(AssertionError):
             _check_synth(L, orc)
+
+
+SV_MUTANTS = [
+    ("first target column dropped", "if (px >= 0 && px < a.X) {", "if (px > 0 && px < a.X) {"),
+    ("cell end rounded down", "hi[d] = min(dims[d], (int)ceilf(h * (g[d] + 1)));",
+     "hi[d] = min(dims[d], (int)floorf(h * (g[d] + 1)));"),
+    ("target mean over the source count", "xo[1] = bf16_bits(cnt_t ? sum_t / cnt_t",
+     "xo[1] = bf16_bits(cnt_t ? sum_t / cnt_s"),
+]
+
+
+def test_training_input_comparison_catches_planted_mistakes(orc, tmp_path):
+    src = open(NN_CU).read()
+    for text in (m[1] for m in SV_MUTANTS):
+        assert src.count(text) == 1, text
+    for L in _build_all(_build_synth, src, SV_MUTANTS, tmp_path):
+        with pytest.raises(AssertionError):
+            _check_synth_views(L, orc)
 
 
 # ------------------- the measurement's warp routine under a lockstep warp emulation
