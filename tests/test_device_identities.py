@@ -107,6 +107,10 @@ names; the package never builds or loads any of this.
    are each caught.  The pairs' network input (k_synth_views) is their
    full-resolution views box-averaged as the oracle box-averages a real
    volume; three planted mistakes are each caught.
+18. The tensor-core path's operand layout (umma.cuh's tile_offset) is a
+   bijection of 8 x 8 core matrices whose strides are the LBO / SBO the
+   GEMM puts in its descriptors, and the descriptors' fields decode as the
+   PTX ISA's tcgen05 formats.
 """
 import os
 import platform
@@ -1033,6 +1037,53 @@ def test_training_input_comparison_catches_planted_mistakes(orc, tmp_path):
     for L in _build_all(_build_synth, src, SV_MUTANTS, tmp_path):
         with pytest.raises(AssertionError):
             _check_synth_views(L, orc)
+
+
+def test_tensor_core_operand_layout_matches_its_descriptors(tmp_path):
+    # The GEMM's operand tiles (K-major, no swizzle): tile_offset is a
+    # bijection onto the tile's bytes, each 8 x 8 core matrix is 128
+    # contiguous bytes, and its K and row-group strides are the LBO and SBO
+    # the kernel puts in its descriptors, whose fields decode as the PTX
+    # ISA's tcgen05 shared-memory and kind::f16 instruction descriptors
+    import ctypes as C
+    so = str(tmp_path / "libumma.so")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-I" + SHIM,
+                    os.path.join(ROOT, "tests", "umma_layout_host.cpp"), "-o", so], check=True)
+    L = C.CDLL(so)
+    L.dm_tile_offset.restype = C.c_uint32
+    L.dm_tile_offset.argtypes = [C.c_int, C.c_int, C.c_int]
+    L.dm_smem_desc.restype = C.c_uint64
+    L.dm_smem_desc.argtypes = [C.c_uint32, C.c_uint32, C.c_uint32]
+    L.dm_idesc.restype = C.c_uint32
+    L.dm_idesc.argtypes = [C.c_int, C.c_int]
+    nn_src = open(NN_CU).read()
+    assert nn_src.count("constexpr int kChunkK = 64;") == 1
+    n_a = nn_src.count("umma::smem_desc(a + 256 * kk, 128, 16 * kChunkK)")   # the K-major GEMMs' A and B
+    assert n_a >= 1 and nn_src.count("umma::smem_desc(b + 256 * kk, 128, 16 * kChunkK)") == n_a
+    for rows, kcols in ((128, 64), (32, 64), (128, 16)):
+        off = np.array([[L.dm_tile_offset(r, k, kcols) for k in range(kcols)] for r in range(rows)], np.int64)
+        assert np.array_equal(np.sort(off.ravel()), 2 * np.arange(rows * kcols))      # bijection, bf16 steps
+        for g in range(rows // 8):
+            for j in range(kcols // 8):
+                core = off[8 * g:8 * g + 8, 8 * j:8 * j + 8]
+                base = core.min()
+                assert np.array_equal(core - base, 16 * np.arange(8)[:, None] + 2 * np.arange(8)[None, :])
+                assert base == g * 16 * kcols + j * 128                              # SBO, LBO
+        for m in range(kcols // 16):
+            assert off[0, 16 * m] == 256 * m                                         # per-MMA K advance
+    for addr, lbo, sbo in ((0x400, 128, 1024), (0x3FFF0, 128, 16 * 64), (0x1230, 2048, 512)):
+        d = L.dm_smem_desc(addr, lbo, sbo)
+        assert d & 0x3FFF == (addr >> 4) & 0x3FFF
+        assert (d >> 16) & 0x3FFF == lbo >> 4 and (d >> 32) & 0x3FFF == sbo >> 4
+        assert (d >> 46) & 0x7 == 1 and (d >> 49) & 0x7 == 0 and (d >> 52) & 1 == 0 and d >> 61 == 0
+        assert (d >> 14) & 3 == 0 and (d >> 30) & 3 == 0 and (d >> 53) & 0xFF == 0
+    for M, N in ((128, 32), (128, 256), (64, 8)):
+        i = L.dm_idesc(M, N)
+        assert i & 0xF == 0 and (i >> 4) & 3 == 1 and (i >> 6) & 1 == 0              # dense, f32 D
+        assert (i >> 7) & 7 == 1 and (i >> 10) & 7 == 1                               # bf16 A, B
+        assert (i >> 13) & 0xF == 0                                                   # no negate, K-major
+        assert (i >> 17) & 0x3F == N >> 3 and (i >> 23) & 1 == 0 and (i >> 24) & 0x1F == M >> 4
+        assert i >> 29 == 0
 
 
 # ------------------- the measurement's warp routine under a lockstep warp emulation
